@@ -1,0 +1,501 @@
+#!/usr/bin/env python
+"""Throughput of the UPSLAM per-sweep hot path on GB300.
+
+Workload (the headline configuration): 64 x 1024 lidar sweeps (FOV +-16.6 deg,
+range 0.5-120 m, sigma 2 cm, 2 % dropouts) along a seeded 200 m trajectory
+through a procedural tunnel / corridor network; keyframe panoramas 512 x 2048
+with FP32 depth, FP32 normals and FP32 sample counts; a new keyframe every 5 m.
+One step = one sweep through the whole path: projection + z-buffer, normals,
+motion prior, ICP (up to 15 Gauss-Newton steps, one persistent launch) and the
+keyframe update (plus a new keyframe every 50 sweeps).
+
+Metric: sweeps per second (ICP + fusion scans/s at 64 x 1024).  Inputs are
+resident in HBM when the timed region starts; the timed steps run as one CUDA
+graph with event-record nodes around every step and around the ICP and fusion
+launches; L2 is flushed (a 256 MiB write) between steps, outside the events.
+``e2e`` repeats the measurement through the public API from pinned host memory
+(host->device copy of each sweep, device->host read of its pose and record,
+one synchronisation per sweep).  ``cpu_baseline`` times the FP64 oracle on the
+host cores on a bounded sample of the same sweeps.
+
+``--impl reference`` times the oracle (the only reference there is) on the host
+cores, rank 0 only, on a bounded sample sized to finish in a few minutes.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "ICP+fusion scans/s at 64x1024"
+UNIT = "scans/s"
+KF_ROWS, KF_COLS = 512, 2048
+FLUSH_BYTES = 256 << 20
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--e2e-steps", type=int, default=300)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-graph", action="store_true", help="launch eagerly instead of replaying a CUDA graph")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quiet", action="store_true")
+    return ap.parse_args()
+
+
+def log(msg):
+    sys.stderr.write(msg + "\n")
+    sys.stderr.flush()
+
+
+# ----------------------------------------------------------------------------- distributed plumbing
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def init_dist(ws, backend):
+    if ws > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend=backend)
+        return dist
+    return None
+
+
+def combine_ranks(local_ms: float, dist, device="cpu") -> float:
+    """Timed duration of the whole job: the maximum over ranks (replicas run independently)."""
+    if dist is None:
+        return local_ms
+    import torch
+    t = torch.tensor([local_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(steps: int, world: int, total_ms: float) -> float:
+    """Whole-job throughput: every rank's sweeps over the slowest rank's time."""
+    return world * steps / (total_ms * 1e-3)
+
+
+# ----------------------------------------------------------------------------- workload
+
+def make_workload(n_scans: int, rank: int = 0):
+    from synth import configs
+    seq = configs.tunnel_sequence(n_scans=max(n_scans, 2))
+    t0 = time.time()
+    scans = np.stack([seq.scan(k) for k in range(n_scans)])
+    log(f"[bench] rank {rank}: generated {n_scans} sweeps of {scans.shape[1]} points in {time.time() - t0:.1f} s")
+    return seq, scans
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            with open(path) as f:
+                d = json.load(f)
+            for key in ("hbm_gbs", "hbm_GBs", "hbm"):
+                if key in d:
+                    v = d[key]
+                    if isinstance(v, dict):
+                        v = v.get("value", v.get("burst"))
+                    return float(v), "measured"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+# ----------------------------------------------------------------------------- CUDA events usable inside graphs
+
+class Cudart:
+    """cudaEventRecordWithFlags(..., cudaEventRecordExternal) so events become graph nodes."""
+
+    def __init__(self):
+        lib = None
+        for name in ("libcudart.so.13", "libcudart.so.12", "libcudart.so"):
+            try:
+                lib = ctypes.CDLL(name)
+                break
+            except OSError:
+                continue
+        if lib is None:
+            raise RuntimeError("libcudart not found")
+        self.lib = lib
+        lib.cudaEventCreate.argtypes = [ctypes.POINTER(ctypes.c_void_p)]
+        lib.cudaEventRecordWithFlags.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint]
+        lib.cudaEventElapsedTime.argtypes = [ctypes.POINTER(ctypes.c_float), ctypes.c_void_p, ctypes.c_void_p]
+        lib.cudaEventSynchronize.argtypes = [ctypes.c_void_p]
+        lib.cudaEventDestroy.argtypes = [ctypes.c_void_p]
+
+    def event(self):
+        ev = ctypes.c_void_p()
+        assert self.lib.cudaEventCreate(ctypes.byref(ev)) == 0
+        return ev
+
+    def record(self, ev, stream, external=True):
+        rc = self.lib.cudaEventRecordWithFlags(ev, ctypes.c_void_p(stream), 1 if external else 0)
+        assert rc == 0, rc
+
+    def elapsed(self, a, b) -> float:
+        ms = ctypes.c_float()
+        assert self.lib.cudaEventSynchronize(b) == 0
+        assert self.lib.cudaEventElapsedTime(ctypes.byref(ms), a, b) == 0
+        return ms.value
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        time.sleep(0.3)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.1)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[3:7]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- our arm
+
+def run_ours(args, ws, rank, local):
+    import torch
+    import paper_2101_00585_gb300 as up
+
+    torch.cuda.set_device(local)
+    dist = init_dist(ws, "nccl")
+    device = torch.device("cuda", local)
+    W, K = args.warmup, args.steps
+    n_scans = 1 + W + K
+    seq, scans = make_workload(n_scans, rank)
+    p = up.Params(accept_quality=0.1)
+    trk = up.Tracker(seq.sweep, seq.kf, p, device=device, constant_velocity=True)
+    kf_every = seq.kf_every
+    # keyframe pool: every keyframe the sequence will start, zeroed up front
+    n_kf = 2 + n_scans // kf_every
+    pool = [trk.kf] + [up.KeyframeBuffer(seq.kf, device) for _ in range(n_kf)]
+    pool_pos = [0]
+    h_scans = torch.from_numpy(scans).pin_memory()
+    d_scans = h_scans.to(device)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=device)
+    hist_pose = torch.zeros((n_scans, 12), dtype=torch.float64, device=device)
+    hist_stats = torch.zeros((n_scans, up._abi.STATS_BYTES), dtype=torch.uint8, device=device)
+    switched_after = []
+
+    def switch_keyframe():
+        pool_pos[0] += 1
+        trk.new_keyframe(buffer=pool[pool_pos[0]])
+
+    def step(k):
+        trk.track(d_scans[k])
+        if k % kf_every == 0:
+            switch_keyframe()
+            switched_after.append(k)
+
+    torch.cuda.synchronize()
+    # sweep 0 opens the first keyframe; warm-up sweeps 1..W run eagerly
+    trk.new_keyframe(d_scans[0])
+    for k in range(1, 1 + W):
+        step(k)
+        hist_pose[k].copy_(trk.state.pose)
+        hist_stats[k].copy_(trk.state.stats)
+    torch.cuda.synchronize()
+
+    cr = Cudart()
+    s = torch.cuda.Stream(device)
+    ev = [(cr.event(), cr.event()) for _ in range(K)]
+    ev_icp = [(cr.event(), cr.event()) for _ in range(K)]
+    ev_fuse = [(cr.event(), cr.event()) for _ in range(K)]
+    ev_proj = [(cr.event(), cr.event()) for _ in range(K)]
+    trk.timing = None
+    launches = [0]
+
+    def timed_steps():
+        st = torch.cuda.current_stream().cuda_stream
+        for i in range(K):
+            k = 1 + W + i
+            trk.timing = (cr, st, ev_proj[i], ev_icp[i], ev_fuse[i])
+            cr.record(ev[i][0], st)
+            step(k)
+            cr.record(ev[i][1], st)
+            launches[0] += up.Tracker.LAUNCHES_PER_TRACK + (up.Tracker.LAUNCHES_PER_NEW_KEYFRAME
+                                                            if k % kf_every == 0 else 0)
+            hist_pose[k].copy_(trk.state.pose)
+            hist_stats[k].copy_(trk.state.stats)
+            flush.zero_()
+        trk.timing = None
+
+    used_graph = False
+    with torch.cuda.stream(s):
+        if not args.no_graph:
+            try:
+                g = torch.cuda.CUDAGraph()
+                saved = (pool_pos[0], list(switched_after))
+                with torch.cuda.graph(g, stream=s):
+                    timed_steps()
+                pool_pos[0], switched_after[:] = saved[0], saved[1]
+                used_graph = True
+            except Exception as e:  # capture unsupported: launch eagerly
+                log(f"[bench] graph capture failed ({e}); launching eagerly")
+                torch.cuda.synchronize()
+                launches[0] = 0
+        sampler = ClockSampler(local)
+        sampler.start()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter()
+        if used_graph:
+            g.replay()
+        else:
+            timed_steps()
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+        clocks = sampler.stop()
+    step_ms = [cr.elapsed(a, b) for a, b in ev]
+    icp_ms = [cr.elapsed(a, b) for a, b in ev_icp]
+    fuse_ms = [cr.elapsed(a, b) for a, b in ev_fuse]
+    proj_ms = [cr.elapsed(a, b) for a, b in ev_proj]
+    total_ms = combine_ranks(float(sum(step_ms)), dist, device)
+
+    # accuracy of the timed trajectory (host-side, after the fact)
+    from paper_2101_00585_gb300._abi import IcpStats
+    poses = hist_pose.cpu().numpy().reshape(-1, 3, 4)
+    stats_raw = hist_stats.cpu().numpy()
+    recs = [IcpStats.from_buffer_copy(bytes(stats_raw[k])) for k in range(n_scans)]
+    iters = [recs[1 + W + i].iters for i in range(K)]
+    accepted = sum(recs[1 + W + i].accepted for i in range(K))
+    import synth
+    P_kf = seq.poses[0]
+    errs = []
+    for k in range(1, n_scans):
+        Pw = synth.pose_mul(P_kf, poses[k])
+        errs.append(synth.pose_error(Pw, seq.poses[k]))
+        if k % kf_every == 0:
+            P_kf = Pw
+
+    hbm, hbm_src = peaks()
+    kf_px, sw_px = KF_ROWS * KF_COLS, seq.sweep.pixels
+    icp_bytes = kf_px * 20 + sw_px * 32
+    fuse_bytes = kf_px * 40 + sw_px * 32 * 2
+    icp_avg, fuse_avg, proj_avg = (statistics.mean(icp_ms), statistics.mean(fuse_ms), statistics.mean(proj_ms))
+    kernels = {
+        "icp_persistent": {"ms_avg": icp_avg, "share": sum(icp_ms) / total_ms, "bytes": icp_bytes,
+                           "gbs": icp_bytes / (icp_avg * 1e-3) / 1e9, "iters_avg": statistics.mean(iters),
+                           "l2_bytes_per_launch": icp_bytes * statistics.mean(iters)},
+        "fuse": {"ms_avg": fuse_avg, "share": sum(fuse_ms) / total_ms, "bytes": fuse_bytes,
+                 "gbs": fuse_bytes / (fuse_avg * 1e-3) / 1e9},
+        "project_normals": {"ms_avg": proj_avg, "share": sum(proj_ms) / total_ms},
+    }
+    dom = "icp_persistent" if sum(icp_ms) >= sum(fuse_ms) else "fuse"
+    kd = kernels[dom]
+    traffic = None
+    roofline = {"kernel": dom, "bound": "hbm", "achieved": round(kd["gbs"], 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(kd["gbs"] / hbm, 4), "traffic": traffic, "peak_source": hbm_src}
+    value = job_value(K, ws, total_ms)
+    out = {
+        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
+        "ms_per_step": round(total_ms / K, 5), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "tunnel 64x1024 sweeps vs 512x2048 FP32 keyframes, keyframe every 5 m, <=15 ICP iters",
+                   "sweep": "64x1024", "keyframe": "512x2048 f32", "scans": K, "parallelism": f"replicas{ws}",
+                   "l2": "flushed between steps (256 MiB write, outside the step events)",
+                   "graph": used_graph},
+        "roofline": roofline,
+        "kernels": {k: {kk: (round(vv, 5) if isinstance(vv, float) else vv) for kk, vv in v.items()}
+                    for k, v in kernels.items()},
+        "gpu_launches": launches[0],
+        "clocks": clocks,
+        "accuracy": {"trans_err_m_median": float(np.median([e[0] for e in errs])),
+                     "trans_err_m_max": float(np.max([e[0] for e in errs])),
+                     "rot_err_deg_max": float(np.degrees(np.max([e[1] for e in errs]))),
+                     "accepted": int(accepted), "icp_iters_avg": float(np.mean(iters))},
+        "wall_s_timed": round(t_wall, 4),
+    }
+    if rank == 0 and args.e2e_steps > 0:
+        out["e2e"] = run_e2e(args, seq, h_scans, device, up)
+    if dist:
+        dist.barrier()
+    return out
+
+
+def run_e2e(args, seq, h_scans, device, up):
+    """Public API from pinned host memory: H2D sweep, track, D2H pose + record, sync, every step."""
+    import torch
+    K = min(args.e2e_steps, h_scans.shape[0] - 1)
+    p = up.Params(accept_quality=0.1)
+    trk = up.Tracker(seq.sweep, seq.kf, p, device=device, constant_velocity=True)
+    n_kf = 2 + K // seq.kf_every
+    pool = [trk.kf] + [up.KeyframeBuffer(seq.kf, device) for _ in range(n_kf)]
+    staging = torch.empty(h_scans.shape[1:], dtype=torch.float32, device=device)
+    out_pose = torch.empty(12, dtype=torch.float64).pin_memory()
+    out_stats = torch.empty(up._abi.STATS_BYTES, dtype=torch.uint8).pin_memory()
+    staging.copy_(h_scans[0], non_blocking=True)
+    trk.new_keyframe(staging)
+    torch.cuda.synchronize()
+    pos = 0
+    t0 = time.perf_counter()
+    for k in range(1, K + 1):
+        staging.copy_(h_scans[k], non_blocking=True)
+        trk.track(staging)
+        if k % seq.kf_every == 0:
+            pos += 1
+            trk.new_keyframe(buffer=pool[pos])
+        out_pose.copy_(trk.state.pose, non_blocking=True)
+        out_stats.copy_(trk.state.stats, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+    dt = time.perf_counter() - t0
+    return {"value": round(K / dt, 2), "unit": UNIT, "steps": K,
+            "h2d_bytes_per_step": int(h_scans[0].numel() * 4),
+            "d2h_bytes_per_step": int(12 * 8 + up._abi.STATS_BYTES)}
+
+
+# ----------------------------------------------------------------------------- oracle timing
+
+def oracle_rate(seq, scans, budget_s: float, warm: int = 1, max_steps: int | None = None):
+    """Sweeps/s of the FP64 oracle over consecutive sweeps, within a time budget."""
+    import oracle
+    import synth
+    prm = oracle.Params(accept_quality=0.1)
+    I = np.hstack([np.eye(3), np.zeros((3, 1))])
+    kf = oracle.Keyframe(seq.kf)
+    sp, sn, _, _ = oracle.sweep_frame(scans[0], seq.sweep, prm)
+    oracle.fuse(kf, sp, sn, seq.sweep, I, prm)
+    T_prev, M = I.copy(), I.copy()
+
+    def one(k):
+        nonlocal kf, T_prev, M
+        T0 = synth.pose_mul(T_prev, M)
+        u, _, vt = np.linalg.svd(T0[:, :3])
+        T0[:, :3] = u @ vt
+        T, st, it, acc = oracle.process_scan(kf, scans[k], seq.sweep, T0, prm)
+        M = synth.pose_mul(synth.pose_inv(T_prev), T)
+        T_prev = T
+        if k % seq.kf_every == 0:
+            kf = oracle.Keyframe(seq.kf)
+            sp, sn, _, _ = oracle.sweep_frame(scans[k], seq.sweep, prm)
+            oracle.fuse(kf, sp, sn, seq.sweep, I, prm)
+            T_prev = I.copy()
+
+    k = 1
+    for _ in range(warm):
+        one(k)
+        k += 1
+    n = 0
+    t0 = time.perf_counter()
+    while k < len(scans) and (max_steps is None or n < max_steps):
+        one(k)
+        k += 1
+        n += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return n / dt, n, dt
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return None
+    W = max(1, args.warmup)
+    n = 1 + W + min(args.steps, 400)
+    seq, scans = make_workload(n, rank)
+    rate, steps, dt = oracle_rate(seq, scans, budget_s=150.0, warm=W, max_steps=args.steps)
+    sample = (f"the first {steps} sweeps after {W} warm-up sweeps of the tunnel sequence (whole path per sweep), "
+              f"capped at 150 s of CPU time")
+    return {"impl": "reference", "metric": METRIC, "value": round(rate, 4), "unit": UNIT, "n_gpus": ws,
+            "steps": steps, "warmup": W, "ms_per_step": round(dt / max(steps, 1) * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "tunnel 64x1024 sweeps vs 512x2048 FP32 keyframes, keyframe every 5 m, <=15 ICP "
+                                   "iters", "parallelism": "single host thread"},
+            "cpu_baseline": {"value": round(rate, 4), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(rate, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        out = run_reference(args, ws, rank)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    out = run_ours(args, ws, rank, local)
+    if rank == 0 and not args.no_cpu_baseline:
+        seq, scans = make_workload(1 + 40, rank)
+        rate, n, dt = oracle_rate(seq, scans, budget_s=args.cpu_seconds, warm=1)
+        out["cpu_baseline"] = {"value": round(rate, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "sample": f"{n} consecutive tunnel sweeps (whole path each) after 1 warm-up, "
+                                         f"{dt:.1f} s on one host thread"}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,250 @@
+/*
+ * upslam.h -- C ABI of the GB300 (sm_103a) UPSLAM per-sweep hot path.
+ *
+ * The library implements the data-parallel path of UPSLAM: Union of Panoramas
+ * SLAM (Cowley, Miller, Taylor; arXiv 2101.00585):
+ *   1. spherical projection of a lidar sweep into a panoramic depth image with a
+ *      deterministic z-buffer                                  (Sec. III-A)
+ *   2. per-pixel normals from two image neighbours             (Sec. III-A)
+ *   3. point-to-plane ICP over projective correspondences
+ *      filtered by the similarity test Omega_{d,theta}         (Sec. III-B, Eq. 1)
+ *   4. keyframe update: weighted per-pixel average with a
+ *      sample count saturated at 10, gated by registration quality (Sec. III-C)
+ *
+ * Conventions
+ * -----------
+ * - Every pointer named d_* is DEVICE memory owned by the caller.  The library
+ *   allocates nothing and keeps no state between calls.  Host pointers (the
+ *   parameter structs) are read during the call only.
+ * - "float4" arrays are 16-byte aligned arrays of 4 floats; "half4" arrays are
+ *   8-byte aligned arrays of 4 IEEE binary16 values.
+ * - Panoramas are row-major [rows][cols].  Row 0 is the top edge (elevation
+ *   el_top); column 0 starts at azimuth +pi and columns advance clockwise.
+ *   A point p falls in pixel (row, col) by the FP32 binning rule below.
+ * - A pose is 12 doubles, row-major [R | t] (3x4), mapping sweep coordinates
+ *   to keyframe coordinates (T = T_kf<-sweep, the T of Eq. 1 that acts on the
+ *   sweep point s2).
+ * - Calls are asynchronous and ordered on the given CUDA stream (a
+ *   cudaStream_t passed as void*; NULL = the legacy default stream).  Results
+ *   that the device decides (pose, convergence, inlier counts) stay in device
+ *   memory so a sequence of calls can be captured in a CUDA graph.
+ * - Errors: argument errors are found on the host before any launch and
+ *   return UPSLAM_ERR_INVALID_ARG; a failed launch returns UPSLAM_ERR_CUDA.
+ *   Conditions found on the device (degenerate normal equations, a wait that
+ *   timed out) are written to the stats record.  No C++ exception crosses this
+ *   boundary.
+ *
+ * FP32 binning rule (shared definition; the kernels and any checker must apply
+ * these IEEE round-to-nearest operations in this order, without fused
+ * multiply-add):
+ *   xy2 = x*x + y*y;  r = sqrt(xy2 + z*z);  reject unless r_min <= r <= r_max
+ *   az = atan2p(y, x);  el = atan2p(z, sqrt(xy2))
+ *   fc = (PI_F - az) * s_az;  fr = (el_top - el) * s_el
+ *   reject unless 0 <= fr < rows;  row = floor(fr);  col = floor(fc) (col == cols -> 0)
+ * where atan2p reduces atan2 to atan(t), t = min/max in [0,1], evaluated as
+ * t * P(t*t) with the 8-term polynomial of Abramowitz & Stegun 4.4.49
+ * (Horner, separate multiply and add), then a = pi/2 - a if |y| > |x|,
+ * a = pi - a if x < 0, a = -a if y < 0 (-0 counts as +0; atan2p(0,0) = 0).
+ * A transformed point is p = ((r00*x + r01*y) + r02*z) + t0 (etc.) with the
+ * pose rounded to FP32; the inverse is q = (r00*dx + r10*dy) + r20*dz with
+ * d = s - t.  The z-buffer key of point i is (bits(r) << 32) | i and the
+ * smallest key wins, so winners are unique and independent of thread order.
+ */
+#ifndef UPSLAM_H
+#define UPSLAM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    UPSLAM_OK = 0,
+    UPSLAM_ERR_INVALID_ARG = 1,
+    UPSLAM_ERR_CUDA = 2,
+    UPSLAM_ERR_DEGENERATE = 3,   /* too few inliers or a Cholesky pivot <= pivot_eps * max diag */
+    UPSLAM_ERR_NOT_CONVERGED = 4,
+    UPSLAM_ERR_TIMEOUT = 5,      /* a bounded device-side wait gave up */
+    UPSLAM_ERR_UNSUPPORTED = 6   /* e.g. a cooperative launch the device cannot host */
+} upslam_status;
+
+/* Storage precision of normals and sample counts. */
+typedef enum {
+    UPSLAM_F32 = 0, /* float4 (nx, ny, nz, w) */
+    UPSLAM_F16 = 1  /* half4  (nx, ny, nz, w) */
+} upslam_precision;
+
+/* Panorama geometry.  The FP32 values are the definition (computed once by the
+ * caller, e.g. s_az = cols / 2pi rounded to FP32). */
+typedef struct {
+    int32_t rows, cols;
+    float el_top; /* elevation of the top edge of row 0, radians */
+    float s_az;   /* columns per radian of azimuth */
+    float s_el;   /* rows per radian of elevation */
+    float r_min, r_max; /* accepted range interval, metres */
+} upslam_pano;
+
+/* Normal estimation (Sec. III-A).  A neighbour is unusable when
+ * |r_nb - r| > jump_rel * r + jump_abs (FP32); a normal is invalid when
+ * |a x b| < min_cross * |a| |b|. */
+typedef struct {
+    float jump_rel, jump_abs, min_cross;
+} upslam_normal_params;
+
+/* ICP (Sec. III-B, Eq. 1).  Omega keeps a correspondence when the points are
+ * within d_max metres and the normals' cosine is >= cos_theta_max. */
+typedef struct {
+    float d_max, cos_theta_max;
+    int32_t max_iters;   /* iterations of upslam_icp */
+    int32_t min_inliers; /* fewer inliers -> degenerate */
+    double eps_rot, eps_trans; /* converged when |omega| < eps_rot and |v| < eps_trans */
+    double pivot_eps;          /* Cholesky pivot threshold relative to the largest diagonal */
+} upslam_icp_params;
+
+/* Keyframe update (Sec. III-C). */
+typedef struct {
+    float d_max, cos_theta_max; /* similarity gate for averaging a sample in */
+    float w_max;                /* sample count saturation (10 in the paper) */
+    float accept_quality;       /* fuse only when inliers / valid >= accept_quality */
+} upslam_fuse_params;
+
+/* ICP result record, written by the device. */
+typedef struct {
+    double A[21];   /* upper triangle of sum J^T J at the last linearisation, row-major */
+    double b[6];    /* sum J^T r */
+    double sse;     /* sum r^2 */
+    int64_t inliers;
+    int64_t valid;  /* sweep pixels holding a point */
+    int32_t status; /* upslam_status of the last step */
+    int32_t converged;
+    double xi[6];   /* last update (omega, v) */
+    int32_t iters;  /* Gauss-Newton steps taken by upslam_icp */
+    int32_t accepted; /* set by upslam_fuse: 1 when the sweep was fused */
+} upslam_icp_stats;
+
+/* A sweep after projection and normal estimation. */
+typedef struct {
+    upslam_pano pano;
+    const float *d_pix;  /* float4 [rows*cols]: the pixel's point (x, y, z, valid) */
+    const void *d_nrm;   /* float4 or half4 [rows*cols]: (nx, ny, nz, valid) */
+    int32_t nrm_precision; /* upslam_precision of d_nrm */
+} upslam_sweep;
+
+/* A keyframe panorama (Sec. III: depth plus surface normals, and the
+ * per-pixel sample count of Sec. III-C).  Empty pixels have depth 0, w 0. */
+typedef struct {
+    upslam_pano pano;
+    float *d_depth;      /* float [rows*cols]: range along the pixel-centre ray */
+    void *d_nw;          /* float4 or half4 [rows*cols]: (nx, ny, nz, w) */
+    int32_t precision;   /* upslam_precision of d_nw */
+    const float *d_dirs; /* direction table from upslam_pano_dirs */
+} upslam_keyframe;
+
+/* Size in floats of a panorama's direction table: 2*rows + 2*cols. */
+size_t upslam_pano_dirs_floats(const upslam_pano *pp);
+
+/*
+ * Direction table of a panorama: cos/sin of every row-centre elevation and
+ * column-centre azimuth, computed in FP64 and rounded to FP32
+ * (d_dirs[2v], d_dirs[2v+1] = cos, sin of el_v; then d_dirs[2*rows + 2u],
+ * [.. + 1] = cos, sin of az_u).  The FP32 point of pixel (v, u) at depth d is
+ * d * (ce*ca, ce*sa, se).  Call once per panorama geometry.
+ */
+upslam_status upslam_pano_dirs(const upslam_pano *pp, float *d_dirs, void *stream);
+
+/*
+ * Spherical projection with a deterministic z-buffer (Sec. III-A).
+ * d_pts: float4 [n] points (x, y, z, valid); invalid (valid == 0) points are skipped.
+ * d_pose12: optional transform applied first (NULL = identity).
+ * d_zbuf: uint64 [rows*cols] scratch that must hold all-ones on entry; it is
+ *   left all-ones on return (each pixel is reset as it is resolved).
+ * Outputs: d_depth [rows*cols] range of the nearest point (0 if empty),
+ *   d_idx [rows*cols] its index (-1 if empty), and, if d_pix != NULL,
+ *   d_pix float4 [rows*cols] = (x, y, z, 1) of that input point as given.
+ */
+upslam_status upslam_project(const float *d_pts, int32_t n, const double *d_pose12, const upslam_pano *pp,
+                             uint64_t *d_zbuf, float *d_depth, int32_t *d_idx, float *d_pix, void *stream);
+
+/* Keyframe pixel points d_pix float4 [rows*cols] = depth * dir (valid = depth > 0). */
+upslam_status upslam_unproject(const float *d_depth, const upslam_pano *pp, const float *d_dirs, float *d_pix,
+                               void *stream);
+
+/*
+ * Per-pixel normals (Sec. III-A): n = a x b, a toward column + 1 (wrapping),
+ * b toward row + 1; an unusable neighbour is replaced by the opposite one with
+ * the vector's sign flipped.  Normalised, oriented toward the sensor.
+ * d_pix float4 [rows*cols] pixel points, d_depth [rows*cols] their ranges.
+ * d_nrm float4 or half4 [rows*cols] = (nx, ny, nz, valid).
+ */
+upslam_status upslam_normals(const float *d_pix, const float *d_depth, const upslam_pano *pp,
+                             const upslam_normal_params *np, void *d_nrm, int32_t nrm_precision, void *stream);
+
+/* Workspace bytes that upslam_icp_step / upslam_icp need for this keyframe. */
+size_t upslam_icp_workspace_bytes(const upslam_keyframe *kf);
+
+/*
+ * One Gauss-Newton step of Eq. 1 (squared point-to-plane error).  Every
+ * keyframe pixel holding a sample is put at d * dir, taken into the sweep frame
+ * by T^-1 and binned into the sweep panorama; the sweep pixel's point s2 and the
+ * keyframe point s1 form a correspondence kept by Omega.  The normal equations
+ * J^T J xi = -J^T r (J = [p x n, n], p = T s2, left update) are reduced on the
+ * device, solved by an FP64 Cholesky, and d_pose12 <- exp(xi^) d_pose12.
+ * A degenerate system leaves d_pose12 unchanged (stats.status = 3).
+ * d_ws: workspace of upslam_icp_workspace_bytes(kf) bytes; it must be zeroed
+ * once before its first use and is left reusable.
+ */
+upslam_status upslam_icp_step(const upslam_keyframe *kf, const upslam_sweep *sw, double *d_pose12,
+                              const upslam_icp_params *ip, upslam_icp_stats *d_stats, void *d_ws, size_t ws_bytes,
+                              void *stream);
+
+/*
+ * Up to ip->max_iters Gauss-Newton steps in ONE persistent cooperative launch
+ * (one CTA group resident per SM; a bounded grid-wide barrier per step; the
+ * last CTA to arrive solves in FP64).  Stops early on convergence or a
+ * degenerate system.  stats.iters counts the steps taken.  A barrier that
+ * waits longer than about a second gives up and sets stats.status = 5.
+ */
+upslam_status upslam_icp(const upslam_keyframe *kf, const upslam_sweep *sw, double *d_pose12,
+                         const upslam_icp_params *ip, upslam_icp_stats *d_stats, void *d_ws, size_t ws_bytes,
+                         void *stream);
+
+/*
+ * Keyframe update (Sec. III-C) with T = d_pose12.  Runs only when d_stats is
+ * NULL or the registration was accepted (status 0 and inliers / valid >=
+ * accept_quality); stats.accepted records the outcome.  Averaging: every
+ * keyframe pixel with w > 0 is projected onto the sweep image and, if Omega
+ * keeps the pair, d <- (w d + |T s2|)/(w + 1), n <- unit(w n + R m),
+ * w <- min(w + 1, w_max).  Hole fill: every sweep pixel with a point and a
+ * normal is binned (with T) into the keyframe; each empty keyframe pixel takes
+ * its nearest sample (z-buffer on (range, sweep pixel index)) with w = 1.
+ * d_zbuf_kf: uint64 [kf rows*cols] scratch, all-ones on entry and on return.
+ */
+upslam_status upslam_fuse(const upslam_keyframe *kf, const upslam_sweep *sw, const double *d_pose12,
+                          const upslam_fuse_params *fp, upslam_icp_stats *d_stats, uint64_t *d_zbuf_kf,
+                          void *stream);
+
+/*
+ * Motion prior for the ICP initial guess (Sec. IV-F footnote: a zero-velocity
+ * prior by default, a zero-acceleration prior as the alternative).
+ * upslam_predict_pose: d_T_out = d_T_prev * d_motion (d_motion NULL: the
+ *   zero-velocity prior, d_T_out = d_T_prev).  Poses are 12 doubles [R | t];
+ *   the product's rotation is re-orthonormalised.  d_T_out may alias d_T_prev.
+ * upslam_update_motion: d_motion = d_T_prev^-1 * d_T (the last inter-sweep motion).
+ * One thread each, FP64, stream-ordered.
+ */
+upslam_status upslam_predict_pose(const double *d_T_prev, const double *d_motion, double *d_T_out, void *stream);
+upslam_status upslam_update_motion(const double *d_T_prev, const double *d_T, double *d_motion, void *stream);
+
+/* Human-readable name of a status code (static storage). */
+const char *upslam_status_string(upslam_status s);
+
+/* Library version string. */
+const char *upslam_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* UPSLAM_H */

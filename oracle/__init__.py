@@ -96,7 +96,7 @@ def _load():
         "orc_xform_inv_f32": (None, [_D, ctypes.c_float, ctypes.c_float, ctypes.c_float, _F, _F, _F]),
         "orc_dir_table": (None, [P(Pano), _F, _F]),
         "orc_project": (ctypes.c_int64, [_F, ctypes.c_int32, _D, P(Pano), _F, _I32]),
-        "orc_normals": (None, [_F, _F, P(Pano), P(NormalParams), _D, _U8]),
+        "orc_normals": (None, [_F, _F, P(Pano), P(NormalParams), _D, _U8, _D]),
         "orc_se3_exp_left": (None, [_D, _D]),
         "orc_solve6": (ctypes.c_int, [_D, _D, ctypes.c_double, _D]),
         "orc_icp_normal_equations": (None, [_F, _F, P(Pano), _F, _F, P(Pano), _D, P(IcpParams), P(IcpStats)]),
@@ -218,14 +218,17 @@ def keyframe_points(depth: np.ndarray, pp) -> np.ndarray:
     return out
 
 
-def normals(pix_pts: np.ndarray, depth: np.ndarray, pp, prm: Params = Params()):
-    """Sec. III-A cross-product normals -> (normals [H,W,3] FP64, valid [H,W] bool)."""
+def normals(pix_pts: np.ndarray, depth: np.ndarray, pp, prm: Params = Params(), with_conditioning: bool = False):
+    """Sec. III-A cross-product normals -> (normals [H,W,3] FP64, valid [H,W] bool[, sin(a, b) [H,W]])."""
     pix = np.ascontiguousarray(pix_pts, dtype=np.float32)
     dep = np.ascontiguousarray(depth, dtype=np.float32)
     nrm = np.empty((pp.rows, pp.cols, 3))
     val = np.empty((pp.rows, pp.cols), np.uint8)
+    sab = np.empty((pp.rows, pp.cols))
     _load().orc_normals(_f(pix), _f(dep), ctypes.byref(pano(pp)), ctypes.byref(prm.normal_params()), _d(nrm),
-                        val.ctypes.data_as(_U8))
+                        val.ctypes.data_as(_U8), _d(sab))
+    if with_conditioning:
+        return nrm, val.astype(bool), sab
     return nrm, val.astype(bool)
 
 

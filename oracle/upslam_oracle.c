@@ -256,16 +256,20 @@ static int nb_ok(const float *pts4, const float *depth, int64_t k, int64_t kn, c
  * unusable the opposite neighbour is used with the vector's sign flipped.  The
  * normal is normalised and oriented toward the sensor (n . P < 0).
  * Inputs: pts4 [rows*cols] pixel points (w != 0 valid), depth [rows*cols].
- * Outputs: nrm [rows*cols*3] (zeros when invalid), valid [rows*cols].
+ * Outputs: nrm [rows*cols*3] (zeros when invalid), valid [rows*cols], and, if
+ * sin_ab is not NULL, |a x b| / (|a| |b|) per pixel: the conditioning of the
+ * cross product (a tolerance for any lower-precision evaluation scales with
+ * its inverse).
  */
 void orc_normals(const float *pts4, const float *depth, const orc_pano *pp, const orc_normal_params *np,
-                 double *nrm, uint8_t *valid) {
+                 double *nrm, uint8_t *valid, double *sin_ab) {
     int H = pp->rows, W = pp->cols;
     for (int v = 0; v < H; ++v) {
         for (int u = 0; u < W; ++u) {
             int64_t k = (int64_t)v * W + u;
             nrm[3 * k] = nrm[3 * k + 1] = nrm[3 * k + 2] = 0.0;
             valid[k] = 0;
+            if (sin_ab) sin_ab[k] = 0.0;
             if (pts4[4 * k + 3] == 0.0f) continue;
             double P[3] = { pts4[4 * k], pts4[4 * k + 1], pts4[4 * k + 2] };
             double a[3], b[3];
@@ -284,6 +288,7 @@ void orc_normals(const float *pts4, const float *depth, const orc_pano *pp, cons
             double nn = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
             double na = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
             double nb = sqrt(b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
+            if (sin_ab && na > 0.0 && nb > 0.0) sin_ab[k] = nn / (na * nb);
             if (!(nn >= (double)np->min_cross * na * nb) || nn == 0.0) continue;
             double s = (n[0] * P[0] + n[1] * P[1] + n[2] * P[2]) > 0.0 ? -1.0 / nn : 1.0 / nn;
             nrm[3 * k] = n[0] * s;

@@ -1,0 +1,306 @@
+"""Python binding of the UPSLAM hot path over torch CUDA tensors.
+
+Argument marshalling only: every step runs in ``libupslam.so`` kernels on the
+current torch CUDA stream.  torch provides device memory and streams.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+from dataclasses import dataclass
+
+import torch
+
+from . import _abi
+
+F32, F16 = _abi.F32, _abi.F16
+
+
+def _stream() -> int:
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _p(t: torch.Tensor | None):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _require_cuda(*ts):
+    for t in ts:
+        if t is not None and not t.is_cuda:
+            raise ValueError("expected a CUDA tensor")
+
+
+def pano_struct(p) -> _abi.Pano:
+    """C panorama struct from an object with rows, cols, el_top, s_az, s_el, r_min, r_max."""
+    f = lambda x: float(torch.tensor(float(x), dtype=torch.float32).item())  # noqa: E731  (round to FP32)
+    return _abi.Pano(int(p.rows), int(p.cols), f(p.el_top), f(p.s_az), f(p.s_el), f(p.r_min), f(p.r_max))
+
+
+@dataclass
+class Params:
+    """Thresholds the paper leaves open; these values are this implementation's readings."""
+    jump_rel: float = 0.05
+    jump_abs: float = 0.1
+    min_cross: float = 1e-4
+    d_max: float = 0.5
+    cos_theta_max: float = math.cos(math.radians(30.0))
+    max_iters: int = 15
+    min_inliers: int = 6
+    eps_rot: float = 1e-6
+    eps_trans: float = 1e-6
+    pivot_eps: float = 1e-12
+    fuse_d_max: float = 0.2
+    fuse_cos_theta_max: float = math.cos(math.radians(30.0))
+    w_max: float = 10.0
+    accept_quality: float = 0.1
+
+    def normal(self):
+        return _abi.NormalParams(self.jump_rel, self.jump_abs, self.min_cross)
+
+    def icp(self):
+        return _abi.IcpParams(self.d_max, self.cos_theta_max, self.max_iters, self.min_inliers, self.eps_rot,
+                              self.eps_trans, self.pivot_eps)
+
+    def fuse(self):
+        return _abi.FuseParams(self.fuse_d_max, self.fuse_cos_theta_max, self.w_max, self.accept_quality)
+
+
+def empty_zbuf(npx: int, device) -> torch.Tensor:
+    """z-buffer scratch in its required resting state (all bits set)."""
+    return torch.full((npx,), -1, dtype=torch.int64, device=device)
+
+
+def identity_pose(device) -> torch.Tensor:
+    T = torch.zeros(12, dtype=torch.float64, device=device)
+    T[0] = T[5] = T[10] = 1.0
+    return T
+
+
+# ----------------------------------------------------------------------------- single calls
+
+def pano_dirs(pp, device="cuda") -> torch.Tensor:
+    ps = pano_struct(pp)
+    n = _abi.lib().upslam_pano_dirs_floats(ctypes.byref(ps))
+    out = torch.empty(n, dtype=torch.float32, device=device)
+    _abi.check("upslam_pano_dirs", _abi.lib().upslam_pano_dirs(ctypes.byref(ps), _p(out), _stream()))
+    return out
+
+
+def project(pts4: torch.Tensor, pp, pose: torch.Tensor | None = None, zbuf: torch.Tensor | None = None,
+            with_points: bool = True):
+    """Sec. III-A projection -> (depth [H,W] f32, idx [H,W] i32, pix [H,W,4] f32 or None)."""
+    _require_cuda(pts4, pose, zbuf)
+    pts4 = pts4.contiguous()
+    assert pts4.dtype == torch.float32 and pts4.shape[-1] == 4
+    H, W = int(pp.rows), int(pp.cols)
+    dev = pts4.device
+    if zbuf is None:
+        zbuf = empty_zbuf(H * W, dev)
+    depth = torch.empty((H, W), dtype=torch.float32, device=dev)
+    idx = torch.empty((H, W), dtype=torch.int32, device=dev)
+    pix = torch.empty((H, W, 4), dtype=torch.float32, device=dev) if with_points else None
+    ps = pano_struct(pp)
+    _abi.check("upslam_project", _abi.lib().upslam_project(_p(pts4), pts4.shape[0], _p(pose), ctypes.byref(ps),
+                                                           _p(zbuf), _p(depth), _p(idx), _p(pix), _stream()))
+    return depth, idx, pix
+
+
+def unproject(depth: torch.Tensor, pp, dirs: torch.Tensor) -> torch.Tensor:
+    _require_cuda(depth, dirs)
+    pix = torch.empty(depth.shape + (4,), dtype=torch.float32, device=depth.device)
+    ps = pano_struct(pp)
+    _abi.check("upslam_unproject", _abi.lib().upslam_unproject(_p(depth.contiguous()), ctypes.byref(ps), _p(dirs),
+                                                               _p(pix), _stream()))
+    return pix
+
+
+def normals(pix: torch.Tensor, depth: torch.Tensor, pp, params: Params = Params(), precision: int = F32):
+    """Sec. III-A cross-product normals -> [H,W,4] (nx, ny, nz, valid) in f32 or f16."""
+    _require_cuda(pix, depth)
+    dt = torch.float32 if precision == F32 else torch.float16
+    out = torch.empty(depth.shape + (4,), dtype=dt, device=depth.device)
+    ps = pano_struct(pp)
+    npar = params.normal()
+    _abi.check("upslam_normals", _abi.lib().upslam_normals(_p(pix.contiguous()), _p(depth.contiguous()),
+                                                           ctypes.byref(ps), ctypes.byref(npar), _p(out), precision,
+                                                           _stream()))
+    return out
+
+
+class SweepFrame:
+    """Device buffers of one sweep panorama: pixel points and normals."""
+
+    def __init__(self, pp, device="cuda", precision: int = F32):
+        self.pp = pp
+        self.precision = precision
+        H, W = int(pp.rows), int(pp.cols)
+        self.zbuf = empty_zbuf(H * W, device)
+        self.depth = torch.zeros((H, W), dtype=torch.float32, device=device)
+        self.idx = torch.zeros((H, W), dtype=torch.int32, device=device)
+        self.pix = torch.zeros((H, W, 4), dtype=torch.float32, device=device)
+        self.nrm = torch.zeros((H, W, 4), dtype=torch.float32 if precision == F32 else torch.float16, device=device)
+        self._ps = pano_struct(pp)
+
+    def struct(self) -> _abi.Sweep:
+        return _abi.Sweep(self._ps, self.pix.data_ptr(), self.nrm.data_ptr(), self.precision)
+
+    def load(self, pts4: torch.Tensor, params: Params) -> None:
+        """project + normals for a scan already on the device (float4 points)."""
+        L = _abi.lib()
+        s = _stream()
+        _abi.check("upslam_project", L.upslam_project(_p(pts4), pts4.shape[0], None, ctypes.byref(self._ps),
+                                                      _p(self.zbuf), _p(self.depth), _p(self.idx), _p(self.pix), s))
+        npar = params.normal()
+        _abi.check("upslam_normals", L.upslam_normals(_p(self.pix), _p(self.depth), ctypes.byref(self._ps),
+                                                      ctypes.byref(npar), _p(self.nrm), self.precision, s))
+
+    def set(self, pix: torch.Tensor, nrm: torch.Tensor) -> None:
+        """Use given pixel points / normals (e.g. test inputs) instead of computing them."""
+        self.pix.copy_(pix)
+        self.nrm.copy_(nrm)
+
+
+class KeyframeBuffer:
+    """Device keyframe panorama: depth, normals + sample count, direction table."""
+
+    def __init__(self, pp, device="cuda", precision: int = F32):
+        self.pp = pp
+        self.precision = precision
+        H, W = int(pp.rows), int(pp.cols)
+        self.depth = torch.zeros((H, W), dtype=torch.float32, device=device)
+        self.nw = torch.zeros((H, W, 4), dtype=torch.float32 if precision == F32 else torch.float16, device=device)
+        self.dirs = pano_dirs(pp, device)
+        self.zbuf = empty_zbuf(H * W, device)
+        self._ps = pano_struct(pp)
+
+    def struct(self) -> _abi.Keyframe:
+        return _abi.Keyframe(self._ps, self.depth.data_ptr(), self.nw.data_ptr(), self.precision,
+                             self.dirs.data_ptr())
+
+    def clear(self) -> None:
+        self.depth.zero_()
+        self.nw.zero_()
+
+    def set(self, depth: torch.Tensor, nw: torch.Tensor) -> None:
+        self.depth.copy_(depth)
+        self.nw.copy_(nw)
+
+
+class IcpState:
+    """Device-resident pose, stats and workspace for one registration problem."""
+
+    def __init__(self, kf: KeyframeBuffer, device="cuda"):
+        L = _abi.lib()
+        ks = kf.struct()
+        self.ws_bytes = int(L.upslam_icp_workspace_bytes(ctypes.byref(ks)))
+        self.ws = torch.zeros(self.ws_bytes, dtype=torch.uint8, device=device)
+        self.stats = torch.zeros(_abi.STATS_BYTES, dtype=torch.uint8, device=device)
+        self.pose = identity_pose(device)
+
+    def read_stats(self) -> dict:
+        raw = bytes(self.stats.cpu().numpy())
+        st = _abi.IcpStats.from_buffer_copy(raw)
+        return {"A": list(st.A), "b": list(st.b), "sse": st.sse, "inliers": st.inliers, "valid": st.valid,
+                "status": st.status, "converged": st.converged, "xi": list(st.xi), "iters": st.iters,
+                "accepted": st.accepted}
+
+
+def icp_step(kf: KeyframeBuffer, sw: SweepFrame, state: IcpState, params: Params = Params()) -> None:
+    ks, ss, ip = kf.struct(), sw.struct(), params.icp()
+    _abi.check("upslam_icp_step", _abi.lib().upslam_icp_step(ctypes.byref(ks), ctypes.byref(ss), _p(state.pose),
+                                                             ctypes.byref(ip), _p(state.stats), _p(state.ws),
+                                                             state.ws_bytes, _stream()))
+
+
+def icp(kf: KeyframeBuffer, sw: SweepFrame, state: IcpState, params: Params = Params()) -> None:
+    ks, ss, ip = kf.struct(), sw.struct(), params.icp()
+    _abi.check("upslam_icp", _abi.lib().upslam_icp(ctypes.byref(ks), ctypes.byref(ss), _p(state.pose),
+                                                   ctypes.byref(ip), _p(state.stats), _p(state.ws), state.ws_bytes,
+                                                   _stream()))
+
+
+def fuse(kf: KeyframeBuffer, sw: SweepFrame, pose: torch.Tensor, params: Params = Params(),
+         stats: torch.Tensor | None = None) -> None:
+    ks, ss, fp = kf.struct(), sw.struct(), params.fuse()
+    _abi.check("upslam_fuse", _abi.lib().upslam_fuse(ctypes.byref(ks), ctypes.byref(ss), _p(pose), ctypes.byref(fp),
+                                                     _p(stats), _p(kf.zbuf), _stream()))
+
+
+# ----------------------------------------------------------------------------- the per-sweep path
+
+class Tracker:
+    """Registers a stream of sweeps against keyframes and fuses them in (Sec. III).
+
+    Everything stays on the device: the pose of the current sweep in the
+    current keyframe (``state.pose``), the last inter-sweep motion, the
+    registration record.  ``track`` launches project, normals, the motion
+    prior, the persistent ICP and the keyframe update on the current stream
+    with no host synchronisation.  ``new_keyframe`` starts a keyframe at the
+    current sweep (its frame becomes the keyframe frame) by hole-filling an
+    empty panorama.
+    """
+
+    def __init__(self, sweep_pano, kf_pano, params: Params = Params(), precision: int = F32, device="cuda",
+                 constant_velocity: bool = True):
+        self.params = params
+        self.sw = SweepFrame(sweep_pano, device, precision)
+        self.kf = KeyframeBuffer(kf_pano, device, precision)
+        self.state = IcpState(self.kf, device)
+        self.motion = identity_pose(device)
+        self.prev = identity_pose(device)
+        self.identity = identity_pose(device)
+        self.constant_velocity = constant_velocity
+        self._ip, self._fp = params.icp(), params.fuse()
+
+    def new_keyframe(self, pts4: torch.Tensor | None = None, buffer: KeyframeBuffer | None = None) -> None:
+        """Start a keyframe at the sweep in ``self.sw`` (loading ``pts4`` first if given).
+
+        ``buffer``: an all-zero keyframe buffer to use from now on (for example one of a
+        pre-allocated pool); without it the current buffer is cleared and reused.
+        """
+        if pts4 is not None:
+            self.sw.load(pts4, self.params)
+        if buffer is not None:
+            self.kf = buffer
+        else:
+            self.kf.clear()
+        fuse(self.kf, self.sw, self.identity, self.params, None)
+        self.prev.copy_(self.identity)
+
+    # optional profiling hook: (recorder, stream, proj_events, icp_events, fuse_events); the recorder's
+    # record(event, stream) is called around the three phases of track()
+    timing = None
+
+    def _mark(self, which: int, edge: int) -> None:
+        tm = self.timing
+        if tm is not None:
+            tm[0].record(tm[2 + which][edge], tm[1])
+
+    def track(self, pts4: torch.Tensor) -> None:
+        """One sweep: project, normals, prior, ICP, keyframe update (all asynchronous)."""
+        L = _abi.lib()
+        s = _stream()
+        self._mark(0, 0)
+        self.sw.load(pts4, self.params)
+        self._mark(0, 1)
+        _abi.check("upslam_predict_pose", L.upslam_predict_pose(_p(self.prev),
+                                                                _p(self.motion) if self.constant_velocity else None,
+                                                                _p(self.state.pose), s))
+        ks, ss = self.kf.struct(), self.sw.struct()
+        self._mark(1, 0)
+        _abi.check("upslam_icp", L.upslam_icp(ctypes.byref(ks), ctypes.byref(ss), _p(self.state.pose),
+                                              ctypes.byref(self._ip), _p(self.state.stats), _p(self.state.ws),
+                                              self.state.ws_bytes, s))
+        self._mark(1, 1)
+        _abi.check("upslam_update_motion", L.upslam_update_motion(_p(self.prev), _p(self.state.pose),
+                                                                  _p(self.motion), s))
+        self._mark(2, 0)
+        _abi.check("upslam_fuse", L.upslam_fuse(ctypes.byref(ks), ctypes.byref(ss), _p(self.state.pose),
+                                                ctypes.byref(self._fp), _p(self.state.stats), _p(self.kf.zbuf), s))
+        self._mark(2, 1)
+        self.prev.copy_(self.state.pose)
+
+    # kernels launched by one track() call: project (2), normals, predict, icp, motion, fuse (2)
+    LAUNCHES_PER_TRACK = 8
+    # kernels launched by new_keyframe() (after loading): fuse (2)
+    LAUNCHES_PER_NEW_KEYFRAME = 2

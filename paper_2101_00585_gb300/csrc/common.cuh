@@ -1,0 +1,324 @@
+// Device-side building blocks shared by the UPSLAM kernels (sm_103a).
+//
+// The FP32 functions here implement the binning rule stated in upslam.h with
+// explicit round-to-nearest intrinsics, so no multiply-add is ever contracted
+// into an FMA: the pixel a point falls in, and therefore every z-buffer winner
+// and every projective correspondence, is a bit-exact function of the inputs.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/upslam.h"
+
+namespace upslam {
+
+constexpr float kPiF = 3.14159265358979323846f;
+constexpr float kHalfPiF = 1.57079632679489661923f;
+constexpr unsigned long long kEmptyKey = 0xffffffffffffffffull;
+constexpr int kNumSums = 29;  // 21 (J^T J) + 6 (J^T r) + sse + inliers
+
+// ----------------------------------------------------------------------------- FP32 decisions
+
+// atan2 reduced by octant symmetry to atan(t), t in [0, 1], with the odd
+// polynomial of Abramowitz & Stegun 4.4.49 (|error| <= 2e-8 before rounding).
+__device__ __forceinline__ float atan2p(float y, float x) {
+    const float ax = fabsf(x), ay = fabsf(y);
+    const float mx = ax > ay ? ax : ay;
+    const float mn = ax > ay ? ay : ax;
+    if (mx == 0.0f) return 0.0f;
+    const float t = __fdiv_rn(mn, mx);
+    const float s = __fmul_rn(t, t);
+    float p = 0.0028662257f;
+    p = __fadd_rn(__fmul_rn(p, s), -0.0161657367f);
+    p = __fadd_rn(__fmul_rn(p, s), 0.0429096138f);
+    p = __fadd_rn(__fmul_rn(p, s), -0.0752896400f);
+    p = __fadd_rn(__fmul_rn(p, s), 0.1065626393f);
+    p = __fadd_rn(__fmul_rn(p, s), -0.1420889944f);
+    p = __fadd_rn(__fmul_rn(p, s), 0.1999355085f);
+    p = __fadd_rn(__fmul_rn(p, s), -0.3333314528f);
+    p = __fadd_rn(__fmul_rn(p, s), 1.0f);
+    float a = __fmul_rn(t, p);
+    if (ay > ax) a = __fsub_rn(kHalfPiF, a);
+    if (x < 0.0f) a = __fsub_rn(kPiF, a);
+    if (y < 0.0f) a = -a;
+    return a;
+}
+
+// Pixel (row, col) and range of an FP32 point; false when outside the panorama.
+__device__ __forceinline__ bool bin_point(float x, float y, float z, const upslam_pano &pp, int &row, int &col,
+                                          float &r) {
+    const float xy2 = __fadd_rn(__fmul_rn(x, x), __fmul_rn(y, y));
+    r = __fsqrt_rn(__fadd_rn(xy2, __fmul_rn(z, z)));
+    if (!(r >= pp.r_min && r <= pp.r_max)) return false;
+    const float rho = __fsqrt_rn(xy2);
+    const float az = atan2p(y, x);
+    const float el = atan2p(z, rho);
+    const float fc = __fmul_rn(__fsub_rn(kPiF, az), pp.s_az);
+    const float fr = __fmul_rn(__fsub_rn(pp.el_top, el), pp.s_el);
+    if (!(fr >= 0.0f) || !(fr < (float)pp.rows)) return false;
+    row = (int)floorf(fr);
+    col = (int)floorf(fc);
+    if (row >= pp.rows) return false;
+    if (col >= pp.cols) col -= pp.cols;
+    if (col < 0) col += pp.cols;
+    return true;
+}
+
+// Pose rounded to FP32, row-major [R | t].
+struct PoseF {
+    float r[12];
+};
+
+__device__ __forceinline__ PoseF pose_to_f32(const double *T) {
+    PoseF p;
+#pragma unroll
+    for (int i = 0; i < 12; ++i) p.r[i] = (float)T[i];
+    return p;
+}
+
+// Pose read through L2 only (never a stale L1 line): for poses other CTAs rewrite.
+__device__ __forceinline__ PoseF pose_to_f32_cg(const double *T) {
+    PoseF p;
+#pragma unroll
+    for (int i = 0; i < 12; ++i) p.r[i] = (float)__ldcg(T + i);
+    return p;
+}
+
+// p = R q + t, fixed order ((r0 x + r1 y) + r2 z) + t0, no contraction.
+__device__ __forceinline__ float3 xform(const PoseF &T, float qx, float qy, float qz) {
+    const float *r = T.r;
+    float3 p;
+    p.x = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(r[0], qx), __fmul_rn(r[1], qy)), __fmul_rn(r[2], qz)), r[3]);
+    p.y = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(r[4], qx), __fmul_rn(r[5], qy)), __fmul_rn(r[6], qz)), r[7]);
+    p.z = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(r[8], qx), __fmul_rn(r[9], qy)), __fmul_rn(r[10], qz)), r[11]);
+    return p;
+}
+
+// q = R^T (s - t), fixed order.
+__device__ __forceinline__ float3 xform_inv(const PoseF &T, float sx, float sy, float sz) {
+    const float *r = T.r;
+    const float dx = __fsub_rn(sx, r[3]), dy = __fsub_rn(sy, r[7]), dz = __fsub_rn(sz, r[11]);
+    float3 q;
+    q.x = __fadd_rn(__fadd_rn(__fmul_rn(r[0], dx), __fmul_rn(r[4], dy)), __fmul_rn(r[8], dz));
+    q.y = __fadd_rn(__fadd_rn(__fmul_rn(r[1], dx), __fmul_rn(r[5], dy)), __fmul_rn(r[9], dz));
+    q.z = __fadd_rn(__fadd_rn(__fmul_rn(r[2], dx), __fmul_rn(r[6], dy)), __fmul_rn(r[10], dz));
+    return q;
+}
+
+// Rotation only (values, FMA allowed).
+__device__ __forceinline__ float3 rotate(const PoseF &T, float x, float y, float z) {
+    const float *r = T.r;
+    return make_float3(r[0] * x + r[1] * y + r[2] * z, r[4] * x + r[5] * y + r[6] * z,
+                       r[8] * x + r[9] * y + r[10] * z);
+}
+
+// FP32 point of pixel (v, u) at depth d from the direction table: d * (ce*ca, ce*sa, se).
+__device__ __forceinline__ float3 pixel_point(const float *dirs, int rows, int v, int u, float d) {
+    const float2 e = __ldg(reinterpret_cast<const float2 *>(dirs) + v);
+    const float2 a = __ldg(reinterpret_cast<const float2 *>(dirs + 2 * rows) + u);
+    return make_float3(__fmul_rn(d, __fmul_rn(e.x, a.x)), __fmul_rn(d, __fmul_rn(e.x, a.y)), __fmul_rn(d, e.y));
+}
+
+// ----------------------------------------------------------------------------- storage helpers
+
+__device__ __forceinline__ float4 load_nw(const void *base, int64_t k, int precision) {
+    if (precision == UPSLAM_F32) return __ldg(reinterpret_cast<const float4 *>(base) + k);
+    const uint2 raw = __ldg(reinterpret_cast<const uint2 *>(base) + k);
+    const __half2 a = *reinterpret_cast<const __half2 *>(&raw.x);
+    const __half2 b = *reinterpret_cast<const __half2 *>(&raw.y);
+    const float2 fa = __half22float2(a), fb = __half22float2(b);
+    return make_float4(fa.x, fa.y, fb.x, fb.y);
+}
+
+// Same load, through L2 only (for data rewritten during the kernel's lifetime by other CTAs).
+__device__ __forceinline__ float4 load_nw_cg(const void *base, int64_t k, int precision) {
+    if (precision == UPSLAM_F32) return __ldcg(reinterpret_cast<const float4 *>(base) + k);
+    const uint2 raw = __ldcg(reinterpret_cast<const uint2 *>(base) + k);
+    const __half2 a = *reinterpret_cast<const __half2 *>(&raw.x);
+    const __half2 b = *reinterpret_cast<const __half2 *>(&raw.y);
+    const float2 fa = __half22float2(a), fb = __half22float2(b);
+    return make_float4(fa.x, fa.y, fb.x, fb.y);
+}
+
+__device__ __forceinline__ void store_nw(void *base, int64_t k, int precision, float4 v) {
+    if (precision == UPSLAM_F32) {
+        reinterpret_cast<float4 *>(base)[k] = v;
+        return;
+    }
+    const __half2 a = __floats2half2_rn(v.x, v.y), b = __floats2half2_rn(v.z, v.w);
+    uint2 raw;
+    raw.x = *reinterpret_cast<const unsigned int *>(&a);
+    raw.y = *reinterpret_cast<const unsigned int *>(&b);
+    reinterpret_cast<uint2 *>(base)[k] = raw;
+}
+
+// ----------------------------------------------------------------------------- reductions
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// ----------------------------------------------------------------------------- FP64 solve
+//
+// GB300 runs FP64 at a small fraction of its FP32 rate, and a dependent FP64
+// FMA costs tens of cycles (a division an order of magnitude more), so the
+// solve is written for a short dependency chain: fully unrolled (every value
+// in a register), no FP64 division or square root on the critical path.
+
+// 1/d for a positive normal d: FP32 seed, one FP64 Newton step (relative error
+// about 2^-46, far below the FP32 accumulation error of the normal equations).
+__device__ __forceinline__ double rcp64(double d) {
+    double x = (double)__frcp_rn((float)d);
+    const double e = fma(-d, x, 1.0);
+    return fma(x, e, x);
+}
+
+// sin(t)/t, (1 - cos t)/t^2, (t - sin t)/t^3 from t^2: Taylor series (truncation
+// below 1e-18 for t <= 0.25), sincos otherwise.
+__device__ __forceinline__ void se3_coeffs(double th2, double &A, double &B, double &C) {
+    if (th2 <= 0.0625) {
+        A = fma(th2, fma(th2, fma(th2, fma(th2, fma(th2, fma(th2, 1.0 / 6227020800.0, -1.0 / 39916800.0),
+                                                    1.0 / 362880.0), -1.0 / 5040.0), 1.0 / 120.0), -1.0 / 6.0), 1.0);
+        B = fma(th2, fma(th2, fma(th2, fma(th2, fma(th2, fma(th2, 1.0 / 87178291200.0, -1.0 / 479001600.0),
+                                                    1.0 / 3628800.0), -1.0 / 40320.0), 1.0 / 720.0), -1.0 / 24.0), 0.5);
+        C = fma(th2, fma(th2, fma(th2, fma(th2, fma(th2, fma(th2, 1.0 / 1307674368000.0, -1.0 / 6227020800.0),
+                                                    1.0 / 39916800.0), -1.0 / 362880.0), 1.0 / 5040.0), -1.0 / 120.0),
+                1.0 / 6.0);
+    } else {
+        const double th = sqrt(th2);
+        double sn, cs;
+        sincos(th, &sn, &cs);
+        A = sn / th;
+        B = (1.0 - cs) / th2;
+        C = (th - sn) / (th2 * th);
+    }
+}
+
+// T <- exp(xi^) T (left update), xi = (omega, v): Rodrigues rotation
+// R = I + A W + B W^2 and translation V v with V = I + B W + C W^2, where
+// W = [omega]_x and W^2 = omega omega^T - |omega|^2 I.
+__device__ __forceinline__ void se3_exp_left(const double xi[6], double T[12]) {
+    const double w0 = xi[0], w1 = xi[1], w2 = xi[2];
+    const double th2 = fma(w0, w0, fma(w1, w1, w2 * w2));
+    double A, B, C;
+    se3_coeffs(th2, A, B, C);
+    const double W[9] = {0.0, -w2, w1, w2, 0.0, -w0, -w1, w0, 0.0};
+    const double om[3] = {w0, w1, w2};
+    double R[9], V[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const double W2 = fma(om[i], om[j], i == j ? -th2 : 0.0);
+            const double I = i == j ? 1.0 : 0.0;
+            R[3 * i + j] = fma(A, W[3 * i + j], fma(B, W2, I));
+            V[3 * i + j] = fma(B, W[3 * i + j], fma(C, W2, I));
+        }
+    double Tn[12];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            Tn[4 * i + j] = fma(R[3 * i], T[j], fma(R[3 * i + 1], T[4 + j], R[3 * i + 2] * T[8 + j]));
+        const double te = fma(V[3 * i], xi[3], fma(V[3 * i + 1], xi[4], V[3 * i + 2] * xi[5]));
+        Tn[4 * i + 3] = fma(R[3 * i], T[3], fma(R[3 * i + 1], T[7], fma(R[3 * i + 2], T[11], te)));
+    }
+#pragma unroll
+    for (int i = 0; i < 12; ++i) T[i] = Tn[i];
+}
+
+// Solve M x = rhs for the symmetric positive-definite 6x6 M given by its
+// row-major upper triangle, by the square-root-free Cholesky factorisation
+// M = L D L^T (elimination on the upper triangle, then back substitution).
+// Returns false when a pivot D_j <= pivot_eps * max diagonal (the same
+// quantity a square-root Cholesky compares before its square root).
+__device__ __forceinline__ bool solve6(const double *Aup, const double *rhs, double pivot_eps, double *x) {
+    double U[6][6];
+    double y[6], r[6];
+    {
+        int p = 0;
+#pragma unroll
+        for (int i = 0; i < 6; ++i)
+#pragma unroll
+            for (int j = i; j < 6; ++j) U[i][j] = Aup[p++];
+    }
+    double dmax = U[0][0];
+#pragma unroll
+    for (int i = 1; i < 6; ++i) dmax = fmax(dmax, U[i][i]);
+    if (!(dmax > 0.0)) return false;
+    const double lim = pivot_eps * dmax;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) y[i] = rhs[i];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        const double d = U[j][j];
+        if (!(d > lim) || !(d > 1e-300)) return false;
+        r[j] = rcp64(d);
+#pragma unroll
+        for (int i = j + 1; i < 6; ++i) {
+            const double l = U[j][i] * r[j];  // M symmetric: row j, column i of the reduced matrix
+#pragma unroll
+            for (int k = i; k < 6; ++k) U[i][k] = fma(-l, U[j][k], U[i][k]);
+            y[i] = fma(-l, y[j], y[i]);
+        }
+    }
+#pragma unroll
+    for (int i = 5; i >= 0; --i) {
+        double s = y[i];
+#pragma unroll
+        for (int k = i + 1; k < 6; ++k) s = fma(-U[i][k], x[k], s);
+        x[i] = s * r[i];
+    }
+    return true;
+}
+
+// Neumaier-compensated FP32 accumulation: (s, c) holds s + c.
+__device__ __forceinline__ void kadd(float &s, float &c, float v) {
+    const float t = s + v;
+    c += fabsf(s) >= fabsf(v) ? (s - t) + v : (v - t) + s;
+    s = t;
+}
+
+}  // namespace upslam
+
+// ----------------------------------------------------------------------------- host helpers
+
+#define UPSLAM_CHECK_LAUNCH()                                     \
+    do {                                                          \
+        if (cudaPeekAtLastError() != cudaSuccess) {               \
+            (void)cudaGetLastError();                             \
+            return UPSLAM_ERR_CUDA;                               \
+        }                                                         \
+    } while (0)
+
+static inline bool upslam_pano_ok(const upslam_pano *pp) {
+    return pp && pp->rows > 0 && pp->cols > 0 && (int64_t)pp->rows * pp->cols < (int64_t(1) << 31) &&
+           pp->s_az > 0.0f && pp->s_el > 0.0f && pp->r_max >= pp->r_min;
+}
+
+static inline bool upslam_aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+// Multiprocessor count of the current device, cached per device ordinal.
+static inline int upslam_sm_count() {
+    static int cache[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+    if (cache[dev] == 0) {
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 152;
+        cache[dev] = sms;
+    }
+    return cache[dev];
+}
+
+// Grid for a grid-stride loop over `work` items: enough CTAs to fill every SM
+// several times over, never more than the work needs.
+static inline int upslam_grid(int64_t work, int threads, int per_sm = 8) {
+    const int64_t want = (work + threads - 1) / threads;
+    const int64_t cap = (int64_t)upslam_sm_count() * per_sm;
+    return (int)(want < 1 ? 1 : (want < cap ? want : cap));
+}

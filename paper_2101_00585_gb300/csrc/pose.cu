@@ -1,0 +1,80 @@
+// Motion prior for the ICP initial guess (UPSLAM Sec. IV-F footnote: a zero
+// velocity prior by default, a zero acceleration prior as the alternative).
+//
+// Kept on the device so a whole sweep can run without a host round trip:
+//   predict:        T0 = T_prev * M   (M = identity for the zero-velocity prior)
+//   update motion:  M  = T_prev^-1 * T
+// Rotations are re-orthonormalised (Gram-Schmidt on the rows) after every
+// product so rounding cannot compound from sweep to sweep.  FP64, one thread.
+#include "common.cuh"
+
+namespace upslam {
+
+__device__ void mul34(const double *A, const double *B, double *C) {
+    double t[12];
+    for (int i = 0; i < 3; ++i) {
+        for (int j = 0; j < 3; ++j) t[4 * i + j] = A[4 * i] * B[j] + A[4 * i + 1] * B[4 + j] + A[4 * i + 2] * B[8 + j];
+        t[4 * i + 3] = A[4 * i] * B[3] + A[4 * i + 1] * B[7] + A[4 * i + 2] * B[11] + A[4 * i + 3];
+    }
+    for (int i = 0; i < 12; ++i) C[i] = t[i];
+}
+
+__device__ void inv34(const double *A, double *B) {
+    double t[12];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) t[4 * i + j] = A[4 * j + i];
+    for (int i = 0; i < 3; ++i) t[4 * i + 3] = -(t[4 * i] * A[3] + t[4 * i + 1] * A[7] + t[4 * i + 2] * A[11]);
+    for (int i = 0; i < 12; ++i) B[i] = t[i];
+}
+
+__device__ void orthonormalise(double *T) {
+    double *r0 = T, *r1 = T + 4, *r2 = T + 8;
+    double n = sqrt(r0[0] * r0[0] + r0[1] * r0[1] + r0[2] * r0[2]);
+    for (int i = 0; i < 3; ++i) r0[i] /= n;
+    double d = r0[0] * r1[0] + r0[1] * r1[1] + r0[2] * r1[2];
+    for (int i = 0; i < 3; ++i) r1[i] -= d * r0[i];
+    n = sqrt(r1[0] * r1[0] + r1[1] * r1[1] + r1[2] * r1[2]);
+    for (int i = 0; i < 3; ++i) r1[i] /= n;
+    r2[0] = r0[1] * r1[2] - r0[2] * r1[1];
+    r2[1] = r0[2] * r1[0] - r0[0] * r1[2];
+    r2[2] = r0[0] * r1[1] - r0[1] * r1[0];
+}
+
+__global__ void predict_kernel(const double *T_prev, const double *M, double *T_out) {
+    double t[12];
+    if (M) {
+        mul34(T_prev, M, t);
+        orthonormalise(t);
+    } else {
+        for (int i = 0; i < 12; ++i) t[i] = T_prev[i];
+    }
+    for (int i = 0; i < 12; ++i) T_out[i] = t[i];
+}
+
+__global__ void motion_kernel(const double *T_prev, const double *T, double *M) {
+    double inv[12], t[12];
+    inv34(T_prev, inv);
+    mul34(inv, T, t);
+    orthonormalise(t);
+    for (int i = 0; i < 12; ++i) M[i] = t[i];
+}
+
+}  // namespace upslam
+
+using namespace upslam;
+
+extern "C" upslam_status upslam_predict_pose(const double *d_T_prev, const double *d_motion, double *d_T_out,
+                                             void *stream) {
+    if (!d_T_prev || !d_T_out) return UPSLAM_ERR_INVALID_ARG;
+    predict_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(d_T_prev, d_motion, d_T_out);
+    UPSLAM_CHECK_LAUNCH();
+    return UPSLAM_OK;
+}
+
+extern "C" upslam_status upslam_update_motion(const double *d_T_prev, const double *d_T, double *d_motion,
+                                              void *stream) {
+    if (!d_T_prev || !d_T || !d_motion) return UPSLAM_ERR_INVALID_ARG;
+    motion_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(d_T_prev, d_T, d_motion);
+    UPSLAM_CHECK_LAUNCH();
+    return UPSLAM_OK;
+}

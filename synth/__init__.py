@@ -106,10 +106,15 @@ def relative(P_w_kf: np.ndarray, P_w_s: np.ndarray) -> np.ndarray:
 
 
 def pose_error(A: np.ndarray, B: np.ndarray):
-    """(translation error m, rotation error rad) between two poses."""
+    """(translation error m, rotation error rad) between two poses.
+
+    The angle of R_A^T R_B is atan2(|vee(M - M^T)| / 2, (tr M - 1) / 2), which stays
+    accurate for tiny angles (an arccos of the trace would not)."""
     dt = float(np.linalg.norm(A[:, 3] - B[:, 3]))
-    c = (np.trace(A[:, :3].T @ B[:, :3]) - 1.0) / 2.0
-    return dt, float(math.acos(max(-1.0, min(1.0, c))))
+    M = A[:, :3].T @ B[:, :3]
+    s = 0.5 * math.sqrt((M[2, 1] - M[1, 2]) ** 2 + (M[0, 2] - M[2, 0]) ** 2 + (M[1, 0] - M[0, 1]) ** 2)
+    c = 0.5 * (np.trace(M) - 1.0)
+    return dt, float(math.atan2(s, c))
 
 
 def perturb(P: np.ndarray, rng: np.random.Generator, trans_m: float, rot_rad: float) -> np.ndarray:

@@ -1,0 +1,103 @@
+"""Host-side checks of the C ABI (no GPU needed): exports and argument validation."""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2101_00585_gb300 as up
+from paper_2101_00585_gb300 import _abi
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    txt = open(os.path.join(ROOT, "include", "upslam.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(upslam_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    L = up.lib()
+    names = declared_symbols()
+    assert len(names) >= 13
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(names) <= set(_abi.SIGNATURES), set(names) - set(_abi.SIGNATURES)
+    assert L.upslam_version().startswith(b"upslam-gb300")
+
+
+def test_status_strings():
+    L = up.lib()
+    for code in range(7):
+        assert L.upslam_status_string(code)
+    assert L.upslam_status_string(99) == b"unknown status"
+
+
+def _pano(rows=4, cols=8):
+    return _abi.Pano(rows, cols, 0.5, cols / 6.283185307, rows / 1.0, 0.1, 100.0)
+
+
+def test_invalid_arguments_are_rejected_on_the_host():
+    """Bad arguments return INVALID_ARG before any CUDA call (safe without a GPU)."""
+    L = up.lib()
+    pp = _pano()
+    bad = _abi.Pano(0, 8, 0.5, 1.0, 1.0, 0.1, 100.0)
+    fake = ctypes.c_void_p(256)
+    assert L.upslam_project(fake, 10, None, ctypes.byref(bad), fake, fake, fake, None, None) == _abi.ERR_INVALID_ARG
+    assert L.upslam_project(None, 10, None, ctypes.byref(pp), fake, fake, fake, None, None) == _abi.ERR_INVALID_ARG
+    assert L.upslam_project(fake, -1, None, ctypes.byref(pp), fake, fake, fake, None, None) == _abi.ERR_INVALID_ARG
+    misaligned = ctypes.c_void_p(256 + 4)
+    assert L.upslam_project(misaligned, 10, None, ctypes.byref(pp), fake, fake, fake, None,
+                            None) == _abi.ERR_INVALID_ARG
+    npar = _abi.NormalParams(0.05, 0.1, 1e-4)
+    assert L.upslam_normals(fake, fake, ctypes.byref(pp), ctypes.byref(npar), fake, 7, None) == _abi.ERR_INVALID_ARG
+    assert L.upslam_pano_dirs(ctypes.byref(bad), fake, None) == _abi.ERR_INVALID_ARG
+    assert L.upslam_pano_dirs_floats(ctypes.byref(bad)) == 0
+    assert L.upslam_pano_dirs_floats(ctypes.byref(pp)) == 2 * 4 + 2 * 8
+    ks = _abi.Keyframe(pp, 256, 256, 0, 256)
+    ss = _abi.Sweep(pp, 256, 256, 0)
+    ip = _abi.IcpParams(0.5, 0.86, 10, 6, 1e-6, 1e-6, 1e-12)
+    ws = int(L.upslam_icp_workspace_bytes(ctypes.byref(ks)))
+    assert ws >= 256
+    # workspace too small / stats missing / bad precision
+    assert L.upslam_icp_step(ctypes.byref(ks), ctypes.byref(ss), fake, ctypes.byref(ip), fake, fake, 16,
+                             None) == _abi.ERR_INVALID_ARG
+    assert L.upslam_icp(ctypes.byref(ks), ctypes.byref(ss), fake, ctypes.byref(ip), None, fake, ws,
+                        None) == _abi.ERR_INVALID_ARG
+    ks_bad = _abi.Keyframe(pp, 256, 256, 5, 256)
+    assert L.upslam_icp_step(ctypes.byref(ks_bad), ctypes.byref(ss), fake, ctypes.byref(ip), fake, fake, ws,
+                             None) == _abi.ERR_INVALID_ARG
+    fp = _abi.FuseParams(0.2, 0.86, 0.5, 0.1)  # w_max < 1
+    assert L.upslam_fuse(ctypes.byref(ks), ctypes.byref(ss), fake, ctypes.byref(fp), None, fake,
+                         None) == _abi.ERR_INVALID_ARG
+    assert L.upslam_predict_pose(None, None, fake, None) == _abi.ERR_INVALID_ARG
+    assert L.upslam_update_motion(fake, None, fake, None) == _abi.ERR_INVALID_ARG
+
+
+def test_struct_layouts_match_header():
+    """ctypes mirrors of the header structs have the C sizes the library expects."""
+    assert ctypes.sizeof(_abi.Pano) == 28
+    assert ctypes.sizeof(_abi.IcpParams) == 40
+    assert ctypes.sizeof(_abi.IcpStats) == 21 * 8 + 6 * 8 + 8 + 8 + 8 + 4 + 4 + 6 * 8 + 4 + 4
+
+
+def test_product_path_has_no_oracle_or_cpu_fallback():
+    """The package never imports the oracle and refuses to run without its library."""
+    pkg = os.path.join(ROOT, "paper_2101_00585_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                src = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in src and "from oracle" not in src, f
+                assert "upslam_oracle" not in src, f
+    with pytest.raises(RuntimeError):
+        saved = _abi._lib, _abi.LIB_PATH
+        try:
+            _abi._lib = None
+            _abi.LIB_PATH = "/nonexistent/libupslam.so"
+            _abi.lib(build_if_missing=False)
+        finally:
+            _abi._lib, _abi.LIB_PATH = saved
