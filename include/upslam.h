@@ -67,7 +67,8 @@ typedef enum {
     UPSLAM_ERR_DEGENERATE = 3,   /* too few inliers or a Cholesky pivot <= pivot_eps * max diag */
     UPSLAM_ERR_NOT_CONVERGED = 4,
     UPSLAM_ERR_TIMEOUT = 5,      /* a bounded device-side wait gave up */
-    UPSLAM_ERR_UNSUPPORTED = 6   /* e.g. a cooperative launch the device cannot host */
+    UPSLAM_ERR_UNSUPPORTED = 6,  /* e.g. a cooperative launch the device cannot host */
+    UPSLAM_ERR_CAPACITY = 7      /* the request needs more than a fixed-size scratch array holds */
 } upslam_status;
 
 /* Storage precision of normals and sample counts. */
@@ -224,6 +225,32 @@ upslam_status upslam_icp(const upslam_keyframe *kf, const upslam_sweep *sw, doub
 upslam_status upslam_fuse(const upslam_keyframe *kf, const upslam_sweep *sw, const double *d_pose12,
                           const upslam_fuse_params *fp, upslam_icp_stats *d_stats, uint64_t *d_zbuf_kf,
                           void *stream);
+
+/*
+ * Allocation-free ICP.  The paper has no counterpart: this exists for callers
+ * that cannot allocate device memory once they are running, such as a robot's
+ * real-time control loop (a cudaMalloc can block on a driver lock and miss the
+ * sweep deadline), a plugin whose host runtime owns the device allocator, or
+ * code that may only use memory fixed at load time.  It runs exactly what
+ * upslam_icp runs, but its workspace is a static device array inside the
+ * library (upslam_icp_noalloc_capacity_bytes() bytes, 512.25 KiB, held on
+ * every GPU that loads the library until the process exits) instead of d_ws.
+ * The caller still provides the keyframe, sweep, pose and stats buffers.
+ * - Allocates nothing: no cudaMalloc / cudaFree, no allocating library call.
+ *   The scratch's barrier counters are cleared with cudaMemsetAsync on the
+ *   stream at every call.
+ * - The first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before any stream capture.
+ * - Returns UPSLAM_ERR_CAPACITY when the launch this device needs would not fit
+ *   the array (more than 2048 CTAs).
+ * - Every call shares the one array: calls that overlap on the GPU (other
+ *   streams, other threads) race and corrupt each other's results; serialise
+ *   them on one stream.
+ */
+size_t upslam_icp_noalloc_capacity_bytes(void);
+upslam_status upslam_icp_noalloc(const upslam_keyframe *kf, const upslam_sweep *sw, double *d_pose12,
+                                 const upslam_icp_params *ip, upslam_icp_stats *d_stats, void *stream);
 
 /*
  * Motion prior for the ICP initial guess (Sec. IV-F footnote: a zero-velocity

@@ -12,7 +12,7 @@ import threading
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libupslam.so")
 
-OK, ERR_INVALID_ARG, ERR_CUDA, ERR_DEGENERATE, ERR_NOT_CONVERGED, ERR_TIMEOUT, ERR_UNSUPPORTED = range(7)
+OK, ERR_INVALID_ARG, ERR_CUDA, ERR_DEGENERATE, ERR_NOT_CONVERGED, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_CAPACITY = range(8)
 F32, F16 = 0, 1
 
 
@@ -69,6 +69,8 @@ SIGNATURES = {
     "upslam_icp_step": (ctypes.c_int, [_P(Keyframe), _P(Sweep), _vp, _P(IcpParams), _vp, _vp, ctypes.c_size_t, _vp]),
     "upslam_icp": (ctypes.c_int, [_P(Keyframe), _P(Sweep), _vp, _P(IcpParams), _vp, _vp, ctypes.c_size_t, _vp]),
     "upslam_fuse": (ctypes.c_int, [_P(Keyframe), _P(Sweep), _vp, _P(FuseParams), _vp, _vp, _vp]),
+    "upslam_icp_noalloc_capacity_bytes": (ctypes.c_size_t, []),
+    "upslam_icp_noalloc": (ctypes.c_int, [_P(Keyframe), _P(Sweep), _vp, _P(IcpParams), _vp, _vp]),
     "upslam_predict_pose": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "upslam_update_motion": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "upslam_status_string": (ctypes.c_char_p, [ctypes.c_int]),

@@ -10,6 +10,7 @@ extern "C" const char *upslam_status_string(upslam_status s) {
         case UPSLAM_ERR_NOT_CONVERGED: return "not converged";
         case UPSLAM_ERR_TIMEOUT: return "device-side wait timed out";
         case UPSLAM_ERR_UNSUPPORTED: return "unsupported on this device";
+        case UPSLAM_ERR_CAPACITY: return "request exceeds the fixed scratch capacity";
     }
     return "unknown status";
 }

@@ -23,6 +23,8 @@
 // Roofline: per step the keyframe is streamed once (4 B depth + 16 B or 8 B
 // normal/weight per pixel) and each correspondence gathers 32 B (16 B in FP16)
 // of sweep data that stays resident in L2.
+#include <mutex>
+
 #include "common.cuh"
 
 namespace upslam {
@@ -404,6 +406,87 @@ extern "C" upslam_status upslam_icp(const upslam_keyframe *kf, const upslam_swee
     if (grid > max_ctas()) grid = max_ctas();
     IcpCtrl *ctrl = reinterpret_cast<IcpCtrl *>(d_ws);
     float *partials = reinterpret_cast<float *>(reinterpret_cast<char *>(d_ws) + kCtrlBytes);
+    upslam_icp_params ipc = *ip;
+    void *args[] = {&a, &d_pose12, &ipc, &d_stats, &ctrl, &partials};
+    if (cudaLaunchCooperativeKernel((const void *)icp_persistent_kernel, dim3(grid), dim3(kIcpThreads), args, 0,
+                                    (cudaStream_t)stream) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return UPSLAM_ERR_CUDA;
+    }
+    return UPSLAM_OK;
+}
+
+// ----------------------------------------------------------------------------- allocation-free variant
+//
+// upslam_icp_noalloc runs the same persistent kernel as upslam_icp, but its
+// workspace is this file-scope device array instead of caller memory.  The
+// array is part of the library image: every GPU that loads the library holds
+// it until the process exits.  Host code must not hand the symbol itself to a
+// kernel (on the host it only names a stand-in); the device address is looked
+// up once per device with cudaGetSymbolAddress.
+
+namespace upslam {
+
+constexpr int kNoAllocMaxCtas = 2048;
+constexpr size_t kNoAllocBytes = kCtrlBytes + (size_t)kNoAllocMaxCtas * kSlots * sizeof(float);  // 512.25 KiB
+
+static __device__ __align__(256) unsigned char g_icp_noalloc_ws[kNoAllocBytes];
+
+static std::mutex g_noalloc_mutex;
+static void *g_noalloc_addr[64] = {nullptr};
+
+// Device address of the scratch array on the current device (looked up on first use).
+static upslam_status noalloc_scratch(void **out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        (void)cudaGetLastError();
+        return UPSLAM_ERR_CUDA;
+    }
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_icp_noalloc_ws) != cudaSuccess || !p) {
+            (void)cudaGetLastError();
+            return UPSLAM_ERR_CUDA;
+        }
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return UPSLAM_OK;
+}
+
+}  // namespace upslam
+
+extern "C" size_t upslam_icp_noalloc_capacity_bytes(void) { return kNoAllocBytes; }
+
+extern "C" upslam_status upslam_icp_noalloc(const upslam_keyframe *kf, const upslam_sweep *sw, double *d_pose12,
+                                            const upslam_icp_params *ip, upslam_icp_stats *d_stats, void *stream) {
+    if (!views_ok(kf, sw) || !d_pose12 || !ip || !d_stats) return UPSLAM_ERR_INVALID_ARG;
+    if (!(ip->d_max > 0.0f) || ip->max_iters < 0 || ip->min_inliers < 0) return UPSLAM_ERR_INVALID_ARG;
+    if (ip->max_iters == 0) return UPSLAM_OK;
+    int dev = 0, coop = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    if (!coop) return UPSLAM_ERR_UNSUPPORTED;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, icp_persistent_kernel, kIcpThreads, 0) != cudaSuccess ||
+        per_sm < 1)
+        return UPSLAM_ERR_UNSUPPORTED;
+    if (per_sm > 4) per_sm = 4;
+    int grid = upslam_sm_count() * per_sm;
+    if (grid > max_ctas()) grid = max_ctas();
+    // the scratch a launch of this grid needs must fit the fixed array
+    if (kCtrlBytes + (size_t)grid * kSlots * sizeof(float) > kNoAllocBytes) return UPSLAM_ERR_CAPACITY;
+    void *ws = nullptr;
+    const upslam_status st = noalloc_scratch(&ws);
+    if (st != UPSLAM_OK) return st;
+    // the barrier counters must start at zero; the per-CTA sums are written before they are read
+    if (cudaMemsetAsync(ws, 0, kCtrlBytes, (cudaStream_t)stream) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return UPSLAM_ERR_CUDA;
+    }
+    IcpArgs a = make_args(kf, sw, ip);
+    IcpCtrl *ctrl = reinterpret_cast<IcpCtrl *>(ws);
+    float *partials = reinterpret_cast<float *>(reinterpret_cast<char *>(ws) + kCtrlBytes);
     upslam_icp_params ipc = *ip;
     void *args[] = {&a, &d_pose12, &ipc, &d_stats, &ctrl, &partials};
     if (cudaLaunchCooperativeKernel((const void *)icp_persistent_kernel, dim3(grid), dim3(kIcpThreads), args, 0,
