@@ -154,8 +154,11 @@ class Cudart:
         assert self.lib.cudaEventCreate(ctypes.byref(ev)) == 0
         return ev
 
-    def record(self, ev, stream, external=True):
-        rc = self.lib.cudaEventRecordWithFlags(ev, ctypes.c_void_p(stream), 1 if external else 0)
+    # events become graph nodes only while a stream is being captured; eager launches record plainly
+    external = True
+
+    def record(self, ev, stream):
+        rc = self.lib.cudaEventRecordWithFlags(ev, ctypes.c_void_p(stream), 1 if self.external else 0)
         assert rc == 0, rc
 
     def elapsed(self, a, b) -> float:
@@ -306,6 +309,7 @@ def run_ours(args, ws, rank, local):
                 log(f"[bench] graph capture failed ({e}); launching eagerly")
                 torch.cuda.synchronize()
                 launches[0] = 0
+        cr.external = used_graph
         sampler = ClockSampler(local)
         sampler.start()
         if dist:

@@ -50,39 +50,52 @@ __global__ void __launch_bounds__(256) fuse_main_kernel(FuseArgs a, const double
     if (!accepted(st, a.accept)) return;
     const PoseF T = pose_to_f32(pose);
     if ((int)blockIdx.x < gk) {
+        // averaging: each thread takes 4 pixels a CTA-width apart, issuing their keyframe loads together
+        constexpr int kB = 4;
         const int npx = a.kp.rows * a.kp.cols;
         const int W = a.kp.cols;
-        for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < npx; k += gk * blockDim.x) {
-            const float4 n = load_nw(a.knw, k, a.kprec);
-            const float w = n.w;
-            if (!(w > 0.0f)) continue;
-            const float d = a.kdepth[k];
-            const int v = k / W, u = k - v * W;
-            const float3 s = pixel_point(a.kdirs, a.kp.rows, v, u, d);
-            const float3 q = xform_inv(T, s.x, s.y, s.z);
-            int jv, ju;
-            float rr;
-            if (!bin_point(q.x, q.y, q.z, a.sp, jv, ju, rr)) continue;
-            const int j = jv * a.sp.cols + ju;
-            const float4 P = __ldg(a.spix + j);
-            if (P.w == 0.0f) continue;
-            const float4 m = load_nw(a.snrm, j, a.sprec);
-            if (m.w == 0.0f) continue;
-            const float *r = T.r;
-            const float px = fmaf(r[0], P.x, fmaf(r[1], P.y, fmaf(r[2], P.z, r[3])));
-            const float py = fmaf(r[4], P.x, fmaf(r[5], P.y, fmaf(r[6], P.z, r[7])));
-            const float pz = fmaf(r[8], P.x, fmaf(r[9], P.y, fmaf(r[10], P.z, r[11])));
-            const float ex = px - s.x, ey = py - s.y, ez = pz - s.z;
-            if (!(ex * ex + ey * ey + ez * ez <= a.d_max2)) continue;
-            const float3 Rm = rotate(T, m.x, m.y, m.z);
-            if (!(Rm.x * n.x + Rm.y * n.y + Rm.z * n.z >= a.cos_min)) continue;
-            const float dm = sqrtf(px * px + py * py + pz * pz);
-            const float inv = 1.0f / (w + 1.0f);
-            a.kdepth[k] = (w * d + dm) * inv;
-            float nx = w * n.x + Rm.x, ny = w * n.y + Rm.y, nz = w * n.z + Rm.z;
-            const float l = 1.0f / sqrtf(nx * nx + ny * ny + nz * nz);
-            const float wn = w + 1.0f < a.w_max ? w + 1.0f : a.w_max;
-            store_nw(a.knw, k, a.kprec, make_float4(nx * l, ny * l, nz * l, wn));
+        const int stride = gk * blockDim.x * kB;
+        for (int base = blockIdx.x * blockDim.x * kB + threadIdx.x; base < npx; base += stride) {
+            float4 n[kB];
+            float d[kB];
+#pragma unroll
+            for (int b = 0; b < kB; ++b) {
+                const int k = base + b * blockDim.x;
+                n[b] = k < npx ? load_nw(a.knw, k, a.kprec) : make_float4(0.f, 0.f, 0.f, 0.f);
+                d[b] = k < npx ? __ldg(a.kdepth + k) : 0.0f;
+            }
+#pragma unroll
+            for (int b = 0; b < kB; ++b) {
+                const int k = base + b * blockDim.x;
+                const float w = n[b].w;
+                if (!(w > 0.0f)) continue;
+                const int v = k / W, u = k - v * W;
+                const float3 s = pixel_point(a.kdirs, a.kp.rows, v, u, d[b]);
+                const float3 q = xform_inv(T, s.x, s.y, s.z);
+                int jv, ju;
+                float rr;
+                if (!bin_point(q.x, q.y, q.z, a.sp, jv, ju, rr)) continue;
+                const int j = jv * a.sp.cols + ju;
+                const float4 P = __ldg(a.spix + j);
+                const float4 m = load_nw(a.snrm, j, a.sprec);
+                if (P.w == 0.0f || m.w == 0.0f) continue;
+                const float *r = T.r;
+                const float px = fmaf(r[0], P.x, fmaf(r[1], P.y, fmaf(r[2], P.z, r[3])));
+                const float py = fmaf(r[4], P.x, fmaf(r[5], P.y, fmaf(r[6], P.z, r[7])));
+                const float pz = fmaf(r[8], P.x, fmaf(r[9], P.y, fmaf(r[10], P.z, r[11])));
+                const float ex = px - s.x, ey = py - s.y, ez = pz - s.z;
+                if (!(ex * ex + ey * ey + ez * ez <= a.d_max2)) continue;
+                const float3 Rm = rotate(T, m.x, m.y, m.z);
+                const float4 nk = n[b];
+                if (!(Rm.x * nk.x + Rm.y * nk.y + Rm.z * nk.z >= a.cos_min)) continue;
+                const float dm = sqrtf(px * px + py * py + pz * pz);
+                const float inv = 1.0f / (w + 1.0f);
+                a.kdepth[k] = (w * d[b] + dm) * inv;
+                const float nx = w * nk.x + Rm.x, ny = w * nk.y + Rm.y, nz = w * nk.z + Rm.z;
+                const float l = rsqrtf(nx * nx + ny * ny + nz * nz);
+                const float wn = w + 1.0f < a.w_max ? w + 1.0f : a.w_max;
+                store_nw(a.knw, k, a.kprec, make_float4(nx * l, ny * l, nz * l, wn));
+            }
         }
     } else {
         const int ns = a.sp.rows * a.sp.cols;
@@ -165,7 +178,7 @@ extern "C" upslam_status upslam_fuse(const upslam_keyframe *kf, const upslam_swe
     unsigned long long *zb = reinterpret_cast<unsigned long long *>(d_zbuf_kf);
     const int64_t npx = (int64_t)kf->pano.rows * kf->pano.cols;
     const int64_t ns = (int64_t)sw->pano.rows * sw->pano.cols;
-    const int gk = upslam_grid(npx, 256, 8);
+    const int gk = upslam_grid((npx + 3) / 4, 256, 8);
     const int gs = upslam_grid(ns, 256, 2);
     fuse_main_kernel<<<gk + gs, 256, 0, s>>>(a, d_pose12, d_stats, zb, gk);
     UPSLAM_CHECK_LAUNCH();

@@ -52,10 +52,11 @@ struct IcpArgs {
 };
 
 struct IcpCtrl {
-    unsigned int arrive;  // CTAs arrived at the current barrier
-    unsigned int gen;     // barrier generation (monotonic across launches)
-    unsigned int ticket;  // single-step "last CTA" ticket
-    int valid;            // sweep pixels with a point (persistent form, step 0)
+    unsigned int arrive;               // unused by the current kernels (kept zero)
+    unsigned int gen;                  // unused by the current kernels (kept zero)
+    unsigned int ticket;               // single-step "last CTA" ticket
+    int valid;                         // unused by the current kernels (kept zero)
+    unsigned long long arrive64;       // persistent form: CTA arrivals, monotonic across launches
 };
 
 __device__ __forceinline__ void accumulate_pixel(const IcpArgs &a, const PoseF &T, int k, float acc[28], int &inl) {
@@ -252,74 +253,426 @@ __global__ void __launch_bounds__(kIcpThreads) icp_step_kernel(IcpArgs a, double
     }
 }
 
-__global__ void __launch_bounds__(kIcpThreads) icp_persistent_kernel(IcpArgs a, double *pose, upslam_icp_params ip,
-                                                                     upslam_icp_stats *st, IcpCtrl *ctrl,
-                                                                     float *partials) {
-    __shared__ float sh[kIcpWarps][32];
-    __shared__ int shi[kIcpWarps][2];
+// ----------------------------------------------------------------------------- tiled persistent form
+//
+// One CTA of 512 threads per SM.  The keyframe is cut into chunks of 512
+// pixels dealt round-robin to the CTAs (samples only occupy the rows the sensor
+// sees, so contiguous slices would leave most CTAs idle).  Before the first
+// step each CTA streams its chunks once from HBM and stages every pixel that
+// holds a sample (depth > 0, unit normal) into shared memory as its FP32 point
+// s = d * dir and normal n, compacted in pixel order (a block-wide ballot
+// prefix, so the order and therefore the sums are deterministic).  Every
+// Gauss-Newton step then reads the staged points from shared memory and gathers
+// only the sweep pixel each one lands in.  Chunks beyond the shared-memory
+// capacity are read from global memory each step.
+
+constexpr int kTileThreads = 512;
+constexpr int kTileWarps = kTileThreads / 32;
+
+// One staged correspondence, branch-free: a rejected pair contributes zeros.
+__device__ __forceinline__ void accumulate_entry(const IcpArgs &a, const PoseF &T, float3 s, float3 n, float acc[28],
+                                                 int &inl) {
+    const float3 q = xform_inv(T, s.x, s.y, s.z);
+    int jv = 0, ju = 0;
+    float rr;
+    bool ok = bin_point(q.x, q.y, q.z, a.sp, jv, ju, rr);
+    const int j = ok ? jv * a.sp.cols + ju : 0;
+    const float4 P = __ldg(a.spix + j);
+    const float4 m = load_nw(a.snrm, j, a.sprec);
+    ok = ok && P.w != 0.0f && m.w != 0.0f;
+    const float *r = T.r;
+    const float px = fmaf(r[0], P.x, fmaf(r[1], P.y, fmaf(r[2], P.z, r[3])));
+    const float py = fmaf(r[4], P.x, fmaf(r[5], P.y, fmaf(r[6], P.z, r[7])));
+    const float pz = fmaf(r[8], P.x, fmaf(r[9], P.y, fmaf(r[10], P.z, r[11])));
+    const float3 Rm = rotate(T, m.x, m.y, m.z);
+    const float ex = px - s.x, ey = py - s.y, ez = pz - s.z;
+    ok = ok && (ex * ex + ey * ey + ez * ez <= a.d_max2) && (Rm.x * n.x + Rm.y * n.y + Rm.z * n.z >= a.cos_min);
+    const float w = ok ? 1.0f : 0.0f;
+    const float res = (ex * n.x + ey * n.y + ez * n.z) * w;
+    float J[6];
+    J[0] = (py * n.z - pz * n.y) * w;
+    J[1] = (pz * n.x - px * n.z) * w;
+    J[2] = (px * n.y - py * n.x) * w;
+    J[3] = n.x * w;
+    J[4] = n.y * w;
+    J[5] = n.z * w;
+    int p = 0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int c = i; c < 6; ++c) {
+            acc[p] = fmaf(J[i], J[c], acc[p]);
+            ++p;
+        }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) acc[21 + i] = fmaf(J[i], res, acc[21 + i]);
+    acc[27] = fmaf(res, res, acc[27]);
+    inl += ok ? 1 : 0;
+}
+
+// CTA partial record (64 words): sums [0, 28), inliers [28], valid [29], compensations [32, 60).
+__device__ __forceinline__ void tile_partial(float acc[28], int inl, int valid, float *partial, float (*sh)[32],
+                                             int (*shi)[2]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < 28; ++i) {
+        const float v = warp_sum(acc[i]);
+        if (lane == 0) sh[warp][i] = v;
+    }
+    const int si = __reduce_add_sync(0xffffffffu, inl);
+    const int sv = __reduce_add_sync(0xffffffffu, valid);
+    if (lane == 0) {
+        shi[warp][0] = si;
+        shi[warp][1] = sv;
+    }
+    __syncthreads();
+    if (threadIdx.x < 28) {
+        float t = 0.0f, c = 0.0f;
+#pragma unroll
+        for (int w = 0; w < kTileWarps; ++w) kadd(t, c, sh[w][threadIdx.x]);
+        partial[threadIdx.x] = t;
+        partial[32 + threadIdx.x] = c;
+    } else if (threadIdx.x < 30) {
+        int t = 0;
+#pragma unroll
+        for (int w = 0; w < kTileWarps; ++w) t += shi[w][threadIdx.x - 28];
+        partial[threadIdx.x] = __int_as_float(t);
+    }
+}
+
+// Lane of the upper-triangle element (i, k), i <= k, in row-major order (0..20).
+__device__ __forceinline__ int uidx(int i, int k) { return i * 6 - (i * (i - 1)) / 2 + (k - i); }
+
+// FP64 solve of A xi = -b by the square-root-free Cholesky factorisation
+// A = L D L^T, spread over the lanes of one warp: lanes 0..20 hold the upper
+// triangle of A (lane uidx(i, k)), lanes 21..26 the right-hand side.  Each
+// elimination step is a handful of warp-wide FP64 instructions (GB300 issues
+// FP64 at a low rate per instruction, so independent work goes across lanes,
+// not into more instructions).  Every lane returns the same xi.  False when a
+// pivot D_j <= pivot_eps * max diagonal.
+__device__ __forceinline__ bool warp_solve6(const double *tot, double pivot_eps, double xi[6]) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const bool is_u = lane < 21, is_y = lane >= 21 && lane < 27;
+    int li = -1, lk = -1;
+    if (is_u) {
+        int i = 0, rem = lane;
+        while (rem >= 6 - i) {
+            rem -= 6 - i;
+            ++i;
+        }
+        li = i;
+        lk = i + rem;
+    } else if (is_y) {
+        li = lane - 21;
+        lk = 6;
+    }
+    double u = is_u ? tot[lane] : (is_y ? -tot[lane] : 0.0);
+    double dmax = tot[0];
+#pragma unroll
+    for (int i = 1; i < 6; ++i) dmax = fmax(dmax, tot[uidx(i, i)]);
+    if (!(dmax > 0.0)) return false;
+    const double lim = pivot_eps * dmax;
+    double r[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        const double d = __shfl_sync(full, u, uidx(j, j));
+        if (!(d > lim) || !(d > 1e-300)) return false;
+        r[j] = rcp64(d);
+        const bool act = li > j;
+        const int src_l = act ? uidx(j, li) : lane;
+        const int src_k = act ? (is_u ? uidx(j, lk) : 21 + j) : lane;
+        const double ujl = __shfl_sync(full, u, src_l);
+        const double ujk = __shfl_sync(full, u, src_k);
+        if (act) u = fma(-(ujl * r[j]), ujk, u);
+    }
+#pragma unroll
+    for (int i = 5; i >= 0; --i) {
+        const double x = __shfl_sync(full, u, 21 + i) * r[i];
+        xi[i] = x;
+        const bool act = is_y && li < i;
+        const double umi = __shfl_sync(full, u, act ? uidx(li, i) : lane);
+        if (act) u = fma(-umi, x, u);
+    }
+    return true;
+}
+
+// T <- exp(xi^) T on one warp: lanes 0..2 evaluate the coefficients A, B, C;
+// lanes 0..8 the rotation R = I + A W + B W^2 and lanes 9..17 V = I + B W + C W^2
+// (one matrix entry each); lanes 0..11 then each compose one entry of [R T | R t + V v].
+// T lives in shared memory (12 doubles) and is updated in place; xi is the same in every lane.
+__device__ __forceinline__ void warp_se3_update(const double xi[6], double *T) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const double w0 = xi[0], w1 = xi[1], w2 = xi[2];
+    const double th2 = fma(w0, w0, fma(w1, w1, w2 * w2));
+    double coef;
+    if (th2 <= 0.0625) {
+        // Taylor series in th2 of sin(t)/t, (1 - cos t)/t^2, (t - sin t)/t^3, one per lane
+        const int c = lane < 3 ? lane : 0;
+        const double k0 = c == 0 ? 1.0 : (c == 1 ? 0.5 : 1.0 / 6.0);
+        const double k1 = c == 0 ? -1.0 / 6.0 : (c == 1 ? -1.0 / 24.0 : -1.0 / 120.0);
+        const double k2 = c == 0 ? 1.0 / 120.0 : (c == 1 ? 1.0 / 720.0 : 1.0 / 5040.0);
+        const double k3 = c == 0 ? -1.0 / 5040.0 : (c == 1 ? -1.0 / 40320.0 : -1.0 / 362880.0);
+        const double k4 = c == 0 ? 1.0 / 362880.0 : (c == 1 ? 1.0 / 3628800.0 : 1.0 / 39916800.0);
+        const double k5 = c == 0 ? -1.0 / 39916800.0 : (c == 1 ? -1.0 / 479001600.0 : -1.0 / 6227020800.0);
+        const double k6 = c == 0 ? 1.0 / 6227020800.0 : (c == 1 ? 1.0 / 87178291200.0 : 1.0 / 1307674368000.0);
+        coef = fma(th2, fma(th2, fma(th2, fma(th2, fma(th2, fma(th2, k6, k5), k4), k3), k2), k1), k0);
+    } else {
+        double A, B, C;
+        se3_coeffs(th2, A, B, C);
+        coef = lane == 0 ? A : (lane == 1 ? B : C);
+    }
+    const double A = __shfl_sync(full, coef, 0), B = __shfl_sync(full, coef, 1), C = __shfl_sync(full, coef, 2);
+    // one entry of R (lanes 0..8) or V (lanes 9..17)
+    const int e = lane < 9 ? lane : (lane < 18 ? lane - 9 : 0);
+    const int ei = e / 3, ek = e - 3 * (e / 3);
+    const double om_i = ei == 0 ? w0 : (ei == 1 ? w1 : w2);
+    const double om_k = ek == 0 ? w0 : (ek == 1 ? w1 : w2);
+    // W = [omega]_x: W[i][k] = -eps_ikl omega_l
+    double Wik = 0.0;
+    if (ei == 0 && ek == 1) Wik = -w2;
+    if (ei == 0 && ek == 2) Wik = w1;
+    if (ei == 1 && ek == 0) Wik = w2;
+    if (ei == 1 && ek == 2) Wik = -w0;
+    if (ei == 2 && ek == 0) Wik = -w1;
+    if (ei == 2 && ek == 1) Wik = w0;
+    const double delta = ei == ek ? 1.0 : 0.0;
+    const double W2 = fma(om_i, om_k, -delta * th2);
+    const double c1 = lane < 9 ? A : B, c2 = lane < 9 ? B : C;
+    const double ent = fma(c1, Wik, fma(c2, W2, delta));
+    // compose: lane e < 12 owns output (i, j), i = e / 4, j = e % 4
+    const int oi = lane < 12 ? lane / 4 : 0, oj = lane < 12 ? lane % 4 : 0;
+    const double R0 = __shfl_sync(full, ent, 3 * oi), R1 = __shfl_sync(full, ent, 3 * oi + 1),
+                 R2 = __shfl_sync(full, ent, 3 * oi + 2);
+    const double V0 = __shfl_sync(full, ent, 9 + 3 * oi), V1 = __shfl_sync(full, ent, 9 + 3 * oi + 1),
+                 V2 = __shfl_sync(full, ent, 9 + 3 * oi + 2);
+    const double te = oj == 3 ? fma(V0, xi[3], fma(V1, xi[4], V2 * xi[5])) : 0.0;
+    const double T0 = T[oj], T1 = T[4 + oj], T2 = T[8 + oj];
+    const double out = fma(R0, T0, fma(R1, T1, fma(R2, T2, te)));
+    __syncwarp();
+    if (lane < 12) T[lane] = out;
+    __syncwarp();
+}
+
+// Sum every CTA record of one step (compensated FP32, a fixed order, so every
+// CTA obtains bit-identical totals) into tot[0..29] (FP64).
+__device__ __forceinline__ void sum_records(const float *rec, int nrec, float (*sh)[32], float (*shc)[32],
+                                            int (*shn)[32], double *tot) {
+    const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+    float s = 0.0f, c = 0.0f;
+    int n = 0;
+    constexpr int kBatch = 10;
+    for (int b0 = g; b0 < nrec; b0 += kTileWarps * kBatch) {
+        float x[kBatch], y[kBatch];
+#pragma unroll
+        for (int q = 0; q < kBatch; ++q) {
+            const int b = b0 + q * kTileWarps;
+            x[q] = b < nrec ? __ldcg(rec + (size_t)b * kSlots + lane) : 0.0f;
+            y[q] = b < nrec ? __ldcg(rec + (size_t)b * kSlots + 32 + lane) : 0.0f;
+        }
+#pragma unroll
+        for (int q = 0; q < kBatch; ++q) {
+            if (lane < 28) {
+                kadd(s, c, x[q]);
+                c += y[q];
+            } else if (lane < 30) {
+                n += __float_as_int(x[q]);
+            }
+        }
+    }
+    sh[g][lane] = s;
+    shc[g][lane] = c;
+    shn[g][lane] = n;
+    __syncthreads();
+    if (threadIdx.x < 28) {
+        float t = 0.0f, cc = 0.0f;
+#pragma unroll
+        for (int q = 0; q < kTileWarps; ++q) {
+            kadd(t, cc, sh[q][threadIdx.x]);
+            cc += shc[q][threadIdx.x];
+        }
+        tot[threadIdx.x] = (double)t + (double)cc;
+    } else if (threadIdx.x < 30) {
+        long long t = 0;
+#pragma unroll
+        for (int q = 0; q < kTileWarps; ++q) t += shn[q][threadIdx.x];
+        tot[threadIdx.x] = (double)t;
+    }
+    __syncthreads();
+}
+
+// The tiled persistent kernel.  Each step: accumulate the CTA's staged (and
+// spilled) correspondences, publish the CTA record (double-buffered by step
+// parity), arrive at a grid barrier (a monotonic 64-bit arrival counter), then
+// every CTA sums all records and solves redundantly: identical arithmetic on
+// identical data gives every CTA the same pose, so no CTA waits for another
+// to broadcast it.  CTA 0 writes the pose and the record at the end.
+__global__ void __launch_bounds__(kTileThreads, 1)
+    icp_tile_kernel(IcpArgs a, double *pose, upslam_icp_params ip, upslam_icp_stats *st, IcpCtrl *ctrl,
+                    float *partials, int cap) {
+    extern __shared__ float stage[];
+    float *sx = stage, *sy = stage + cap, *sz = stage + 2 * cap;
+    float *snx = stage + 3 * cap, *sny = stage + 4 * cap, *snz = stage + 5 * cap;
+    __shared__ float sh[kTileWarps][32];
+    __shared__ float shc[kTileWarps][32];
+    __shared__ int shn[kTileWarps][32];
+    __shared__ int shi[kTileWarps][2];
     __shared__ double tot[32];
-    __shared__ float pose_s[12];
-    __shared__ int flag;  // 1 = last arriver, 2 = stop, 3 = timeout
+    __shared__ double Tsh[12];
+    __shared__ double xi_sh[6];
+    __shared__ int wcnt[kTileWarps];
+    __shared__ int base_s, spill_s, flag, status_s, conv_s, valid_s;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int npx = a.kp.rows * a.kp.cols;
-    unsigned int my_gen = 0;
-    if (threadIdx.x == 0) my_gen = *((volatile unsigned int *)&ctrl->gen);
-    for (int it = 0; it < ip.max_iters; ++it) {
-        if (threadIdx.x < 12) pose_s[threadIdx.x] = (float)__ldcg(pose + threadIdx.x);
+    const int nchunks = (npx + kTileThreads - 1) / kTileThreads;
+    const int W = a.kp.cols;
+    const unsigned long long G = gridDim.x;
+    unsigned long long base = 0;
+    if (threadIdx.x == 0) base = (*((volatile unsigned long long *)&ctrl->arrive64) / G) * G;
+    if (threadIdx.x < 12) Tsh[threadIdx.x] = __ldcg(pose + threadIdx.x);
+
+    // ---- stage the CTA's chunks into shared memory (once per launch).  Chunks of
+    // 512 pixels are dealt round-robin (chunk q goes to CTA q mod gridDim), so every
+    // CTA gets an even share of the rows that hold samples.  A chunk that no longer
+    // fits is left, with every later chunk of this CTA, to the global-memory path.
+    if (threadIdx.x == 0) {
+        base_s = 0;
+        spill_s = nchunks;
+    }
+    __syncthreads();
+    for (int q = blockIdx.x; q < nchunks; q += gridDim.x) {
+        const int k = q * kTileThreads + threadIdx.x;
+        bool ok = false;
+        float3 s = make_float3(0.f, 0.f, 0.f), n = make_float3(0.f, 0.f, 0.f);
+        if (k < npx) {
+            const float d = __ldg(a.kdepth + k);
+            const float4 n4 = load_nw(a.knw, k, a.kprec);
+            if (d > 0.0f &&
+                __fadd_rn(__fadd_rn(__fmul_rn(n4.x, n4.x), __fmul_rn(n4.y, n4.y)), __fmul_rn(n4.z, n4.z)) > 0.25f) {
+                ok = true;
+                const int v = k / W;
+                s = pixel_point(a.kdirs, a.kp.rows, v, k - v * W, d);
+                n = make_float3(n4.x, n4.y, n4.z);
+            }
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, ok);
+        if (lane == 0) wcnt[warp] = __popc(bal);
         __syncthreads();
+        int off = base_s, total = base_s;
+        for (int w = 0; w < kTileWarps; ++w) {
+            const int c = wcnt[w];
+            off += w < warp ? c : 0;
+            total += c;
+        }
+        if (total > cap) {  // this chunk does not fit: it and the CTA's later chunks stay in global memory
+            if (threadIdx.x == 0) spill_s = q;
+            __syncthreads();
+            break;
+        }
+        const int slot = off + __popc(bal & ((1u << lane) - 1u));
+        if (ok) {
+            sx[slot] = s.x;
+            sy[slot] = s.y;
+            sz[slot] = s.z;
+            snx[slot] = n.x;
+            sny[slot] = n.y;
+            snz[slot] = n.z;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) base_s = total;
+        __syncthreads();
+    }
+    const int staged = base_s;
+    const int spill_q = spill_s;
+
+    int it = 0;
+    for (; it < ip.max_iters; ++it) {
         PoseF T;
 #pragma unroll
-        for (int i = 0; i < 12; ++i) T.r[i] = pose_s[i];
+        for (int i = 0; i < 12; ++i) T.r[i] = (float)Tsh[i];
         float acc[28];
 #pragma unroll
         for (int i = 0; i < 28; ++i) acc[i] = 0.0f;
         int inl = 0;
-        for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < npx; k += gridDim.x * blockDim.x)
-            accumulate_pixel(a, T, k, acc, inl);
+#pragma unroll 2
+        for (int e = threadIdx.x; e < staged; e += kTileThreads)
+            accumulate_entry(a, T, make_float3(sx[e], sy[e], sz[e]), make_float3(snx[e], sny[e], snz[e]), acc, inl);
+        for (int q = spill_q; q < nchunks; q += gridDim.x) {
+            const int k = q * kTileThreads + threadIdx.x;
+            if (k < npx) accumulate_pixel(a, T, k, acc, inl);
+        }
         const int valid = it == 0 ? count_valid(a) : 0;
-        cta_partial(acc, inl, valid, partials + (size_t)blockIdx.x * kSlots, sh, shi);
+        float *rec = partials + (size_t)(it & 1) * gridDim.x * kSlots;
+        tile_partial(acc, inl, valid, rec + (size_t)blockIdx.x * kSlots, sh, shi);
         __syncthreads();
         if (threadIdx.x == 0) {
             __threadfence();
-            flag = atomicAdd(&ctrl->arrive, 1u) == gridDim.x - 1 ? 1 : 0;
-        }
-        __syncthreads();
-        if (flag == 1) {
-            __threadfence();
-            // the valid count is summed at step 0 and kept for the later steps
-            finalize(partials, gridDim.x, pose, ip, st, it == 0 ? -1 : __ldcg(&ctrl->valid), it, sh, shi, tot);
-            if (threadIdx.x == 0) {
-                if (it == 0) ctrl->valid = (int)st->valid;
-                __threadfence();
-                ctrl->arrive = 0;
-                __threadfence();
-                atomicAdd(&ctrl->gen, 1u);
-            }
-        } else if (threadIdx.x == 0) {
+            atomicAdd(&ctrl->arrive64, 1ull);
+            const unsigned long long target = base + G * (unsigned long long)(it + 1);
             const long long t0 = clock64();
-            int timed_out = 0;
-            while (*((volatile unsigned int *)&ctrl->gen) == my_gen) {
+            flag = 0;
+            while (*((volatile unsigned long long *)&ctrl->arrive64) < target) {
                 if (clock64() - t0 > kWaitCycles) {
-                    timed_out = 1;
+                    flag = 3;
+                    st->status = UPSLAM_ERR_TIMEOUT;
                     break;
                 }
-                __nanosleep(64);
-            }
-            if (timed_out) {
-                st->status = UPSLAM_ERR_TIMEOUT;
-                flag = 3;
+                __nanosleep(20);
             }
             __threadfence();
         }
-        if (threadIdx.x == 0) ++my_gen;
         __syncthreads();
         if (flag == 3) return;
-        if (threadIdx.x == 0) {
-            const int status = *((volatile int *)&st->status);
-            const int conv = *((volatile int *)&st->converged);
-            flag = (status != UPSLAM_OK || conv) ? 2 : 0;
+        sum_records(rec, gridDim.x, sh, shc, shn, tot);
+        if (warp == 0) {
+            const long long inliers = (long long)tot[28];
+            double xi[6] = {0, 0, 0, 0, 0, 0};
+            int status = UPSLAM_OK, conv = 0;
+            if (inliers < ip.min_inliers) {
+                status = UPSLAM_ERR_DEGENERATE;
+            } else {
+                if (!warp_solve6(tot, ip.pivot_eps, xi)) {
+                    status = UPSLAM_ERR_DEGENERATE;
+#pragma unroll
+                    for (int i = 0; i < 6; ++i) xi[i] = 0.0;
+                } else {
+                    warp_se3_update(xi, Tsh);
+                    const double wn2 = fma(xi[0], xi[0], fma(xi[1], xi[1], xi[2] * xi[2]));
+                    const double vn2 = fma(xi[3], xi[3], fma(xi[4], xi[4], xi[5] * xi[5]));
+                    conv = (wn2 < ip.eps_rot * ip.eps_rot && vn2 < ip.eps_trans * ip.eps_trans) ? 1 : 0;
+                }
+            }
+            if (lane == 0) {
+                status_s = status;
+                conv_s = conv;
+                if (it == 0) valid_s = (int)tot[29];
+#pragma unroll
+                for (int i = 0; i < 6; ++i) xi_sh[i] = xi[i];
+            }
         }
         __syncthreads();
-        if (flag == 2) return;
+        if (status_s != UPSLAM_OK || conv_s) {
+            ++it;
+            break;
+        }
+    }
+    // CTA 0 publishes the pose and the record of the last linearisation
+    if (blockIdx.x == 0) {
+        if (threadIdx.x < 12) pose[threadIdx.x] = Tsh[threadIdx.x];
+        if (threadIdx.x < 21) st->A[threadIdx.x] = tot[threadIdx.x];
+        else if (threadIdx.x < 27) st->b[threadIdx.x - 21] = tot[threadIdx.x];
+        else if (threadIdx.x == 27) st->sse = tot[27];
+        else if (threadIdx.x == 28) st->inliers = (long long)tot[28];
+        else if (threadIdx.x == 29) st->valid = valid_s;
+        else if (threadIdx.x == 30) {
+            st->status = status_s;
+            st->converged = conv_s;
+            st->iters = it;
+            st->accepted = 0;
+        } else if (threadIdx.x >= 32 && threadIdx.x < 38) {
+            st->xi[threadIdx.x - 32] = xi_sh[threadIdx.x - 32];
+        }
     }
 }
 
@@ -354,13 +707,63 @@ static bool views_ok(const upslam_keyframe *kf, const upslam_sweep *sw) {
 
 static int max_ctas() { return upslam_sm_count() * 8; }
 
+
+// Launch the tiled persistent kernel: one CTA per SM, the keyframe slice staged
+// in as much dynamic shared memory as the slice needs (up to the opt-in limit).
+static upslam_status launch_tile(const IcpArgs &a, double *pose, const upslam_icp_params *ip, upslam_icp_stats *st,
+                                 void *ws, size_t ws_bytes, cudaStream_t stream) {
+    int dev = 0, coop = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return UPSLAM_ERR_CUDA;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (!coop) return UPSLAM_ERR_UNSUPPORTED;
+    static bool attr_set[64] = {false};
+    static size_t static_smem[64] = {0};
+    if (dev < 0 || dev >= 64) return UPSLAM_ERR_UNSUPPORTED;
+    const size_t reserve = 1024;
+    if (!attr_set[dev]) {
+        cudaFuncAttributes fa;
+        if (cudaFuncGetAttributes(&fa, icp_tile_kernel) != cudaSuccess) return UPSLAM_ERR_CUDA;
+        static_smem[dev] = fa.sharedSizeBytes;
+        const int dyn_max = optin - (int)fa.sharedSizeBytes - (int)reserve;
+        if (dyn_max <= 0 ||
+            cudaFuncSetAttribute(icp_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max) != cudaSuccess)
+            return UPSLAM_ERR_UNSUPPORTED;
+        attr_set[dev] = true;
+    }
+    const int grid = upslam_sm_count();
+    const int64_t npx = (int64_t)a.kp.rows * a.kp.cols;
+    const int64_t nchunks = (npx + kTileThreads - 1) / kTileThreads;
+    const int64_t per = (nchunks + grid - 1) / grid * kTileThreads;  // most pixels one CTA can stage
+    const int64_t cap_max = ((int64_t)optin - (int64_t)static_smem[dev] - (int64_t)reserve) / (6 * (int64_t)sizeof(float));
+    const int cap = (int)(per < cap_max ? (per > 0 ? per : 1) : cap_max);
+    const size_t dyn = (size_t)cap * 6 * sizeof(float);
+    if (kCtrlBytes + 2 * (size_t)grid * kSlots * sizeof(float) > ws_bytes) return UPSLAM_ERR_CAPACITY;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, icp_tile_kernel, kTileThreads, dyn) != cudaSuccess ||
+        per_sm < 1)
+        return UPSLAM_ERR_UNSUPPORTED;
+    IcpCtrl *ctrl = reinterpret_cast<IcpCtrl *>(ws);
+    float *partials = reinterpret_cast<float *>(reinterpret_cast<char *>(ws) + kCtrlBytes);
+    IcpArgs ac = a;
+    upslam_icp_params ipc = *ip;
+    int capc = cap;
+    void *args[] = {&ac, &pose, &ipc, &st, &ctrl, &partials, &capc};
+    if (cudaLaunchCooperativeKernel((const void *)icp_tile_kernel, dim3(grid), dim3(kTileThreads), args, dyn, stream) !=
+        cudaSuccess) {
+        (void)cudaGetLastError();
+        return UPSLAM_ERR_CUDA;
+    }
+    return UPSLAM_OK;
+}
+
 }  // namespace upslam
 
 using namespace upslam;
 
 extern "C" size_t upslam_icp_workspace_bytes(const upslam_keyframe *kf) {
     (void)kf;
-    return kCtrlBytes + (size_t)max_ctas() * kSlots * sizeof(float);
+    return kCtrlBytes + 2 * (size_t)max_ctas() * kSlots * sizeof(float);
 }
 
 static upslam_status icp_common_checks(const upslam_keyframe *kf, const upslam_sweep *sw, double *d_pose12,
@@ -393,27 +796,7 @@ extern "C" upslam_status upslam_icp(const upslam_keyframe *kf, const upslam_swee
     const upslam_status chk = icp_common_checks(kf, sw, d_pose12, ip, d_stats, d_ws, ws_bytes);
     if (chk != UPSLAM_OK) return chk;
     if (ip->max_iters == 0) return UPSLAM_OK;
-    IcpArgs a = make_args(kf, sw, ip);
-    int dev = 0, coop = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
-    if (!coop) return UPSLAM_ERR_UNSUPPORTED;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, icp_persistent_kernel, kIcpThreads, 0) != cudaSuccess ||
-        per_sm < 1)
-        return UPSLAM_ERR_UNSUPPORTED;
-    if (per_sm > 4) per_sm = 4;
-    int grid = upslam_sm_count() * per_sm;
-    if (grid > max_ctas()) grid = max_ctas();
-    IcpCtrl *ctrl = reinterpret_cast<IcpCtrl *>(d_ws);
-    float *partials = reinterpret_cast<float *>(reinterpret_cast<char *>(d_ws) + kCtrlBytes);
-    upslam_icp_params ipc = *ip;
-    void *args[] = {&a, &d_pose12, &ipc, &d_stats, &ctrl, &partials};
-    if (cudaLaunchCooperativeKernel((const void *)icp_persistent_kernel, dim3(grid), dim3(kIcpThreads), args, 0,
-                                    (cudaStream_t)stream) != cudaSuccess) {
-        (void)cudaGetLastError();
-        return UPSLAM_ERR_CUDA;
-    }
-    return UPSLAM_OK;
+    return launch_tile(make_args(kf, sw, ip), d_pose12, ip, d_stats, d_ws, ws_bytes, (cudaStream_t)stream);
 }
 
 // ----------------------------------------------------------------------------- allocation-free variant
@@ -464,18 +847,9 @@ extern "C" upslam_status upslam_icp_noalloc(const upslam_keyframe *kf, const ups
     if (!views_ok(kf, sw) || !d_pose12 || !ip || !d_stats) return UPSLAM_ERR_INVALID_ARG;
     if (!(ip->d_max > 0.0f) || ip->max_iters < 0 || ip->min_inliers < 0) return UPSLAM_ERR_INVALID_ARG;
     if (ip->max_iters == 0) return UPSLAM_OK;
-    int dev = 0, coop = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
-    if (!coop) return UPSLAM_ERR_UNSUPPORTED;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, icp_persistent_kernel, kIcpThreads, 0) != cudaSuccess ||
-        per_sm < 1)
-        return UPSLAM_ERR_UNSUPPORTED;
-    if (per_sm > 4) per_sm = 4;
-    int grid = upslam_sm_count() * per_sm;
-    if (grid > max_ctas()) grid = max_ctas();
-    // the scratch a launch of this grid needs must fit the fixed array
-    if (kCtrlBytes + (size_t)grid * kSlots * sizeof(float) > kNoAllocBytes) return UPSLAM_ERR_CAPACITY;
+    // the scratch a launch on this device needs (two records per SM) must fit the fixed array
+    if (kCtrlBytes + 2 * (size_t)upslam_sm_count() * kSlots * sizeof(float) > kNoAllocBytes)
+        return UPSLAM_ERR_CAPACITY;
     void *ws = nullptr;
     const upslam_status st = noalloc_scratch(&ws);
     if (st != UPSLAM_OK) return st;
@@ -484,15 +858,5 @@ extern "C" upslam_status upslam_icp_noalloc(const upslam_keyframe *kf, const ups
         (void)cudaGetLastError();
         return UPSLAM_ERR_CUDA;
     }
-    IcpArgs a = make_args(kf, sw, ip);
-    IcpCtrl *ctrl = reinterpret_cast<IcpCtrl *>(ws);
-    float *partials = reinterpret_cast<float *>(reinterpret_cast<char *>(ws) + kCtrlBytes);
-    upslam_icp_params ipc = *ip;
-    void *args[] = {&a, &d_pose12, &ipc, &d_stats, &ctrl, &partials};
-    if (cudaLaunchCooperativeKernel((const void *)icp_persistent_kernel, dim3(grid), dim3(kIcpThreads), args, 0,
-                                    (cudaStream_t)stream) != cudaSuccess) {
-        (void)cudaGetLastError();
-        return UPSLAM_ERR_CUDA;
-    }
-    return UPSLAM_OK;
+    return launch_tile(make_args(kf, sw, ip), d_pose12, ip, d_stats, ws, kNoAllocBytes, (cudaStream_t)stream);
 }
