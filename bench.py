@@ -288,8 +288,8 @@ def run_ours(args, ws, rank, local):
             cr.record(ev[i][0], st)
             step(k)
             cr.record(ev[i][1], st)
-            launches[0] += up.Tracker.LAUNCHES_PER_TRACK + (up.Tracker.LAUNCHES_PER_NEW_KEYFRAME
-                                                            if k % kf_every == 0 else 0)
+            launches[0] += trk.launches_per_track + (up.Tracker.LAUNCHES_PER_NEW_KEYFRAME
+                                                     if k % kf_every == 0 else 0)
             hist_pose[k].copy_(trk.state.pose)
             hist_stats[k].copy_(trk.state.stats)
             flush.zero_()
@@ -347,18 +347,31 @@ def run_ours(args, ws, rank, local):
 
     hbm, hbm_src = peaks()
     kf_px, sw_px = KF_ROWS * KF_COLS, seq.sweep.pixels
-    icp_bytes = kf_px * 20 + sw_px * 32
-    fuse_bytes = kf_px * 40 + sw_px * 32 * 2
     icp_avg, fuse_avg, proj_avg = (statistics.mean(icp_ms), statistics.mean(fuse_ms), statistics.mean(proj_ms))
-    kernels = {
-        "icp_persistent": {"ms_avg": icp_avg, "share": sum(icp_ms) / total_ms, "bytes": icp_bytes,
-                           "gbs": icp_bytes / (icp_avg * 1e-3) / 1e9, "iters_avg": statistics.mean(iters),
-                           "l2_bytes_per_launch": icp_bytes * statistics.mean(iters)},
-        "fuse": {"ms_avg": fuse_avg, "share": sum(fuse_ms) / total_ms, "bytes": fuse_bytes,
-                 "gbs": fuse_bytes / (fuse_avg * 1e-3) / 1e9},
-        "project_normals": {"ms_avg": proj_avg, "share": sum(proj_ms) / total_ms},
-    }
-    dom = "icp_persistent" if sum(icp_ms) >= sum(fuse_ms) else "fuse"
+    if trk.fused:
+        # one persistent launch: ICP + keyframe update; the keyframe must be read once and written
+        # once (20 B/px each way) and the sweep read once (32 B/px)
+        track_bytes = kf_px * 40 + sw_px * 32
+        kernels = {
+            "icp_tile_kernel (register + keyframe update)": {
+                "ms_avg": icp_avg, "share": sum(icp_ms) / total_ms, "bytes": track_bytes,
+                "gbs": track_bytes / (icp_avg * 1e-3) / 1e9, "iters_avg": statistics.mean(iters)},
+            "project + resolve + normals": {"ms_avg": proj_avg, "share": sum(proj_ms) / total_ms,
+                                            "bytes": sw_px * (16 + 8 + 8 + 4 + 4 + 16 + 36),
+                                            "gbs": sw_px * 92 / (proj_avg * 1e-3) / 1e9},
+        }
+        dom = "icp_tile_kernel (register + keyframe update)"
+    else:
+        icp_bytes = kf_px * 20 + sw_px * 32
+        fuse_bytes = kf_px * 40 + sw_px * 32 * 2
+        kernels = {
+            "icp_tile_kernel": {"ms_avg": icp_avg, "share": sum(icp_ms) / total_ms, "bytes": icp_bytes,
+                                "gbs": icp_bytes / (icp_avg * 1e-3) / 1e9, "iters_avg": statistics.mean(iters)},
+            "fuse_main + fuse_fill": {"ms_avg": fuse_avg, "share": sum(fuse_ms) / total_ms, "bytes": fuse_bytes,
+                                      "gbs": fuse_bytes / (fuse_avg * 1e-3) / 1e9},
+            "project + resolve + normals": {"ms_avg": proj_avg, "share": sum(proj_ms) / total_ms},
+        }
+        dom = "icp_tile_kernel" if sum(icp_ms) >= sum(fuse_ms) else "fuse_main + fuse_fill"
     kd = kernels[dom]
     traffic = None
     roofline = {"kernel": dom, "bound": "hbm", "achieved": round(kd["gbs"], 1), "peak": hbm, "unit": "GB/s",

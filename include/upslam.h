@@ -212,6 +212,35 @@ upslam_status upslam_icp(const upslam_keyframe *kf, const upslam_sweep *sw, doub
                          void *stream);
 
 /*
+ * Registration of one sweep in one launch: the motion prior (Sec. IV-F
+ * footnote), then upslam_icp, then the motion update.
+ * prior = 0: start from d_pose12 as given (d_prev, d_motion unused);
+ *         1: zero-velocity prior, start from d_prev;
+ *         2: zero-acceleration prior, start from d_prev * d_motion (rotation
+ *            re-orthonormalised).
+ * With prior >= 1, on return d_motion = d_prev^-1 * pose and d_prev = pose
+ * (the registered pose), so the next sweep's call needs no host step; to
+ * start a new keyframe at this sweep set d_prev to the identity.
+ * d_pose12 receives the registered pose in every mode.  Workspace, stats and
+ * stopping rules as upslam_icp.
+ */
+upslam_status upslam_register(const upslam_keyframe *kf, const upslam_sweep *sw, double *d_prev, double *d_motion,
+                              double *d_pose12, int32_t prior, const upslam_icp_params *ip,
+                              upslam_icp_stats *d_stats, void *d_ws, size_t ws_bytes, void *stream);
+
+/*
+ * The whole registration and keyframe update of one sweep in ONE persistent
+ * launch: upslam_register followed by upslam_fuse with the registered pose
+ * (gated by the same acceptance test), reusing the keyframe samples the ICP
+ * staged in shared memory.  Arguments as those two calls; ip->max_iters >= 1.
+ * stats.accepted records whether the sweep was fused.
+ */
+upslam_status upslam_track(const upslam_keyframe *kf, const upslam_sweep *sw, double *d_prev, double *d_motion,
+                           double *d_pose12, int32_t prior, const upslam_icp_params *ip,
+                           const upslam_fuse_params *fp, upslam_icp_stats *d_stats, void *d_ws, size_t ws_bytes,
+                           uint64_t *d_zbuf_kf, void *stream);
+
+/*
  * Keyframe update (Sec. III-C) with T = d_pose12.  Runs only when d_stats is
  * NULL or the registration was accepted (status 0 and inliers / valid >=
  * accept_quality); stats.accepted records the outcome.  Averaging: every

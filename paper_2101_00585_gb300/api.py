@@ -241,7 +241,7 @@ class Tracker:
     """
 
     def __init__(self, sweep_pano, kf_pano, params: Params = Params(), precision: int = F32, device="cuda",
-                 constant_velocity: bool = True):
+                 constant_velocity: bool = True, fused: bool = True):
         self.params = params
         self.sw = SweepFrame(sweep_pano, device, precision)
         self.kf = KeyframeBuffer(kf_pano, device, precision)
@@ -250,6 +250,7 @@ class Tracker:
         self.prev = identity_pose(device)
         self.identity = identity_pose(device)
         self.constant_velocity = constant_velocity
+        self.fused = fused
         self._ip, self._fp = params.icp(), params.fuse()
 
     def new_keyframe(self, pts4: torch.Tensor | None = None, buffer: KeyframeBuffer | None = None) -> None:
@@ -283,24 +284,35 @@ class Tracker:
         self._mark(0, 0)
         self.sw.load(pts4, self.params)
         self._mark(0, 1)
-        _abi.check("upslam_predict_pose", L.upslam_predict_pose(_p(self.prev),
-                                                                _p(self.motion) if self.constant_velocity else None,
-                                                                _p(self.state.pose), s))
         ks, ss = self.kf.struct(), self.sw.struct()
         self._mark(1, 0)
-        _abi.check("upslam_icp", L.upslam_icp(ctypes.byref(ks), ctypes.byref(ss), _p(self.state.pose),
-                                              ctypes.byref(self._ip), _p(self.state.stats), _p(self.state.ws),
-                                              self.state.ws_bytes, s))
+        if self.fused:
+            # prior + ICP + motion update + keyframe update in one persistent launch
+            _abi.check("upslam_track", L.upslam_track(ctypes.byref(ks), ctypes.byref(ss), _p(self.prev),
+                                                      _p(self.motion), _p(self.state.pose),
+                                                      2 if self.constant_velocity else 1, ctypes.byref(self._ip),
+                                                      ctypes.byref(self._fp), _p(self.state.stats), _p(self.state.ws),
+                                                      self.state.ws_bytes, _p(self.kf.zbuf), s))
+            self._mark(1, 1)
+            self._mark(2, 0)
+            self._mark(2, 1)
+            return
+        # prior + ICP + motion update in one launch; afterwards prev holds this sweep's pose
+        _abi.check("upslam_register", L.upslam_register(ctypes.byref(ks), ctypes.byref(ss), _p(self.prev),
+                                                        _p(self.motion), _p(self.state.pose),
+                                                        2 if self.constant_velocity else 1, ctypes.byref(self._ip),
+                                                        _p(self.state.stats), _p(self.state.ws), self.state.ws_bytes,
+                                                        s))
         self._mark(1, 1)
-        _abi.check("upslam_update_motion", L.upslam_update_motion(_p(self.prev), _p(self.state.pose),
-                                                                  _p(self.motion), s))
         self._mark(2, 0)
         _abi.check("upslam_fuse", L.upslam_fuse(ctypes.byref(ks), ctypes.byref(ss), _p(self.state.pose),
                                                 ctypes.byref(self._fp), _p(self.state.stats), _p(self.kf.zbuf), s))
         self._mark(2, 1)
-        self.prev.copy_(self.state.pose)
 
-    # kernels launched by one track() call: project (2), normals, predict, icp, motion, fuse (2)
-    LAUNCHES_PER_TRACK = 8
+    # kernels launched by one track() call: project (2), normals, then one persistent
+    # register + update launch (fused), or register + fuse (2) otherwise
+    @property
+    def launches_per_track(self) -> int:
+        return 4 if self.fused else 6
     # kernels launched by new_keyframe() (after loading): fuse (2)
     LAUNCHES_PER_NEW_KEYFRAME = 2

@@ -276,11 +276,135 @@ __device__ __forceinline__ bool solve6(const double *Aup, const double *rhs, dou
     return true;
 }
 
+// 1/sqrt(x) for a positive normal x: FP32 seed, two FP64 Newton steps.
+__device__ __forceinline__ double rsqrt64(double x) {
+    double y = (double)rsqrtf((float)x);
+    const double hx = 0.5 * x;
+    y = y * fma(-hx * y, y, 1.5);
+    y = y * fma(-hx * y, y, 1.5);
+    return y;
+}
+
+// Gram-Schmidt on the rows of the rotation of a 3x4 pose (FP64, one thread).
+__device__ __forceinline__ void orthonormalise_rows(double *T) {
+    double *r0 = T, *r1 = T + 4, *r2 = T + 8;
+    double n = rsqrt64(fma(r0[0], r0[0], fma(r0[1], r0[1], r0[2] * r0[2])));
+    r0[0] *= n;
+    r0[1] *= n;
+    r0[2] *= n;
+    const double d = fma(r0[0], r1[0], fma(r0[1], r1[1], r0[2] * r1[2]));
+    r1[0] = fma(-d, r0[0], r1[0]);
+    r1[1] = fma(-d, r0[1], r1[1]);
+    r1[2] = fma(-d, r0[2], r1[2]);
+    n = rsqrt64(fma(r1[0], r1[0], fma(r1[1], r1[1], r1[2] * r1[2])));
+    r1[0] *= n;
+    r1[1] *= n;
+    r1[2] *= n;
+    r2[0] = r0[1] * r1[2] - r0[2] * r1[1];
+    r2[1] = r0[2] * r1[0] - r0[0] * r1[2];
+    r2[2] = r0[0] * r1[1] - r0[1] * r1[0];
+}
+
+// C = A B for 3x4 poses on one warp: lane e < 12 computes entry e.  C may alias an input: every
+// lane reads its operands before any lane writes.
+__device__ __forceinline__ void warp_pose_mul(const double *A, const double *B, double *C) {
+    const int lane = threadIdx.x & 31;
+    const int i = lane < 12 ? lane / 4 : 0, j = lane < 12 ? lane % 4 : 0;
+    const double v =
+        fma(A[4 * i], B[j], fma(A[4 * i + 1], B[4 + j], fma(A[4 * i + 2], B[8 + j], j == 3 ? A[4 * i + 3] : 0.0)));
+    __syncwarp();
+    if (lane < 12) C[lane] = v;
+    __syncwarp();
+}
+
+// C = A^-1 = [R^T | -R^T t] on one warp.
+__device__ __forceinline__ void warp_pose_inv(const double *A, double *C) {
+    const int lane = threadIdx.x & 31;
+    const int i = lane < 12 ? lane / 4 : 0, j = lane < 12 ? lane % 4 : 0;
+    const double v = j < 3 ? A[4 * j + i] : -fma(A[i], A[3], fma(A[4 + i], A[7], A[8 + i] * A[11]));
+    __syncwarp();
+    if (lane < 12) C[lane] = v;
+    __syncwarp();
+}
+
 // Neumaier-compensated FP32 accumulation: (s, c) holds s + c.
 __device__ __forceinline__ void kadd(float &s, float &c, float v) {
     const float t = s + v;
     c += fabsf(s) >= fabsf(v) ? (s - t) + v : (v - t) + s;
     s = t;
+}
+
+// ----------------------------------------------------------------------------- keyframe update pieces
+
+// Everything one keyframe update reads and writes.
+struct FuseView {
+    upslam_pano kp;
+    float *kdepth;
+    void *knw;
+    int kprec;
+    const float *kdirs;
+    upslam_pano sp;
+    const float4 *spix;
+    const void *snrm;
+    int sprec;
+    float d_max2, cos_min, w_max, accept;
+    unsigned long long *zbuf;
+};
+
+// Average the sweep sample that keyframe pixel k (point s, normal + count nk,
+// depth d, nk.w > 0) projects onto into the pixel, if the similarity gate keeps
+// the pair (Sec. III-C).  Shared by upslam_fuse and the fused register+update.
+__device__ __forceinline__ void fuse_average(const FuseView &f, const PoseF &T, int k, float3 s, float4 nk, float d) {
+    const float w = nk.w;
+    const float3 q = xform_inv(T, s.x, s.y, s.z);
+    int jv, ju;
+    float rr;
+    if (!bin_point(q.x, q.y, q.z, f.sp, jv, ju, rr)) return;
+    const int j = jv * f.sp.cols + ju;
+    const float4 P = __ldg(f.spix + j);
+    const float4 m = load_nw(f.snrm, j, f.sprec);
+    if (P.w == 0.0f || m.w == 0.0f) return;
+    const float *r = T.r;
+    const float px = fmaf(r[0], P.x, fmaf(r[1], P.y, fmaf(r[2], P.z, r[3])));
+    const float py = fmaf(r[4], P.x, fmaf(r[5], P.y, fmaf(r[6], P.z, r[7])));
+    const float pz = fmaf(r[8], P.x, fmaf(r[9], P.y, fmaf(r[10], P.z, r[11])));
+    const float ex = px - s.x, ey = py - s.y, ez = pz - s.z;
+    if (!(fmaf(ex, ex, fmaf(ey, ey, ez * ez)) <= f.d_max2)) return;
+    const float3 Rm = rotate(T, m.x, m.y, m.z);
+    if (!(fmaf(Rm.x, nk.x, fmaf(Rm.y, nk.y, Rm.z * nk.z)) >= f.cos_min)) return;
+    const float dm = sqrtf(fmaf(px, px, fmaf(py, py, pz * pz)));
+    const float inv = 1.0f / (w + 1.0f);
+    f.kdepth[k] = fmaf(w, d, dm) * inv;
+    const float nx = fmaf(w, nk.x, Rm.x), ny = fmaf(w, nk.y, Rm.y), nz = fmaf(w, nk.z, Rm.z);
+    const float l = rsqrtf(fmaf(nx, nx, fmaf(ny, ny, nz * nz)));
+    const float wn = w + 1.0f < f.w_max ? w + 1.0f : f.w_max;
+    store_nw(f.knw, k, f.kprec, make_float4(nx * l, ny * l, nz * l, wn));
+}
+
+// Hole fill, first pass for sweep pixel j: its z-buffer key into the empty
+// keyframe pixel it lands on.  Returns false when it lands on no empty pixel.
+__device__ __forceinline__ bool holefill_key(const FuseView &f, const PoseF &T, int j, int &k,
+                                             unsigned long long &key, float &range, float4 &m) {
+    const float4 P = __ldg(f.spix + j);
+    if (P.w == 0.0f) return false;
+    m = load_nw(f.snrm, j, f.sprec);
+    if (m.w == 0.0f) return false;
+    const float3 p = xform(T, P.x, P.y, P.z);
+    int v, u;
+    if (!bin_point(p.x, p.y, p.z, f.kp, v, u, range)) return false;
+    k = v * f.kp.cols + u;
+    key = ((unsigned long long)__float_as_uint(range) << 32) | (unsigned int)j;
+    return true;
+}
+
+// Hole fill, second pass: the winning sweep pixel writes the keyframe pixel
+// (d = range, n = unit(R m), w = 1) and resets its z-buffer word.
+__device__ __forceinline__ void holefill_write(const FuseView &f, const PoseF &T, int k, float range, float4 m) {
+    f.zbuf[k] = 0xffffffffffffffffull;
+    const float3 Rm = rotate(T, m.x, m.y, m.z);
+    const float l = rsqrtf(fmaf(Rm.x, Rm.x, fmaf(Rm.y, Rm.y, Rm.z * Rm.z)));
+    f.kdepth[k] = range;
+    store_nw(f.knw, k, f.kprec, make_float4(Rm.x * l, Rm.y * l, Rm.z * l, 1.0f));
 }
 
 }  // namespace upslam

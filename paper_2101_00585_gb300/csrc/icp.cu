@@ -24,6 +24,7 @@
 // normal/weight per pixel) and each correspondence gathers 32 B (16 B in FP16)
 // of sweep data that stays resident in L2.
 #include <mutex>
+#include <string.h>
 
 #include "common.cuh"
 
@@ -49,6 +50,15 @@ struct IcpArgs {
     int sprec;
     float d_max2;
     float cos_min;
+};
+
+// Motion prior folded into the persistent launch (upslam_register).
+struct PriorArgs {
+    const double *prev;  // previous sweep's pose in the keyframe (mode >= 1)
+    const double *motion;  // last inter-sweep motion (mode 2)
+    double *motion_out;  // if set: prev^-1 * registered pose
+    double *prev_out;    // if set: the registered pose
+    int mode;            // 0: start from *pose, 1: zero velocity, 2: constant velocity
 };
 
 struct IcpCtrl {
@@ -510,16 +520,19 @@ __device__ __forceinline__ void sum_records(const float *rec, int nrec, float (*
 // to broadcast it.  CTA 0 writes the pose and the record at the end.
 __global__ void __launch_bounds__(kTileThreads, 1)
     icp_tile_kernel(IcpArgs a, double *pose, upslam_icp_params ip, upslam_icp_stats *st, IcpCtrl *ctrl,
-                    float *partials, int cap) {
+                    float *partials, int cap, PriorArgs pr, FuseView fz, int fuse_on) {
     extern __shared__ float stage[];
     float *sx = stage, *sy = stage + cap, *sz = stage + 2 * cap;
     float *snx = stage + 3 * cap, *sny = stage + 4 * cap, *snz = stage + 5 * cap;
+    float *sw8 = stage + 6 * cap, *sd = stage + 7 * cap;
+    int *sk = reinterpret_cast<int *>(stage + 8 * cap);
     __shared__ float sh[kTileWarps][32];
     __shared__ float shc[kTileWarps][32];
     __shared__ int shn[kTileWarps][32];
     __shared__ int shi[kTileWarps][2];
     __shared__ double tot[32];
     __shared__ double Tsh[12];
+    __shared__ double Tprev[12], Tmot[12];
     __shared__ double xi_sh[6];
     __shared__ int wcnt[kTileWarps];
     __shared__ int base_s, spill_s, flag, status_s, conv_s, valid_s;
@@ -530,7 +543,23 @@ __global__ void __launch_bounds__(kTileThreads, 1)
     const unsigned long long G = gridDim.x;
     unsigned long long base = 0;
     if (threadIdx.x == 0) base = (*((volatile unsigned long long *)&ctrl->arrive64) / G) * G;
-    if (threadIdx.x < 12) Tsh[threadIdx.x] = __ldcg(pose + threadIdx.x);
+    if (pr.mode == 0) {
+        if (threadIdx.x < 12) Tsh[threadIdx.x] = __ldcg(pose + threadIdx.x);
+    } else if (warp == 0) {
+        // initial guess from the motion prior: T0 = prev (zero velocity) or prev * motion
+        if (lane < 12) {
+            Tprev[lane] = __ldcg(pr.prev + lane);
+            Tmot[lane] = pr.mode == 2 ? __ldcg(pr.motion + lane) : 0.0;
+        }
+        __syncwarp();
+        if (pr.mode == 2) {
+            warp_pose_mul(Tprev, Tmot, Tsh);
+            if (lane == 0) orthonormalise_rows(Tsh);
+        } else if (lane < 12) {
+            Tsh[lane] = Tprev[lane];
+        }
+        __syncwarp();
+    }
 
     // ---- stage the CTA's chunks into shared memory (once per launch).  Chunks of
     // 512 pixels are dealt round-robin (chunk q goes to CTA q mod gridDim), so every
@@ -545,6 +574,7 @@ __global__ void __launch_bounds__(kTileThreads, 1)
         const int k = q * kTileThreads + threadIdx.x;
         bool ok = false;
         float3 s = make_float3(0.f, 0.f, 0.f), n = make_float3(0.f, 0.f, 0.f);
+        float wk = 0.0f, dk = 0.0f;
         if (k < npx) {
             const float d = __ldg(a.kdepth + k);
             const float4 n4 = load_nw(a.knw, k, a.kprec);
@@ -554,6 +584,8 @@ __global__ void __launch_bounds__(kTileThreads, 1)
                 const int v = k / W;
                 s = pixel_point(a.kdirs, a.kp.rows, v, k - v * W, d);
                 n = make_float3(n4.x, n4.y, n4.z);
+                wk = n4.w;
+                dk = d;
             }
         }
         const unsigned bal = __ballot_sync(0xffffffffu, ok);
@@ -578,6 +610,9 @@ __global__ void __launch_bounds__(kTileThreads, 1)
             snx[slot] = n.x;
             sny[slot] = n.y;
             snz[slot] = n.z;
+            sw8[slot] = wk;
+            sd[slot] = dk;
+            sk[slot] = k;
         }
         __syncthreads();
         if (threadIdx.x == 0) base_s = total;
@@ -657,7 +692,86 @@ __global__ void __launch_bounds__(kTileThreads, 1)
             break;
         }
     }
-    // CTA 0 publishes the pose and the record of the last linearisation
+    // ---- keyframe update with the registered pose (Sec. III-C), gated by the
+    // registration quality: every CTA holds the same totals, so all take the same decision.
+    int accepted_flag = 0;
+    if (fuse_on) {
+        const bool acc_ok = status_s == UPSLAM_OK && valid_s > 0 && tot[28] >= (double)fz.accept * (double)valid_s;
+        accepted_flag = acc_ok ? 1 : 0;
+        PoseF T;
+#pragma unroll
+        for (int i = 0; i < 12; ++i) T.r[i] = (float)Tsh[i];
+        const int ns = fz.sp.rows * fz.sp.cols;
+        if (acc_ok) {
+            // average the staged samples straight from shared memory, spilled chunks from global memory
+            for (int e = threadIdx.x; e < staged; e += kTileThreads)
+                fuse_average(fz, T, sk[e], make_float3(sx[e], sy[e], sz[e]), make_float4(snx[e], sny[e], snz[e], sw8[e]),
+                             sd[e]);
+            for (int q = spill_q; q < nchunks; q += gridDim.x) {
+                const int k = q * kTileThreads + threadIdx.x;
+                if (k >= npx) continue;
+                const float4 n4 = load_nw(fz.knw, k, fz.kprec);
+                if (!(n4.w > 0.0f)) continue;
+                const float d = __ldg(fz.kdepth + k);
+                const int v = k / W;
+                fuse_average(fz, T, k, pixel_point(fz.kdirs, fz.kp.rows, v, k - v * W, d), n4, d);
+            }
+            // hole fill, first pass: z-buffer atomics into empty keyframe pixels
+            for (int j = blockIdx.x * kTileThreads + threadIdx.x; j < ns; j += gridDim.x * kTileThreads) {
+                int k;
+                unsigned long long key;
+                float r;
+                float4 m;
+                if (!holefill_key(fz, T, j, k, key, r, m)) continue;
+                if (load_nw(fz.knw, k, fz.kprec).w != 0.0f) continue;
+                atomicMin(fz.zbuf + k, key);
+            }
+        }
+        // one more grid barrier (every CTA arrives, accepted or not)
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(&ctrl->arrive64, 1ull);
+            const unsigned long long target = base + G * (unsigned long long)(it + 1);
+            const long long t0 = clock64();
+            flag = 0;
+            while (*((volatile unsigned long long *)&ctrl->arrive64) < target) {
+                if (clock64() - t0 > kWaitCycles) {
+                    flag = 3;
+                    st->status = UPSLAM_ERR_TIMEOUT;
+                    break;
+                }
+                __nanosleep(20);
+            }
+            __threadfence();
+        }
+        __syncthreads();
+        if (flag == 3) return;
+        if (acc_ok) {
+            // hole fill, second pass: the winning sweep pixel writes the keyframe pixel
+            for (int j = blockIdx.x * kTileThreads + threadIdx.x; j < ns; j += gridDim.x * kTileThreads) {
+                int k;
+                unsigned long long key;
+                float r;
+                float4 m;
+                if (!holefill_key(fz, T, j, k, key, r, m)) continue;
+                if (__ldcg(fz.zbuf + k) != key) continue;
+                holefill_write(fz, T, k, r, m);
+            }
+        }
+    }
+    // CTA 0 publishes the pose, the motion update and the record of the last linearisation
+    if (blockIdx.x == 0 && warp == 0 && pr.mode != 0 && pr.motion_out) {
+        warp_pose_inv(Tprev, Tmot);
+        double M[12];
+        warp_pose_mul(Tmot, Tsh, Tmot);
+        if (lane == 0) {
+            for (int i = 0; i < 12; ++i) M[i] = Tmot[i];
+            orthonormalise_rows(M);
+            for (int i = 0; i < 12; ++i) pr.motion_out[i] = M[i];
+        }
+    }
+    if (blockIdx.x == 0 && pr.prev_out && threadIdx.x < 12) pr.prev_out[threadIdx.x] = Tsh[threadIdx.x];
     if (blockIdx.x == 0) {
         if (threadIdx.x < 12) pose[threadIdx.x] = Tsh[threadIdx.x];
         if (threadIdx.x < 21) st->A[threadIdx.x] = tot[threadIdx.x];
@@ -669,7 +783,7 @@ __global__ void __launch_bounds__(kTileThreads, 1)
             st->status = status_s;
             st->converged = conv_s;
             st->iters = it;
-            st->accepted = 0;
+            st->accepted = accepted_flag;
         } else if (threadIdx.x >= 32 && threadIdx.x < 38) {
             st->xi[threadIdx.x - 32] = xi_sh[threadIdx.x - 32];
         }
@@ -711,7 +825,8 @@ static int max_ctas() { return upslam_sm_count() * 8; }
 // Launch the tiled persistent kernel: one CTA per SM, the keyframe slice staged
 // in as much dynamic shared memory as the slice needs (up to the opt-in limit).
 static upslam_status launch_tile(const IcpArgs &a, double *pose, const upslam_icp_params *ip, upslam_icp_stats *st,
-                                 void *ws, size_t ws_bytes, cudaStream_t stream) {
+                                 void *ws, size_t ws_bytes, cudaStream_t stream, PriorArgs pr = PriorArgs{},
+                                 const FuseView *fz = nullptr) {
     int dev = 0, coop = 0, optin = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return UPSLAM_ERR_CUDA;
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
@@ -735,9 +850,11 @@ static upslam_status launch_tile(const IcpArgs &a, double *pose, const upslam_ic
     const int64_t npx = (int64_t)a.kp.rows * a.kp.cols;
     const int64_t nchunks = (npx + kTileThreads - 1) / kTileThreads;
     const int64_t per = (nchunks + grid - 1) / grid * kTileThreads;  // most pixels one CTA can stage
-    const int64_t cap_max = ((int64_t)optin - (int64_t)static_smem[dev] - (int64_t)reserve) / (6 * (int64_t)sizeof(float));
+    // each staged sample: point (3), normal (3), count, depth, pixel index
+    constexpr int64_t kWords = 9;
+    const int64_t cap_max = ((int64_t)optin - (int64_t)static_smem[dev] - (int64_t)reserve) / (kWords * (int64_t)sizeof(float));
     const int cap = (int)(per < cap_max ? (per > 0 ? per : 1) : cap_max);
-    const size_t dyn = (size_t)cap * 6 * sizeof(float);
+    const size_t dyn = (size_t)cap * kWords * sizeof(float);
     if (kCtrlBytes + 2 * (size_t)grid * kSlots * sizeof(float) > ws_bytes) return UPSLAM_ERR_CAPACITY;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, icp_tile_kernel, kTileThreads, dyn) != cudaSuccess ||
@@ -748,7 +865,16 @@ static upslam_status launch_tile(const IcpArgs &a, double *pose, const upslam_ic
     IcpArgs ac = a;
     upslam_icp_params ipc = *ip;
     int capc = cap;
-    void *args[] = {&ac, &pose, &ipc, &st, &ctrl, &partials, &capc};
+    PriorArgs prc = pr;
+    FuseView fzc;
+    int fuse_on = 0;
+    if (fz) {
+        fzc = *fz;
+        fuse_on = 1;
+    } else {
+        memset(&fzc, 0, sizeof(fzc));
+    }
+    void *args[] = {&ac, &pose, &ipc, &st, &ctrl, &partials, &capc, &prc, &fzc, &fuse_on};
     if (cudaLaunchCooperativeKernel((const void *)icp_tile_kernel, dim3(grid), dim3(kTileThreads), args, dyn, stream) !=
         cudaSuccess) {
         (void)cudaGetLastError();
@@ -797,6 +923,46 @@ extern "C" upslam_status upslam_icp(const upslam_keyframe *kf, const upslam_swee
     if (chk != UPSLAM_OK) return chk;
     if (ip->max_iters == 0) return UPSLAM_OK;
     return launch_tile(make_args(kf, sw, ip), d_pose12, ip, d_stats, d_ws, ws_bytes, (cudaStream_t)stream);
+}
+
+extern "C" upslam_status upslam_register(const upslam_keyframe *kf, const upslam_sweep *sw, double *d_prev,
+                                         double *d_motion, double *d_pose12, int32_t prior,
+                                         const upslam_icp_params *ip, upslam_icp_stats *d_stats, void *d_ws,
+                                         size_t ws_bytes, void *stream) {
+    const upslam_status chk = icp_common_checks(kf, sw, d_pose12, ip, d_stats, d_ws, ws_bytes);
+    if (chk != UPSLAM_OK) return chk;
+    if (prior < 0 || prior > 2 || (prior >= 1 && !d_prev) || (prior == 2 && !d_motion)) return UPSLAM_ERR_INVALID_ARG;
+    if (ip->max_iters == 0) return UPSLAM_OK;
+    PriorArgs pr;
+    pr.prev = d_prev;
+    pr.motion = d_motion;
+    pr.motion_out = prior >= 1 ? d_motion : nullptr;
+    pr.prev_out = prior >= 1 ? d_prev : nullptr;
+    pr.mode = prior;
+    return launch_tile(make_args(kf, sw, ip), d_pose12, ip, d_stats, d_ws, ws_bytes, (cudaStream_t)stream, pr);
+}
+
+bool upslam_fuse_view(const upslam_keyframe *kf, const upslam_sweep *sw, const upslam_fuse_params *fp,
+                      uint64_t *d_zbuf_kf, FuseView &f);
+
+extern "C" upslam_status upslam_track(const upslam_keyframe *kf, const upslam_sweep *sw, double *d_prev,
+                                      double *d_motion, double *d_pose12, int32_t prior,
+                                      const upslam_icp_params *ip, const upslam_fuse_params *fp,
+                                      upslam_icp_stats *d_stats, void *d_ws, size_t ws_bytes, uint64_t *d_zbuf_kf,
+                                      void *stream) {
+    const upslam_status chk = icp_common_checks(kf, sw, d_pose12, ip, d_stats, d_ws, ws_bytes);
+    if (chk != UPSLAM_OK) return chk;
+    if (prior < 0 || prior > 2 || (prior >= 1 && !d_prev) || (prior == 2 && !d_motion)) return UPSLAM_ERR_INVALID_ARG;
+    FuseView f;
+    if (!upslam_fuse_view(kf, sw, fp, d_zbuf_kf, f)) return UPSLAM_ERR_INVALID_ARG;
+    if (ip->max_iters < 1) return UPSLAM_ERR_INVALID_ARG;
+    PriorArgs pr;
+    pr.prev = d_prev;
+    pr.motion = d_motion;
+    pr.motion_out = prior >= 1 ? d_motion : nullptr;
+    pr.prev_out = prior >= 1 ? d_prev : nullptr;
+    pr.mode = prior;
+    return launch_tile(make_args(kf, sw, ip), d_pose12, ip, d_stats, d_ws, ws_bytes, (cudaStream_t)stream, pr, &f);
 }
 
 // ----------------------------------------------------------------------------- allocation-free variant

@@ -28,28 +28,7 @@ __device__ void inv34(const double *A, double *B) {
     for (int i = 0; i < 12; ++i) B[i] = t[i];
 }
 
-// 1/sqrt(x) for a positive normal x: FP32 seed, two FP64 Newton steps (GB300's
-// FP64 square root and division are long instruction sequences; this is a few FMAs).
-__device__ __forceinline__ double rsqrt64(double x) {
-    double y = (double)rsqrtf((float)x);
-    const double hx = 0.5 * x;
-    y = y * fma(-hx * y, y, 1.5);
-    y = y * fma(-hx * y, y, 1.5);
-    return y;
-}
-
-__device__ void orthonormalise(double *T) {
-    double *r0 = T, *r1 = T + 4, *r2 = T + 8;
-    double n = rsqrt64(fma(r0[0], r0[0], fma(r0[1], r0[1], r0[2] * r0[2])));
-    for (int i = 0; i < 3; ++i) r0[i] *= n;
-    const double d = fma(r0[0], r1[0], fma(r0[1], r1[1], r0[2] * r1[2]));
-    for (int i = 0; i < 3; ++i) r1[i] = fma(-d, r0[i], r1[i]);
-    n = rsqrt64(fma(r1[0], r1[0], fma(r1[1], r1[1], r1[2] * r1[2])));
-    for (int i = 0; i < 3; ++i) r1[i] *= n;
-    r2[0] = r0[1] * r1[2] - r0[2] * r1[1];
-    r2[1] = r0[2] * r1[0] - r0[0] * r1[2];
-    r2[2] = r0[0] * r1[1] - r0[1] * r1[0];
-}
+__device__ void orthonormalise(double *T) { orthonormalise_rows(T); }
 
 __global__ void predict_kernel(const double *T_prev, const double *M, double *T_out) {
     double t[12];

@@ -394,3 +394,61 @@ def test_tracker_sequence_matches_oracle():
         assert st["accepted"] == int(acc_ref)
     et, er = rot_err(pose_host(trk.state.pose), synth.relative(seq.poses[0], seq.poses[n - 1]))
     assert et < 0.03 and er < math.radians(0.3)
+
+
+def test_register_equals_prior_icp_motion_chain():
+    """upslam_register (prior + persistent ICP + motion update in one launch) equals the
+    separate calls upslam_predict_pose -> upslam_icp -> upslam_update_motion."""
+    import ctypes
+    from paper_2101_00585_gb300 import _abi
+    c, prm, sp4, sn4, kd, kn = room_sweep_and_keyframe(noise=True)
+    kf = _kf_buffers(kd, kn, c.kf)
+    sw = _sweep_buffers(sp4, sn4, c.sweep)
+    p = up.Params(max_iters=10)
+    rng = np.random.default_rng(31)
+    prev0 = synth.perturb(IDENTITY, rng, 0.02, 0.01)
+    mot0 = synth.perturb(IDENTITY, rng, 0.02, 0.01)
+    L = up.lib()
+    s = torch.cuda.current_stream().cuda_stream
+    ks, ss, ip = kf.struct(), sw.struct(), p.icp()
+    # chain of separate entry points
+    a = up.IcpState(kf)
+    prev_a, mot_a = pose_dev(prev0), pose_dev(mot0)
+    assert L.upslam_predict_pose(ctypes.c_void_p(prev_a.data_ptr()), ctypes.c_void_p(mot_a.data_ptr()),
+                                 ctypes.c_void_p(a.pose.data_ptr()), ctypes.c_void_p(s)) == 0
+    up.icp(kf, sw, a, p)
+    assert L.upslam_update_motion(ctypes.c_void_p(prev_a.data_ptr()), ctypes.c_void_p(a.pose.data_ptr()),
+                                  ctypes.c_void_p(mot_a.data_ptr()), ctypes.c_void_p(s)) == 0
+    # one launch
+    b = up.IcpState(kf)
+    prev_b, mot_b = pose_dev(prev0), pose_dev(mot0)
+    rc = L.upslam_register(ctypes.byref(ks), ctypes.byref(ss), ctypes.c_void_p(prev_b.data_ptr()),
+                           ctypes.c_void_p(mot_b.data_ptr()), ctypes.c_void_p(b.pose.data_ptr()), 2,
+                           ctypes.byref(ip), ctypes.c_void_p(b.stats.data_ptr()), ctypes.c_void_p(b.ws.data_ptr()),
+                           ctypes.c_size_t(b.ws_bytes), ctypes.c_void_p(s))
+    assert rc == _abi.OK
+    for x, y in ((a.pose, b.pose), (mot_a, mot_b), (a.pose, prev_b)):
+        dt, dr = rot_err(pose_host(x), pose_host(y))
+        assert dt < 1e-9 and dr < 1e-9
+    assert a.read_stats()["iters"] == b.read_stats()["iters"]
+
+
+def test_track_equals_register_then_fuse():
+    """upslam_track (one launch) equals upslam_register followed by upslam_fuse on the same inputs."""
+    seq = configs.tunnel_sequence(n_scans=4)
+    scans = [seq.scan(k) for k in range(4)]
+    p = up.Params(accept_quality=0.1)
+    a = up.Tracker(seq.sweep, seq.kf, p, fused=True)
+    b = up.Tracker(seq.sweep, seq.kf, p, fused=False)
+    for trk in (a, b):
+        trk.new_keyframe(dev(scans[0]))
+        for k in range(1, 4):
+            trk.track(dev(scans[k]))
+    torch.cuda.synchronize()
+    dt, dr = rot_err(pose_host(a.state.pose), pose_host(b.state.pose))
+    assert dt < 1e-9 and dr < 1e-9
+    ra, rb = a.state.read_stats(), b.state.read_stats()
+    assert ra["accepted"] == rb["accepted"] == 1 and ra["iters"] == rb["iters"]
+    assert torch.equal(a.kf.nw[..., 3], b.kf.nw[..., 3])
+    assert torch.allclose(a.kf.depth, b.kf.depth, rtol=1e-6, atol=0)
+    assert bool((a.kf.zbuf == -1).all()) and bool((b.kf.zbuf == -1).all())
