@@ -293,6 +293,35 @@ upslam_status upslam_icp_noalloc(const upslam_keyframe *kf, const upslam_sweep *
 upslam_status upslam_predict_pose(const double *d_T_prev, const double *d_motion, double *d_T_out, void *stream);
 upslam_status upslam_update_motion(const double *d_T_prev, const double *d_T, double *d_motion, void *stream);
 
+/*
+ * Batched persistent ICP (the grid search of Sec. III-C carried to full
+ * registrations): one sweep against n_kf keyframes of any sizes, with n_hyp
+ * initial poses per keyframe, i.e. n_kf * n_hyp problems (problem
+ * p = kf * n_hyp + h), all in ONE cooperative launch.  Every problem follows
+ * upslam_icp (Eq. 1, FP64 solve, same stopping rules); all active problems
+ * advance one Gauss-Newton step at a time and a keyframe sample is evaluated
+ * for all hypotheses of its keyframe at once.
+ * d_kfs: device array [n_kf] of keyframe views; kfs: the same array on the host
+ *   (sizes and validation).  n_kf <= 256, n_kf * n_hyp <= 1024.
+ * d_poses: [n_kf * n_hyp][12] FP64, initial poses in, registered poses out.
+ * d_stats: [n_kf * n_hyp] records.
+ * d_ws: upslam_icp_batched_workspace_bytes(...) bytes (256-byte aligned); its
+ *   first 8 bytes must be zero before the first use (arrival counter).
+ * tiles: CTA width (256 or 512) and keyframe chunk (a multiple of it), or NULL
+ *   for 512 / 512; the package's autotuner picks them per device and shape.
+ */
+typedef struct {
+    int32_t threads; /* threads per CTA: 256 or 512 */
+    int32_t chunk;   /* keyframe pixels per chunk, a multiple of threads */
+} upslam_batch_tiles;
+
+size_t upslam_icp_batched_workspace_bytes(const upslam_keyframe *kfs, int32_t n_kf, int32_t n_hyp,
+                                          const upslam_batch_tiles *tiles);
+upslam_status upslam_icp_batched(const upslam_keyframe *d_kfs, const upslam_keyframe *kfs, int32_t n_kf,
+                                 const upslam_sweep *sw, int32_t n_hyp, double *d_poses, const upslam_icp_params *ip,
+                                 upslam_icp_stats *d_stats, void *d_ws, size_t ws_bytes,
+                                 const upslam_batch_tiles *tiles, void *stream);
+
 /* Human-readable name of a status code (static storage). */
 const char *upslam_status_string(upslam_status s);
 

@@ -9,9 +9,9 @@ ICP and keyframe fusion as hand-written CUDA behind the C ABI of include/upslam.
 The library is built in-tree by ``paper_2101_00585_gb300.build.build()``.
 """
 from ._abi import F16, F32, LIB_PATH, UpslamError, lib  # noqa: F401
-from .api import (IcpState, KeyframeBuffer, Params, SweepFrame, Tracker, empty_zbuf, fuse, icp, icp_step,  # noqa: F401
+from .api import (Batch, IcpState, KeyframeBuffer, Params, SweepFrame, Tracker, empty_zbuf, fuse, icp, icp_step,  # noqa: F401
                   identity_pose, normals, pano_dirs, pano_struct, project, unproject)
 
-__all__ = ["Tracker", "Params", "SweepFrame", "KeyframeBuffer", "IcpState", "project", "normals", "icp", "icp_step",
+__all__ = ["Batch", "Tracker", "Params", "SweepFrame", "KeyframeBuffer", "IcpState", "project", "normals", "icp", "icp_step",
            "fuse", "unproject", "pano_dirs", "pano_struct", "identity_pose", "empty_zbuf", "lib", "UpslamError", "F32",
            "F16", "LIB_PATH"]

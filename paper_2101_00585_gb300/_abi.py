@@ -54,7 +54,12 @@ class Keyframe(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("d_dirs", ctypes.c_void_p)]
 
 
+class BatchTiles(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_int32), ("chunk", ctypes.c_int32)]
+
+
 STATS_BYTES = ctypes.sizeof(IcpStats)
+KEYFRAME_BYTES = ctypes.sizeof(Keyframe)
 _P = ctypes.POINTER
 _vp = ctypes.c_void_p
 
@@ -77,6 +82,10 @@ SIGNATURES = {
     "upslam_icp_noalloc": (ctypes.c_int, [_P(Keyframe), _P(Sweep), _vp, _P(IcpParams), _vp, _vp]),
     "upslam_predict_pose": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "upslam_update_motion": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "upslam_icp_batched_workspace_bytes": (ctypes.c_size_t, [_P(Keyframe), ctypes.c_int32, ctypes.c_int32,
+                                                             _P(BatchTiles)]),
+    "upslam_icp_batched": (ctypes.c_int, [_vp, _P(Keyframe), ctypes.c_int32, _P(Sweep), ctypes.c_int32, _vp,
+                                          _P(IcpParams), _vp, _vp, ctypes.c_size_t, _P(BatchTiles), _vp]),
     "upslam_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "upslam_version": (ctypes.c_char_p, []),
 }

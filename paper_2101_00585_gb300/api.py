@@ -316,3 +316,53 @@ class Tracker:
         return 4 if self.fused else 6
     # kernels launched by new_keyframe() (after loading): fuse (2)
     LAUNCHES_PER_NEW_KEYFRAME = 2
+
+
+# ----------------------------------------------------------------------------- batched registration
+
+class Batch:
+    """One sweep against several keyframes with several initial poses each, solved in one launch.
+
+    Problem p = kf * n_hyp + h.  ``run(init_poses)`` registers all problems; the
+    results are in ``poses`` ([n_prob, 12] FP64) and ``read_stats()``.
+    """
+
+    def __init__(self, sweep: SweepFrame, keyframes: list, n_hyp: int, tiles: tuple | None = None, device="cuda"):
+        self.sw = sweep
+        self.kfs = list(keyframes)
+        self.n_kf, self.n_hyp = len(self.kfs), int(n_hyp)
+        self.n_prob = self.n_kf * self.n_hyp
+        arr = (_abi.Keyframe * self.n_kf)(*[k.struct() for k in self.kfs])
+        self._host = arr
+        raw = bytes(arr)
+        self.d_table = torch.frombuffer(bytearray(raw), dtype=torch.uint8).to(device)
+        self.set_tiles(tiles)
+        self.poses = torch.zeros((self.n_prob, 12), dtype=torch.float64, device=device)
+        self.stats = torch.zeros((self.n_prob, _abi.STATS_BYTES), dtype=torch.uint8, device=device)
+        self.device = device
+
+    def set_tiles(self, tiles):
+        self.tiles = _abi.BatchTiles(*(tiles or (512, 512)))
+        L = _abi.lib()
+        self.ws_bytes = int(L.upslam_icp_batched_workspace_bytes(self._host, self.n_kf, self.n_hyp,
+                                                                  ctypes.byref(self.tiles)))
+        if getattr(self, "ws", None) is None or self.ws.numel() < self.ws_bytes:
+            self.ws = torch.zeros(self.ws_bytes, dtype=torch.uint8, device=self.sw.pix.device)
+
+    def run(self, init_poses: torch.Tensor, params: Params = Params()) -> None:
+        self.poses.copy_(init_poses.reshape(self.n_prob, 12))
+        ip = params.icp()
+        ss = self.sw.struct()
+        _abi.check("upslam_icp_batched",
+                   _abi.lib().upslam_icp_batched(_p(self.d_table), self._host, self.n_kf, ctypes.byref(ss), self.n_hyp,
+                                                 _p(self.poses), ctypes.byref(ip), _p(self.stats), _p(self.ws),
+                                                 self.ws_bytes, ctypes.byref(self.tiles), _stream()))
+
+    def read_stats(self) -> list:
+        raw = self.stats.cpu().numpy()
+        out = []
+        for p in range(self.n_prob):
+            st = _abi.IcpStats.from_buffer_copy(bytes(raw[p]))
+            out.append({"A": list(st.A), "b": list(st.b), "sse": st.sse, "inliers": st.inliers, "valid": st.valid,
+                        "status": st.status, "converged": st.converged, "xi": list(st.xi), "iters": st.iters})
+        return out

@@ -1,0 +1,447 @@
+// Batched persistent ICP: many registration problems in one cooperative launch.
+//
+// A batch is one sweep registered against n_kf keyframes of mixed sizes, with
+// n_hyp initial-pose hypotheses per keyframe (problem p = kf * n_hyp + h).  The
+// paper evaluates several hundred candidate transforms when it searches for a
+// loop closure (Sec. III-C, grid search); here every candidate is a full
+// Gauss-Newton ICP problem (Sec. III-B, Eq. 1), all advancing in lockstep.
+//
+// Prologue (once): every CTA takes the keyframe chunks q = blockIdx, +grid, ...
+// of each keyframe and compacts the pixels holding a sample into its own
+// entry lists in the workspace (FP32 point d*dir and normal, structure of
+// arrays), so later steps touch samples only.
+//
+// Each step:
+//  1. for each keyframe, each staged sample is evaluated under every active
+//     hypothesis of that keyframe (the sample is loaded once for all of them);
+//     a warp reduce-scatter (31 shuffles for 32 sums) turns 32 lanes'
+//     contributions into one sum per lane, added to per-problem accumulators
+//     in shared memory;
+//  2. every CTA writes one record (29 sums) per problem; grid barrier;
+//  3. problem p is owned by CTA p mod grid: its warps sum the records of p
+//     (compensated FP32), one warp solves in FP64 (L D L^T, SE(3) exp) and
+//     writes the pose, the record and the active flag; grid barrier;
+//  4. every CTA reloads the poses and flags of the active problems.
+// The launch ends when no problem is active or after max_iters steps.
+// Grid barriers are a monotonic 64-bit arrival counter with a clock64 budget.
+#include <string.h>
+
+#include "common.cuh"
+
+namespace upslam {
+
+constexpr int kBatchMaxProblems = 1024;
+constexpr int kBatchMaxKf = 256;
+constexpr long long kBatchWaitCycles = 8000000000ll;  // about 4 s at 2 GHz
+constexpr int kRecWords = 32;
+
+struct BatchCtrl {
+    unsigned long long arrive;
+    int valid;  // sweep pixels holding a point
+    int pad;
+};
+
+struct BatchArgs {
+    const upslam_keyframe *kfs;  // device array [n_kf]
+    int n_kf, n_hyp, n_prob;
+    upslam_pano sp;
+    const float4 *spix;
+    const void *snrm;
+    int sprec;
+    float d_max2, cos_min;
+    double *poses;            // [n_prob][12] in/out
+    upslam_icp_stats *stats;  // [n_prob]
+    int *active;              // [n_prob] workspace flags
+    float *entries;           // per-CTA entry regions
+    long long cta_cap;        // entries per CTA region
+    float *records;           // [n_prob][grid][kRecWords]
+    BatchCtrl *ctrl;
+    upslam_icp_params ip;
+    int chunk;  // pixels per chunk (a multiple of blockDim)
+};
+
+// Lane L ends with the sum over the warp's lanes of v[L] (32 values per lane).
+__device__ __forceinline__ float warp_reduce_scatter(float v[32]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        const bool upper = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < o; ++i) {
+            const float send = upper ? v[i] : v[i + o];
+            const float keep = upper ? v[i + o] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    return v[0];
+}
+
+__device__ __forceinline__ bool grid_wait(BatchCtrl *ctrl, unsigned long long target) {
+    const long long t0 = clock64();
+    while (*((volatile unsigned long long *)&ctrl->arrive) < target) {
+        if (clock64() - t0 > kBatchWaitCycles) return false;
+        __nanosleep(32);
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(512, 1) icp_batched_kernel(BatchArgs a) {
+    extern __shared__ float smem[];
+    float *acc = smem;                                 // [n_prob][kRecWords]
+    float *pose_f = acc + a.n_prob * kRecWords;        // [n_prob][12]
+    int *act = reinterpret_cast<int *>(pose_f + a.n_prob * 12);  // [n_prob]
+    __shared__ int kf_off[kBatchMaxKf], kf_cnt[kBatchMaxKf];
+    __shared__ int wcnt[32];
+    __shared__ int base_s, flag_s, any_active;
+    __shared__ double tot[32];
+    __shared__ double Tsh[16][12];
+    __shared__ float shs[16][32], shc[16][32];
+    const int T = blockDim.x, nw = T / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned long long G = gridDim.x;
+    unsigned long long base = 0;
+    if (threadIdx.x == 0) base = (*((volatile unsigned long long *)&a.ctrl->arrive) / G) * G;
+    float *ent = a.entries + (size_t)blockIdx.x * 6 * a.cta_cap;  // SoA: [6][cta_cap]
+
+    // ---- prologue: compact this CTA's keyframe chunks
+    if (threadIdx.x == 0) base_s = 0;
+    __syncthreads();
+    for (int kf = 0; kf < a.n_kf; ++kf) {
+        const upslam_keyframe K = a.kfs[kf];
+        const int npx = K.pano.rows * K.pano.cols, W = K.pano.cols;
+        const int nch = (npx + a.chunk - 1) / a.chunk;
+        if (threadIdx.x == 0) kf_off[kf] = base_s;
+        __syncthreads();
+        for (int c = blockIdx.x; c < nch; c += gridDim.x) {
+            for (int b0 = c * a.chunk; b0 < min(npx, (c + 1) * a.chunk); b0 += T) {
+                const int k = b0 + threadIdx.x;
+                bool ok = false;
+                float3 s = make_float3(0.f, 0.f, 0.f);
+                float4 n4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (k < npx && k < (c + 1) * a.chunk) {
+                    const float d = __ldg(K.d_depth + k);
+                    n4 = load_nw(K.d_nw, k, K.precision);
+                    if (d > 0.0f && __fadd_rn(__fadd_rn(__fmul_rn(n4.x, n4.x), __fmul_rn(n4.y, n4.y)),
+                                              __fmul_rn(n4.z, n4.z)) > 0.25f) {
+                        ok = true;
+                        const int v = k / W;
+                        s = pixel_point(K.d_dirs, K.pano.rows, v, k - v * W, d);
+                    }
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, ok);
+                if (lane == 0) wcnt[warp] = __popc(bal);
+                __syncthreads();
+                int off = base_s, total = base_s;
+                for (int w = 0; w < nw; ++w) {
+                    off += w < warp ? wcnt[w] : 0;
+                    total += wcnt[w];
+                }
+                const int slot = off + __popc(bal & ((1u << lane) - 1u));
+                if (ok && slot < a.cta_cap) {
+                    ent[slot] = s.x;
+                    ent[a.cta_cap + slot] = s.y;
+                    ent[2 * a.cta_cap + slot] = s.z;
+                    ent[3 * a.cta_cap + slot] = n4.x;
+                    ent[4 * a.cta_cap + slot] = n4.y;
+                    ent[5 * a.cta_cap + slot] = n4.z;
+                }
+                __syncthreads();
+                if (threadIdx.x == 0) base_s = total < a.cta_cap ? total : (int)a.cta_cap;
+                __syncthreads();
+            }
+        }
+        if (threadIdx.x == 0) kf_cnt[kf] = base_s - kf_off[kf];
+        __syncthreads();
+    }
+    // sweep pixels holding a point (for the registration quality)
+    {
+        int c = 0;
+        const int ns = a.sp.rows * a.sp.cols;
+        for (int j = blockIdx.x * T + threadIdx.x; j < ns; j += gridDim.x * T) c += __ldg(&a.spix[j].w) != 0.0f;
+        c = __reduce_add_sync(0xffffffffu, c);
+        if (lane == 0 && c) atomicAdd(&a.ctrl->valid, c);
+    }
+    for (int p = threadIdx.x; p < a.n_prob; p += T) {
+        act[p] = 1;
+        for (int i = 0; i < 12; ++i) pose_f[p * 12 + i] = (float)__ldcg(a.poses + (size_t)p * 12 + i);
+    }
+    __syncthreads();
+
+    int it = 0;
+    for (; it < a.ip.max_iters; ++it) {
+        for (int i = threadIdx.x; i < a.n_prob * kRecWords; i += T) acc[i] = 0.0f;
+        __syncthreads();
+        // ---- 1. accumulate every active hypothesis of every keyframe over this CTA's samples
+        for (int kf = 0; kf < a.n_kf; ++kf) {
+            const int cnt = kf_cnt[kf], off = kf_off[kf];
+            const upslam_keyframe K = a.kfs[kf];
+            (void)K;
+            for (int e0 = warp * 32; e0 < cnt; e0 += T) {
+                const int e = e0 + lane;
+                const bool have = e < cnt;
+                float3 s = make_float3(0.f, 0.f, 0.f), n = make_float3(0.f, 0.f, 0.f);
+                if (have) {
+                    const int q = off + e;
+                    s = make_float3(ent[q], ent[a.cta_cap + q], ent[2 * a.cta_cap + q]);
+                    n = make_float3(ent[3 * a.cta_cap + q], ent[4 * a.cta_cap + q], ent[5 * a.cta_cap + q]);
+                }
+                for (int h = 0; h < a.n_hyp; ++h) {
+                    const int p = kf * a.n_hyp + h;
+                    if (!act[p]) continue;
+                    PoseF Tp;
+#pragma unroll
+                    for (int i = 0; i < 12; ++i) Tp.r[i] = pose_f[p * 12 + i];
+                    const float3 q = xform_inv(Tp, s.x, s.y, s.z);
+                    int jv = 0, ju = 0;
+                    float rr;
+                    bool ok = have && bin_point(q.x, q.y, q.z, a.sp, jv, ju, rr);
+                    const int j = ok ? jv * a.sp.cols + ju : 0;
+                    const float4 P = __ldg(a.spix + j);
+                    const float4 m = load_nw(a.snrm, j, a.sprec);
+                    ok = ok && P.w != 0.0f && m.w != 0.0f;
+                    const float *r = Tp.r;
+                    const float px = fmaf(r[0], P.x, fmaf(r[1], P.y, fmaf(r[2], P.z, r[3])));
+                    const float py = fmaf(r[4], P.x, fmaf(r[5], P.y, fmaf(r[6], P.z, r[7])));
+                    const float pz = fmaf(r[8], P.x, fmaf(r[9], P.y, fmaf(r[10], P.z, r[11])));
+                    const float3 Rm = rotate(Tp, m.x, m.y, m.z);
+                    const float ex = px - s.x, ey = py - s.y, ez = pz - s.z;
+                    ok = ok && (ex * ex + ey * ey + ez * ez <= a.d_max2) &&
+                         (Rm.x * n.x + Rm.y * n.y + Rm.z * n.z >= a.cos_min);
+                    const float w = ok ? 1.0f : 0.0f;
+                    const float res = (ex * n.x + ey * n.y + ez * n.z) * w;
+                    float J[6];
+                    J[0] = (py * n.z - pz * n.y) * w;
+                    J[1] = (pz * n.x - px * n.z) * w;
+                    J[2] = (px * n.y - py * n.x) * w;
+                    J[3] = n.x * w;
+                    J[4] = n.y * w;
+                    J[5] = n.z * w;
+                    float v[32];
+                    int c = 0;
+#pragma unroll
+                    for (int i = 0; i < 6; ++i)
+#pragma unroll
+                        for (int k2 = i; k2 < 6; ++k2) v[c++] = J[i] * J[k2];
+#pragma unroll
+                    for (int i = 0; i < 6; ++i) v[21 + i] = J[i] * res;
+                    v[27] = res * res;
+                    v[28] = w;
+                    v[29] = 0.0f;
+                    v[30] = 0.0f;
+                    v[31] = 0.0f;
+                    const float sum = warp_reduce_scatter(v);
+                    if (lane < 29) atomicAdd(&acc[p * kRecWords + lane], sum);
+                }
+            }
+        }
+        __syncthreads();
+        // ---- 2. publish this CTA's record of every active problem
+        for (int i = threadIdx.x; i < a.n_prob * kRecWords; i += T) {
+            const int p = i / kRecWords;
+            if (act[p]) a.records[((size_t)p * gridDim.x + blockIdx.x) * kRecWords + (i % kRecWords)] = acc[i];
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(&a.ctrl->arrive, 1ull);
+            flag_s = grid_wait(a.ctrl, base + G * (2ull * it + 1ull)) ? 0 : 1;
+            __threadfence();
+        }
+        __syncthreads();
+        if (flag_s) break;
+        // ---- 3. the problems this CTA owns: sum records, solve, publish
+        for (int p = blockIdx.x; p < a.n_prob; p += gridDim.x) {
+            if (!act[p]) continue;
+            float s = 0.0f, c = 0.0f;
+            for (int b = warp; b < (int)gridDim.x; b += nw) {
+                const float x = __ldcg(a.records + ((size_t)p * gridDim.x + b) * kRecWords + lane);
+                kadd(s, c, x);
+            }
+            shs[warp][lane] = s;
+            shc[warp][lane] = c;
+            __syncthreads();
+            if (threadIdx.x < 29) {
+                float t = 0.0f, cc = 0.0f;
+                for (int w = 0; w < nw; ++w) {
+                    kadd(t, cc, shs[w][threadIdx.x]);
+                    cc += shc[w][threadIdx.x];
+                }
+                tot[threadIdx.x] = (double)t + (double)cc;
+            }
+            if (threadIdx.x < 12) Tsh[0][threadIdx.x] = __ldcg(a.poses + (size_t)p * 12 + threadIdx.x);
+            __syncthreads();
+            if (warp == 0) {
+                const long long inliers = (long long)(tot[28] + 0.5);
+                double xi[6] = {0, 0, 0, 0, 0, 0};
+                int status = UPSLAM_OK, conv = 0;
+                if (inliers < a.ip.min_inliers) {
+                    status = UPSLAM_ERR_DEGENERATE;
+                } else if (!warp_solve6(tot, a.ip.pivot_eps, xi)) {
+                    status = UPSLAM_ERR_DEGENERATE;
+#pragma unroll
+                    for (int i = 0; i < 6; ++i) xi[i] = 0.0;
+                } else {
+                    warp_se3_update(xi, Tsh[0]);
+                    const double wn2 = fma(xi[0], xi[0], fma(xi[1], xi[1], xi[2] * xi[2]));
+                    const double vn2 = fma(xi[3], xi[3], fma(xi[4], xi[4], xi[5] * xi[5]));
+                    conv = (wn2 < a.ip.eps_rot * a.ip.eps_rot && vn2 < a.ip.eps_trans * a.ip.eps_trans) ? 1 : 0;
+                }
+                upslam_icp_stats *st = a.stats + p;
+                if (lane < 12) a.poses[(size_t)p * 12 + lane] = Tsh[0][lane];
+                if (lane < 21) st->A[lane] = tot[lane];
+                else if (lane < 27) st->b[lane - 21] = tot[lane];
+                if (lane < 6) st->xi[lane] = xi[lane];
+                if (lane == 0) {
+                    st->sse = tot[27];
+                    st->inliers = inliers;
+                    st->valid = *((volatile int *)&a.ctrl->valid);
+                    st->status = status;
+                    st->converged = conv;
+                    st->iters = it + 1;
+                    st->accepted = 0;
+                    a.active[p] = (status == UPSLAM_OK && !conv) ? 1 : 0;
+                }
+            }
+            __syncthreads();
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(&a.ctrl->arrive, 1ull);
+            flag_s = grid_wait(a.ctrl, base + G * (2ull * it + 2ull)) ? 0 : 1;
+            __threadfence();
+            any_active = 0;
+        }
+        __syncthreads();
+        if (flag_s) break;
+        // ---- 4. reload poses and flags
+        for (int p = threadIdx.x; p < a.n_prob; p += T) {
+            if (!act[p]) continue;
+            const int still = __ldcg(a.active + p);
+            act[p] = still;
+            if (still) {
+                any_active = 1;
+                for (int i = 0; i < 12; ++i) pose_f[p * 12 + i] = (float)__ldcg(a.poses + (size_t)p * 12 + i);
+            }
+        }
+        __syncthreads();
+        if (!any_active) break;
+    }
+    if (flag_s && threadIdx.x == 0) {
+        for (int p = blockIdx.x; p < a.n_prob; p += gridDim.x) a.stats[p].status = UPSLAM_ERR_TIMEOUT;
+    }
+}
+
+}  // namespace upslam
+
+using namespace upslam;
+
+static size_t batch_region_entries(const upslam_keyframe *kfs, int32_t n_kf, int grid, int chunk) {
+    // per CTA: ceil(chunks / grid) chunks of every keyframe, each up to `chunk` samples
+    size_t cap = 0;
+    for (int i = 0; i < n_kf; ++i) {
+        const int64_t npx = (int64_t)kfs[i].pano.rows * kfs[i].pano.cols;
+        const int64_t nch = (npx + chunk - 1) / chunk;
+        cap += (size_t)((nch + grid - 1) / grid) * chunk;
+    }
+    return cap;
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static size_t batch_ws_layout(const upslam_keyframe *kfs, int32_t n_kf, int32_t n_prob, int grid, int chunk,
+                              size_t *off_active, size_t *off_records, size_t *off_entries, size_t *cap) {
+    *cap = batch_region_entries(kfs, n_kf, grid, chunk);
+    size_t o = 256;  // control block
+    *off_active = o;
+    o = align256(o + (size_t)n_prob * sizeof(int));
+    *off_records = o;
+    o = align256(o + (size_t)n_prob * grid * kRecWords * sizeof(float));
+    *off_entries = o;
+    o = align256(o + (size_t)grid * 6 * (*cap) * sizeof(float));
+    return o;
+}
+
+static int batch_chunk(const upslam_batch_tiles *tiles) { return tiles ? tiles->chunk : 512; }
+static int batch_threads(const upslam_batch_tiles *tiles) { return tiles ? tiles->threads : 512; }
+
+extern "C" size_t upslam_icp_batched_workspace_bytes(const upslam_keyframe *kfs, int32_t n_kf, int32_t n_hyp,
+                                                     const upslam_batch_tiles *tiles) {
+    if (!kfs || n_kf <= 0 || n_hyp <= 0) return 0;
+    size_t a, r, e, cap;
+    return batch_ws_layout(kfs, n_kf, n_kf * n_hyp, upslam_sm_count(), batch_chunk(tiles), &a, &r, &e, &cap);
+}
+
+extern "C" upslam_status upslam_icp_batched(const upslam_keyframe *d_kfs, const upslam_keyframe *kfs, int32_t n_kf,
+                                            const upslam_sweep *sw, int32_t n_hyp, double *d_poses,
+                                            const upslam_icp_params *ip, upslam_icp_stats *d_stats, void *d_ws,
+                                            size_t ws_bytes, const upslam_batch_tiles *tiles, void *stream) {
+    if (!d_kfs || !kfs || n_kf <= 0 || n_kf > kBatchMaxKf || n_hyp <= 0 || !sw || !d_poses || !ip || !d_stats ||
+        !d_ws)
+        return UPSLAM_ERR_INVALID_ARG;
+    const int n_prob = n_kf * n_hyp;
+    if (n_prob > kBatchMaxProblems) return UPSLAM_ERR_CAPACITY;
+    if (!upslam_pano_ok(&sw->pano) || !sw->d_pix || !sw->d_nrm || !upslam_aligned(sw->d_pix, 16) ||
+        (sw->nrm_precision != UPSLAM_F32 && sw->nrm_precision != UPSLAM_F16))
+        return UPSLAM_ERR_INVALID_ARG;
+    for (int i = 0; i < n_kf; ++i) {
+        const upslam_keyframe &K = kfs[i];
+        if (!upslam_pano_ok(&K.pano) || !K.d_depth || !K.d_nw || !K.d_dirs ||
+            (K.precision != UPSLAM_F32 && K.precision != UPSLAM_F16))
+            return UPSLAM_ERR_INVALID_ARG;
+    }
+    const int threads = batch_threads(tiles), chunk = batch_chunk(tiles);
+    if ((threads != 256 && threads != 512) || chunk < threads || chunk % threads) return UPSLAM_ERR_INVALID_ARG;
+    if (!(ip->d_max > 0.0f) || ip->max_iters < 1 || !upslam_aligned(d_ws, 256)) return UPSLAM_ERR_INVALID_ARG;
+    int dev = 0, coop = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (!coop) return UPSLAM_ERR_UNSUPPORTED;
+    const int grid = upslam_sm_count();
+    size_t off_active, off_records, off_entries, cap;
+    const size_t need = batch_ws_layout(kfs, n_kf, n_prob, grid, chunk, &off_active, &off_records, &off_entries, &cap);
+    if (ws_bytes < need) return UPSLAM_ERR_INVALID_ARG;
+    const size_t dyn = (size_t)n_prob * (kRecWords + 12) * sizeof(float) + (size_t)n_prob * sizeof(int);
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, icp_batched_kernel) != cudaSuccess) return UPSLAM_ERR_CUDA;
+    if ((int)(dyn + fa.sharedSizeBytes) > optin) return UPSLAM_ERR_CAPACITY;
+    if (cudaFuncSetAttribute(icp_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             optin - (int)fa.sharedSizeBytes) != cudaSuccess)
+        return UPSLAM_ERR_UNSUPPORTED;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, icp_batched_kernel, threads, dyn) != cudaSuccess ||
+        per_sm < 1)
+        return UPSLAM_ERR_UNSUPPORTED;
+    char *ws = reinterpret_cast<char *>(d_ws);
+    // control block: valid counter must start at zero each call (arrivals are monotonic)
+    if (cudaMemsetAsync(ws + offsetof(BatchCtrl, valid), 0, sizeof(int), (cudaStream_t)stream) != cudaSuccess)
+        return UPSLAM_ERR_CUDA;
+    BatchArgs a;
+    a.kfs = d_kfs;
+    a.n_kf = n_kf;
+    a.n_hyp = n_hyp;
+    a.n_prob = n_prob;
+    a.sp = sw->pano;
+    a.spix = reinterpret_cast<const float4 *>(sw->d_pix);
+    a.snrm = sw->d_nrm;
+    a.sprec = sw->nrm_precision;
+    a.d_max2 = ip->d_max * ip->d_max;
+    a.cos_min = ip->cos_theta_max;
+    a.poses = d_poses;
+    a.stats = d_stats;
+    a.active = reinterpret_cast<int *>(ws + off_active);
+    a.entries = reinterpret_cast<float *>(ws + off_entries);
+    a.cta_cap = (long long)cap;
+    a.records = reinterpret_cast<float *>(ws + off_records);
+    a.ctrl = reinterpret_cast<BatchCtrl *>(ws);
+    a.ip = *ip;
+    a.chunk = chunk;
+    void *args[] = {&a};
+    if (cudaLaunchCooperativeKernel((const void *)icp_batched_kernel, dim3(grid), dim3(threads), args, dyn,
+                                    (cudaStream_t)stream) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return UPSLAM_ERR_CUDA;
+    }
+    return UPSLAM_OK;
+}

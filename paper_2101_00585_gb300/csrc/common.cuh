@@ -334,6 +334,121 @@ __device__ __forceinline__ void kadd(float &s, float &c, float v) {
     s = t;
 }
 
+// Lane of the upper-triangle element (i, k), i <= k, in row-major order (0..20).
+__device__ __forceinline__ int uidx(int i, int k) { return i * 6 - (i * (i - 1)) / 2 + (k - i); }
+
+// FP64 solve of A xi = -b by the square-root-free Cholesky factorisation
+// A = L D L^T, spread over the lanes of one warp: lanes 0..20 hold the upper
+// triangle of A (lane uidx(i, k)), lanes 21..26 the right-hand side.  Each
+// elimination step is a handful of warp-wide FP64 instructions (GB300 issues
+// FP64 at a low rate per instruction, so independent work goes across lanes,
+// not into more instructions).  Every lane returns the same xi.  False when a
+// pivot D_j <= pivot_eps * max diagonal.
+__device__ __forceinline__ bool warp_solve6(const double *tot, double pivot_eps, double xi[6]) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const bool is_u = lane < 21, is_y = lane >= 21 && lane < 27;
+    int li = -1, lk = -1;
+    if (is_u) {
+        int i = 0, rem = lane;
+        while (rem >= 6 - i) {
+            rem -= 6 - i;
+            ++i;
+        }
+        li = i;
+        lk = i + rem;
+    } else if (is_y) {
+        li = lane - 21;
+        lk = 6;
+    }
+    double u = is_u ? tot[lane] : (is_y ? -tot[lane] : 0.0);
+    double dmax = tot[0];
+#pragma unroll
+    for (int i = 1; i < 6; ++i) dmax = fmax(dmax, tot[uidx(i, i)]);
+    if (!(dmax > 0.0)) return false;
+    const double lim = pivot_eps * dmax;
+    double r[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        const double d = __shfl_sync(full, u, uidx(j, j));
+        if (!(d > lim) || !(d > 1e-300)) return false;
+        r[j] = rcp64(d);
+        const bool act = li > j;
+        const int src_l = act ? uidx(j, li) : lane;
+        const int src_k = act ? (is_u ? uidx(j, lk) : 21 + j) : lane;
+        const double ujl = __shfl_sync(full, u, src_l);
+        const double ujk = __shfl_sync(full, u, src_k);
+        if (act) u = fma(-(ujl * r[j]), ujk, u);
+    }
+#pragma unroll
+    for (int i = 5; i >= 0; --i) {
+        const double x = __shfl_sync(full, u, 21 + i) * r[i];
+        xi[i] = x;
+        const bool act = is_y && li < i;
+        const double umi = __shfl_sync(full, u, act ? uidx(li, i) : lane);
+        if (act) u = fma(-umi, x, u);
+    }
+    return true;
+}
+
+// T <- exp(xi^) T on one warp: lanes 0..2 evaluate the coefficients A, B, C;
+// lanes 0..8 the rotation R = I + A W + B W^2 and lanes 9..17 V = I + B W + C W^2
+// (one matrix entry each); lanes 0..11 then each compose one entry of [R T | R t + V v].
+// T lives in shared memory (12 doubles) and is updated in place; xi is the same in every lane.
+__device__ __forceinline__ void warp_se3_update(const double xi[6], double *T) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const double w0 = xi[0], w1 = xi[1], w2 = xi[2];
+    const double th2 = fma(w0, w0, fma(w1, w1, w2 * w2));
+    double coef;
+    if (th2 <= 0.0625) {
+        // Taylor series in th2 of sin(t)/t, (1 - cos t)/t^2, (t - sin t)/t^3, one per lane
+        const int c = lane < 3 ? lane : 0;
+        const double k0 = c == 0 ? 1.0 : (c == 1 ? 0.5 : 1.0 / 6.0);
+        const double k1 = c == 0 ? -1.0 / 6.0 : (c == 1 ? -1.0 / 24.0 : -1.0 / 120.0);
+        const double k2 = c == 0 ? 1.0 / 120.0 : (c == 1 ? 1.0 / 720.0 : 1.0 / 5040.0);
+        const double k3 = c == 0 ? -1.0 / 5040.0 : (c == 1 ? -1.0 / 40320.0 : -1.0 / 362880.0);
+        const double k4 = c == 0 ? 1.0 / 362880.0 : (c == 1 ? 1.0 / 3628800.0 : 1.0 / 39916800.0);
+        const double k5 = c == 0 ? -1.0 / 39916800.0 : (c == 1 ? -1.0 / 479001600.0 : -1.0 / 6227020800.0);
+        const double k6 = c == 0 ? 1.0 / 6227020800.0 : (c == 1 ? 1.0 / 87178291200.0 : 1.0 / 1307674368000.0);
+        coef = fma(th2, fma(th2, fma(th2, fma(th2, fma(th2, fma(th2, k6, k5), k4), k3), k2), k1), k0);
+    } else {
+        double A, B, C;
+        se3_coeffs(th2, A, B, C);
+        coef = lane == 0 ? A : (lane == 1 ? B : C);
+    }
+    const double A = __shfl_sync(full, coef, 0), B = __shfl_sync(full, coef, 1), C = __shfl_sync(full, coef, 2);
+    // one entry of R (lanes 0..8) or V (lanes 9..17)
+    const int e = lane < 9 ? lane : (lane < 18 ? lane - 9 : 0);
+    const int ei = e / 3, ek = e - 3 * (e / 3);
+    const double om_i = ei == 0 ? w0 : (ei == 1 ? w1 : w2);
+    const double om_k = ek == 0 ? w0 : (ek == 1 ? w1 : w2);
+    // W = [omega]_x: W[i][k] = -eps_ikl omega_l
+    double Wik = 0.0;
+    if (ei == 0 && ek == 1) Wik = -w2;
+    if (ei == 0 && ek == 2) Wik = w1;
+    if (ei == 1 && ek == 0) Wik = w2;
+    if (ei == 1 && ek == 2) Wik = -w0;
+    if (ei == 2 && ek == 0) Wik = -w1;
+    if (ei == 2 && ek == 1) Wik = w0;
+    const double delta = ei == ek ? 1.0 : 0.0;
+    const double W2 = fma(om_i, om_k, -delta * th2);
+    const double c1 = lane < 9 ? A : B, c2 = lane < 9 ? B : C;
+    const double ent = fma(c1, Wik, fma(c2, W2, delta));
+    // compose: lane e < 12 owns output (i, j), i = e / 4, j = e % 4
+    const int oi = lane < 12 ? lane / 4 : 0, oj = lane < 12 ? lane % 4 : 0;
+    const double R0 = __shfl_sync(full, ent, 3 * oi), R1 = __shfl_sync(full, ent, 3 * oi + 1),
+                 R2 = __shfl_sync(full, ent, 3 * oi + 2);
+    const double V0 = __shfl_sync(full, ent, 9 + 3 * oi), V1 = __shfl_sync(full, ent, 9 + 3 * oi + 1),
+                 V2 = __shfl_sync(full, ent, 9 + 3 * oi + 2);
+    const double te = oj == 3 ? fma(V0, xi[3], fma(V1, xi[4], V2 * xi[5])) : 0.0;
+    const double T0 = T[oj], T1 = T[4 + oj], T2 = T[8 + oj];
+    const double out = fma(R0, T0, fma(R1, T1, fma(R2, T2, te)));
+    __syncwarp();
+    if (lane < 12) T[lane] = out;
+    __syncwarp();
+}
+
 // ----------------------------------------------------------------------------- keyframe update pieces
 
 // Everything one keyframe update reads and writes.
