@@ -322,6 +322,50 @@ upslam_status upslam_icp_batched(const upslam_keyframe *d_kfs, const upslam_keyf
                                  upslam_icp_stats *d_stats, void *d_ws, size_t ws_bytes,
                                  const upslam_batch_tiles *tiles, void *stream);
 
+/*
+ * Pose-proposal network (learned initial guess).  The paper has no learned
+ * component: it relies on a zero-velocity or zero-acceleration prior (Sec. IV-F
+ * footnote), and a large motion is left to the registration itself.  This
+ * network is a design addition that predicts the relative pose of a
+ * keyframe/sweep pair so ICP (Sec. III-B) can start near it; the caller gates
+ * the result by the ICP residual and falls back to the plain prior.
+ *
+ * Input: BF16 NHWC [batch][64][256][8]: keyframe (depth / scale, nx, ny, nz)
+ * then sweep (the same), each from upslam_downsample.  Output: FP32 [batch][6]
+ * xi = (omega, v), the keyframe-from-sweep pose as exp(xi^).
+ * Parameters: one FP32 array of upslam_cnn_param_count() values in the order
+ * w0 b0 w1 b1 w2 b2 w3 b3 wf bf (conv weights [C_out][3][3][C_in] for
+ * 8->32->64->128->128 channels, head wf [6][128]).  Convolutions run as BF16
+ * tensor-core GEMMs (mma.sync m16n8k16) with FP32 accumulation.
+ * d_ws: upslam_cnn_workspace_bytes(batch) bytes; it keeps the activations of
+ *   the last forward call, which upslam_cnn_backward reads.
+ */
+size_t upslam_cnn_param_count(void);
+size_t upslam_cnn_workspace_bytes(int32_t batch);
+upslam_status upslam_cnn_forward(const float *d_params, const void *d_x, int32_t batch, float *d_out, void *d_ws,
+                                 size_t ws_bytes, void *stream);
+/* Loss sum_b sum_i w_i (out - target)^2 / batch into *d_loss and every parameter's gradient into d_grads
+ * (overwritten), for the activations of the preceding upslam_cnn_forward on the same workspace. */
+upslam_status upslam_cnn_backward(const float *d_params, const void *d_x, int32_t batch, const float *d_out,
+                                  const float *d_target, const float *d_wloss6, float *d_grads, float *d_loss,
+                                  void *d_ws, size_t ws_bytes, void *stream);
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8, bias-corrected for step >= 1) on the FP32 master parameters. */
+upslam_status upslam_cnn_adam(float *d_params, const float *d_grads, float *d_m, float *d_v, int32_t step, float lr,
+                              void *stream);
+/*
+ * Downsample a panorama to out_rows x out_cols cells (rows and cols must
+ * divide evenly): per cell the mean over pixels holding a sample of
+ * (depth / depth_scale, nx, ny, nz), zeros where none, written as BF16 to
+ * d_out[cell * c_stride + c_off + 0..3].  d_nrm: float4 or half4
+ * (nx, ny, nz, w-or-valid).
+ */
+upslam_status upslam_downsample(const float *d_depth, const void *d_nrm, int32_t precision, const upslam_pano *pp,
+                                int32_t out_rows, int32_t out_cols, float depth_scale, void *d_out, int32_t c_stride,
+                                int32_t c_off, void *stream);
+
+/* Poses exp(xi^) (FP64 [n][12], row-major [R | t]) of n FP32 twists xi = (omega, v), e.g. network outputs. */
+upslam_status upslam_se3_exp(const float *d_xi, int32_t n, double *d_poses, void *stream);
+
 /* Human-readable name of a status code (static storage). */
 const char *upslam_status_string(upslam_status s);
 

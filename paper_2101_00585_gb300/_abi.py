@@ -86,6 +86,15 @@ SIGNATURES = {
                                                              _P(BatchTiles)]),
     "upslam_icp_batched": (ctypes.c_int, [_vp, _P(Keyframe), ctypes.c_int32, _P(Sweep), ctypes.c_int32, _vp,
                                           _P(IcpParams), _vp, _vp, ctypes.c_size_t, _P(BatchTiles), _vp]),
+    "upslam_cnn_param_count": (ctypes.c_size_t, []),
+    "upslam_cnn_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int32]),
+    "upslam_cnn_forward": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, _vp, _vp, ctypes.c_size_t, _vp]),
+    "upslam_cnn_backward": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_size_t,
+                                           _vp]),
+    "upslam_cnn_adam": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_int32, ctypes.c_float, _vp]),
+    "upslam_downsample": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, _P(Pano), ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.c_float, _vp, ctypes.c_int32, ctypes.c_int32, _vp]),
+    "upslam_se3_exp": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, _vp]),
     "upslam_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "upslam_version": (ctypes.c_char_p, []),
 }

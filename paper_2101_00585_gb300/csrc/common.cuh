@@ -6,6 +6,7 @@
 // and every projective correspondence, is a bit-exact function of the inputs.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>

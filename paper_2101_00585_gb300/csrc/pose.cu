@@ -68,3 +68,24 @@ extern "C" upslam_status upslam_update_motion(const double *d_T_prev, const doub
     UPSLAM_CHECK_LAUNCH();
     return UPSLAM_OK;
 }
+
+namespace upslam {
+
+__global__ void se3_exp_batch_kernel(const float *xi, int n, double *poses) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double x[6], T[12] = {1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0};
+    for (int k = 0; k < 6; ++k) x[k] = (double)xi[6 * i + k];
+    se3_exp_left(x, T);
+    for (int k = 0; k < 12; ++k) poses[12 * i + k] = T[k];
+}
+
+}  // namespace upslam
+
+extern "C" upslam_status upslam_se3_exp(const float *d_xi, int32_t n, double *d_poses, void *stream) {
+    if (!d_xi || !d_poses || n < 0) return UPSLAM_ERR_INVALID_ARG;
+    if (n == 0) return UPSLAM_OK;
+    se3_exp_batch_kernel<<<(n + 127) / 128, 128, 0, (cudaStream_t)stream>>>(d_xi, n, d_poses);
+    UPSLAM_CHECK_LAUNCH();
+    return UPSLAM_OK;
+}
