@@ -53,8 +53,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["tunnel", "campus", "forest-batch"], default="tunnel",
-                    help="tunnel: the headline line; campus: the FP16 precision form; forest-batch: the batched form")
+    ap.add_argument("--workload", choices=["tunnel", "campus", "forest-batch", "learned"], default="tunnel",
+                    help="tunnel: the headline line; campus: the FP16 precision form; forest-batch: the batched "
+                         "form; learned: train the pose proposal and evaluate learned vs plain initialisation")
+    ap.add_argument("--train-pairs", type=int, default=200000)
+    ap.add_argument("--eval-pairs", type=int, default=5000)
+    ap.add_argument("--epochs", type=int, default=8)
     ap.add_argument("--e2e-steps", type=int, default=300)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-graph", action="store_true", help="launch eagerly instead of replaying a CUDA graph")
@@ -628,11 +632,51 @@ def run_forest_batch(args, local):
             "within_2cm_0.1deg": int(ok), "problems": batch.n_prob}
 
 
+def run_learned(args, local):
+    """Learned-proposal form: train on pairs the plain pipeline makes, then learned + ICP vs plain + ICP."""
+    import torch
+    import paper_2101_00585_gb300 as up  # noqa: F401
+    from paper_2101_00585_gb300 import proposal
+    torch.cuda.set_device(local)
+    t0 = time.perf_counter()
+    x, xi, _ = proposal.make_pairs(args.train_pairs, seed=20210106)
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t0
+    net = proposal.PoseNet(256)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    hist = proposal.train(net, x, xi, epochs=args.epochs, lr=2e-3, seed=7, log=log)
+    b.record()
+    b.synchronize()
+    t_train = a.elapsed_time(b) * 1e-3
+    steps = args.epochs * (args.train_pairs // net.batch)
+    pairs_trained = steps * net.batch
+    flops = pairs_trained * 0.34e9  # forward 0.113 GFLOP + backward about twice that, per pair
+    del x
+    xt, xit, ext = proposal.make_pairs(args.eval_pairs, seed=20210107, keep_scans=True)
+    res = proposal.evaluate(net, xt, ext["motions"], ext["scans"])
+    peak = 1922.5
+    return {"metric": "learned-init vs plain-init ICP success within 2 cm / 0.1 deg (held-out pairs)",
+            "value": res["gated_success"] / res["pairs"], "unit": "fraction of pairs", "higher_is_better": True,
+            "plain_fraction": res["plain_success"] / res["pairs"], "learned_only_fraction":
+                res["learned_success"] / res["pairs"], "fallbacks": res["fallbacks"], "pairs": res["pairs"],
+            "plain_pairs_per_s": round(res["plain_pairs_per_s"], 1),
+            "gated_pairs_per_s": round(res["gated_pairs_per_s"], 1), "cnn_ms_per_pair": res["cnn_ms_per_pair"],
+            "train": {"pairs": args.train_pairs, "epochs": args.epochs, "batch": net.batch, "loss": hist,
+                      "seconds": round(t_train, 2), "pairs_per_s": round(pairs_trained / t_train, 1),
+                      "tflops": round(flops / t_train / 1e12, 2),
+                      "frac_of_bf16_peak": round(flops / t_train / 1e12 / peak, 5),
+                      "pair_generation_s": round(t_gen, 1)},
+            "dtype": "bf16 weights/activations, f32 accumulate", "data": "synthetic",
+            "config": {"workload": "tunnel/forest/road pairs, motion <= 1 m / 30 deg, 64x256 inputs"}}
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
     if args.impl == "ours" and args.workload != "tunnel":
-        out = run_campus(args, local) if args.workload == "campus" else run_forest_batch(args, local)
+        runner = {"campus": run_campus, "forest-batch": run_forest_batch, "learned": run_learned}[args.workload]
+        out = runner(args, local)
         print(json.dumps(out), flush=True)
         return
     if args.impl == "reference":

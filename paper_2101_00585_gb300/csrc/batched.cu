@@ -52,6 +52,7 @@ struct BatchArgs {
     double *poses;            // [n_prob][12] in/out
     upslam_icp_stats *stats;  // [n_prob]
     int *active;              // [n_prob] workspace flags
+    float *poses_f;           // [n_prob][12] FP32 copies written by each problem's owner
     float *entries;           // per-CTA entry regions
     long long cta_cap;        // entries per CTA region
     float *records;           // [n_prob][grid][kRecWords]
@@ -287,7 +288,10 @@ __global__ void __launch_bounds__(512, 1) icp_batched_kernel(BatchArgs a) {
                     conv = (wn2 < a.ip.eps_rot * a.ip.eps_rot && vn2 < a.ip.eps_trans * a.ip.eps_trans) ? 1 : 0;
                 }
                 upslam_icp_stats *st = a.stats + p;
-                if (lane < 12) a.poses[(size_t)p * 12 + lane] = Tsh[0][lane];
+                if (lane < 12) {
+                    a.poses[(size_t)p * 12 + lane] = Tsh[0][lane];
+                    a.poses_f[(size_t)p * 12 + lane] = (float)Tsh[0][lane];
+                }
                 if (lane < 21) st->A[lane] = tot[lane];
                 else if (lane < 27) st->b[lane - 21] = tot[lane];
                 if (lane < 6) st->xi[lane] = xi[lane];
@@ -321,7 +325,8 @@ __global__ void __launch_bounds__(512, 1) icp_batched_kernel(BatchArgs a) {
             act[p] = still;
             if (still) {
                 any_active = 1;
-                for (int i = 0; i < 12; ++i) pose_f[p * 12 + i] = (float)__ldcg(a.poses + (size_t)p * 12 + i);
+                // the owner's FP32 copy: no FP64 conversion here (slow on GB300)
+                for (int i = 0; i < 12; ++i) pose_f[p * 12 + i] = __ldcg(a.poses_f + (size_t)p * 12 + i);
             }
         }
         __syncthreads();
@@ -350,11 +355,14 @@ static size_t batch_region_entries(const upslam_keyframe *kfs, int32_t n_kf, int
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 static size_t batch_ws_layout(const upslam_keyframe *kfs, int32_t n_kf, int32_t n_prob, int grid, int chunk,
-                              size_t *off_active, size_t *off_records, size_t *off_entries, size_t *cap) {
+                              size_t *off_active, size_t *off_records, size_t *off_entries, size_t *cap,
+                              size_t *off_posef = nullptr) {
     *cap = batch_region_entries(kfs, n_kf, grid, chunk);
     size_t o = 256;  // control block
     *off_active = o;
     o = align256(o + (size_t)n_prob * sizeof(int));
+    if (off_posef) *off_posef = o;
+    o = align256(o + (size_t)n_prob * 12 * sizeof(float));
     *off_records = o;
     o = align256(o + (size_t)n_prob * grid * kRecWords * sizeof(float));
     *off_entries = o;
@@ -399,8 +407,9 @@ extern "C" upslam_status upslam_icp_batched(const upslam_keyframe *d_kfs, const 
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (!coop) return UPSLAM_ERR_UNSUPPORTED;
     const int grid = upslam_sm_count();
-    size_t off_active, off_records, off_entries, cap;
-    const size_t need = batch_ws_layout(kfs, n_kf, n_prob, grid, chunk, &off_active, &off_records, &off_entries, &cap);
+    size_t off_active, off_records, off_entries, cap, off_posef;
+    const size_t need =
+        batch_ws_layout(kfs, n_kf, n_prob, grid, chunk, &off_active, &off_records, &off_entries, &cap, &off_posef);
     if (ws_bytes < need) return UPSLAM_ERR_INVALID_ARG;
     const size_t dyn = (size_t)n_prob * (kRecWords + 12) * sizeof(float) + (size_t)n_prob * sizeof(int);
     cudaFuncAttributes fa;
@@ -431,6 +440,7 @@ extern "C" upslam_status upslam_icp_batched(const upslam_keyframe *d_kfs, const 
     a.poses = d_poses;
     a.stats = d_stats;
     a.active = reinterpret_cast<int *>(ws + off_active);
+    a.poses_f = reinterpret_cast<float *>(ws + off_posef);
     a.entries = reinterpret_cast<float *>(ws + off_entries);
     a.cta_cap = (long long)cap;
     a.records = reinterpret_cast<float *>(ws + off_records);

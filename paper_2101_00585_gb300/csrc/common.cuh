@@ -79,6 +79,21 @@ __device__ __forceinline__ PoseF pose_to_f32(const double *T) {
     return p;
 }
 
+// The CTA's pose in FP32, converted once: threads 0..11 convert one entry each
+// into shared memory and every thread reads the FP32 copy.  (An FP64 -> FP32
+// conversion issues on GB300's FP64 pipe; converting per thread would cost
+// every warp twelve slow instructions.)  Must be reached by the whole CTA.
+__device__ __forceinline__ PoseF cta_pose_f32(const double *T, bool through_l2 = false) {
+    __shared__ float ps[12];
+    __syncthreads();
+    if (threadIdx.x < 12) ps[threadIdx.x] = (float)(through_l2 ? __ldcg(T + threadIdx.x) : T[threadIdx.x]);
+    __syncthreads();
+    PoseF p;
+#pragma unroll
+    for (int i = 0; i < 12; ++i) p.r[i] = ps[i];
+    return p;
+}
+
 // Pose read through L2 only (never a stale L1 line): for poses other CTAs rewrite.
 __device__ __forceinline__ PoseF pose_to_f32_cg(const double *T) {
     PoseF p;

@@ -26,16 +26,24 @@
 
 namespace upslam {
 
+// Registration accepted?  Decided by one thread per CTA (in FP32, off the FP64 pipe) and broadcast.
 __device__ __forceinline__ bool accepted(const upslam_icp_stats *st, float accept) {
-    if (!st) return true;
-    if (st->status != UPSLAM_OK) return false;
-    const long long valid = st->valid;
-    return valid > 0 && (double)st->inliers >= (double)accept * (double)valid;
+    __shared__ int ok;
+    if (threadIdx.x == 0) {
+        if (!st) {
+            ok = 1;
+        } else {
+            const long long valid = st->valid;
+            ok = st->status == UPSLAM_OK && valid > 0 && (float)st->inliers >= accept * (float)valid;
+        }
+    }
+    __syncthreads();
+    return ok != 0;
 }
 
 __global__ void __launch_bounds__(256) fuse_main_kernel(FuseView f, const double *pose, upslam_icp_stats *st, int gk) {
     if (!accepted(st, f.accept)) return;
-    const PoseF T = pose_to_f32(pose);
+    const PoseF T = cta_pose_f32(pose);
     if ((int)blockIdx.x < gk) {
         // averaging: each thread takes 4 pixels a CTA-width apart, issuing their keyframe loads together
         constexpr int kB = 4;
@@ -77,7 +85,7 @@ __global__ void __launch_bounds__(256) fuse_main_kernel(FuseView f, const double
 
 __global__ void __launch_bounds__(256) fuse_fill_kernel(FuseView f, const double *pose, upslam_icp_stats *st) {
     if (!accepted(st, f.accept)) return;
-    const PoseF T = pose_to_f32(pose);
+    const PoseF T = cta_pose_f32(pose);
     const int ns = f.sp.rows * f.sp.cols;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < ns; j += gridDim.x * blockDim.x) {
         int k;

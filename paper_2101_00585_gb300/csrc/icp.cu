@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(kIcpThreads) icp_step_kernel(IcpArgs a, double
     __shared__ int shi[kIcpWarps][2];
     __shared__ double tot[32];
     __shared__ int last;
-    const PoseF T = pose_to_f32_cg(pose);
+    const PoseF T = cta_pose_f32(pose, true);
     float acc[28];
 #pragma unroll
     for (int i = 0; i < 28; ++i) acc[i] = 0.0f;
@@ -418,6 +418,8 @@ __global__ void __launch_bounds__(kTileThreads, 1)
     __shared__ double tot[32];
     __shared__ double Tsh[12];
     __shared__ double Tprev[12], Tmot[12];
+    __shared__ float Tf[12];
+    __shared__ int acc_ok_s;
     __shared__ double xi_sh[6];
     __shared__ int wcnt[kTileWarps];
     __shared__ int base_s, spill_s, flag, status_s, conv_s, valid_s;
@@ -508,9 +510,12 @@ __global__ void __launch_bounds__(kTileThreads, 1)
 
     int it = 0;
     for (; it < ip.max_iters; ++it) {
+        // the pose in FP32: converted once per CTA (FP64 conversions are slow on GB300), read by all
+        if (threadIdx.x < 12) Tf[threadIdx.x] = (float)Tsh[threadIdx.x];
+        __syncthreads();
         PoseF T;
 #pragma unroll
-        for (int i = 0; i < 12; ++i) T.r[i] = (float)Tsh[i];
+        for (int i = 0; i < 12; ++i) T.r[i] = Tf[i];
         float acc[28];
 #pragma unroll
         for (int i = 0; i < 28; ++i) acc[i] = 0.0f;
@@ -581,11 +586,16 @@ __global__ void __launch_bounds__(kTileThreads, 1)
     // registration quality: every CTA holds the same totals, so all take the same decision.
     int accepted_flag = 0;
     if (fuse_on) {
-        const bool acc_ok = status_s == UPSLAM_OK && valid_s > 0 && tot[28] >= (double)fz.accept * (double)valid_s;
+        if (threadIdx.x == 0) {
+            acc_ok_s = status_s == UPSLAM_OK && valid_s > 0 && (float)tot[28] >= fz.accept * (float)valid_s;
+        }
+        if (threadIdx.x < 12) Tf[threadIdx.x] = (float)Tsh[threadIdx.x];
+        __syncthreads();
+        const bool acc_ok = acc_ok_s != 0;
         accepted_flag = acc_ok ? 1 : 0;
         PoseF T;
 #pragma unroll
-        for (int i = 0; i < 12; ++i) T.r[i] = (float)Tsh[i];
+        for (int i = 0; i < 12; ++i) T.r[i] = Tf[i];
         const int ns = fz.sp.rows * fz.sp.cols;
         if (acc_ok) {
             // average the staged samples straight from shared memory, spilled chunks from global memory

@@ -37,7 +37,7 @@ template <bool kPose>
 __global__ void __launch_bounds__(256) project_kernel(const float4 *__restrict__ pts, int n, const double *pose,
                                                       upslam_pano pp, unsigned long long *__restrict__ zbuf) {
     PoseF T;
-    if (kPose) T = pose_to_f32(pose);
+    if (kPose) T = cta_pose_f32(pose);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const float4 p = __ldg(pts + i);
         if (p.w == 0.0f) continue;

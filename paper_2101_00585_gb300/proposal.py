@@ -282,7 +282,7 @@ def train(net: PoseNet, x: torch.Tensor, xi: torch.Tensor, epochs: int = 3, lr: 
 
 
 def evaluate(net: PoseNet, x: torch.Tensor, motions: list, scans, params: Params = Params(),
-             gate_rms: float = 0.05, gate_quality: float = 0.5, tol_m: float = 0.02, tol_deg: float = 0.1) -> dict:
+             gate_rms: float = 0.05, gate_quality: float = 0.2, tol_m: float = 0.02, tol_deg: float = 0.1) -> dict:
     """Plain init + ICP against learned init + ICP (gated, with plain fallback) on held-out pairs.
 
     Success: final pose within tol_m and tol_deg of the true motion.  The gate accepts the learned start's result
