@@ -337,8 +337,10 @@ upslam_status upslam_icp_batched(const upslam_keyframe *d_kfs, const upslam_keyf
  * w0 b0 w1 b1 w2 b2 w3 b3 wf bf (conv weights [C_out][3][3][C_in] for
  * 8->32->64->128->128 channels, head wf [6][128]).  Convolutions run as BF16
  * tensor-core GEMMs (mma.sync m16n8k16) with FP32 accumulation.
- * d_ws: upslam_cnn_workspace_bytes(batch) bytes; it keeps the activations of
- *   the last forward call, which upslam_cnn_backward reads.
+ * d_ws: upslam_cnn_workspace_bytes(batch) bytes, 256-byte aligned; it keeps
+ *   the activations of the last forward call, which upslam_cnn_backward reads.
+ * d_x must be 16-byte aligned.  A null pointer, batch <= 0, a short or
+ * misaligned workspace returns UPSLAM_ERR_INVALID_ARG before any launch.
  */
 size_t upslam_cnn_param_count(void);
 size_t upslam_cnn_workspace_bytes(int32_t batch);

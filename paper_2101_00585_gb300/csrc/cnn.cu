@@ -82,6 +82,15 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(GemmArgs g) {
                 if (m < g.M) v = *reinterpret_cast<const uint4 *>(g.A + (long long)m * g.sam + k0 + c8);
                 *reinterpret_cast<uint4 *>(&As[r][c8]) = v;
             }
+        } else if (g.sam == 1 && (g.sak % 8) == 0 && m0 + BM <= g.M && k0 + BK <= kend) {
+            // M contiguous: 8 consecutive rows of one column per 16-byte load, transposed into the tile
+            for (int i = tid; i < (BM / 8) * BK; i += 128) {
+                const int c = i / (BM / 8), r8 = (i % (BM / 8)) * 8;
+                const uint4 v = *reinterpret_cast<const uint4 *>(g.A + (long long)(k0 + c) * g.sak + m0 + r8);
+                const __nv_bfloat16 *e = reinterpret_cast<const __nv_bfloat16 *>(&v);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) As[r8 + q][c] = e[q];
+            }
         } else {
             for (int i = tid; i < BM * BK; i += 128) {
                 const int r = i / BK, c = i % BK;
@@ -96,6 +105,15 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(GemmArgs g) {
                 uint4 v = make_uint4(0, 0, 0, 0);
                 if (n < g.N) v = *reinterpret_cast<const uint4 *>(g.B + (long long)n * g.sbn + k0 + c8);
                 *reinterpret_cast<uint4 *>(&Bs[r][c8]) = v;
+            }
+        } else if (g.sbn == 1 && (g.sbk % 8) == 0 && n0 + BN <= g.N && k0 + BK <= kend) {
+            // N contiguous: 8 consecutive columns of one k per 16-byte load, transposed into the tile
+            for (int i = tid; i < (BN / 8) * BK; i += 128) {
+                const int c = i / (BN / 8), r8 = (i % (BN / 8)) * 8;
+                const uint4 v = *reinterpret_cast<const uint4 *>(g.B + (long long)(k0 + c) * g.sbk + n0 + r8);
+                const __nv_bfloat16 *e = reinterpret_cast<const __nv_bfloat16 *>(&v);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) Bs[r8 + q][c] = e[q];
             }
         } else {
             for (int i = tid; i < BN * BK; i += 128) {
@@ -467,7 +485,7 @@ extern "C" upslam_status upslam_cnn_backward(const float *d_params, const void *
                                              float *d_grads, float *d_loss, void *d_ws, size_t ws_bytes,
                                              void *stream) {
     if (!d_params || !d_x || !d_out || !d_target || !d_wloss6 || !d_grads || !d_loss || !d_ws || batch <= 0 ||
-        ws_bytes < upslam_cnn_workspace_bytes(batch))
+        !upslam_aligned(d_ws, 256) || !upslam_aligned(d_x, 16) || ws_bytes < upslam_cnn_workspace_bytes(batch))
         return UPSLAM_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     CnnWs w;
