@@ -61,22 +61,6 @@ struct BatchArgs {
     int chunk;  // pixels per chunk (a multiple of blockDim)
 };
 
-// Lane L ends with the sum over the warp's lanes of v[L] (32 values per lane).
-__device__ __forceinline__ float warp_reduce_scatter(float v[32]) {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) {
-        const bool upper = (lane & o) != 0;
-#pragma unroll
-        for (int i = 0; i < o; ++i) {
-            const float send = upper ? v[i] : v[i + o];
-            const float keep = upper ? v[i + o] : v[i];
-            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
-        }
-    }
-    return v[0];
-}
-
 __device__ __forceinline__ bool grid_wait(BatchCtrl *ctrl, unsigned long long target) {
     const long long t0 = clock64();
     while (*((volatile unsigned long long *)&ctrl->arrive) < target) {
@@ -283,9 +267,7 @@ __global__ void __launch_bounds__(512, 1) icp_batched_kernel(BatchArgs a) {
                     for (int i = 0; i < 6; ++i) xi[i] = 0.0;
                 } else {
                     warp_se3_update(xi, Tsh[0]);
-                    const double wn2 = fma(xi[0], xi[0], fma(xi[1], xi[1], xi[2] * xi[2]));
-                    const double vn2 = fma(xi[3], xi[3], fma(xi[4], xi[4], xi[5] * xi[5]));
-                    conv = (wn2 < a.ip.eps_rot * a.ip.eps_rot && vn2 < a.ip.eps_trans * a.ip.eps_trans) ? 1 : 0;
+                    conv = warp_converged(xi, a.ip.eps_rot * a.ip.eps_rot, a.ip.eps_trans * a.ip.eps_trans) ? 1 : 0;
                 }
                 upslam_icp_stats *st = a.stats + p;
                 if (lane < 12) {

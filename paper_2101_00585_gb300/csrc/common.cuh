@@ -172,10 +172,21 @@ __device__ __forceinline__ void store_nw(void *base, int64_t k, int precision, f
 
 // ----------------------------------------------------------------------------- reductions
 
-__device__ __forceinline__ float warp_sum(float v) {
+// Warp reduce-scatter: lane L ends with the sum over the warp's lanes of v[L]
+// (32 values per lane, 31 shuffles in all; v is overwritten).
+__device__ __forceinline__ float warp_reduce_scatter(float v[32]) {
+    const int lane = threadIdx.x & 31;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
+    for (int o = 16; o >= 1; o >>= 1) {
+        const bool upper = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < o; ++i) {
+            const float send = upper ? v[i] : v[i + o];
+            const float keep = upper ? v[i + o] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    return v[0];
 }
 
 // ----------------------------------------------------------------------------- FP64 solve
@@ -185,12 +196,30 @@ __device__ __forceinline__ float warp_sum(float v) {
 // solve is written for a short dependency chain: fully unrolled (every value
 // in a register), no FP64 division or square root on the critical path.
 
-// 1/d for a positive normal d: FP32 seed, one FP64 Newton step (relative error
-// about 2^-46, far below the FP32 accumulation error of the normal equations).
+// FP64 helpers that stay off the FP64 pipe.  Comparisons, maxima, sign flips
+// and format changes work on the bit patterns with integer instructions: for
+// doubles that are not NaN, the signed 64-bit order of the bit patterns of
+// non-negative values is their numeric order.
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+__device__ __forceinline__ bool dfinite(double x) { return ((__double2hiint(x) >> 20) & 0x7ff) != 0x7ff; }
+__device__ __forceinline__ double dneg(double x) {
+    return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ull);
+}
+
+// 1/d for a positive d.  The FP32 seed is d's exponent and top 23 mantissa bits
+// (truncation: relative error below 2^-23), formed and widened back with integer
+// instructions; one FP64 Newton step then leaves a relative error below 2^-44,
+// far below the FP32 accumulation error of the normal equations.  d outside
+// [2^-126, 2^126) takes an FP64 division.
 __device__ __forceinline__ double rcp64(double d) {
-    double x = (double)__frcp_rn((float)d);
-    const double e = fma(-d, x, 1.0);
-    return fma(x, e, x);
+    const int hi = __double2hiint(d), lo = __double2loint(d);
+    const int e = ((hi >> 20) & 0x7ff) - (1023 - 127);
+    if (hi < 0 || e < 1 || e > 252) return 1.0 / d;
+    const float f = __int_as_float((e << 23) | ((hi & 0xfffff) << 3) | (int)((unsigned)lo >> 29));
+    const int rb = __float_as_int(__frcp_rn(f));  // normal: f in [2^-126, 2^126)
+    const int m = rb & 0x7fffff;
+    const double x = __hiloint2double((((rb >> 23) & 0xff) + (1023 - 127)) << 20 | (m >> 3), m << 29);
+    return fma(x, fma(-d, x, 1.0), x);
 }
 
 // sin(t)/t, (1 - cos t)/t^2, (t - sin t)/t^3 from t^2: Taylor series (truncation
@@ -355,11 +384,14 @@ __device__ __forceinline__ int uidx(int i, int k) { return i * 6 - (i * (i - 1))
 
 // FP64 solve of A xi = -b by the square-root-free Cholesky factorisation
 // A = L D L^T, spread over the lanes of one warp: lanes 0..20 hold the upper
-// triangle of A (lane uidx(i, k)), lanes 21..26 the right-hand side.  Each
-// elimination step is a handful of warp-wide FP64 instructions (GB300 issues
-// FP64 at a low rate per instruction, so independent work goes across lanes,
-// not into more instructions).  Every lane returns the same xi.  False when a
-// pivot D_j <= pivot_eps * max diagonal.
+// triangle of A (lane uidx(i, k)), lanes 21..26 the right-hand side.  GB300
+// issues an FP64 warp instruction at a low rate whatever its active lanes, so
+// independent work goes across lanes, and pivot tests, maxima and reciprocal
+// seeds use integer instructions: per pivot the FP64 work is the two Newton
+// multiply-adds, one multiply and one multiply-add.  Back substitution first
+// scales every row by its reciprocal pivot (one instruction for all rows), then
+// takes one multiply-add per unknown.  Every lane returns the same xi.  False
+// when a pivot D_j <= max(pivot_eps * max diagonal, 1e-300) or is not finite.
 __device__ __forceinline__ bool warp_solve6(const double *tot, double pivot_eps, double xi[6]) {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -377,57 +409,85 @@ __device__ __forceinline__ bool warp_solve6(const double *tot, double pivot_eps,
         li = lane - 21;
         lk = 6;
     }
-    double u = is_u ? tot[lane] : (is_y ? -tot[lane] : 0.0);
-    double dmax = tot[0];
+    const double t = (is_u || is_y) ? tot[lane] : 0.0;
+    double u = is_y ? dneg(t) : t;
+    long long dm = dbits(tot[0]);
 #pragma unroll
-    for (int i = 1; i < 6; ++i) dmax = fmax(dmax, tot[uidx(i, i)]);
-    if (!(dmax > 0.0)) return false;
-    const double lim = pivot_eps * dmax;
-    double r[6];
+    for (int i = 1; i < 6; ++i) dm = max(dm, dbits(tot[uidx(i, i)]));
+    if (!(dm > 0) || !dfinite(__longlong_as_double(dm))) return false;
+    const long long lim = max(dbits(pivot_eps * __longlong_as_double(dm)), dbits(1e-300));
+    double rl = 0.0;  // reciprocal of this lane's row pivot
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
         const double d = __shfl_sync(full, u, uidx(j, j));
-        if (!(d > lim) || !(d > 1e-300)) return false;
-        r[j] = rcp64(d);
+        if (!(dbits(d) > lim) || !dfinite(d)) return false;
+        const double r = rcp64(d);
+        rl = li == j ? r : rl;
         const bool act = li > j;
         const int src_l = act ? uidx(j, li) : lane;
         const int src_k = act ? (is_u ? uidx(j, lk) : 21 + j) : lane;
         const double ujl = __shfl_sync(full, u, src_l);
         const double ujk = __shfl_sync(full, u, src_k);
-        if (act) u = fma(-(ujl * r[j]), ujk, u);
+        if (act) u = fma(-(ujl * r), ujk, u);
     }
+    // rows scaled by 1 / D_i: lane (i, k) holds L_ki, lane 21 + i holds y_i / D_i
+    double v = u * rl;
 #pragma unroll
     for (int i = 5; i >= 0; --i) {
-        const double x = __shfl_sync(full, u, 21 + i) * r[i];
+        const double x = __shfl_sync(full, v, 21 + i);
         xi[i] = x;
-        const bool act = is_y && li < i;
-        const double umi = __shfl_sync(full, u, act ? uidx(li, i) : lane);
-        if (act) u = fma(-umi, x, u);
+        if (i > 0) {
+            const bool act = is_y && li < i;
+            const double lmi = __shfl_sync(full, v, act ? uidx(li, i) : lane);
+            if (act) v = fma(-lmi, x, v);
+        }
     }
     return true;
 }
 
+// (-1)^n / (2n + 1 + c)!: the n-th Taylor coefficient in t^2 of sin(t)/t (c = 0),
+// (1 - cos t)/t^2 (c = 1) and (t - sin t)/t^3 (c = 2).
+__device__ __forceinline__ double se3_taylor_coef(int n, int c) {
+    constexpr double k[6][3] = {
+        {1.0, 1.0 / 2.0, 1.0 / 6.0},
+        {-1.0 / 6.0, -1.0 / 24.0, -1.0 / 120.0},
+        {1.0 / 120.0, 1.0 / 720.0, 1.0 / 5040.0},
+        {-1.0 / 5040.0, -1.0 / 40320.0, -1.0 / 362880.0},
+        {1.0 / 362880.0, 1.0 / 3628800.0, 1.0 / 39916800.0},
+        {-1.0 / 39916800.0, -1.0 / 479001600.0, -1.0 / 6227020800.0},
+    };
+    return c == 0 ? k[n][0] : (c == 1 ? k[n][1] : k[n][2]);
+}
+
 // T <- exp(xi^) T on one warp: lanes 0..2 evaluate the coefficients A, B, C;
 // lanes 0..8 the rotation R = I + A W + B W^2 and lanes 9..17 V = I + B W + C W^2
-// (one matrix entry each); lanes 0..11 then each compose one entry of [R T | R t + V v].
+// (one matrix entry each); then, in the same three multiply-adds, lanes 0..11
+// each compose one entry of R T and lanes 12..14 one entry of V v, which the
+// translation lanes add.  The series is cut where its remainder (below the
+// first omitted term) is under 5e-17 relative: degree 3 in t^2 for t^2 <= 2^-9,
+// degree 4 for t^2 <= 2^-6, degree 5 for t^2 <= 1/16, sincos beyond.
 // T lives in shared memory (12 doubles) and is updated in place; xi is the same in every lane.
 __device__ __forceinline__ void warp_se3_update(const double xi[6], double *T) {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const double w0 = xi[0], w1 = xi[1], w2 = xi[2];
     const double th2 = fma(w0, w0, fma(w1, w1, w2 * w2));
+    const long long tb = dbits(th2);
+    const int c = lane < 3 ? lane : 0;
     double coef;
-    if (th2 <= 0.0625) {
-        // Taylor series in th2 of sin(t)/t, (1 - cos t)/t^2, (t - sin t)/t^3, one per lane
-        const int c = lane < 3 ? lane : 0;
-        const double k0 = c == 0 ? 1.0 : (c == 1 ? 0.5 : 1.0 / 6.0);
-        const double k1 = c == 0 ? -1.0 / 6.0 : (c == 1 ? -1.0 / 24.0 : -1.0 / 120.0);
-        const double k2 = c == 0 ? 1.0 / 120.0 : (c == 1 ? 1.0 / 720.0 : 1.0 / 5040.0);
-        const double k3 = c == 0 ? -1.0 / 5040.0 : (c == 1 ? -1.0 / 40320.0 : -1.0 / 362880.0);
-        const double k4 = c == 0 ? 1.0 / 362880.0 : (c == 1 ? 1.0 / 3628800.0 : 1.0 / 39916800.0);
-        const double k5 = c == 0 ? -1.0 / 39916800.0 : (c == 1 ? -1.0 / 479001600.0 : -1.0 / 6227020800.0);
-        const double k6 = c == 0 ? 1.0 / 6227020800.0 : (c == 1 ? 1.0 / 87178291200.0 : 1.0 / 1307674368000.0);
-        coef = fma(th2, fma(th2, fma(th2, fma(th2, fma(th2, fma(th2, k6, k5), k4), k3), k2), k1), k0);
+    if (tb <= dbits(0.001953125)) {
+        coef = fma(th2, fma(th2, fma(th2, se3_taylor_coef(3, c), se3_taylor_coef(2, c)), se3_taylor_coef(1, c)),
+                   se3_taylor_coef(0, c));
+    } else if (tb <= dbits(0.015625)) {
+        coef = fma(th2,
+                   fma(th2, fma(th2, fma(th2, se3_taylor_coef(4, c), se3_taylor_coef(3, c)), se3_taylor_coef(2, c)),
+                       se3_taylor_coef(1, c)),
+                   se3_taylor_coef(0, c));
+    } else if (tb <= dbits(0.0625)) {
+        double p = se3_taylor_coef(5, c);
+#pragma unroll
+        for (int n = 4; n >= 0; --n) p = fma(th2, p, se3_taylor_coef(n, c));
+        coef = p;
     } else {
         double A, B, C;
         se3_coeffs(th2, A, B, C);
@@ -441,28 +501,39 @@ __device__ __forceinline__ void warp_se3_update(const double xi[6], double *T) {
     const double om_k = ek == 0 ? w0 : (ek == 1 ? w1 : w2);
     // W = [omega]_x: W[i][k] = -eps_ikl omega_l
     double Wik = 0.0;
-    if (ei == 0 && ek == 1) Wik = -w2;
+    if (ei == 0 && ek == 1) Wik = dneg(w2);
     if (ei == 0 && ek == 2) Wik = w1;
     if (ei == 1 && ek == 0) Wik = w2;
-    if (ei == 1 && ek == 2) Wik = -w0;
-    if (ei == 2 && ek == 0) Wik = -w1;
+    if (ei == 1 && ek == 2) Wik = dneg(w0);
+    if (ei == 2 && ek == 0) Wik = dneg(w1);
     if (ei == 2 && ek == 1) Wik = w0;
-    const double delta = ei == ek ? 1.0 : 0.0;
-    const double W2 = fma(om_i, om_k, -delta * th2);
+    const double W2 = fma(om_i, om_k, ei == ek ? dneg(th2) : 0.0);
     const double c1 = lane < 9 ? A : B, c2 = lane < 9 ? B : C;
-    const double ent = fma(c1, Wik, fma(c2, W2, delta));
-    // compose: lane e < 12 owns output (i, j), i = e / 4, j = e % 4
-    const int oi = lane < 12 ? lane / 4 : 0, oj = lane < 12 ? lane % 4 : 0;
-    const double R0 = __shfl_sync(full, ent, 3 * oi), R1 = __shfl_sync(full, ent, 3 * oi + 1),
-                 R2 = __shfl_sync(full, ent, 3 * oi + 2);
-    const double V0 = __shfl_sync(full, ent, 9 + 3 * oi), V1 = __shfl_sync(full, ent, 9 + 3 * oi + 1),
-                 V2 = __shfl_sync(full, ent, 9 + 3 * oi + 2);
-    const double te = oj == 3 ? fma(V0, xi[3], fma(V1, xi[4], V2 * xi[5])) : 0.0;
-    const double T0 = T[oj], T1 = T[4 + oj], T2 = T[8 + oj];
-    const double out = fma(R0, T0, fma(R1, T1, fma(R2, T2, te)));
+    const double ent = fma(c1, Wik, fma(c2, W2, ei == ek ? 1.0 : 0.0));
+    // lanes 0..11: (R T)(i, j), i = lane / 4, j = lane % 4; lanes 12..14: (V v)(lane - 12)
+    const bool comp = lane < 12, tv = lane >= 12 && lane < 15;
+    const int oi = comp ? lane / 4 : (tv ? lane - 12 : 0), oj = comp ? lane % 4 : 0;
+    const int src = tv ? 9 + 3 * oi : 3 * oi;
+    const double M0 = __shfl_sync(full, ent, src), M1 = __shfl_sync(full, ent, src + 1),
+                 M2 = __shfl_sync(full, ent, src + 2);
+    const double X0 = tv ? xi[3] : T[oj], X1 = tv ? xi[4] : T[4 + oj], X2 = tv ? xi[5] : T[8 + oj];
+    const double o = fma(M0, X0, fma(M1, X1, M2 * X2));
+    const double te = __shfl_sync(full, o, 12 + oi);
+    const double out = oj == 3 ? o + te : o;
     __syncwarp();
     if (lane < 12) T[lane] = out;
     __syncwarp();
+}
+
+// Convergence test on one warp: |omega|^2 < er2 and |v|^2 < et2 (lane 0 takes
+// the rotation, lane 1 the translation, in the same instructions).
+__device__ __forceinline__ bool warp_converged(const double xi[6], double er2, double et2) {
+    const int lane = threadIdx.x & 31;
+    const bool tr = lane == 1;
+    const double a = tr ? xi[3] : xi[0], b = tr ? xi[4] : xi[1], c = tr ? xi[5] : xi[2];
+    const double n2 = fma(a, a, fma(b, b, c * c));
+    const bool below = dbits(n2) < dbits(tr ? et2 : er2);
+    return (__ballot_sync(0xffffffffu, below) & 3u) == 3u;
 }
 
 // ----------------------------------------------------------------------------- keyframe update pieces

@@ -113,15 +113,15 @@ __device__ __forceinline__ void accumulate_pixel(const IcpArgs &a, const PoseF &
     inl += 1;
 }
 
-// Warp shuffles, then the CTA's warps summed (compensated FP32) into its partial record.
+// Warp reduce-scatter, then the CTA's warps summed (compensated FP32) into its partial record.
 __device__ __forceinline__ void cta_partial(float acc[28], int inl, int valid, float *partial, float (*sh)[32],
                                             int (*shi)[2]) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float v[32];
 #pragma unroll
-    for (int i = 0; i < 28; ++i) {
-        const float s = warp_sum(acc[i]);
-        if (lane == 0) sh[warp][i] = s;
-    }
+    for (int i = 0; i < 32; ++i) v[i] = i < 28 ? acc[i] : 0.0f;
+    const float s = warp_reduce_scatter(v);  // lane i: the warp's sum of acc[i]
+    if (lane < 28) sh[warp][lane] = s;
     const int si = __reduce_add_sync(0xffffffffu, inl);
     const int sv = __reduce_add_sync(0xffffffffu, valid);
     if (lane == 0) {
@@ -278,6 +278,7 @@ __global__ void __launch_bounds__(kIcpThreads) icp_step_kernel(IcpArgs a, double
 
 constexpr int kTileThreads = 512;
 constexpr int kTileWarps = kTileThreads / 32;
+constexpr int kStageGroup = 4;  // keyframe chunks staged per memory round trip
 
 // One staged correspondence, branch-free: a rejected pair contributes zeros.
 __device__ __forceinline__ void accumulate_entry(const IcpArgs &a, const PoseF &T, float3 s, float3 n, float acc[28],
@@ -324,11 +325,11 @@ __device__ __forceinline__ void accumulate_entry(const IcpArgs &a, const PoseF &
 __device__ __forceinline__ void tile_partial(float acc[28], int inl, int valid, float *partial, float (*sh)[32],
                                              int (*shi)[2]) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float v[32];
 #pragma unroll
-    for (int i = 0; i < 28; ++i) {
-        const float v = warp_sum(acc[i]);
-        if (lane == 0) sh[warp][i] = v;
-    }
+    for (int i = 0; i < 32; ++i) v[i] = i < 28 ? acc[i] : 0.0f;
+    const float s = warp_reduce_scatter(v);  // lane i: the warp's sum of acc[i]
+    if (lane < 28) sh[warp][lane] = s;
     const int si = __reduce_add_sync(0xffffffffu, inl);
     const int sv = __reduce_add_sync(0xffffffffu, valid);
     if (lane == 0) {
@@ -351,9 +352,10 @@ __device__ __forceinline__ void tile_partial(float acc[28], int inl, int valid, 
 }
 
 // Sum every CTA record of one step (compensated FP32, a fixed order, so every
-// CTA obtains bit-identical totals) into tot[0..29] (FP64).
+// CTA obtains bit-identical totals) into tot[0..27] (FP64) and the inlier and
+// valid counts into totn[0..1].
 __device__ __forceinline__ void sum_records(const float *rec, int nrec, float (*sh)[32], float (*shc)[32],
-                                            int (*shn)[32], double *tot) {
+                                            int (*shn)[32], double *tot, long long *totn) {
     const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
     float s = 0.0f, c = 0.0f;
     int n = 0;
@@ -392,7 +394,7 @@ __device__ __forceinline__ void sum_records(const float *rec, int nrec, float (*
         long long t = 0;
 #pragma unroll
         for (int q = 0; q < kTileWarps; ++q) t += shn[q][threadIdx.x];
-        tot[threadIdx.x] = (double)t;
+        totn[threadIdx.x - 28] = t;
     }
     __syncthreads();
 }
@@ -416,13 +418,14 @@ __global__ void __launch_bounds__(kTileThreads, 1)
     __shared__ int shn[kTileWarps][32];
     __shared__ int shi[kTileWarps][2];
     __shared__ double tot[32];
+    __shared__ long long totn[2];
     __shared__ double Tsh[12];
     __shared__ double Tprev[12], Tmot[12];
     __shared__ float Tf[12];
     __shared__ int acc_ok_s;
     __shared__ double xi_sh[6];
-    __shared__ int wcnt[kTileWarps];
-    __shared__ int base_s, spill_s, flag, status_s, conv_s, valid_s;
+    __shared__ int wcnt[2][kStageGroup][kTileWarps];
+    __shared__ int flag, status_s, conv_s, valid_s;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int npx = a.kp.rows * a.kp.cols;
     const int nchunks = (npx + kTileThreads - 1) / kTileThreads;
@@ -450,64 +453,81 @@ __global__ void __launch_bounds__(kTileThreads, 1)
 
     // ---- stage the CTA's chunks into shared memory (once per launch).  Chunks of
     // 512 pixels are dealt round-robin (chunk q goes to CTA q mod gridDim), so every
-    // CTA gets an even share of the rows that hold samples.  A chunk that no longer
-    // fits is left, with every later chunk of this CTA, to the global-memory path.
-    if (threadIdx.x == 0) {
-        base_s = 0;
-        spill_s = nchunks;
-    }
-    __syncthreads();
-    for (int q = blockIdx.x; q < nchunks; q += gridDim.x) {
-        const int k = q * kTileThreads + threadIdx.x;
-        bool ok = false;
-        float3 s = make_float3(0.f, 0.f, 0.f), n = make_float3(0.f, 0.f, 0.f);
-        float wk = 0.0f, dk = 0.0f;
-        if (k < npx) {
-            const float d = __ldg(a.kdepth + k);
-            const float4 n4 = load_nw(a.knw, k, a.kprec);
-            if (d > 0.0f &&
-                __fadd_rn(__fadd_rn(__fmul_rn(n4.x, n4.x), __fmul_rn(n4.y, n4.y)), __fmul_rn(n4.z, n4.z)) > 0.25f) {
-                ok = true;
+    // CTA gets an even share of the rows that hold samples.  kStageGroup chunks are
+    // loaded together (one memory round trip for the group) and compacted with one
+    // barrier: the per-warp counts are double-buffered by group parity.  A chunk
+    // that no longer fits is left, with every later chunk of this CTA, to the
+    // global-memory path.
+    int staged = 0, spill_q = nchunks;
+    for (int q0 = blockIdx.x, par = 0; q0 < nchunks; q0 += kStageGroup * gridDim.x, par ^= 1) {
+        float dg[kStageGroup];
+        float4 ng[kStageGroup];
+        float2 eg[kStageGroup], ag[kStageGroup];
+#pragma unroll
+        for (int g = 0; g < kStageGroup; ++g) {
+            const int k = (q0 + g * gridDim.x) * kTileThreads + threadIdx.x;
+            dg[g] = 0.0f;
+            ng[g] = make_float4(0.f, 0.f, 0.f, 0.f);
+            eg[g] = ag[g] = make_float2(0.f, 0.f);
+            if (q0 + g * (int)gridDim.x < nchunks && k < npx) {
                 const int v = k / W;
-                s = pixel_point(a.kdirs, a.kp.rows, v, k - v * W, d);
-                n = make_float3(n4.x, n4.y, n4.z);
-                wk = n4.w;
-                dk = d;
+                dg[g] = __ldg(a.kdepth + k);
+                ng[g] = load_nw(a.knw, k, a.kprec);
+                eg[g] = __ldg(reinterpret_cast<const float2 *>(a.kdirs) + v);
+                ag[g] = __ldg(reinterpret_cast<const float2 *>(a.kdirs + 2 * a.kp.rows) + (k - v * W));
             }
         }
-        const unsigned bal = __ballot_sync(0xffffffffu, ok);
-        if (lane == 0) wcnt[warp] = __popc(bal);
+        unsigned bal[kStageGroup];
+#pragma unroll
+        for (int g = 0; g < kStageGroup; ++g) {
+            const float4 n4 = ng[g];
+            const bool ok = dg[g] > 0.0f && __fadd_rn(__fadd_rn(__fmul_rn(n4.x, n4.x), __fmul_rn(n4.y, n4.y)),
+                                                      __fmul_rn(n4.z, n4.z)) > 0.25f;
+            bal[g] = __ballot_sync(0xffffffffu, ok);
+            if (lane == 0) wcnt[par][g][warp] = __popc(bal[g]);
+        }
         __syncthreads();
-        int off = base_s, total = base_s;
-        for (int w = 0; w < kTileWarps; ++w) {
-            const int c = wcnt[w];
-            off += w < warp ? c : 0;
-            total += c;
+        // every thread derives the same offsets and totals from the counts
+        int fit = kStageGroup;
+        int off[kStageGroup];
+        int total = staged;
+#pragma unroll
+        for (int g = 0; g < kStageGroup; ++g) {
+            int o = total;
+            for (int w = 0; w < kTileWarps; ++w) {
+                const int c = wcnt[par][g][w];
+                o += w < warp ? c : 0;
+                total += c;
+            }
+            off[g] = o + __popc(bal[g] & ((1u << lane) - 1u));
+            if (fit == kStageGroup && total > cap) fit = g;
+            if (fit == kStageGroup) staged = total;
         }
-        if (total > cap) {  // this chunk does not fit: it and the CTA's later chunks stay in global memory
-            if (threadIdx.x == 0) spill_s = q;
-            __syncthreads();
-            break;
-        }
-        const int slot = off + __popc(bal & ((1u << lane) - 1u));
-        if (ok) {
-            sx[slot] = s.x;
-            sy[slot] = s.y;
-            sz[slot] = s.z;
-            snx[slot] = n.x;
-            sny[slot] = n.y;
-            snz[slot] = n.z;
-            sw8[slot] = wk;
-            sd[slot] = dk;
+#pragma unroll
+        for (int g = 0; g < kStageGroup; ++g) {
+            if (g >= fit || !((bal[g] >> lane) & 1u)) continue;
+            const int k = (q0 + g * gridDim.x) * kTileThreads + threadIdx.x;
+            const int slot = off[g];
+            const float d = dg[g];
+            sx[slot] = __fmul_rn(d, __fmul_rn(eg[g].x, ag[g].x));
+            sy[slot] = __fmul_rn(d, __fmul_rn(eg[g].x, ag[g].y));
+            sz[slot] = __fmul_rn(d, eg[g].y);
+            snx[slot] = ng[g].x;
+            sny[slot] = ng[g].y;
+            snz[slot] = ng[g].z;
+            sw8[slot] = ng[g].w;
+            sd[slot] = d;
             sk[slot] = k;
         }
-        __syncthreads();
-        if (threadIdx.x == 0) base_s = total;
-        __syncthreads();
+        if (fit < kStageGroup) {  // uniform across the CTA: the counts are shared
+            spill_q = q0 + fit * gridDim.x;
+            break;
+        }
     }
-    const int staged = base_s;
-    const int spill_q = spill_s;
+    __syncthreads();
 
+    // convergence thresholds, squared once per launch (read by warp 0 only)
+    const double er2 = warp == 0 ? ip.eps_rot * ip.eps_rot : 0.0, et2 = warp == 0 ? ip.eps_trans * ip.eps_trans : 0.0;
     int it = 0;
     for (; it < ip.max_iters; ++it) {
         // the pose in FP32: converted once per CTA (FP64 conversions are slow on GB300), read by all
@@ -549,9 +569,9 @@ __global__ void __launch_bounds__(kTileThreads, 1)
         }
         __syncthreads();
         if (flag == 3) return;
-        sum_records(rec, gridDim.x, sh, shc, shn, tot);
+        sum_records(rec, gridDim.x, sh, shc, shn, tot, totn);
         if (warp == 0) {
-            const long long inliers = (long long)tot[28];
+            const long long inliers = totn[0];
             double xi[6] = {0, 0, 0, 0, 0, 0};
             int status = UPSLAM_OK, conv = 0;
             if (inliers < ip.min_inliers) {
@@ -563,15 +583,13 @@ __global__ void __launch_bounds__(kTileThreads, 1)
                     for (int i = 0; i < 6; ++i) xi[i] = 0.0;
                 } else {
                     warp_se3_update(xi, Tsh);
-                    const double wn2 = fma(xi[0], xi[0], fma(xi[1], xi[1], xi[2] * xi[2]));
-                    const double vn2 = fma(xi[3], xi[3], fma(xi[4], xi[4], xi[5] * xi[5]));
-                    conv = (wn2 < ip.eps_rot * ip.eps_rot && vn2 < ip.eps_trans * ip.eps_trans) ? 1 : 0;
+                    conv = warp_converged(xi, er2, et2) ? 1 : 0;
                 }
             }
             if (lane == 0) {
                 status_s = status;
                 conv_s = conv;
-                if (it == 0) valid_s = (int)tot[29];
+                if (it == 0) valid_s = (int)totn[1];
 #pragma unroll
                 for (int i = 0; i < 6; ++i) xi_sh[i] = xi[i];
             }
@@ -587,7 +605,7 @@ __global__ void __launch_bounds__(kTileThreads, 1)
     int accepted_flag = 0;
     if (fuse_on) {
         if (threadIdx.x == 0) {
-            acc_ok_s = status_s == UPSLAM_OK && valid_s > 0 && (float)tot[28] >= fz.accept * (float)valid_s;
+            acc_ok_s = status_s == UPSLAM_OK && valid_s > 0 && (float)totn[0] >= fz.accept * (float)valid_s;
         }
         if (threadIdx.x < 12) Tf[threadIdx.x] = (float)Tsh[threadIdx.x];
         __syncthreads();
@@ -672,7 +690,7 @@ __global__ void __launch_bounds__(kTileThreads, 1)
         if (threadIdx.x < 21) st->A[threadIdx.x] = tot[threadIdx.x];
         else if (threadIdx.x < 27) st->b[threadIdx.x - 21] = tot[threadIdx.x];
         else if (threadIdx.x == 27) st->sse = tot[27];
-        else if (threadIdx.x == 28) st->inliers = (long long)tot[28];
+        else if (threadIdx.x == 28) st->inliers = totn[0];
         else if (threadIdx.x == 29) st->valid = valid_s;
         else if (threadIdx.x == 30) {
             st->status = status_s;
