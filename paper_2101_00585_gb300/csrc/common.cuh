@@ -206,6 +206,17 @@ __device__ __forceinline__ double dneg(double x) {
     return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ull);
 }
 
+// Exact FP32 -> FP64 widening: the exponent is rebiased (+896) and the
+// mantissa shifted into place with integer instructions.  Zero, subnormal,
+// infinite and NaN inputs take the conversion instruction.
+__device__ __forceinline__ double f2d(float f) {
+    const unsigned b = __float_as_uint(f);
+    const unsigned e = (b >> 23) & 0xffu;
+    if (e == 0u || e == 0xffu) return (double)f;
+    const unsigned m = b & 0x7fffffu;
+    return __hiloint2double((int)((b & 0x80000000u) | ((e + 896u) << 20) | (m >> 3)), (int)(m << 29));
+}
+
 // 1/d for a positive d.  The FP32 seed is d's exponent and top 23 mantissa bits
 // (truncation: relative error below 2^-23), formed and widened back with integer
 // instructions; one FP64 Newton step then leaves a relative error below 2^-44,

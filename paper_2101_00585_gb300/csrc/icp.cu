@@ -323,7 +323,7 @@ __device__ __forceinline__ void accumulate_entry(const IcpArgs &a, const PoseF &
 
 // CTA partial record (64 words): sums [0, 28), inliers [28], valid [29], compensations [32, 60).
 __device__ __forceinline__ void tile_partial(float acc[28], int inl, int valid, float *partial, float (*sh)[32],
-                                             int (*shi)[2]) {
+                                             int (*shi)[2], float (*sg)[4][32]) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float v[32];
 #pragma unroll
@@ -337,10 +337,22 @@ __device__ __forceinline__ void tile_partial(float acc[28], int inl, int valid, 
         shi[warp][1] = sv;
     }
     __syncthreads();
+    // the 16 warp sums in two compensated levels: 4 groups of 4 warps, then the groups
+    if (warp < 4 && lane < 28) {
+        float t = 0.0f, c = 0.0f;
+#pragma unroll
+        for (int w = 4 * warp; w < 4 * warp + 4; ++w) kadd(t, c, sh[w][lane]);
+        sg[0][warp][lane] = t;
+        sg[1][warp][lane] = c;
+    }
+    __syncthreads();
     if (threadIdx.x < 28) {
         float t = 0.0f, c = 0.0f;
 #pragma unroll
-        for (int w = 0; w < kTileWarps; ++w) kadd(t, c, sh[w][threadIdx.x]);
+        for (int q = 0; q < 4; ++q) {
+            kadd(t, c, sg[0][q][threadIdx.x]);
+            c += sg[1][q][threadIdx.x];
+        }
         partial[threadIdx.x] = t;
         partial[32 + threadIdx.x] = c;
     } else if (threadIdx.x < 30) {
@@ -355,9 +367,10 @@ __device__ __forceinline__ void tile_partial(float acc[28], int inl, int valid, 
 // CTA obtains bit-identical totals) into tot[0..27] (FP64) and the inlier and
 // valid counts into totn[0..1].
 __device__ __forceinline__ void sum_records(const float *rec, int nrec, float (*sh)[32], float (*shc)[32],
-                                            int (*shn)[32], double *tot, long long *totn) {
+                                            int (*shn)[32], float (*sg)[4][32], double *tot, long long *totn) {
     const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
-    float s = 0.0f, c = 0.0f;
+    // two interleaved compensated chains per lane (even and odd records of the warp)
+    float s0 = 0.0f, c0 = 0.0f, s1 = 0.0f, c1 = 0.0f;
     int n = 0;
     constexpr int kBatch = 10;
     for (int b0 = g; b0 < nrec; b0 += kTileWarps * kBatch) {
@@ -369,27 +382,41 @@ __device__ __forceinline__ void sum_records(const float *rec, int nrec, float (*
             y[q] = b < nrec ? __ldcg(rec + (size_t)b * kSlots + 32 + lane) : 0.0f;
         }
 #pragma unroll
-        for (int q = 0; q < kBatch; ++q) {
+        for (int q = 0; q < kBatch; q += 2) {
             if (lane < 28) {
-                kadd(s, c, x[q]);
-                c += y[q];
+                kadd(s0, c0, x[q]);
+                c0 += y[q];
+                kadd(s1, c1, x[q + 1]);
+                c1 += y[q + 1];
             } else if (lane < 30) {
-                n += __float_as_int(x[q]);
+                n += __float_as_int(x[q]) + __float_as_int(x[q + 1]);
             }
         }
     }
-    sh[g][lane] = s;
-    shc[g][lane] = c;
+    kadd(s0, c0, s1);
+    sh[g][lane] = s0;
+    shc[g][lane] = c0 + c1;
     shn[g][lane] = n;
+    __syncthreads();
+    if (g < 4 && lane < 28) {
+        float t = 0.0f, cc = 0.0f;
+#pragma unroll
+        for (int w = 4 * g; w < 4 * g + 4; ++w) {
+            kadd(t, cc, sh[w][lane]);
+            cc += shc[w][lane];
+        }
+        sg[0][g][lane] = t;
+        sg[1][g][lane] = cc;
+    }
     __syncthreads();
     if (threadIdx.x < 28) {
         float t = 0.0f, cc = 0.0f;
 #pragma unroll
-        for (int q = 0; q < kTileWarps; ++q) {
-            kadd(t, cc, sh[q][threadIdx.x]);
-            cc += shc[q][threadIdx.x];
+        for (int q = 0; q < 4; ++q) {
+            kadd(t, cc, sg[0][q][threadIdx.x]);
+            cc += sg[1][q][threadIdx.x];
         }
-        tot[threadIdx.x] = (double)t + (double)cc;
+        tot[threadIdx.x] = f2d(t) + f2d(cc);
     } else if (threadIdx.x < 30) {
         long long t = 0;
 #pragma unroll
@@ -397,6 +424,25 @@ __device__ __forceinline__ void sum_records(const float *rec, int nrec, float (*
         totn[threadIdx.x - 28] = t;
     }
     __syncthreads();
+}
+
+// Grid barrier on a monotonic 64-bit arrival counter, called by one thread per
+// CTA after a __syncthreads.  The release add publishes everything the CTA
+// wrote before the barrier; the polls are relaxed loads, and one acquire fence
+// after the last makes every other CTA's writes visible (the caller's next
+// __syncthreads extends both to the whole CTA).  False when the count has not
+// reached target after kWaitCycles (the caller reports UPSLAM_ERR_TIMEOUT).
+__device__ __forceinline__ bool grid_arrive_wait(unsigned long long *ctr, unsigned long long target) {
+    asm volatile("red.release.gpu.global.add.u64 [%0], 1;" ::"l"(ctr) : "memory");
+    const long long t0 = clock64();
+    unsigned long long v;
+    for (;;) {
+        asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(ctr) : "memory");
+        if (v >= target) break;
+        if (clock64() - t0 > kWaitCycles) return false;
+    }
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+    return true;
 }
 
 // The tiled persistent kernel.  Each step: accumulate the CTA's staged (and
@@ -417,6 +463,7 @@ __global__ void __launch_bounds__(kTileThreads, 1)
     __shared__ float shc[kTileWarps][32];
     __shared__ int shn[kTileWarps][32];
     __shared__ int shi[kTileWarps][2];
+    __shared__ float sg[2][4][32];
     __shared__ double tot[32];
     __shared__ long long totn[2];
     __shared__ double Tsh[12];
@@ -549,27 +596,18 @@ __global__ void __launch_bounds__(kTileThreads, 1)
         }
         const int valid = it == 0 ? count_valid(a) : 0;
         float *rec = partials + (size_t)(it & 1) * gridDim.x * kSlots;
-        tile_partial(acc, inl, valid, rec + (size_t)blockIdx.x * kSlots, sh, shi);
+        tile_partial(acc, inl, valid, rec + (size_t)blockIdx.x * kSlots, sh, shi, sg);
         __syncthreads();
         if (threadIdx.x == 0) {
-            __threadfence();
-            atomicAdd(&ctrl->arrive64, 1ull);
-            const unsigned long long target = base + G * (unsigned long long)(it + 1);
-            const long long t0 = clock64();
             flag = 0;
-            while (*((volatile unsigned long long *)&ctrl->arrive64) < target) {
-                if (clock64() - t0 > kWaitCycles) {
-                    flag = 3;
-                    st->status = UPSLAM_ERR_TIMEOUT;
-                    break;
-                }
-                __nanosleep(20);
+            if (!grid_arrive_wait(&ctrl->arrive64, base + G * (unsigned long long)(it + 1))) {
+                flag = 3;
+                st->status = UPSLAM_ERR_TIMEOUT;
             }
-            __threadfence();
         }
         __syncthreads();
         if (flag == 3) return;
-        sum_records(rec, gridDim.x, sh, shc, shn, tot, totn);
+        sum_records(rec, gridDim.x, sh, shc, shn, sg, tot, totn);
         if (warp == 0) {
             const long long inliers = totn[0];
             double xi[6] = {0, 0, 0, 0, 0, 0};
@@ -643,20 +681,11 @@ __global__ void __launch_bounds__(kTileThreads, 1)
         // one more grid barrier (every CTA arrives, accepted or not)
         __syncthreads();
         if (threadIdx.x == 0) {
-            __threadfence();
-            atomicAdd(&ctrl->arrive64, 1ull);
-            const unsigned long long target = base + G * (unsigned long long)(it + 1);
-            const long long t0 = clock64();
             flag = 0;
-            while (*((volatile unsigned long long *)&ctrl->arrive64) < target) {
-                if (clock64() - t0 > kWaitCycles) {
-                    flag = 3;
-                    st->status = UPSLAM_ERR_TIMEOUT;
-                    break;
-                }
-                __nanosleep(20);
+            if (!grid_arrive_wait(&ctrl->arrive64, base + G * (unsigned long long)(it + 1))) {
+                flag = 3;
+                st->status = UPSLAM_ERR_TIMEOUT;
             }
-            __threadfence();
         }
         __syncthreads();
         if (flag == 3) return;
