@@ -13,6 +13,7 @@ Every function follows a passage of UPSLAM (arXiv 2101.00585):
 ``pixel_points``       the z-buffer winner's own xyz at every pixel
 ``normals``            Sec. III-A: cross product of the vectors to two image
                        neighbours
+``atrous``             Sec. III-A: edge-avoiding a-trous smoothing of the normals
 ``icp_step``           Sec. III-B, Eq. 1 (point-to-plane over projective
                        correspondences filtered by Omega_{d,theta}), squared and
                        solved by Gauss-Newton
@@ -32,6 +33,8 @@ import subprocess
 from dataclasses import dataclass
 
 import numpy as np
+
+from .atrous import atrous  # noqa: F401  (Sec. III-A normal smoothing)
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "upslam_oracle.c")
@@ -148,6 +151,10 @@ class Params:
     fuse_cos_theta_max: float = float(np.cos(np.radians(30.0)))
     w_max: float = 10.0
     accept_quality: float = 0.3
+    # a-trous smoothing of the sweep normals (Sec. III-A); 0 levels = off
+    atrous_levels: int = 0
+    atrous_sigma_n: float = 0.5
+    atrous_sigma_x: float = 0.02
 
     def normal_params(self) -> NormalParams:
         return NormalParams(self.jump_rel, self.jump_abs, self.min_cross)
@@ -353,10 +360,14 @@ def quality(stats: dict) -> float:
 # ----------------------------------------------------------------------------- whole sweep
 
 def sweep_frame(scan4: np.ndarray, sw, prm: Params = Params()):
-    """project -> pixel points -> normals for one sweep: (sp4 [H,W,4] f32, sn4 [H,W,4] f32, depth, idx)."""
+    """project -> pixel points -> normals (-> a-trous smoothing when prm.atrous_levels > 0) for one sweep:
+    (sp4 [H,W,4] f32, sn4 [H,W,4] f32, depth, idx)."""
     depth, idx = project(scan4, sw)
     sp4 = pixel_points(scan4, idx)
     nrm, val = normals(sp4, depth, sw, prm)
+    if prm.atrous_levels > 0:
+        nrm, val = atrous(sp4, normals4(nrm, val)[..., :3], val, prm.atrous_levels, prm.atrous_sigma_n,
+                          prm.atrous_sigma_x)
     return sp4, normals4(nrm, val), depth, idx
 
 
