@@ -20,6 +20,7 @@ Every function follows a passage of UPSLAM (arXiv 2101.00585):
 ``fuse``               Sec. III-C: keyframe pixels projected onto the sweep image,
                        similarity-gated, averaged with a count saturated at 10
 ``quality``            Sec. III-C: inliers / valid sweep measurements
+``grid_score``         Sec. III-C: low-resolution alignment checks of candidate poses
 =====================  =============================================================
 
 Pins that tie it to the paper and to mathematics rather than to itself live in
@@ -65,7 +66,7 @@ class NormalParams(ctypes.Structure):
 class IcpParams(ctypes.Structure):
     _fields_ = [("d_max", ctypes.c_float), ("cos_theta_max", ctypes.c_float), ("max_iters", ctypes.c_int32),
                 ("min_inliers", ctypes.c_int32), ("eps_rot", ctypes.c_double), ("eps_trans", ctypes.c_double),
-                ("pivot_eps", ctypes.c_double)]
+                ("pivot_eps", ctypes.c_double), ("loss", ctypes.c_int32), ("loss_delta", ctypes.c_float)]
 
 
 class IcpStats(ctypes.Structure):
@@ -151,6 +152,10 @@ class Params:
     fuse_cos_theta_max: float = float(np.cos(np.radians(30.0)))
     w_max: float = 10.0
     accept_quality: float = 0.3
+    # Eq. 1's |.|: 0 squares the point-to-plane error; 1 minimises it as printed (L1) by IRLS with
+    # weights 1 / max(|r|, loss_delta)
+    loss: int = 0
+    loss_delta: float = 0.01
     # a-trous smoothing of the sweep normals (Sec. III-A); 0 levels = off
     atrous_levels: int = 0
     atrous_sigma_n: float = 0.5
@@ -161,7 +166,7 @@ class Params:
 
     def icp_params(self) -> IcpParams:
         return IcpParams(self.d_max, self.cos_theta_max, self.max_iters, self.min_inliers, self.eps_rot,
-                         self.eps_trans, self.pivot_eps)
+                         self.eps_trans, self.pivot_eps, self.loss, self.loss_delta)
 
     def fuse_params(self) -> FuseParams:
         return FuseParams(self.fuse_d_max, self.fuse_cos_theta_max, self.w_max)
@@ -306,6 +311,20 @@ def residual(v, u, kf_depth, kf_nrm4, kp, sp4, sn4, sw, T, prm: Params = Params(
                                   ctypes.byref(pano(sw)), _d(np.ascontiguousarray(T, np.float64)),
                                   ctypes.byref(prm.icp_params()), ctypes.byref(r), _d(J), ctypes.byref(j))
     return bool(ok), r.value, J, j.value
+
+
+def grid_score(kf_depth, kf_nrm4, kp, sp4, sn4, sw, poses, stride: int, prm: Params = Params()):
+    """Sec. III-C loop closure: a grid search evaluates several hundred candidate transformations with
+    low-resolution projective alignment checks and promotes the best to full-resolution ICP.
+
+    Reading: the check is the ICP association of this oracle (keyframe pixel -> sweep pixel, filter
+    Omega) on the keyframe sampled every ``stride`` rows and columns; a candidate's score is its number
+    of inliers.  -> (scores int64 [n], best: the first candidate with the largest score)."""
+    kd = np.zeros_like(np.asarray(kf_depth, np.float32))
+    kd[::stride, ::stride] = np.asarray(kf_depth, np.float32)[::stride, ::stride]
+    scores = np.array([normal_equations(kd, kf_nrm4, kp, sp4, sn4, sw, np.asarray(T).reshape(3, 4), prm)["inliers"]
+                       for T in poses], dtype=np.int64)
+    return scores, int(np.argmax(scores)) if len(scores) else -1
 
 
 def se3_exp_left(xi, T):

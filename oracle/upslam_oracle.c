@@ -62,6 +62,8 @@ typedef struct {
     int32_t min_inliers;
     double eps_rot, eps_trans; /* convergence on |omega|, |v| of the update */
     double pivot_eps;          /* Cholesky pivot <= pivot_eps * max diag => degenerate */
+    int32_t loss;              /* 0: squared residuals; 1: absolute residuals by IRLS */
+    float loss_delta;          /* IRLS weight 1 / max(|r|, loss_delta) */
 } orc_icp_params;
 
 typedef struct {
@@ -438,8 +440,12 @@ static int associate(const double *T, int v, int u, const float *kf_depth, const
 }
 
 /*
- * Normal equations at T: A = sum J^T J and b = sum J^T r over the inlier
- * correspondences of all keyframe pixels; valid = sweep pixels holding a point.
+ * Normal equations at T: A = sum w J^T J, b = sum w J^T r and sse = sum w r^2
+ * over the inlier correspondences of all keyframe pixels; valid = sweep pixels
+ * holding a point.  Eq. 1 prints the point-to-plane error inside |.|: with
+ * loss 0 it is squared (w = 1, Gauss-Newton); with loss 1 the absolute error is
+ * minimised by iteratively reweighted least squares, w = 1 / max(|r|, delta),
+ * which makes w r^2 = |r| wherever |r| >= delta.
  * kf_depth [H*W], kf_nrm4 [H*W*4] (normal xyz, the 4th value unused);
  * sp4 / sn4 [Hs*Ws*4] sweep pixel points / normals (4th value != 0: valid).
  */
@@ -456,11 +462,16 @@ void orc_icp_normal_equations(const float *kf_depth, const float *kf_nrm4, const
         for (int u = 0; u < kp->cols; ++u) {
             double r, J[6];
             if (!associate(T, v, u, kf_depth, kf_nrm4, kp, rowtab, coltab, sp4, sn4, sw, ip, &r, J, 0)) continue;
+            double w = 1.0;
+            if (ip->loss == 1) {
+                double ar = fabs(r);
+                w = 1.0 / (ar > (double)ip->loss_delta ? ar : (double)ip->loss_delta);
+            }
             int p = 0;
             for (int a = 0; a < 6; ++a)
-                for (int c = a; c < 6; ++c) st->A[p++] += J[a] * J[c];
-            for (int a = 0; a < 6; ++a) st->b[a] += J[a] * r;
-            st->sse += r * r;
+                for (int c = a; c < 6; ++c) st->A[p++] += w * J[a] * J[c];
+            for (int a = 0; a < 6; ++a) st->b[a] += w * J[a] * r;
+            st->sse += w * r * r;
             st->inliers += 1;
         }
     }
