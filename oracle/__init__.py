@@ -21,6 +21,7 @@ Every function follows a passage of UPSLAM (arXiv 2101.00585):
                        similarity-gated, averaged with a count saturated at 10
 ``quality``            Sec. III-C: inliers / valid sweep measurements
 ``grid_score``         Sec. III-C: low-resolution alignment checks of candidate poses
+``consistency``        Sec. III-C: mutual consistency of two keyframes (moving objects)
 =====================  =============================================================
 
 Pins that tie it to the paper and to mathematics rather than to itself live in
@@ -108,6 +109,9 @@ def _load():
         "orc_icp_residual": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _F, _F, P(Pano), _F, _F, P(Pano), _D,
                                             P(IcpParams), _D, _D, _I64]),
         "orc_fuse": (ctypes.c_int64, [_D, _D, _D, P(Pano), _F, _F, P(Pano), _D, P(FuseParams), _I64]),
+        "orc_consistency_flags": (ctypes.c_int64, [_F, P(Pano), _F, P(Pano), _D, ctypes.c_float, ctypes.c_float,
+                                                   _U8]),
+        "orc_pose_inv_fixed": (None, [_D, _D]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -325,6 +329,34 @@ def grid_score(kf_depth, kf_nrm4, kp, sp4, sn4, sw, poses, stride: int, prm: Par
     scores = np.array([normal_equations(kd, kf_nrm4, kp, sp4, sn4, sw, np.asarray(T).reshape(3, 4), prm)["inliers"]
                        for T in poses], dtype=np.int64)
     return scores, int(np.argmax(scores)) if len(scores) else -1
+
+
+def pose_inv_fixed(T) -> np.ndarray:
+    """[R | t]^-1 as [R^T | -R^T t], t' summed in a fixed FP64 order (shared by any bit-exact checker)."""
+    out = np.empty(12)
+    _load().orc_pose_inv_fixed(_d(np.ascontiguousarray(np.asarray(T, np.float64).reshape(12))), _d(out))
+    return out.reshape(3, 4)
+
+
+def consistency(depth_a, pa, depth_b, pb, T_ab, rel: float = 0.05, abs_m: float = 0.2):
+    """Sec. III-C mutual consistency check between keyframes A and B (T_ab: pose of B in A).
+
+    A sample of one keyframe is flagged when the other keyframe's rays through and around it (the
+    3 x 3 pixels about the one it bins into) measured surfaces beyond it by more than rel * r + abs:
+    the other keyframe saw through the sample, which was a moving object.  Both directions use the
+    unmodified depths.  -> (flags_a [Ha, Wa] bool, flags_b [Hb, Wb] bool)."""
+    da = np.ascontiguousarray(depth_a, np.float32)
+    db = np.ascontiguousarray(depth_b, np.float32)
+    fa = np.zeros(da.shape, np.uint8)
+    fb = np.zeros(db.shape, np.uint8)
+    L = _load()
+    Tab = np.ascontiguousarray(np.asarray(T_ab, np.float64).reshape(12))
+    Tba = np.ascontiguousarray(pose_inv_fixed(Tab).reshape(12))
+    L.orc_consistency_flags(_f(da), ctypes.byref(pano(pa)), _f(db), ctypes.byref(pano(pb)), _d(Tab), float(rel),
+                            float(abs_m), fa.ctypes.data_as(_U8))
+    L.orc_consistency_flags(_f(db), ctypes.byref(pano(pb)), _f(da), ctypes.byref(pano(pa)), _d(Tba), float(rel),
+                            float(abs_m), fb.ctypes.data_as(_U8))
+    return fa.astype(bool), fb.astype(bool)
 
 
 def se3_exp_left(xi, T):

@@ -619,3 +619,78 @@ int64_t orc_fuse(double *kf_depth, double *kf_nrm, double *kf_w, const orc_pano 
     free(coltab);
     return fused;
 }
+
+/* ------------------------------------------------------------------ keyframe mutual consistency */
+
+/*
+ * Sec. III-C: when switching keyframes, a mutual consistency check between
+ * keyframes filters moving objects from the map.  The paper gives no rule.
+ * Reading: a sample of keyframe A is inconsistent with keyframe B when B's rays
+ * around it measured surfaces beyond it, i.e. B saw through the place where
+ * A's sample sat.  A's sample s = d dir (FP32 table point) is taken into B's
+ * frame by T_ab^-1 (T_ab = pose of B in A, rounded to FP32, fixed order as
+ * orc_xform_inv_f32) and binned into B with the FP32 rule (pixel j, range r).
+ * It is flagged when B holds a depth at j and every pixel of the 3 x 3
+ * neighbourhood of j (columns wrapped, rows clipped) that holds a depth exceeds
+ * lim = (rel * r + abs) + r, formed in FP32.  The neighbourhood keeps a
+ * half-pixel misalignment of the two keyframes' ray grids at a silhouette edge
+ * from reading as a see-through.  flag_a[k] = 1 for flagged samples of A, else
+ * 0.  Returns the number flagged.
+ */
+int64_t orc_consistency_flags(const float *depth_a, const orc_pano *pa, const float *depth_b, const orc_pano *pb,
+                              const double *T_ab, float rel, float abs_m, uint8_t *flag_a) {
+    float *rowtab = (float *)malloc(sizeof(float) * 2 * (size_t)pa->rows);
+    float *coltab = (float *)malloc(sizeof(float) * 2 * (size_t)pa->cols);
+    orc_dir_table(pa, rowtab, coltab);
+    int64_t n = 0;
+    for (int v = 0; v < pa->rows; ++v) {
+        for (int u = 0; u < pa->cols; ++u) {
+            int64_t k = (int64_t)v * pa->cols + u;
+            flag_a[k] = 0;
+            float d = depth_a[k];
+            if (!(d > 0.0f)) continue;
+            float sx, sy, sz, qx, qy, qz;
+            pixel_point_f32(rowtab, coltab, v, u, d, &sx, &sy, &sz);
+            orc_xform_inv_f32(T_ab, sx, sy, sz, &qx, &qy, &qz);
+            int32_t jv, ju;
+            float r;
+            if (!orc_bin(qx, qy, qz, pb, &jv, &ju, &r)) continue;
+            if (!(depth_b[(int64_t)jv * pb->cols + ju] > 0.0f)) continue;
+            float lim = (rel * r + abs_m) + r;
+            int seen_through = 1;
+            for (int dv = -1; dv <= 1 && seen_through; ++dv) {
+                int vv = jv + dv;
+                if (vv < 0 || vv >= pb->rows) continue;
+                for (int du = -1; du <= 1; ++du) {
+                    int uu = ju + du;
+                    if (uu < 0) uu += pb->cols;
+                    if (uu >= pb->cols) uu -= pb->cols;
+                    float dn = depth_b[(int64_t)vv * pb->cols + uu];
+                    if (dn > 0.0f && !(dn > lim)) {
+                        seen_through = 0;
+                        break;
+                    }
+                }
+            }
+            if (seen_through) {
+                flag_a[k] = 1;
+                ++n;
+            }
+        }
+    }
+    free(rowtab);
+    free(coltab);
+    return n;
+}
+
+/*
+ * Inverse of a rigid pose in a fixed FP64 order: R' = R^T (exact) and
+ * t'_i = -((R_0i t_0 + R_1i t_1) + R_2i t_2), so any implementation that
+ * follows the same order obtains the same bits.
+ */
+void orc_pose_inv_fixed(const double *T, double *out) {
+    for (int i = 0; i < 3; ++i) {
+        for (int j = 0; j < 3; ++j) out[4 * i + j] = T[4 * j + i];
+        out[4 * i + 3] = -((T[i] * T[3] + T[4 + i] * T[7]) + T[8 + i] * T[11]);
+    }
+}
