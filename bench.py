@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=300)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-graph", action="store_true", help="launch eagerly instead of replaying a CUDA graph")
+    ap.add_argument("--atrous-levels", type=int, default=3,
+                    help="also time the a-trous normal smoothing with this many levels (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quiet", action="store_true")
     return ap.parse_args()
@@ -427,9 +429,57 @@ def run_ours(args, ws, rank, local):
     }
     if rank == 0 and args.e2e_steps > 0:
         out["e2e"] = run_e2e(args, seq, h_scans, device, up)
+    if rank == 0 and args.atrous_levels > 0:
+        out["extra_kernels"] = {"atrous_kernel": run_atrous(args, seq, d_scans, device, up, hbm, hbm_src)}
     if dist:
         dist.barrier()
     return out
+
+
+def run_atrous(args, seq, d_scans, device, up, hbm, hbm_src):
+    """The a-trous normal smoothing (Sec. III-A) on the workload's sweeps, timed alone through the C ABI.
+
+    Each repetition loads a different sweep (project + normals, untimed), flushes L2, then times the
+    smoothing launches with CUDA events on the launching stream.  Algorithmic bytes per level and
+    pixel: the normal read (16 B), the point read (16 B) and the normal written (16 B)."""
+    import ctypes
+    import torch
+    levels = args.atrous_levels
+    p = up.Params(accept_quality=0.1, atrous_levels=levels)
+    sw = up.SweepFrame(seq.sweep, device)
+    raw = torch.zeros_like(sw.nrm)
+    out = torch.zeros_like(sw.nrm)
+    tmp = torch.zeros_like(sw.nrm)
+    ps = up.pano_struct(seq.sweep)
+    ap = p.atrous()
+    L = up.lib()
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=device)
+    cr = Cudart()
+    cr.external = False  # eager launches: plain event records
+    reps = min(50, d_scans.shape[0])
+    evs = [(cr.event(), cr.event()) for _ in range(reps)]
+    st = torch.cuda.current_stream().cuda_stream
+    for i in range(reps + 3):
+        sw.load(d_scans[i % d_scans.shape[0]], up.Params(accept_quality=0.1))
+        raw.copy_(sw.nrm)
+        flush.zero_()
+        if i >= 3:
+            cr.record(evs[i - 3][0], st)
+        rc = L.upslam_atrous_normals(ctypes.byref(ps), ctypes.c_void_p(sw.pix.data_ptr()),
+                                     ctypes.c_void_p(raw.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                     ctypes.c_void_p(tmp.data_ptr()), up.F32, ctypes.byref(ap), ctypes.c_void_p(st))
+        assert rc == 0, rc
+        if i >= 3:
+            cr.record(evs[i - 3][1], st)
+    torch.cuda.synchronize()
+    ms = statistics.mean(cr.elapsed(a, b) for a, b in evs)
+    px = seq.sweep.pixels
+    bytes_level = px * 48
+    gbs = bytes_level * levels / (ms * 1e-3) / 1e9
+    return {"levels": levels, "launches": levels, "ms_avg": round(ms, 5), "us_per_level": round(ms * 1e3 / levels, 3),
+            "bytes_per_level": bytes_level, "gbs": round(gbs, 1), "bound": "hbm", "peak": hbm,
+            "frac": round(gbs / hbm, 4), "peak_source": hbm_src, "reps": reps,
+            "l2": "flushed before each repetition (outside the events)"}
 
 
 def run_e2e(args, seq, h_scans, device, up):

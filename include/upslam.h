@@ -94,6 +94,11 @@ typedef struct {
     float jump_rel, jump_abs, min_cross;
 } upslam_normal_params;
 
+/* Point-to-plane error of Eq. 1: squared (Gauss-Newton on sum r^2), or the
+ * absolute value printed in Eq. 1, minimised by iteratively reweighted least
+ * squares: each correspondence weighs w = 1 / max(|r|, loss_delta). */
+typedef enum { UPSLAM_LOSS_L2 = 0, UPSLAM_LOSS_L1 = 1 } upslam_loss;
+
 /* ICP (Sec. III-B, Eq. 1).  Omega keeps a correspondence when the points are
  * within d_max metres and the normals' cosine is >= cos_theta_max. */
 typedef struct {
@@ -102,6 +107,8 @@ typedef struct {
     int32_t min_inliers; /* fewer inliers -> degenerate */
     double eps_rot, eps_trans; /* converged when |omega| < eps_rot and |v| < eps_trans */
     double pivot_eps;          /* Cholesky pivot threshold relative to the largest diagonal */
+    int32_t loss;              /* upslam_loss */
+    float loss_delta;          /* metres; > 0 with UPSLAM_LOSS_L1 */
 } upslam_icp_params;
 
 /* Keyframe update (Sec. III-C). */
@@ -113,9 +120,9 @@ typedef struct {
 
 /* ICP result record, written by the device. */
 typedef struct {
-    double A[21];   /* upper triangle of sum J^T J at the last linearisation, row-major */
-    double b[6];    /* sum J^T r */
-    double sse;     /* sum r^2 */
+    double A[21];   /* upper triangle of sum w J^T J at the last linearisation, row-major */
+    double b[6];    /* sum w J^T r */
+    double sse;     /* sum w r^2 (w = 1 for UPSLAM_LOSS_L2) */
     int64_t inliers;
     int64_t valid;  /* sweep pixels holding a point */
     int32_t status; /* upslam_status of the last step */
@@ -181,6 +188,34 @@ upslam_status upslam_unproject(const float *d_depth, const upslam_pano *pp, cons
  */
 upslam_status upslam_normals(const float *d_pix, const float *d_depth, const upslam_pano *pp,
                              const upslam_normal_params *np, void *d_nrm, int32_t nrm_precision, void *stream);
+
+/*
+ * Edge-avoiding a-trous smoothing of a normal image (Sec. III-A names the
+ * a-trous wavelet filter of Dammertz et al. 2010 for the noisy cross-product
+ * normals; Sec. III-B notes the smoothing aids ICP convergence).  Level
+ * l = 0 .. levels-1 sets each valid pixel p to the normalised sum over the 5 x 5
+ * taps q = p + 2^l (dy, dx), dy, dx in -2..2, of
+ *   h(dy) h(dx) exp(-|N_p - N_q|^2 / sigma_n^2 - (N_p . (P_q - P_p))^2 / (sigma_x |P_p|)^2) N_q,
+ * h = [1, 4, 6, 4, 1] / 16, over valid taps; columns wrap, rows outside the
+ * image are skipped; invalid pixels stay invalid (written as zeros).
+ */
+typedef struct {
+    int32_t levels; /* 0 .. 6, with 2^levels <= cols; 0 copies the input */
+    float sigma_n;  /* normal-difference scale, > 0 */
+    float sigma_x;  /* tangent-plane distance scale relative to the range, > 0 */
+} upslam_atrous_params;
+
+/*
+ * d_pix float4 [rows*cols] pixel points (16-byte aligned); d_nrm_in and
+ * d_nrm_out float4 or half4 [rows*cols] = (nx, ny, nz, valid) in `precision`;
+ * d_tmp a scratch image of the same size, needed when levels >= 2 (else may be
+ * NULL).  The three normal buffers must not alias.  One launch per level on
+ * `stream`; the result is in d_nrm_out.  Invalid arguments return
+ * UPSLAM_ERR_INVALID_ARG before any launch.
+ */
+upslam_status upslam_atrous_normals(const upslam_pano *pp, const float *d_pix, const void *d_nrm_in,
+                                    void *d_nrm_out, void *d_tmp, int32_t precision,
+                                    const upslam_atrous_params *ap, void *stream);
 
 /* Workspace bytes that upslam_icp_step / upslam_icp need for this keyframe. */
 size_t upslam_icp_workspace_bytes(const upslam_keyframe *kf);
@@ -321,6 +356,54 @@ upslam_status upslam_icp_batched(const upslam_keyframe *d_kfs, const upslam_keyf
                                  const upslam_sweep *sw, int32_t n_hyp, double *d_poses, const upslam_icp_params *ip,
                                  upslam_icp_stats *d_stats, void *d_ws, size_t ws_bytes,
                                  const upslam_batch_tiles *tiles, void *stream);
+
+/*
+ * Loop-closure grid search (Sec. III-C): candidate transformations are scored
+ * by low-resolution projective alignment checks and the best is promoted to a
+ * full-resolution ICP registration.  A candidate's score is its number of
+ * inliers of the ICP association (keyframe pixel -> sweep pixel under T^-1,
+ * the FP32 binning rule, Omega with ip->d_max and ip->cos_theta_max) over the
+ * keyframe pixels (stride i, stride j).
+ *
+ * d_poses: FP64 [n][12] candidates, row-major [R | t] (keyframe <- sweep).
+ * d_scores: u64 [n] (overwritten; 8-byte aligned).  d_best: int32 [1], the
+ * first candidate with the largest score.  d_best_pose12: FP64 [12] copy of
+ * that candidate, or NULL.  Two launches (scores, winner) after a memset of
+ * d_scores, all on `stream`; n <= 524280.  Invalid arguments return
+ * UPSLAM_ERR_INVALID_ARG before any launch.
+ */
+upslam_status upslam_grid_score(const upslam_keyframe *kf, const upslam_sweep *sw, const double *d_poses, int32_t n,
+                                int32_t stride, const upslam_icp_params *ip, uint64_t *d_scores, int32_t *d_best,
+                                double *d_best_pose12, void *stream);
+
+/* Candidate poses d_poses[i] = exp(xi_i^) * center (FP64 [n][12]) for FP32 twists
+ * d_xi [n][6] = (omega, v), e.g. a grid of offsets around the current estimate. */
+upslam_status upslam_grid_candidates(const double *d_center12, const float *d_xi, int32_t n, double *d_poses,
+                                     void *stream);
+
+/*
+ * Keyframe mutual consistency check (Sec. III-C: run whenever keyframes are
+ * switched, it filters moving objects from the map).  A sample of keyframe A
+ * is removed when keyframe B saw through it: binned into B (FP32 rule, T_ab =
+ * pose of B in A rounded to FP32, range r), B holds a depth there and every
+ * depth-holding pixel of the 3 x 3 neighbourhood (columns wrapped, rows
+ * clipped) lies beyond (rel * r + abs_m) + r (FP32).  B's samples are checked
+ * against A with T_ba = [R^T | -R^T t] (FP64, t' summed in the order
+ * -((R_0i t_0 + R_1i t_1) + R_2i t_2)).  Both directions read the unmodified
+ * depths; then the flagged pixels of both keyframes are emptied (depth 0,
+ * normal and count 0).
+ *
+ * d_ws: upslam_consistency_workspace_bytes(kf_a, kf_b) bytes, 256-byte aligned;
+ * it keeps the flags (one byte per pixel: A's at offset 0, B's at the next
+ * multiple of 256 after A's).  d_removed2: int64 [2] = samples removed from A and
+ * B (overwritten), or NULL.  The keyframes must be distinct buffers.  Two
+ * launches on `stream`; invalid arguments return UPSLAM_ERR_INVALID_ARG before
+ * any launch.
+ */
+size_t upslam_consistency_workspace_bytes(const upslam_keyframe *kf_a, const upslam_keyframe *kf_b);
+upslam_status upslam_keyframe_consistency(const upslam_keyframe *kf_a, const upslam_keyframe *kf_b,
+                                          const double *d_T_ab12, float rel, float abs_m, void *d_ws, size_t ws_bytes,
+                                          int64_t *d_removed2, void *stream);
 
 /*
  * Pose-proposal network (learned initial guess).  The paper has no learned

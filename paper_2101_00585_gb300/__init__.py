@@ -9,9 +9,12 @@ ICP and keyframe fusion as hand-written CUDA behind the C ABI of include/upslam.
 The library is built in-tree by ``paper_2101_00585_gb300.build.build()``.
 """
 from ._abi import F16, F32, LIB_PATH, UpslamError, lib  # noqa: F401
-from .api import (Batch, IcpState, KeyframeBuffer, Params, SweepFrame, Tracker, empty_zbuf, fuse, icp, icp_step,  # noqa: F401
-                  identity_pose, normals, pano_dirs, pano_struct, project, unproject)
+from .api import (Batch, IcpState, KeyframeBuffer, Params, SweepFrame, Tracker, atrous_normals, empty_zbuf, fuse,  # noqa: F401
+                  grid_candidates, grid_score, icp, icp_step, identity_pose, keyframe_consistency, normals, pano_dirs,
+                  pano_struct, project, unproject)
 
-__all__ = ["Batch", "Tracker", "Params", "SweepFrame", "KeyframeBuffer", "IcpState", "project", "normals", "icp", "icp_step",
+__all__ = ["Batch", "Tracker", "Params", "SweepFrame", "KeyframeBuffer", "IcpState", "project", "normals", "atrous_normals", "grid_candidates",
+           "grid_score", "keyframe_consistency", "icp",
+           "icp_step",
            "fuse", "unproject", "pano_dirs", "pano_struct", "identity_pose", "empty_zbuf", "lib", "UpslamError", "F32",
            "F16", "LIB_PATH"]

@@ -13,6 +13,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libupslam.so")
 
 OK, ERR_INVALID_ARG, ERR_CUDA, ERR_DEGENERATE, ERR_NOT_CONVERGED, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_CAPACITY = range(8)
+LOSS_L2, LOSS_L1 = 0, 1
 F32, F16 = 0, 1
 
 
@@ -29,7 +30,7 @@ class NormalParams(ctypes.Structure):
 class IcpParams(ctypes.Structure):
     _fields_ = [("d_max", ctypes.c_float), ("cos_theta_max", ctypes.c_float), ("max_iters", ctypes.c_int32),
                 ("min_inliers", ctypes.c_int32), ("eps_rot", ctypes.c_double), ("eps_trans", ctypes.c_double),
-                ("pivot_eps", ctypes.c_double)]
+                ("pivot_eps", ctypes.c_double), ("loss", ctypes.c_int32), ("loss_delta", ctypes.c_float)]
 
 
 class FuseParams(ctypes.Structure):
@@ -58,6 +59,10 @@ class BatchTiles(ctypes.Structure):
     _fields_ = [("threads", ctypes.c_int32), ("chunk", ctypes.c_int32)]
 
 
+class AtrousParams(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int32), ("sigma_n", ctypes.c_float), ("sigma_x", ctypes.c_float)]
+
+
 STATS_BYTES = ctypes.sizeof(IcpStats)
 KEYFRAME_BYTES = ctypes.sizeof(Keyframe)
 _P = ctypes.POINTER
@@ -70,6 +75,7 @@ SIGNATURES = {
     "upslam_project": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, _P(Pano), _vp, _vp, _vp, _vp, _vp]),
     "upslam_unproject": (ctypes.c_int, [_vp, _P(Pano), _vp, _vp, _vp]),
     "upslam_normals": (ctypes.c_int, [_vp, _vp, _P(Pano), _P(NormalParams), _vp, ctypes.c_int32, _vp]),
+    "upslam_atrous_normals": (ctypes.c_int, [_P(Pano), _vp, _vp, _vp, _vp, ctypes.c_int32, _P(AtrousParams), _vp]),
     "upslam_icp_workspace_bytes": (ctypes.c_size_t, [_P(Keyframe)]),
     "upslam_icp_step": (ctypes.c_int, [_P(Keyframe), _P(Sweep), _vp, _P(IcpParams), _vp, _vp, ctypes.c_size_t, _vp]),
     "upslam_icp": (ctypes.c_int, [_P(Keyframe), _P(Sweep), _vp, _P(IcpParams), _vp, _vp, ctypes.c_size_t, _vp]),
@@ -86,6 +92,12 @@ SIGNATURES = {
                                                              _P(BatchTiles)]),
     "upslam_icp_batched": (ctypes.c_int, [_vp, _P(Keyframe), ctypes.c_int32, _P(Sweep), ctypes.c_int32, _vp,
                                           _P(IcpParams), _vp, _vp, ctypes.c_size_t, _P(BatchTiles), _vp]),
+    "upslam_grid_score": (ctypes.c_int, [_P(Keyframe), _P(Sweep), _vp, ctypes.c_int32, ctypes.c_int32, _P(IcpParams),
+                                         _vp, _vp, _vp, _vp]),
+    "upslam_grid_candidates": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, _vp, _vp]),
+    "upslam_consistency_workspace_bytes": (ctypes.c_size_t, [_P(Keyframe), _P(Keyframe)]),
+    "upslam_keyframe_consistency": (ctypes.c_int, [_P(Keyframe), _P(Keyframe), _vp, ctypes.c_float, ctypes.c_float,
+                                                   _vp, ctypes.c_size_t, _vp, _vp]),
     "upslam_cnn_param_count": (ctypes.c_size_t, []),
     "upslam_cnn_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int32]),
     "upslam_cnn_forward": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, _vp, _vp, ctypes.c_size_t, _vp]),

@@ -49,20 +49,31 @@ class Params:
     eps_rot: float = 1e-6
     eps_trans: float = 1e-6
     pivot_eps: float = 1e-12
+    # Eq. 1's |.|: LOSS_L2 squares the point-to-plane error (Gauss-Newton); LOSS_L1 minimises it as
+    # printed by IRLS with weights 1 / max(|r|, loss_delta)
+    loss: int = 0
+    loss_delta: float = 0.01
     fuse_d_max: float = 0.2
     fuse_cos_theta_max: float = math.cos(math.radians(30.0))
     w_max: float = 10.0
     accept_quality: float = 0.1
+    # edge-avoiding a-trous smoothing of the sweep normals (Sec. III-A); 0 levels = off
+    atrous_levels: int = 0
+    atrous_sigma_n: float = 0.5
+    atrous_sigma_x: float = 0.02
 
     def normal(self):
         return _abi.NormalParams(self.jump_rel, self.jump_abs, self.min_cross)
 
     def icp(self):
         return _abi.IcpParams(self.d_max, self.cos_theta_max, self.max_iters, self.min_inliers, self.eps_rot,
-                              self.eps_trans, self.pivot_eps)
+                              self.eps_trans, self.pivot_eps, self.loss, self.loss_delta)
 
     def fuse(self):
         return _abi.FuseParams(self.fuse_d_max, self.fuse_cos_theta_max, self.w_max, self.accept_quality)
+
+    def atrous(self):
+        return _abi.AtrousParams(self.atrous_levels, self.atrous_sigma_n, self.atrous_sigma_x)
 
 
 def empty_zbuf(npx: int, device) -> torch.Tensor:
@@ -127,6 +138,19 @@ def normals(pix: torch.Tensor, depth: torch.Tensor, pp, params: Params = Params(
     return out
 
 
+def atrous_normals(pix: torch.Tensor, nrm: torch.Tensor, pp, params: Params = Params(), precision: int = F32):
+    """Edge-avoiding a-trous smoothing (Sec. III-A) of a [H,W,4] normal image -> a new [H,W,4] image."""
+    _require_cuda(pix, nrm)
+    out = torch.empty_like(nrm)
+    tmp = torch.empty_like(nrm)
+    ps = pano_struct(pp)
+    ap = params.atrous()
+    _abi.check("upslam_atrous_normals",
+               _abi.lib().upslam_atrous_normals(ctypes.byref(ps), _p(pix.contiguous()), _p(nrm.contiguous()), _p(out),
+                                                _p(tmp), precision, ctypes.byref(ap), _stream()))
+    return out
+
+
 class SweepFrame:
     """Device buffers of one sweep panorama: pixel points and normals."""
 
@@ -139,20 +163,32 @@ class SweepFrame:
         self.idx = torch.zeros((H, W), dtype=torch.int32, device=device)
         self.pix = torch.zeros((H, W, 4), dtype=torch.float32, device=device)
         self.nrm = torch.zeros((H, W, 4), dtype=torch.float32 if precision == F32 else torch.float16, device=device)
+        self._raw = self._tmp = None  # unsmoothed normals and a-trous scratch, allocated on first use
         self._ps = pano_struct(pp)
 
     def struct(self) -> _abi.Sweep:
         return _abi.Sweep(self._ps, self.pix.data_ptr(), self.nrm.data_ptr(), self.precision)
 
     def load(self, pts4: torch.Tensor, params: Params) -> None:
-        """project + normals for a scan already on the device (float4 points)."""
+        """project + normals (+ a-trous smoothing when params.atrous_levels > 0) for a scan already on
+        the device (float4 points)."""
         L = _abi.lib()
         s = _stream()
         _abi.check("upslam_project", L.upslam_project(_p(pts4), pts4.shape[0], None, ctypes.byref(self._ps),
                                                       _p(self.zbuf), _p(self.depth), _p(self.idx), _p(self.pix), s))
         npar = params.normal()
+        levels = int(params.atrous_levels)
+        if levels > 0 and self._raw is None:
+            self._raw = torch.zeros_like(self.nrm)
+            self._tmp = torch.zeros_like(self.nrm)
+        dst = self._raw if levels > 0 else self.nrm
         _abi.check("upslam_normals", L.upslam_normals(_p(self.pix), _p(self.depth), ctypes.byref(self._ps),
-                                                      ctypes.byref(npar), _p(self.nrm), self.precision, s))
+                                                      ctypes.byref(npar), _p(dst), self.precision, s))
+        if levels > 0:
+            ap = params.atrous()
+            _abi.check("upslam_atrous_normals",
+                       L.upslam_atrous_normals(ctypes.byref(self._ps), _p(self.pix), _p(self._raw), _p(self.nrm),
+                                               _p(self._tmp), self.precision, ctypes.byref(ap), s))
 
     def set(self, pix: torch.Tensor, nrm: torch.Tensor) -> None:
         """Use given pixel points / normals (e.g. test inputs) instead of computing them."""
@@ -253,19 +289,28 @@ class Tracker:
         self.fused = fused
         self._ip, self._fp = params.icp(), params.fuse()
 
-    def new_keyframe(self, pts4: torch.Tensor | None = None, buffer: KeyframeBuffer | None = None) -> None:
+    def new_keyframe(self, pts4: torch.Tensor | None = None, buffer: KeyframeBuffer | None = None,
+                     consistency: bool = False) -> None:
         """Start a keyframe at the sweep in ``self.sw`` (loading ``pts4`` first if given).
 
         ``buffer``: an all-zero keyframe buffer to use from now on (for example one of a
         pre-allocated pool); without it the current buffer is cleared and reused.
+        ``consistency`` (needs ``buffer``): run the mutual consistency check (Sec. III-C)
+        between the keyframe being left and the new one; the new keyframe's pose in the old
+        one is the last registered sweep pose.
         """
         if pts4 is not None:
             self.sw.load(pts4, self.params)
+        old = self.kf
         if buffer is not None:
             self.kf = buffer
         else:
+            if consistency:
+                raise ValueError("the consistency check needs a separate buffer for the new keyframe")
             self.kf.clear()
         fuse(self.kf, self.sw, self.identity, self.params, None)
+        if consistency:
+            self.last_removed = keyframe_consistency(old, self.kf, self.state.pose)[0]
         self.prev.copy_(self.identity)
 
     # optional profiling hook: (recorder, stream, proj_events, icp_events, fuse_events); the recorder's
@@ -309,13 +354,64 @@ class Tracker:
                                                 ctypes.byref(self._fp), _p(self.state.stats), _p(self.kf.zbuf), s))
         self._mark(2, 1)
 
-    # kernels launched by one track() call: project (2), normals, then one persistent
-    # register + update launch (fused), or register + fuse (2) otherwise
+    # kernels launched by one track() call: project (2), normals, one per a-trous level, then
+    # one persistent register + update launch (fused), or register + fuse (2) otherwise
     @property
     def launches_per_track(self) -> int:
-        return 4 if self.fused else 6
+        return (4 if self.fused else 6) + int(self.params.atrous_levels)
     # kernels launched by new_keyframe() (after loading): fuse (2)
     LAUNCHES_PER_NEW_KEYFRAME = 2
+
+
+# ----------------------------------------------------------------------------- loop-closure grid search
+
+def grid_candidates(center: torch.Tensor, xi: torch.Tensor) -> torch.Tensor:
+    """Candidate poses exp(xi_i^) * center: center FP64 [12], xi FP32 [n, 6] -> FP64 [n, 12]."""
+    _require_cuda(center, xi)
+    xi = xi.contiguous().to(torch.float32)
+    out = torch.empty((xi.shape[0], 12), dtype=torch.float64, device=xi.device)
+    _abi.check("upslam_grid_candidates", _abi.lib().upslam_grid_candidates(_p(center.contiguous()), _p(xi),
+                                                                           xi.shape[0], _p(out), _stream()))
+    return out
+
+
+def grid_score(kf: "KeyframeBuffer", sw: "SweepFrame", poses: torch.Tensor, params: Params = Params(),
+               stride: int = 4):
+    """Sec. III-C grid search: inlier counts of the candidates [n, 12] on the keyframe sampled every
+    ``stride`` pixels -> (scores int64 [n], best int32 [1], best pose FP64 [12]), all on the device."""
+    _require_cuda(poses)
+    poses = poses.contiguous()
+    n = poses.shape[0]
+    scores = torch.empty(n, dtype=torch.int64, device=poses.device)
+    best = torch.empty(1, dtype=torch.int32, device=poses.device)
+    best_pose = torch.empty(12, dtype=torch.float64, device=poses.device)
+    ks, ss, ip = kf.struct(), sw.struct(), params.icp()
+    _abi.check("upslam_grid_score", _abi.lib().upslam_grid_score(ctypes.byref(ks), ctypes.byref(ss), _p(poses), n,
+                                                                 int(stride), ctypes.byref(ip), _p(scores), _p(best),
+                                                                 _p(best_pose), _stream()))
+    return scores, best, best_pose
+
+
+# ----------------------------------------------------------------------------- keyframe consistency
+
+def keyframe_consistency(kf_a: "KeyframeBuffer", kf_b: "KeyframeBuffer", T_ab: torch.Tensor, rel: float = 0.05,
+                         abs_m: float = 0.2):
+    """Sec. III-C mutual consistency check between two keyframes (T_ab: pose of B in A, FP64 [12] on the
+    device).  Samples of each keyframe that the other saw through are removed in place.
+    -> (removed int64 [2] on the device, flags_a uint8 [Ha, Wa], flags_b uint8 [Hb, Wb])."""
+    _require_cuda(T_ab)
+    L = _abi.lib()
+    ka, kb = kf_a.struct(), kf_b.struct()
+    nbytes = int(L.upslam_consistency_workspace_bytes(ctypes.byref(ka), ctypes.byref(kb)))
+    ws = torch.zeros(nbytes, dtype=torch.uint8, device=T_ab.device)
+    removed = torch.zeros(2, dtype=torch.int64, device=T_ab.device)
+    _abi.check("upslam_keyframe_consistency",
+               L.upslam_keyframe_consistency(ctypes.byref(ka), ctypes.byref(kb), _p(T_ab.contiguous()), float(rel),
+                                             float(abs_m), _p(ws), nbytes, _p(removed), _stream()))
+    Ha, Wa = int(kf_a.pp.rows), int(kf_a.pp.cols)
+    Hb, Wb = int(kf_b.pp.rows), int(kf_b.pp.cols)
+    off_b = (Ha * Wa + 255) // 256 * 256
+    return removed, ws[:Ha * Wa].view(Ha, Wa), ws[off_b:off_b + Hb * Wb].view(Hb, Wb)
 
 
 # ----------------------------------------------------------------------------- batched registration

@@ -49,6 +49,8 @@ struct BatchArgs {
     const void *snrm;
     int sprec;
     float d_max2, cos_min;
+    int l1;                   // 1: absolute error by IRLS, weights 1 / max(|r|, loss_delta)
+    float loss_delta;
     double *poses;            // [n_prob][12] in/out
     upslam_icp_stats *stats;  // [n_prob]
     int *active;              // [n_prob] workspace flags
@@ -192,8 +194,10 @@ __global__ void __launch_bounds__(512, 1) icp_batched_kernel(BatchArgs a) {
                     const float ex = px - s.x, ey = py - s.y, ez = pz - s.z;
                     ok = ok && (ex * ex + ey * ey + ez * ez <= a.d_max2) &&
                          (Rm.x * n.x + Rm.y * n.y + Rm.z * n.z >= a.cos_min);
-                    const float w = ok ? 1.0f : 0.0f;
-                    const float res = (ex * n.x + ey * n.y + ez * n.z) * w;
+                    const float r0 = ex * n.x + ey * n.y + ez * n.z;
+                    // square root of the IRLS weight (1 for the squared error); 0 for an outlier
+                    const float w = ok ? (a.l1 ? rsqrtf(fmaxf(fabsf(r0), a.loss_delta)) : 1.0f) : 0.0f;
+                    const float res = r0 * w;
                     float J[6];
                     J[0] = (py * n.z - pz * n.y) * w;
                     J[1] = (pz * n.x - px * n.z) * w;
@@ -382,7 +386,7 @@ extern "C" upslam_status upslam_icp_batched(const upslam_keyframe *d_kfs, const 
     }
     const int threads = batch_threads(tiles), chunk = batch_chunk(tiles);
     if ((threads != 256 && threads != 512) || chunk < threads || chunk % threads) return UPSLAM_ERR_INVALID_ARG;
-    if (!(ip->d_max > 0.0f) || ip->max_iters < 1 || !upslam_aligned(d_ws, 256)) return UPSLAM_ERR_INVALID_ARG;
+    if (!upslam_icp_params_ok(ip) || ip->max_iters < 1 || !upslam_aligned(d_ws, 256)) return UPSLAM_ERR_INVALID_ARG;
     int dev = 0, coop = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
@@ -419,6 +423,8 @@ extern "C" upslam_status upslam_icp_batched(const upslam_keyframe *d_kfs, const 
     a.sprec = sw->nrm_precision;
     a.d_max2 = ip->d_max * ip->d_max;
     a.cos_min = ip->cos_theta_max;
+    a.l1 = ip->loss == UPSLAM_LOSS_L1 ? 1 : 0;
+    a.loss_delta = ip->loss_delta;
     a.poses = d_poses;
     a.stats = d_stats;
     a.active = reinterpret_cast<int *>(ws + off_active);

@@ -639,6 +639,11 @@ static inline bool upslam_pano_ok(const upslam_pano *pp) {
 
 static inline bool upslam_aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
+static inline bool upslam_icp_params_ok(const upslam_icp_params *ip) {
+    return ip && ip->d_max > 0.0f && ip->max_iters >= 0 && ip->min_inliers >= 0 &&
+           (ip->loss == UPSLAM_LOSS_L2 || (ip->loss == UPSLAM_LOSS_L1 && ip->loss_delta > 0.0f));
+}
+
 // Multiprocessor count of the current device, cached per device ordinal.
 static inline int upslam_sm_count() {
     static int cache[64] = {0};

@@ -50,7 +50,17 @@ struct IcpArgs {
     int sprec;
     float d_max2;
     float cos_min;
+    int l1;            // 1: absolute error by IRLS (weights 1 / max(|r|, loss_delta)); 0: squared error
+    float loss_delta;
 };
+
+// Square root of the IRLS weight of residual r: each correspondence enters the
+// normal equations as (s J, s r), so J^T J, J^T r and r^2 carry w = s^2.  The
+// loss is a template parameter, so the squared-error kernels carry no trace of it.
+template <int L1>
+__device__ __forceinline__ float irls_scale(const IcpArgs &a, float r) {
+    return L1 ? rsqrtf(fmaxf(fabsf(r), a.loss_delta)) : 1.0f;
+}
 
 // Motion prior folded into the persistent launch (upslam_register).
 struct PriorArgs {
@@ -69,6 +79,7 @@ struct IcpCtrl {
     unsigned long long arrive64;       // persistent form: CTA arrivals, monotonic across launches
 };
 
+template <int L1>
 __device__ __forceinline__ void accumulate_pixel(const IcpArgs &a, const PoseF &T, int k, float acc[28], int &inl) {
     const float d = __ldg(a.kdepth + k);
     if (!(d > 0.0f)) return;
@@ -94,14 +105,16 @@ __device__ __forceinline__ void accumulate_pixel(const IcpArgs &a, const PoseF &
     const float ex = px - s.x, ey = py - s.y, ez = pz - s.z;
     if (!(ex * ex + ey * ey + ez * ez <= a.d_max2)) return;
     if (!(Rm.x * n.x + Rm.y * n.y + Rm.z * n.z >= a.cos_min)) return;
-    const float res = ex * n.x + ey * n.y + ez * n.z;
+    const float r0 = ex * n.x + ey * n.y + ez * n.z;
+    const float w = irls_scale<L1>(a, r0);
+    const float res = r0 * w;
     float J[6];
-    J[0] = py * n.z - pz * n.y;
-    J[1] = pz * n.x - px * n.z;
-    J[2] = px * n.y - py * n.x;
-    J[3] = n.x;
-    J[4] = n.y;
-    J[5] = n.z;
+    J[0] = (py * n.z - pz * n.y) * w;
+    J[1] = (pz * n.x - px * n.z) * w;
+    J[2] = (px * n.y - py * n.x) * w;
+    J[3] = n.x * w;
+    J[4] = n.y * w;
+    J[5] = n.z * w;
     int p = 0;
 #pragma unroll
     for (int i = 0; i < 6; ++i)
@@ -231,6 +244,7 @@ __device__ __forceinline__ int count_valid(const IcpArgs &a) {
     return c;
 }
 
+template <int L1>
 __global__ void __launch_bounds__(kIcpThreads) icp_step_kernel(IcpArgs a, double *pose, upslam_icp_params ip,
                                                                upslam_icp_stats *st, IcpCtrl *ctrl,
                                                                float *partials) {
@@ -245,7 +259,7 @@ __global__ void __launch_bounds__(kIcpThreads) icp_step_kernel(IcpArgs a, double
     int inl = 0;
     const int npx = a.kp.rows * a.kp.cols;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < npx; k += gridDim.x * blockDim.x)
-        accumulate_pixel(a, T, k, acc, inl);
+        accumulate_pixel<L1>(a, T, k, acc, inl);
     const int valid = count_valid(a);
     cta_partial(acc, inl, valid, partials + (size_t)blockIdx.x * kSlots, sh, shi);
     __syncthreads();
@@ -281,6 +295,7 @@ constexpr int kTileWarps = kTileThreads / 32;
 constexpr int kStageGroup = 4;  // keyframe chunks staged per memory round trip
 
 // One staged correspondence, branch-free: a rejected pair contributes zeros.
+template <int L1>
 __device__ __forceinline__ void accumulate_entry(const IcpArgs &a, const PoseF &T, float3 s, float3 n, float acc[28],
                                                  int &inl) {
     const float3 q = xform_inv(T, s.x, s.y, s.z);
@@ -298,8 +313,9 @@ __device__ __forceinline__ void accumulate_entry(const IcpArgs &a, const PoseF &
     const float3 Rm = rotate(T, m.x, m.y, m.z);
     const float ex = px - s.x, ey = py - s.y, ez = pz - s.z;
     ok = ok && (ex * ex + ey * ey + ez * ez <= a.d_max2) && (Rm.x * n.x + Rm.y * n.y + Rm.z * n.z >= a.cos_min);
-    const float w = ok ? 1.0f : 0.0f;
-    const float res = (ex * n.x + ey * n.y + ez * n.z) * w;
+    const float r0 = ex * n.x + ey * n.y + ez * n.z;
+    const float w = ok ? irls_scale<L1>(a, r0) : 0.0f;
+    const float res = r0 * w;
     float J[6];
     J[0] = (py * n.z - pz * n.y) * w;
     J[1] = (pz * n.x - px * n.z) * w;
@@ -451,6 +467,7 @@ __device__ __forceinline__ bool grid_arrive_wait(unsigned long long *ctr, unsign
 // every CTA sums all records and solves redundantly: identical arithmetic on
 // identical data gives every CTA the same pose, so no CTA waits for another
 // to broadcast it.  CTA 0 writes the pose and the record at the end.
+template <int L1>
 __global__ void __launch_bounds__(kTileThreads, 1)
     icp_tile_kernel(IcpArgs a, double *pose, upslam_icp_params ip, upslam_icp_stats *st, IcpCtrl *ctrl,
                     float *partials, int cap, PriorArgs pr, FuseView fz, int fuse_on) {
@@ -589,10 +606,11 @@ __global__ void __launch_bounds__(kTileThreads, 1)
         int inl = 0;
 #pragma unroll 2
         for (int e = threadIdx.x; e < staged; e += kTileThreads)
-            accumulate_entry(a, T, make_float3(sx[e], sy[e], sz[e]), make_float3(snx[e], sny[e], snz[e]), acc, inl);
+            accumulate_entry<L1>(a, T, make_float3(sx[e], sy[e], sz[e]), make_float3(snx[e], sny[e], snz[e]), acc,
+                                 inl);
         for (int q = spill_q; q < nchunks; q += gridDim.x) {
             const int k = q * kTileThreads + threadIdx.x;
-            if (k < npx) accumulate_pixel(a, T, k, acc, inl);
+            if (k < npx) accumulate_pixel<L1>(a, T, k, acc, inl);
         }
         const int valid = it == 0 ? count_valid(a) : 0;
         float *rec = partials + (size_t)(it & 1) * gridDim.x * kSlots;
@@ -745,6 +763,8 @@ static IcpArgs make_args(const upslam_keyframe *kf, const upslam_sweep *sw, cons
     a.sprec = sw->nrm_precision;
     a.d_max2 = ip->d_max * ip->d_max;
     a.cos_min = ip->cos_theta_max;
+    a.l1 = ip->loss == UPSLAM_LOSS_L1 ? 1 : 0;
+    a.loss_delta = ip->loss_delta;
     return a;
 }
 
@@ -774,19 +794,20 @@ static upslam_status launch_tile(const IcpArgs &a, double *pose, const upslam_ic
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (!coop) return UPSLAM_ERR_UNSUPPORTED;
-    static bool attr_set[64] = {false};
-    static size_t static_smem[64] = {0};
+    static bool attr_set[2][64] = {{false}};
+    static size_t static_smem[2][64] = {{0}};
     if (dev < 0 || dev >= 64) return UPSLAM_ERR_UNSUPPORTED;
+    const int var = a.l1 ? 1 : 0;
+    const void *fn = var ? (const void *)icp_tile_kernel<1> : (const void *)icp_tile_kernel<0>;
     const size_t reserve = 1024;
-    if (!attr_set[dev]) {
+    if (!attr_set[var][dev]) {
         cudaFuncAttributes fa;
-        if (cudaFuncGetAttributes(&fa, icp_tile_kernel) != cudaSuccess) return UPSLAM_ERR_CUDA;
-        static_smem[dev] = fa.sharedSizeBytes;
+        if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) return UPSLAM_ERR_CUDA;
+        static_smem[var][dev] = fa.sharedSizeBytes;
         const int dyn_max = optin - (int)fa.sharedSizeBytes - (int)reserve;
-        if (dyn_max <= 0 ||
-            cudaFuncSetAttribute(icp_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max) != cudaSuccess)
+        if (dyn_max <= 0 || cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max) != cudaSuccess)
             return UPSLAM_ERR_UNSUPPORTED;
-        attr_set[dev] = true;
+        attr_set[var][dev] = true;
     }
     const int grid = upslam_sm_count();
     const int64_t npx = (int64_t)a.kp.rows * a.kp.cols;
@@ -794,12 +815,13 @@ static upslam_status launch_tile(const IcpArgs &a, double *pose, const upslam_ic
     const int64_t per = (nchunks + grid - 1) / grid * kTileThreads;  // most pixels one CTA can stage
     // each staged sample: point (3), normal (3), count, depth, pixel index
     constexpr int64_t kWords = 9;
-    const int64_t cap_max = ((int64_t)optin - (int64_t)static_smem[dev] - (int64_t)reserve) / (kWords * (int64_t)sizeof(float));
+    const int64_t cap_max =
+        ((int64_t)optin - (int64_t)static_smem[var][dev] - (int64_t)reserve) / (kWords * (int64_t)sizeof(float));
     const int cap = (int)(per < cap_max ? (per > 0 ? per : 1) : cap_max);
     const size_t dyn = (size_t)cap * kWords * sizeof(float);
     if (kCtrlBytes + 2 * (size_t)grid * kSlots * sizeof(float) > ws_bytes) return UPSLAM_ERR_CAPACITY;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, icp_tile_kernel, kTileThreads, dyn) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kTileThreads, dyn) != cudaSuccess ||
         per_sm < 1)
         return UPSLAM_ERR_UNSUPPORTED;
     IcpCtrl *ctrl = reinterpret_cast<IcpCtrl *>(ws);
@@ -817,7 +839,7 @@ static upslam_status launch_tile(const IcpArgs &a, double *pose, const upslam_ic
         memset(&fzc, 0, sizeof(fzc));
     }
     void *args[] = {&ac, &pose, &ipc, &st, &ctrl, &partials, &capc, &prc, &fzc, &fuse_on};
-    if (cudaLaunchCooperativeKernel((const void *)icp_tile_kernel, dim3(grid), dim3(kTileThreads), args, dyn, stream) !=
+    if (cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kTileThreads), args, dyn, stream) !=
         cudaSuccess) {
         (void)cudaGetLastError();
         return UPSLAM_ERR_CUDA;
@@ -839,7 +861,7 @@ static upslam_status icp_common_checks(const upslam_keyframe *kf, const upslam_s
                                        size_t ws_bytes) {
     if (!views_ok(kf, sw) || !d_pose12 || !ip || !d_stats || !d_ws) return UPSLAM_ERR_INVALID_ARG;
     if (!upslam_aligned(d_ws, 256) || ws_bytes < upslam_icp_workspace_bytes(kf)) return UPSLAM_ERR_INVALID_ARG;
-    if (!(ip->d_max > 0.0f) || ip->max_iters < 0 || ip->min_inliers < 0) return UPSLAM_ERR_INVALID_ARG;
+    if (!upslam_icp_params_ok(ip)) return UPSLAM_ERR_INVALID_ARG;
     return UPSLAM_OK;
 }
 
@@ -853,7 +875,10 @@ extern "C" upslam_status upslam_icp_step(const upslam_keyframe *kf, const upslam
     const int grid = upslam_grid(npx, kIcpThreads, 8);
     IcpCtrl *ctrl = reinterpret_cast<IcpCtrl *>(d_ws);
     float *partials = reinterpret_cast<float *>(reinterpret_cast<char *>(d_ws) + kCtrlBytes);
-    icp_step_kernel<<<grid, kIcpThreads, 0, (cudaStream_t)stream>>>(a, d_pose12, *ip, d_stats, ctrl, partials);
+    if (a.l1)
+        icp_step_kernel<1><<<grid, kIcpThreads, 0, (cudaStream_t)stream>>>(a, d_pose12, *ip, d_stats, ctrl, partials);
+    else
+        icp_step_kernel<0><<<grid, kIcpThreads, 0, (cudaStream_t)stream>>>(a, d_pose12, *ip, d_stats, ctrl, partials);
     UPSLAM_CHECK_LAUNCH();
     return UPSLAM_OK;
 }
@@ -953,7 +978,7 @@ extern "C" size_t upslam_icp_noalloc_capacity_bytes(void) { return kNoAllocBytes
 extern "C" upslam_status upslam_icp_noalloc(const upslam_keyframe *kf, const upslam_sweep *sw, double *d_pose12,
                                             const upslam_icp_params *ip, upslam_icp_stats *d_stats, void *stream) {
     if (!views_ok(kf, sw) || !d_pose12 || !ip || !d_stats) return UPSLAM_ERR_INVALID_ARG;
-    if (!(ip->d_max > 0.0f) || ip->max_iters < 0 || ip->min_inliers < 0) return UPSLAM_ERR_INVALID_ARG;
+    if (!upslam_icp_params_ok(ip)) return UPSLAM_ERR_INVALID_ARG;
     if (ip->max_iters == 0) return UPSLAM_OK;
     // the scratch a launch on this device needs (two records per SM) must fit the fixed array
     if (kCtrlBytes + 2 * (size_t)upslam_sm_count() * kSlots * sizeof(float) > kNoAllocBytes)

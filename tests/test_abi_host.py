@@ -73,14 +73,31 @@ def test_invalid_arguments_are_rejected_on_the_host():
     fp = _abi.FuseParams(0.2, 0.86, 0.5, 0.1)  # w_max < 1
     assert L.upslam_fuse(ctypes.byref(ks), ctypes.byref(ss), fake, ctypes.byref(fp), None, fake,
                          None) == _abi.ERR_INVALID_ARG
+    # unknown loss, or the absolute error without a positive delta
+    for bad_ip in (_abi.IcpParams(0.5, 0.86, 10, 6, 1e-6, 1e-6, 1e-12, 2, 0.01),
+                   _abi.IcpParams(0.5, 0.86, 10, 6, 1e-6, 1e-6, 1e-12, 1, 0.0)):
+        assert L.upslam_icp(ctypes.byref(ks), ctypes.byref(ss), fake, ctypes.byref(bad_ip), fake, fake, ws,
+                            None) == _abi.ERR_INVALID_ARG
     assert L.upslam_predict_pose(None, None, fake, None) == _abi.ERR_INVALID_ARG
     assert L.upslam_update_motion(fake, None, fake, None) == _abi.ERR_INVALID_ARG
+    ap = _abi.AtrousParams(3, 0.5, 0.02)
+    f2 = [ctypes.c_void_p(256 * i) for i in (1, 2, 3, 4)]
+    assert L.upslam_atrous_normals(ctypes.byref(bad), f2[0], f2[1], f2[2], f2[3], 0, ctypes.byref(ap),
+                                   None) == _abi.ERR_INVALID_ARG
+    assert L.upslam_atrous_normals(ctypes.byref(pp), f2[0], f2[1], f2[1], f2[3], 0, ctypes.byref(ap),
+                                   None) == _abi.ERR_INVALID_ARG  # input aliases output
+    assert L.upslam_atrous_normals(ctypes.byref(pp), f2[0], f2[1], f2[2], None, 0, ctypes.byref(ap),
+                                   None) == _abi.ERR_INVALID_ARG  # two or more levels need scratch
+    assert L.upslam_atrous_normals(ctypes.byref(pp), f2[0], f2[1], f2[2], f2[3], 0,
+                                   ctypes.byref(_abi.AtrousParams(4, 0.5, 0.02)), None) == _abi.ERR_INVALID_ARG
+    assert L.upslam_atrous_normals(ctypes.byref(pp), f2[0], f2[1], f2[2], f2[3], 0,
+                                   ctypes.byref(_abi.AtrousParams(2, float("nan"), 0.02)), None) == _abi.ERR_INVALID_ARG
 
 
 def test_struct_layouts_match_header():
     """ctypes mirrors of the header structs have the C sizes the library expects."""
     assert ctypes.sizeof(_abi.Pano) == 28
-    assert ctypes.sizeof(_abi.IcpParams) == 40
+    assert ctypes.sizeof(_abi.IcpParams) == 48
     assert ctypes.sizeof(_abi.IcpStats) == 21 * 8 + 6 * 8 + 8 + 8 + 8 + 4 + 4 + 6 * 8 + 4 + 4
 
 
