@@ -430,10 +430,82 @@ def run_ours(args, ws, rank, local):
     if rank == 0 and args.e2e_steps > 0:
         out["e2e"] = run_e2e(args, seq, h_scans, device, up)
     if rank == 0 and args.atrous_levels > 0:
-        out["extra_kernels"] = {"atrous_kernel": run_atrous(args, seq, d_scans, device, up, hbm, hbm_src)}
+        out["extra_kernels"] = {"atrous_kernel": run_atrous(args, seq, d_scans, device, up, hbm, hbm_src),
+                                "grid_score_kernel": run_grid(trk, device, up, hbm, hbm_src),
+                                "consistency_kernels": run_consistency(pool, hist_pose[kf_every].clone(), device, up, hbm,
+                                                                       hbm_src)}
     if dist:
         dist.barrier()
     return out
+
+
+def _time_calls(fn, reps, flush, warm=3):
+    """Mean ms of fn() over reps calls, CUDA events on the current stream, L2 flushed before each call."""
+    import torch
+    cr = Cudart()
+    cr.external = False
+    st = torch.cuda.current_stream().cuda_stream
+    evs = [(cr.event(), cr.event()) for _ in range(reps)]
+    for i in range(reps + warm):
+        flush.zero_()
+        if i >= warm:
+            cr.record(evs[i - warm][0], st)
+        fn()
+        if i >= warm:
+            cr.record(evs[i - warm][1], st)
+    torch.cuda.synchronize()
+    return statistics.mean(cr.elapsed(a, b) for a, b in evs)
+
+
+def run_grid(trk, device, up, hbm, hbm_src):
+    """Loop-closure grid search (Sec. III-C) on the tracker's last keyframe and sweep: 729 candidates
+    (9 x 9 translations of 0.1 m x 9 yaws of 2 deg) around the last pose, keyframe sampled every 4 pixels.
+    Work unit: a (sampled keyframe pixel, candidate) pair; its gather is 32 B of L2-resident sweep data."""
+    import torch
+    xi = []
+    for i in range(9):
+        for j in range(9):
+            for k in range(9):
+                xi.append([0.0, 0.0, math.radians((k - 4) * 2.0), (i - 4) * 0.1, (j - 4) * 0.1, 0.0])
+    xi = torch.tensor(xi, dtype=torch.float32, device=device)
+    poses = up.grid_candidates(trk.state.pose.clone(), xi)
+    p = up.Params(d_max=0.1)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=device)
+    ms = _time_calls(lambda: up.grid_score(trk.kf, trk.sw, poses, p, 4), 20, flush)
+    samples = int((trk.kf.depth[::4, ::4] > 0).sum().item())
+    pairs = samples * poses.shape[0]
+    return {"candidates": int(poses.shape[0]), "stride": 4, "sampled_keyframe_samples": samples,
+            "launches": 2, "ms_avg": round(ms, 5), "pairs_per_s": round(pairs / (ms * 1e-3), 1),
+            "bound": "alu (FP32 binning rule per pair) + L2 gathers", "l2": "flushed before each call"}
+
+
+def run_consistency(pool, T_ab, device, up, hbm, hbm_src):
+    """Keyframe mutual consistency check (Sec. III-C) between the first two 512 x 2048 keyframes of the run
+    (T_ab: the registered pose of the sweep that started the second one, in the first).
+    Algorithmic bytes per keyframe pixel and side: depth read (4 B), flag written (1 B) and read back (1 B);
+    the neighbourhood gathers of the other keyframe hit L1/L2."""
+    import ctypes
+    import torch
+    a, b = pool[0], pool[1]
+    L = up.lib()
+    ka, kb = a.struct(), b.struct()
+    nbytes = int(L.upslam_consistency_workspace_bytes(ctypes.byref(ka), ctypes.byref(kb)))
+    ws = torch.zeros(nbytes, dtype=torch.uint8, device=device)
+    removed = torch.zeros(2, dtype=torch.int64, device=device)
+    T = T_ab
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    # repeated calls only remove what the first one did not: the timing is of the flag pass and a no-op apply
+    args = (ctypes.byref(ka), ctypes.byref(kb), ctypes.c_void_p(T.data_ptr()), ctypes.c_float(0.05),
+            ctypes.c_float(0.2), ctypes.c_void_p(ws.data_ptr()), ctypes.c_size_t(nbytes),
+            ctypes.c_void_p(removed.data_ptr()), st)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=device)
+    ms = _time_calls(lambda: L.upslam_keyframe_consistency(*args), 20, flush)
+    px = int(a.depth.numel() + b.depth.numel())
+    nbytes_alg = px * 6
+    gbs = nbytes_alg / (ms * 1e-3) / 1e9
+    return {"pixels": px, "launches": 2, "ms_avg": round(ms, 5), "bytes": nbytes_alg, "gbs": round(gbs, 1),
+            "bound": "hbm", "peak": hbm, "frac": round(gbs / hbm, 4), "peak_source": hbm_src,
+            "l2": "flushed before each call"}
 
 
 def run_atrous(args, seq, d_scans, device, up, hbm, hbm_src):

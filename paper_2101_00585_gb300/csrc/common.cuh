@@ -393,16 +393,42 @@ __device__ __forceinline__ void kadd(float &s, float &c, float v) {
 // Lane of the upper-triangle element (i, k), i <= k, in row-major order (0..20).
 __device__ __forceinline__ int uidx(int i, int k) { return i * 6 - (i * (i - 1)) / 2 + (k - i); }
 
-// FP64 solve of A xi = -b by the square-root-free Cholesky factorisation
-// A = L D L^T, spread over the lanes of one warp: lanes 0..20 hold the upper
-// triangle of A (lane uidx(i, k)), lanes 21..26 the right-hand side.  GB300
-// issues an FP64 warp instruction at a low rate whatever its active lanes, so
-// independent work goes across lanes, and pivot tests, maxima and reciprocal
-// seeds use integer instructions: per pivot the FP64 work is the two Newton
-// multiply-adds, one multiply and one multiply-add.  Back substitution first
-// scales every row by its reciprocal pivot (one instruction for all rows), then
-// takes one multiply-add per unknown.  Every lane returns the same xi.  False
-// when a pivot D_j <= max(pivot_eps * max diagonal, 1e-300) or is not finite.
+// d's mantissa as a double in [1, 2) (its exponent field set to the bias) and its unbiased exponent.
+__device__ __forceinline__ double dmant(double d) {
+    return __longlong_as_double((__double_as_longlong(d) & ~(0x7ffLL << 52)) | (1023LL << 52));
+}
+__device__ __forceinline__ int dexpo(double d) { return ((__double2hiint(d) >> 20) & 0x7ff) - 1023; }
+
+// x * 2^-e by exponent arithmetic (exact for normal results); zero stays zero, results below the
+// normal range become signed zero and above it signed infinity.
+__device__ __forceinline__ double dscale2(double x, int e) {
+    const long long b = __double_as_longlong(x);
+    const int ef = (int)((b >> 52) & 0x7ff);
+    if (ef == 0) return x;
+    const int en = ef - e;
+    const long long sign = b & (long long)0x8000000000000000ull;
+    if (en <= 0) return __longlong_as_double(sign);
+    if (en >= 0x7ff) return __longlong_as_double(sign | (0x7ffLL << 52));
+    return __longlong_as_double((b & ~(0x7ffLL << 52)) | ((long long)en << 52));
+}
+
+// FP64 solve of A xi = -b for the symmetric 6x6 A (the square-root-free Cholesky
+// factorisation A = L D L^T, i.e. symmetric Gaussian elimination), spread over the
+// lanes of one warp: lanes 0..20 hold the upper triangle of A (lane uidx(i, k)),
+// lanes 21..26 the right-hand side.  GB300 issues an FP64 warp instruction every
+// 64 cycles whatever its active lanes, so independent work goes across lanes and
+// the elimination is division-free: step j replaces every later row by
+//     row <- mant(D_j) row - (L_jrow 2^-exp(D_j)) row_j,
+// i.e. the Schur complement scaled by D_j / 2^exp(D_j) in [1, 2), with the power
+// of two taken off by exponent arithmetic: one multiply and one multiply-add per
+// step and no reciprocal on the chain.  Row j then holds F_j times the standard
+// pivot row (F_j = prod_{m<j} mant(D_m) < 2^j), so the pivot test uses
+// D_j / F_j, and the back substitution, which the common factor of a row does
+// not change, scales every row by its reciprocal pivot in one instruction and
+// then takes one multiply-add per unknown.  Comparisons, maxima and sign flips
+// are integer instructions on the bit patterns.  Every lane returns the same xi.
+// False when a standard pivot D_j / F_j <= max(pivot_eps * max diagonal, 1e-300),
+// a pivot is not finite, or the solution is not finite.
 __device__ __forceinline__ bool warp_solve6(const double *tot, double pivot_eps, double xi[6]) {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -426,23 +452,35 @@ __device__ __forceinline__ bool warp_solve6(const double *tot, double pivot_eps,
 #pragma unroll
     for (int i = 1; i < 6; ++i) dm = max(dm, dbits(tot[uidx(i, i)]));
     if (!(dm > 0) || !dfinite(__longlong_as_double(dm))) return false;
-    const long long lim = max(dbits(pivot_eps * __longlong_as_double(dm)), dbits(1e-300));
-    double rl = 0.0;  // reciprocal of this lane's row pivot
+    const double lim = __longlong_as_double(max(dbits(pivot_eps * __longlong_as_double(dm)), dbits(1e-300)));
+    double piv[6], mnt[6];
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
         const double d = __shfl_sync(full, u, uidx(j, j));
-        if (!(dbits(d) > lim) || !dfinite(d)) return false;
-        const double r = rcp64(d);
-        rl = li == j ? r : rl;
         const bool act = li > j;
         const int src_l = act ? uidx(j, li) : lane;
         const int src_k = act ? (is_u ? uidx(j, lk) : 21 + j) : lane;
         const double ujl = __shfl_sync(full, u, src_l);
         const double ujk = __shfl_sync(full, u, src_k);
-        if (act) u = fma(-(ujl * r), ujk, u);
+        piv[j] = d;
+        mnt[j] = dmant(d);
+        if (act) u = fma(-dscale2(ujl, dexpo(d)), ujk, mnt[j] * u);
     }
-    // rows scaled by 1 / D_i: lane (i, k) holds L_ki, lane 21 + i holds y_i / D_i
-    double v = u * rl;
+    // pivot test on the standard pivots D_j / F_j: lane j < 6 forms F_j = prod_{m<j} mant(D_m)
+    double F = 1.0;
+#pragma unroll
+    for (int m = 0; m < 5; ++m) F = m < lane ? F * mnt[m] : F;
+    const int jl = lane < 6 ? lane : 0;
+    double pj = piv[0];
+#pragma unroll
+    for (int j = 1; j < 6; ++j) pj = jl == j ? piv[j] : pj;
+    const bool bad = lane < 6 && (!dfinite(pj) || !(dbits(pj) > dbits(lim * F)));
+    if (__any_sync(full, bad)) return false;
+    // back substitution: lane (i, k) -> S_ik / D_i, lane 21 + i -> y_i / D_i
+    double di = piv[0];
+#pragma unroll
+    for (int j = 1; j < 6; ++j) di = li == j ? piv[j] : di;
+    double v = li >= 0 ? u * rcp64(di) : 0.0;
 #pragma unroll
     for (int i = 5; i >= 0; --i) {
         const double x = __shfl_sync(full, v, 21 + i);
@@ -453,7 +491,10 @@ __device__ __forceinline__ bool warp_solve6(const double *tot, double pivot_eps,
             if (act) v = fma(-lmi, x, v);
         }
     }
-    return true;
+    bool fin = true;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) fin = fin && dfinite(xi[i]);
+    return fin;
 }
 
 // (-1)^n / (2n + 1 + c)!: the n-th Taylor coefficient in t^2 of sin(t)/t (c = 0),
