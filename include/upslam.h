@@ -357,6 +357,33 @@ upslam_status upslam_icp_batched(const upslam_keyframe *d_kfs, const upslam_keyf
                                  upslam_icp_stats *d_stats, void *d_ws, size_t ws_bytes,
                                  const upslam_batch_tiles *tiles, void *stream);
 
+/* Sweep buffers written by upslam_track_scan (the outputs of upslam_project and
+ * upslam_normals).  d_zbuf is all ones at rest and left so. */
+typedef struct {
+    upslam_pano pano;
+    uint64_t *d_zbuf;      /* [rows*cols], 8-byte aligned */
+    float *d_depth;        /* [rows*cols] */
+    int32_t *d_idx;        /* [rows*cols] */
+    float *d_pix;          /* float4 [rows*cols], 16-byte aligned */
+    void *d_nrm;           /* float4 or half4 [rows*cols] */
+    int32_t nrm_precision; /* UPSLAM_F32 or UPSLAM_F16 */
+} upslam_sweep_buffers;
+
+/*
+ * One whole sweep in ONE persistent cooperative launch: projection with the
+ * z-buffer, resolve and normals of the scan d_pts4 (float4 [n_pts], 16-byte
+ * aligned) into the sweep buffers (as upslam_project with no pose followed by
+ * upslam_normals, with the same results), then everything upslam_track does.
+ * Three extra grid barriers separate projection, resolve and normals; the
+ * keyframe staging runs before the last so its wait is hidden.  Arguments and
+ * errors as upslam_project, upslam_normals and upslam_track.
+ */
+upslam_status upslam_track_scan(const upslam_keyframe *kf, const float *d_pts4, int32_t n_pts,
+                                const upslam_sweep_buffers *sb, const upslam_normal_params *np, double *d_prev,
+                                double *d_motion, double *d_pose12, int32_t prior, const upslam_icp_params *ip,
+                                const upslam_fuse_params *fp, upslam_icp_stats *d_stats, void *d_ws,
+                                size_t ws_bytes, uint64_t *d_zbuf_kf, void *stream);
+
 /*
  * Loop-closure grid search (Sec. III-C): candidate transformations are scored
  * by low-resolution projective alignment checks and the best is promoted to a

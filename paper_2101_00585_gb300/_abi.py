@@ -55,6 +55,11 @@ class Keyframe(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("d_dirs", ctypes.c_void_p)]
 
 
+class SweepBuffers(ctypes.Structure):
+    _fields_ = [("pano", Pano), ("d_zbuf", ctypes.c_void_p), ("d_depth", ctypes.c_void_p), ("d_idx", ctypes.c_void_p),
+                ("d_pix", ctypes.c_void_p), ("d_nrm", ctypes.c_void_p), ("nrm_precision", ctypes.c_int32)]
+
+
 class BatchTiles(ctypes.Structure):
     _fields_ = [("threads", ctypes.c_int32), ("chunk", ctypes.c_int32)]
 
@@ -82,6 +87,9 @@ SIGNATURES = {
     "upslam_fuse": (ctypes.c_int, [_P(Keyframe), _P(Sweep), _vp, _P(FuseParams), _vp, _vp, _vp]),
     "upslam_track": (ctypes.c_int, [_P(Keyframe), _P(Sweep), _vp, _vp, _vp, ctypes.c_int32, _P(IcpParams),
                                     _P(FuseParams), _vp, _vp, ctypes.c_size_t, _vp, _vp]),
+    "upslam_track_scan": (ctypes.c_int, [_P(Keyframe), _vp, ctypes.c_int32, _P(SweepBuffers), _P(NormalParams), _vp,
+                                         _vp, _vp, ctypes.c_int32, _P(IcpParams), _P(FuseParams), _vp, _vp,
+                                         ctypes.c_size_t, _vp, _vp]),
     "upslam_register": (ctypes.c_int, [_P(Keyframe), _P(Sweep), _vp, _vp, _vp, ctypes.c_int32, _P(IcpParams), _vp, _vp,
                                        ctypes.c_size_t, _vp]),
     "upslam_icp_noalloc_capacity_bytes": (ctypes.c_size_t, []),

@@ -169,6 +169,11 @@ class SweepFrame:
     def struct(self) -> _abi.Sweep:
         return _abi.Sweep(self._ps, self.pix.data_ptr(), self.nrm.data_ptr(), self.precision)
 
+    def buffers(self) -> _abi.SweepBuffers:
+        """The buffers upslam_track_scan writes (projection, resolve, normals)."""
+        return _abi.SweepBuffers(self._ps, self.zbuf.data_ptr(), self.depth.data_ptr(), self.idx.data_ptr(),
+                                 self.pix.data_ptr(), self.nrm.data_ptr(), self.precision)
+
     def load(self, pts4: torch.Tensor, params: Params) -> None:
         """project + normals (+ a-trous smoothing when params.atrous_levels > 0) for a scan already on
         the device (float4 points)."""
@@ -277,7 +282,7 @@ class Tracker:
     """
 
     def __init__(self, sweep_pano, kf_pano, params: Params = Params(), precision: int = F32, device="cuda",
-                 constant_velocity: bool = True, fused: bool = True):
+                 constant_velocity: bool = True, fused: bool = True, front_fused: bool = True):
         self.params = params
         self.sw = SweepFrame(sweep_pano, device, precision)
         self.kf = KeyframeBuffer(kf_pano, device, precision)
@@ -287,7 +292,11 @@ class Tracker:
         self.identity = identity_pose(device)
         self.constant_velocity = constant_velocity
         self.fused = fused
+        # one launch per sweep (projection and normals inside the register + update launch); needs
+        # `fused` and no a-trous smoothing, which runs as launches of its own between the two
+        self.front_fused = front_fused and fused and int(params.atrous_levels) == 0
         self._ip, self._fp = params.icp(), params.fuse()
+        self._np = params.normal()
 
     def new_keyframe(self, pts4: torch.Tensor | None = None, buffer: KeyframeBuffer | None = None,
                      consistency: bool = False) -> None:
@@ -326,6 +335,22 @@ class Tracker:
         """One sweep: project, normals, prior, ICP, keyframe update (all asynchronous)."""
         L = _abi.lib()
         s = _stream()
+        if self.front_fused:
+            # projection, normals, prior, ICP, motion update and keyframe update in one launch
+            ks, sb = self.kf.struct(), self.sw.buffers()
+            self._mark(0, 0)
+            self._mark(0, 1)
+            self._mark(1, 0)
+            _abi.check("upslam_track_scan",
+                       L.upslam_track_scan(ctypes.byref(ks), _p(pts4), pts4.shape[0], ctypes.byref(sb),
+                                           ctypes.byref(self._np), _p(self.prev), _p(self.motion),
+                                           _p(self.state.pose), 2 if self.constant_velocity else 1,
+                                           ctypes.byref(self._ip), ctypes.byref(self._fp), _p(self.state.stats),
+                                           _p(self.state.ws), self.state.ws_bytes, _p(self.kf.zbuf), s))
+            self._mark(1, 1)
+            self._mark(2, 0)
+            self._mark(2, 1)
+            return
         self._mark(0, 0)
         self.sw.load(pts4, self.params)
         self._mark(0, 1)
@@ -354,10 +379,12 @@ class Tracker:
                                                 ctypes.byref(self._fp), _p(self.state.stats), _p(self.kf.zbuf), s))
         self._mark(2, 1)
 
-    # kernels launched by one track() call: project (2), normals, one per a-trous level, then
-    # one persistent register + update launch (fused), or register + fuse (2) otherwise
+    # kernels launched by one track() call: one (front_fused); else project (2), normals, one per
+    # a-trous level, then one persistent register + update launch (fused), or register + fuse (2)
     @property
     def launches_per_track(self) -> int:
+        if self.front_fused:
+            return 1
         return (4 if self.fused else 6) + int(self.params.atrous_levels)
     # kernels launched by new_keyframe() (after loading): fuse (2)
     LAUNCHES_PER_NEW_KEYFRAME = 2

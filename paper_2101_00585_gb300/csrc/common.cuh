@@ -588,6 +588,107 @@ __device__ __forceinline__ bool warp_converged(const double xi[6], double er2, d
     return (__ballot_sync(0xffffffffu, below) & 3u) == 3u;
 }
 
+// ----------------------------------------------------------------------------- sweep front end (Sec. III-A)
+//
+// The per-point and per-pixel bodies of projection, resolve and normals, shared by
+// the standalone kernels and the fused register launch so both give the same bits.
+// kCg selects L2-only loads for data that the same launch wrote earlier (the
+// read-only cache path is only for data no launch writes while it runs).
+
+template <bool kCg, typename T>
+__device__ __forceinline__ T ld_front(const T *p) {
+    return kCg ? __ldcg(p) : __ldg(p);
+}
+
+// Pass 1 of the z-buffer: the point's key (bits(range) << 32 | index) into its pixel.
+__device__ __forceinline__ void project_point(const float4 *pts, int i, const upslam_pano &pp,
+                                              unsigned long long *zbuf) {
+    const float4 p = __ldg(pts + i);
+    if (p.w == 0.0f) return;
+    int v, u;
+    float r;
+    if (!bin_point(p.x, p.y, p.z, pp, v, u, r)) return;
+    const unsigned long long key = ((unsigned long long)__float_as_uint(r) << 32) | (unsigned int)i;
+    atomicMin(zbuf + (size_t)v * pp.cols + u, key);
+}
+
+// Pass 2: decode the pixel's word into depth / index / point and reset the word.
+template <bool kCg>
+__device__ __forceinline__ void resolve_pixel(const float4 *pts, int k, unsigned long long *zbuf, float *depth,
+                                              int *idx, float4 *pix) {
+    const unsigned long long key = kCg ? __ldcg(zbuf + k) : zbuf[k];
+    if (key == kEmptyKey) {
+        depth[k] = 0.0f;
+        idx[k] = -1;
+        if (pix) pix[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+        zbuf[k] = kEmptyKey;
+        const int i = (int)(key & 0xffffffffull);
+        depth[k] = __uint_as_float((unsigned int)(key >> 32));
+        idx[k] = i;
+        if (pix) {
+            const float4 p = __ldg(pts + i);
+            pix[k] = make_float4(p.x, p.y, p.z, 1.0f);
+        }
+    }
+}
+
+// A neighbour is usable when it holds a point and its range is within jump_rel * d + jump_abs (FP32, RN).
+template <bool kCg>
+__device__ __forceinline__ bool normal_nb_ok(const float4 *pix, const float *depth, int kn, float d,
+                                             const upslam_normal_params &np) {
+    if (ld_front<kCg>(&pix[kn].w) == 0.0f) return false;
+    const float dn = ld_front<kCg>(depth + kn);
+    const float jump = fabsf(__fsub_rn(dn, d));
+    const float lim = __fadd_rn(__fmul_rn(np.jump_rel, d), np.jump_abs);
+    return !(jump > lim);
+}
+
+// Normal of pixel k: a toward column + 1 (wrapping), b toward row + 1, each replaced by the
+// opposite neighbour with the sign flipped when unusable; n = a x b, normalised, toward the
+// sensor; (0, 0, 0, 0) when there is none.
+template <bool kCg>
+__device__ __forceinline__ float4 normal_pixel(const float4 *pix, const float *depth, const upslam_pano &pp,
+                                               const upslam_normal_params &np, int k) {
+    const int H = pp.rows, W = pp.cols;
+    const float4 c = ld_front<kCg>(pix + k);
+    float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (c.w == 0.0f) return out;
+    const int v = k / W, u = k - v * W;
+    const float d = ld_front<kCg>(depth + k);
+    const int kr = v * W + (u + 1 == W ? 0 : u + 1);
+    const int kl = v * W + (u == 0 ? W - 1 : u - 1);
+    float3 a, b;
+    if (normal_nb_ok<kCg>(pix, depth, kr, d, np)) {
+        const float4 q = ld_front<kCg>(pix + kr);
+        a = make_float3(q.x - c.x, q.y - c.y, q.z - c.z);
+    } else if (normal_nb_ok<kCg>(pix, depth, kl, d, np)) {
+        const float4 q = ld_front<kCg>(pix + kl);
+        a = make_float3(c.x - q.x, c.y - q.y, c.z - q.z);
+    } else {
+        return out;
+    }
+    if (v + 1 < H && normal_nb_ok<kCg>(pix, depth, k + W, d, np)) {
+        const float4 q = ld_front<kCg>(pix + k + W);
+        b = make_float3(q.x - c.x, q.y - c.y, q.z - c.z);
+    } else if (v >= 1 && normal_nb_ok<kCg>(pix, depth, k - W, d, np)) {
+        const float4 q = ld_front<kCg>(pix + k - W);
+        b = make_float3(c.x - q.x, c.y - q.y, c.z - q.z);
+    } else {
+        return out;
+    }
+    const float3 n = make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+    const float nn = sqrtf(n.x * n.x + n.y * n.y + n.z * n.z);
+    const float na = sqrtf(a.x * a.x + a.y * a.y + a.z * a.z);
+    const float nb = sqrtf(b.x * b.x + b.y * b.y + b.z * b.z);
+    if (nn >= np.min_cross * na * nb && nn > 0.0f) {
+        float s = 1.0f / nn;
+        if (n.x * c.x + n.y * c.y + n.z * c.z > 0.0f) s = -s;
+        out = make_float4(n.x * s, n.y * s, n.z * s, 1.0f);
+    }
+    return out;
+}
+
 // ----------------------------------------------------------------------------- keyframe update pieces
 
 // Everything one keyframe update reads and writes.
@@ -615,8 +716,8 @@ __device__ __forceinline__ void fuse_average(const FuseView &f, const PoseF &T, 
     float rr;
     if (!bin_point(q.x, q.y, q.z, f.sp, jv, ju, rr)) return;
     const int j = jv * f.sp.cols + ju;
-    const float4 P = __ldg(f.spix + j);
-    const float4 m = load_nw(f.snrm, j, f.sprec);
+    const float4 P = __ldcg(f.spix + j);
+    const float4 m = load_nw_cg(f.snrm, j, f.sprec);
     if (P.w == 0.0f || m.w == 0.0f) return;
     const float *r = T.r;
     const float px = fmaf(r[0], P.x, fmaf(r[1], P.y, fmaf(r[2], P.z, r[3])));
@@ -639,9 +740,9 @@ __device__ __forceinline__ void fuse_average(const FuseView &f, const PoseF &T, 
 // keyframe pixel it lands on.  Returns false when it lands on no empty pixel.
 __device__ __forceinline__ bool holefill_key(const FuseView &f, const PoseF &T, int j, int &k,
                                              unsigned long long &key, float &range, float4 &m) {
-    const float4 P = __ldg(f.spix + j);
+    const float4 P = __ldcg(f.spix + j);
     if (P.w == 0.0f) return false;
-    m = load_nw(f.snrm, j, f.sprec);
+    m = load_nw_cg(f.snrm, j, f.sprec);
     if (m.w == 0.0f) return false;
     const float3 p = xform(T, P.x, P.y, P.z);
     int v, u;

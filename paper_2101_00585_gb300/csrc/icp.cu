@@ -71,6 +71,22 @@ struct PriorArgs {
     int mode;            // 0: start from *pose, 1: zero velocity, 2: constant velocity
 };
 
+// Sweep front end folded into the register + update launch (upslam_track_scan):
+// projection with the z-buffer, resolve and normals of the sweep (Sec. III-A),
+// each phase ending at a grid barrier.
+struct FrontArgs {
+    const float4 *pts;          // scan points (x, y, z, valid)
+    int n;                      // points
+    unsigned long long *zbuf;   // sweep z-buffer, all ones at rest (left so)
+    float *depth;               // sweep depth [rows * cols]
+    int *idx;                   // winner index [rows * cols]
+    float4 *pix;                // winner point [rows * cols]
+    void *nrm;                  // sweep normals (nrm_prec)
+    int nrm_prec;
+    upslam_normal_params np;
+    int on;
+};
+
 struct IcpCtrl {
     unsigned int arrive;               // unused by the current kernels (kept zero)
     unsigned int gen;                  // unused by the current kernels (kept zero)
@@ -93,9 +109,9 @@ __device__ __forceinline__ void accumulate_pixel(const IcpArgs &a, const PoseF &
     float rr;
     if (!bin_point(q.x, q.y, q.z, a.sp, jv, ju, rr)) return;
     const int j = jv * a.sp.cols + ju;
-    const float4 P = __ldg(a.spix + j);
+    const float4 P = __ldcg(a.spix + j);
     if (P.w == 0.0f) return;
-    const float4 m = load_nw(a.snrm, j, a.sprec);
+    const float4 m = load_nw_cg(a.snrm, j, a.sprec);
     if (m.w == 0.0f) return;
     const float *r = T.r;
     const float px = fmaf(r[0], P.x, fmaf(r[1], P.y, fmaf(r[2], P.z, r[3])));
@@ -240,7 +256,7 @@ __device__ __forceinline__ int count_valid(const IcpArgs &a) {
     int c = 0;
     const int ns = a.sp.rows * a.sp.cols;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < ns; j += gridDim.x * blockDim.x)
-        c += __ldg(&a.spix[j].w) != 0.0f;
+        c += __ldcg(&a.spix[j].w) != 0.0f;
     return c;
 }
 
@@ -303,8 +319,8 @@ __device__ __forceinline__ void accumulate_entry(const IcpArgs &a, const PoseF &
     float rr;
     bool ok = bin_point(q.x, q.y, q.z, a.sp, jv, ju, rr);
     const int j = ok ? jv * a.sp.cols + ju : 0;
-    const float4 P = __ldg(a.spix + j);
-    const float4 m = load_nw(a.snrm, j, a.sprec);
+    const float4 P = __ldcg(a.spix + j);
+    const float4 m = load_nw_cg(a.snrm, j, a.sprec);
     ok = ok && P.w != 0.0f && m.w != 0.0f;
     const float *r = T.r;
     const float px = fmaf(r[0], P.x, fmaf(r[1], P.y, fmaf(r[2], P.z, r[3])));
@@ -461,6 +477,22 @@ __device__ __forceinline__ bool grid_arrive_wait(unsigned long long *ctr, unsign
     return true;
 }
 
+// A grid barrier for the whole CTA: thread 0 arrives and waits, the CTA follows.
+// False after a timeout (reported in the record).
+__device__ __forceinline__ bool cta_grid_sync(IcpCtrl *ctrl, unsigned long long target, upslam_icp_stats *st,
+                                              int *flag_s) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        *flag_s = 0;
+        if (!grid_arrive_wait(&ctrl->arrive64, target)) {
+            *flag_s = 3;
+            st->status = UPSLAM_ERR_TIMEOUT;
+        }
+    }
+    __syncthreads();
+    return *flag_s != 3;
+}
+
 // The tiled persistent kernel.  Each step: accumulate the CTA's staged (and
 // spilled) correspondences, publish the CTA record (double-buffered by step
 // parity), arrive at a grid barrier (a monotonic 64-bit arrival counter), then
@@ -470,7 +502,7 @@ __device__ __forceinline__ bool grid_arrive_wait(unsigned long long *ctr, unsign
 template <int L1>
 __global__ void __launch_bounds__(kTileThreads, 1)
     icp_tile_kernel(IcpArgs a, double *pose, upslam_icp_params ip, upslam_icp_stats *st, IcpCtrl *ctrl,
-                    float *partials, int cap, PriorArgs pr, FuseView fz, int fuse_on) {
+                    float *partials, int cap, PriorArgs pr, FuseView fz, int fuse_on, FrontArgs fr) {
     extern __shared__ float stage[];
     float *sx = stage, *sy = stage + cap, *sz = stage + 2 * cap;
     float *snx = stage + 3 * cap, *sny = stage + 4 * cap, *snz = stage + 5 * cap;
@@ -513,6 +545,23 @@ __global__ void __launch_bounds__(kTileThreads, 1)
             Tsh[lane] = Tprev[lane];
         }
         __syncwarp();
+    }
+
+    // ---- sweep front end (upslam_track_scan): project, barrier, resolve, barrier,
+    // normals; the barrier after the normals comes after the keyframe staging,
+    // which does not read the sweep, so staging hides its wait.
+    unsigned long long nbar = 0;  // grid barriers passed before the Gauss-Newton steps
+    if (fr.on) {
+        const int ns = a.sp.rows * a.sp.cols;
+        const int stride = gridDim.x * kTileThreads;
+        for (int i = blockIdx.x * kTileThreads + threadIdx.x; i < fr.n; i += stride)
+            project_point(fr.pts, i, a.sp, fr.zbuf);
+        if (!cta_grid_sync(ctrl, base + G * ++nbar, st, &flag)) return;
+        for (int k = blockIdx.x * kTileThreads + threadIdx.x; k < ns; k += stride)
+            resolve_pixel<true>(fr.pts, k, fr.zbuf, fr.depth, fr.idx, fr.pix);
+        if (!cta_grid_sync(ctrl, base + G * ++nbar, st, &flag)) return;
+        for (int k = blockIdx.x * kTileThreads + threadIdx.x; k < ns; k += stride)
+            store_nw(fr.nrm, k, fr.nrm_prec, normal_pixel<true>(fr.pix, fr.depth, a.sp, fr.np, k));
     }
 
     // ---- stage the CTA's chunks into shared memory (once per launch).  Chunks of
@@ -589,6 +638,7 @@ __global__ void __launch_bounds__(kTileThreads, 1)
         }
     }
     __syncthreads();
+    if (fr.on && !cta_grid_sync(ctrl, base + G * ++nbar, st, &flag)) return;
 
     // convergence thresholds, squared once per launch (read by warp 0 only)
     const double er2 = warp == 0 ? ip.eps_rot * ip.eps_rot : 0.0, et2 = warp == 0 ? ip.eps_trans * ip.eps_trans : 0.0;
@@ -618,7 +668,7 @@ __global__ void __launch_bounds__(kTileThreads, 1)
         __syncthreads();
         if (threadIdx.x == 0) {
             flag = 0;
-            if (!grid_arrive_wait(&ctrl->arrive64, base + G * (unsigned long long)(it + 1))) {
+            if (!grid_arrive_wait(&ctrl->arrive64, base + G * (nbar + (unsigned long long)(it + 1)))) {
                 flag = 3;
                 st->status = UPSLAM_ERR_TIMEOUT;
             }
@@ -700,7 +750,7 @@ __global__ void __launch_bounds__(kTileThreads, 1)
         __syncthreads();
         if (threadIdx.x == 0) {
             flag = 0;
-            if (!grid_arrive_wait(&ctrl->arrive64, base + G * (unsigned long long)(it + 1))) {
+            if (!grid_arrive_wait(&ctrl->arrive64, base + G * (nbar + (unsigned long long)(it + 1)))) {
                 flag = 3;
                 st->status = UPSLAM_ERR_TIMEOUT;
             }
@@ -788,7 +838,7 @@ static int max_ctas() { return upslam_sm_count() * 8; }
 // in as much dynamic shared memory as the slice needs (up to the opt-in limit).
 static upslam_status launch_tile(const IcpArgs &a, double *pose, const upslam_icp_params *ip, upslam_icp_stats *st,
                                  void *ws, size_t ws_bytes, cudaStream_t stream, PriorArgs pr = PriorArgs{},
-                                 const FuseView *fz = nullptr) {
+                                 const FuseView *fz = nullptr, const FrontArgs *front = nullptr) {
     int dev = 0, coop = 0, optin = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return UPSLAM_ERR_CUDA;
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
@@ -838,7 +888,13 @@ static upslam_status launch_tile(const IcpArgs &a, double *pose, const upslam_ic
     } else {
         memset(&fzc, 0, sizeof(fzc));
     }
-    void *args[] = {&ac, &pose, &ipc, &st, &ctrl, &partials, &capc, &prc, &fzc, &fuse_on};
+    FrontArgs frc;
+    if (front) {
+        frc = *front;
+    } else {
+        memset(&frc, 0, sizeof(frc));
+    }
+    void *args[] = {&ac, &pose, &ipc, &st, &ctrl, &partials, &capc, &prc, &fzc, &fuse_on, &frc};
     if (cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kTileThreads), args, dyn, stream) !=
         cudaSuccess) {
         (void)cudaGetLastError();
@@ -930,6 +986,49 @@ extern "C" upslam_status upslam_track(const upslam_keyframe *kf, const upslam_sw
     pr.prev_out = prior >= 1 ? d_prev : nullptr;
     pr.mode = prior;
     return launch_tile(make_args(kf, sw, ip), d_pose12, ip, d_stats, d_ws, ws_bytes, (cudaStream_t)stream, pr, &f);
+}
+
+extern "C" upslam_status upslam_track_scan(const upslam_keyframe *kf, const float *d_pts4, int32_t n_pts,
+                                           const upslam_sweep_buffers *sb, const upslam_normal_params *np,
+                                           double *d_prev, double *d_motion, double *d_pose12, int32_t prior,
+                                           const upslam_icp_params *ip, const upslam_fuse_params *fp,
+                                           upslam_icp_stats *d_stats, void *d_ws, size_t ws_bytes,
+                                           uint64_t *d_zbuf_kf, void *stream) {
+    if (!sb || !np || n_pts < 0 || (n_pts > 0 && !d_pts4) || !sb->d_zbuf || !sb->d_depth || !sb->d_idx ||
+        !sb->d_pix || !sb->d_nrm)
+        return UPSLAM_ERR_INVALID_ARG;
+    if ((d_pts4 && !upslam_aligned(d_pts4, 16)) || !upslam_aligned(sb->d_zbuf, 8) || !upslam_aligned(sb->d_pix, 16))
+        return UPSLAM_ERR_INVALID_ARG;
+    upslam_sweep sw;
+    sw.pano = sb->pano;
+    sw.d_pix = sb->d_pix;
+    sw.d_nrm = sb->d_nrm;
+    sw.nrm_precision = sb->nrm_precision;
+    const upslam_status chk = icp_common_checks(kf, &sw, d_pose12, ip, d_stats, d_ws, ws_bytes);
+    if (chk != UPSLAM_OK) return chk;
+    if (prior < 0 || prior > 2 || (prior >= 1 && !d_prev) || (prior == 2 && !d_motion)) return UPSLAM_ERR_INVALID_ARG;
+    FuseView f;
+    if (!upslam_fuse_view(kf, &sw, fp, d_zbuf_kf, f)) return UPSLAM_ERR_INVALID_ARG;
+    if (ip->max_iters < 1) return UPSLAM_ERR_INVALID_ARG;
+    PriorArgs pr;
+    pr.prev = d_prev;
+    pr.motion = d_motion;
+    pr.motion_out = prior >= 1 ? d_motion : nullptr;
+    pr.prev_out = prior >= 1 ? d_prev : nullptr;
+    pr.mode = prior;
+    FrontArgs fr;
+    fr.pts = reinterpret_cast<const float4 *>(d_pts4);
+    fr.n = n_pts;
+    fr.zbuf = reinterpret_cast<unsigned long long *>(sb->d_zbuf);
+    fr.depth = sb->d_depth;
+    fr.idx = sb->d_idx;
+    fr.pix = reinterpret_cast<float4 *>(sb->d_pix);
+    fr.nrm = sb->d_nrm;
+    fr.nrm_prec = sb->nrm_precision;
+    fr.np = *np;
+    fr.on = 1;
+    return launch_tile(make_args(kf, &sw, ip), d_pose12, ip, d_stats, d_ws, ws_bytes, (cudaStream_t)stream, pr, &f,
+                       &fr);
 }
 
 // ----------------------------------------------------------------------------- allocation-free variant

@@ -12,63 +12,12 @@
 
 namespace upslam {
 
-__device__ __forceinline__ bool nb_ok(const float4 *pix, const float *depth, int k, int kn, float d,
-                                      const upslam_normal_params &np) {
-    if (__ldg(&pix[kn].w) == 0.0f) return false;
-    const float dn = __ldg(depth + kn);
-    const float jump = fabsf(__fsub_rn(dn, d));
-    const float lim = __fadd_rn(__fmul_rn(np.jump_rel, d), np.jump_abs);
-    return !(jump > lim);
-}
-
 __global__ void __launch_bounds__(256) normals_kernel(const float4 *__restrict__ pix, const float *__restrict__ depth,
                                                       upslam_pano pp, upslam_normal_params np, void *nrm,
                                                       int precision) {
-    const int H = pp.rows, W = pp.cols, npx = H * W;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < npx; k += gridDim.x * blockDim.x) {
-        const float4 c = __ldg(pix + k);
-        float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (c.w != 0.0f) {
-            const int v = k / W, u = k - v * W;
-            const float d = __ldg(depth + k);
-            const int kr = v * W + (u + 1 == W ? 0 : u + 1);
-            const int kl = v * W + (u == 0 ? W - 1 : u - 1);
-            float3 a, b;
-            bool ok = true;
-            if (nb_ok(pix, depth, k, kr, d, np)) {
-                const float4 q = __ldg(pix + kr);
-                a = make_float3(q.x - c.x, q.y - c.y, q.z - c.z);
-            } else if (nb_ok(pix, depth, k, kl, d, np)) {
-                const float4 q = __ldg(pix + kl);
-                a = make_float3(c.x - q.x, c.y - q.y, c.z - q.z);
-            } else {
-                ok = false;
-            }
-            if (ok) {
-                if (v + 1 < H && nb_ok(pix, depth, k, k + W, d, np)) {
-                    const float4 q = __ldg(pix + k + W);
-                    b = make_float3(q.x - c.x, q.y - c.y, q.z - c.z);
-                } else if (v >= 1 && nb_ok(pix, depth, k, k - W, d, np)) {
-                    const float4 q = __ldg(pix + k - W);
-                    b = make_float3(c.x - q.x, c.y - q.y, c.z - q.z);
-                } else {
-                    ok = false;
-                }
-            }
-            if (ok) {
-                float3 n = make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
-                const float nn = sqrtf(n.x * n.x + n.y * n.y + n.z * n.z);
-                const float na = sqrtf(a.x * a.x + a.y * a.y + a.z * a.z);
-                const float nb = sqrtf(b.x * b.x + b.y * b.y + b.z * b.z);
-                if (nn >= np.min_cross * na * nb && nn > 0.0f) {
-                    float s = 1.0f / nn;
-                    if (n.x * c.x + n.y * c.y + n.z * c.z > 0.0f) s = -s;
-                    out = make_float4(n.x * s, n.y * s, n.z * s, 1.0f);
-                }
-            }
-        }
-        store_nw(nrm, k, precision, out);
-    }
+    const int npx = pp.rows * pp.cols;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < npx; k += gridDim.x * blockDim.x)
+        store_nw(nrm, k, precision, normal_pixel<false>(pix, depth, pp, np, k));
 }
 
 }  // namespace upslam

@@ -36,21 +36,19 @@ __global__ void pano_dirs_kernel(upslam_pano pp, float *dirs) {
 template <bool kPose>
 __global__ void __launch_bounds__(256) project_kernel(const float4 *__restrict__ pts, int n, const double *pose,
                                                       upslam_pano pp, unsigned long long *__restrict__ zbuf) {
-    PoseF T;
-    if (kPose) T = cta_pose_f32(pose);
+    if (!kPose) {
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+            project_point(pts, i, pp, zbuf);
+        return;
+    }
+    const PoseF T = cta_pose_f32(pose);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const float4 p = __ldg(pts + i);
         if (p.w == 0.0f) continue;
-        float x = p.x, y = p.y, z = p.z;
-        if (kPose) {
-            const float3 q = xform(T, x, y, z);
-            x = q.x;
-            y = q.y;
-            z = q.z;
-        }
+        const float3 q = xform(T, p.x, p.y, p.z);
         int v, u;
         float r;
-        if (!bin_point(x, y, z, pp, v, u, r)) continue;
+        if (!bin_point(q.x, q.y, q.z, pp, v, u, r)) continue;
         const unsigned long long key = ((unsigned long long)__float_as_uint(r) << 32) | (unsigned int)i;
         atomicMin(zbuf + (size_t)v * pp.cols + u, key);
     }
@@ -59,23 +57,8 @@ __global__ void __launch_bounds__(256) project_kernel(const float4 *__restrict__
 __global__ void __launch_bounds__(256) resolve_kernel(const float4 *__restrict__ pts, int npx,
                                                       unsigned long long *__restrict__ zbuf, float *__restrict__ depth,
                                                       int *__restrict__ idx, float4 *__restrict__ pix) {
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < npx; k += gridDim.x * blockDim.x) {
-        const unsigned long long key = zbuf[k];
-        if (key == kEmptyKey) {
-            depth[k] = 0.0f;
-            idx[k] = -1;
-            if (pix) pix[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-        } else {
-            zbuf[k] = kEmptyKey;
-            const int i = (int)(key & 0xffffffffull);
-            depth[k] = __uint_as_float((unsigned int)(key >> 32));
-            idx[k] = i;
-            if (pix) {
-                const float4 p = __ldg(pts + i);
-                pix[k] = make_float4(p.x, p.y, p.z, 1.0f);
-            }
-        }
-    }
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < npx; k += gridDim.x * blockDim.x)
+        resolve_pixel<false>(pts, k, zbuf, depth, idx, pix);
 }
 
 __global__ void __launch_bounds__(256) unproject_kernel(const float *__restrict__ depth, upslam_pano pp,

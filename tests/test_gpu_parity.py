@@ -452,3 +452,30 @@ def test_track_equals_register_then_fuse():
     assert torch.equal(a.kf.nw[..., 3], b.kf.nw[..., 3])
     assert torch.allclose(a.kf.depth, b.kf.depth, rtol=1e-6, atol=0)
     assert bool((a.kf.zbuf == -1).all()) and bool((b.kf.zbuf == -1).all())
+
+
+def test_track_scan_one_launch_equals_separate_launches():
+    """upslam_track_scan (projection, normals, prior, ICP, keyframe update in one launch) equals
+    upslam_project + upslam_normals + upslam_track on the same inputs, bit for bit."""
+    seq = configs.tunnel_sequence(n_scans=6)
+    scans = [dev(seq.scan(k)) for k in range(6)]
+    p = up.Params(accept_quality=0.1)
+    a = up.Tracker(seq.sweep, seq.kf, p, front_fused=True)
+    b = up.Tracker(seq.sweep, seq.kf, p, front_fused=False)
+    assert a.front_fused and not b.front_fused and a.launches_per_track == 1
+    for trk in (a, b):
+        trk.new_keyframe(scans[0])
+        for k in range(1, 6):
+            trk.track(scans[k])
+    torch.cuda.synchronize()
+    assert torch.equal(a.state.pose, b.state.pose)
+    assert torch.equal(a.sw.depth, b.sw.depth) and torch.equal(a.sw.idx, b.sw.idx)
+    assert torch.equal(a.sw.pix, b.sw.pix) and torch.equal(a.sw.nrm, b.sw.nrm)
+    assert torch.equal(a.kf.depth, b.kf.depth) and torch.equal(a.kf.nw, b.kf.nw)
+    assert bool((a.sw.zbuf == -1).all()) and bool((a.kf.zbuf == -1).all())
+    ra, rb = a.state.read_stats(), b.state.read_stats()
+    assert ra["iters"] == rb["iters"] and ra["accepted"] == rb["accepted"] == 1
+    # and the sweep buffers equal the oracle's projection (bit-exact) for the last scan
+    d_ref, i_ref = oracle.project(seq.scan(5), seq.sweep)
+    assert np.array_equal(host(a.sw.idx), i_ref)
+    assert np.array_equal(host(a.sw.depth).view(np.uint32), d_ref.view(np.uint32))
