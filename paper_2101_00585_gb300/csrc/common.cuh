@@ -588,6 +588,69 @@ __device__ __forceinline__ bool warp_converged(const double xi[6], double er2, d
     return (__ballot_sync(0xffffffffu, below) & 3u) == 3u;
 }
 
+// ----------------------------------------------------------------------------- exact order-free sums
+//
+// A float v is held as the integer X = v * 2^48 (truncated toward zero below 2^-48, saturated
+// at |v| = 2^47) split into three chunks X = c0 + c1 2^32 + c2 2^64 with |c_k| < 2^32.  Chunks
+// add into 64-bit integers with no carry between them for up to 2^31 terms, so a sum of floats
+// formed this way is exact and does not depend on the order of the additions (integer atomics
+// from any number of CTAs give every reader the same bits).
+
+__device__ __forceinline__ void fx_chunks(float v, long long c[3]) {
+    const unsigned b = __float_as_uint(v);
+    int e = (int)((b >> 23) & 0xffu);
+    unsigned long long m = b & 0x7fffffu;
+    if (e == 0xff) m = 0;  // infinities and NaN do not enter a sum
+    if (e) m |= 0x800000u;
+    else e = 1;
+    int sh = e - 150 + 48;  // X = m * 2^sh
+    if (sh > 71) sh = 71;   // saturate: |X| < 2^95
+    unsigned long long lo, hi;
+    if (sh < 0) {
+        lo = sh > -32 ? (m >> -sh) : 0ull;
+        hi = 0ull;
+    } else if (sh < 64) {
+        lo = m << sh;
+        hi = sh > 40 ? (m >> (64 - sh)) : 0ull;
+    } else {
+        lo = 0ull;
+        hi = m << (sh - 64);
+    }
+    const long long sgn = (b >> 31) ? -1 : 1;
+    c[0] = sgn * (long long)(lo & 0xffffffffull);
+    c[1] = sgn * (long long)(lo >> 32);
+    c[2] = sgn * (long long)hi;
+}
+
+// (s0 + s1 2^32 + s2 2^64) * 2^-48 as the nearest double (ties to even), integer instructions only.
+__device__ __forceinline__ double fx_value(long long s0, long long s1, long long s2) {
+    const __int128 x = (__int128)s0 + ((__int128)s1 << 32) + ((__int128)s2 << 64);
+    if (x == 0) return 0.0;
+    const bool neg = x < 0;
+    const unsigned __int128 mag = neg ? (unsigned __int128)(-x) : (unsigned __int128)x;
+    const unsigned long long h = (unsigned long long)(mag >> 64), l = (unsigned long long)mag;
+    const int nbits = h ? 128 - __clzll((long long)h) : 64 - __clzll((long long)l);
+    unsigned long long mant;
+    int top = nbits;  // the value is mant * 2^(top - 53)
+    if (nbits <= 53) {
+        mant = l << (53 - nbits);
+    } else {
+        const int sh = nbits - 53;
+        mant = (unsigned long long)(mag >> sh);
+        const unsigned __int128 rem = mag & ((((unsigned __int128)1) << sh) - 1);
+        const unsigned __int128 half = ((unsigned __int128)1) << (sh - 1);
+        if (rem > half || (rem == half && (mant & 1ull))) ++mant;
+        if (mant >> 53) {
+            mant >>= 1;
+            ++top;
+        }
+    }
+    const long long ebits = (long long)(top - 1 - 48 + 1023);
+    const long long bits = (neg ? (long long)0x8000000000000000ull : 0ll) | (ebits << 52) |
+                           (long long)(mant & 0xfffffffffffffull);
+    return __longlong_as_double(bits);
+}
+
 // ----------------------------------------------------------------------------- sweep front end (Sec. III-A)
 //
 // The per-point and per-pixel bodies of projection, resolve and normals, shared by
@@ -612,8 +675,8 @@ __device__ __forceinline__ void project_point(const float4 *pts, int i, const up
     atomicMin(zbuf + (size_t)v * pp.cols + u, key);
 }
 
-// Pass 2: decode the pixel's word into depth / index / point and reset the word.
-template <bool kCg>
+// Pass 2: decode the pixel's word into depth / index / point and (kReset) reset the word.
+template <bool kCg, bool kReset = true>
 __device__ __forceinline__ void resolve_pixel(const float4 *pts, int k, unsigned long long *zbuf, float *depth,
                                               int *idx, float4 *pix) {
     const unsigned long long key = kCg ? __ldcg(zbuf + k) : zbuf[k];
@@ -622,7 +685,7 @@ __device__ __forceinline__ void resolve_pixel(const float4 *pts, int k, unsigned
         idx[k] = -1;
         if (pix) pix[k] = make_float4(0.f, 0.f, 0.f, 0.f);
     } else {
-        zbuf[k] = kEmptyKey;
+        if (kReset) zbuf[k] = kEmptyKey;
         const int i = (int)(key & 0xffffffffull);
         depth[k] = __uint_as_float((unsigned int)(key >> 32));
         idx[k] = i;
@@ -633,12 +696,39 @@ __device__ __forceinline__ void resolve_pixel(const float4 *pts, int k, unsigned
     }
 }
 
-// A neighbour is usable when it holds a point and its range is within jump_rel * d + jump_abs (FP32, RN).
+// Pixel data for the normals, read from the resolved arrays (point with validity in .w, range).
 template <bool kCg>
-__device__ __forceinline__ bool normal_nb_ok(const float4 *pix, const float *depth, int kn, float d,
-                                             const upslam_normal_params &np) {
-    if (ld_front<kCg>(&pix[kn].w) == 0.0f) return false;
-    const float dn = ld_front<kCg>(depth + kn);
+struct PixArrays {
+    const float4 *pix;
+    const float *depth;
+    __device__ __forceinline__ float4 point(int k) const { return ld_front<kCg>(pix + k); }
+    __device__ __forceinline__ float range(int k) const { return ld_front<kCg>(depth + k); }
+};
+
+// The same data decoded straight from the z-buffer words (winner index and range in the key),
+// before any resolve pass has run: a pixel's normal can then be formed in the pass that resolves it.
+struct PixZbuf {
+    const float4 *pts;
+    const unsigned long long *zbuf;
+    __device__ __forceinline__ float4 point(int k) const {
+        const unsigned long long key = __ldcg(zbuf + k);
+        if (key == kEmptyKey) return make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 p = __ldg(pts + (int)(key & 0xffffffffull));
+        return make_float4(p.x, p.y, p.z, 1.0f);
+    }
+    __device__ __forceinline__ float range(int k) const {
+        const unsigned long long key = __ldcg(zbuf + k);
+        return key == kEmptyKey ? 0.0f : __uint_as_float((unsigned int)(key >> 32));
+    }
+};
+
+// A neighbour is usable when it holds a point and its range is within jump_rel * d + jump_abs (FP32, RN).
+template <typename Acc>
+__device__ __forceinline__ bool normal_nb_ok(const Acc &px, int kn, float d, const upslam_normal_params &np,
+                                             float4 &q) {
+    q = px.point(kn);
+    if (q.w == 0.0f) return false;
+    const float dn = px.range(kn);
     const float jump = fabsf(__fsub_rn(dn, d));
     const float lim = __fadd_rn(__fmul_rn(np.jump_rel, d), np.jump_abs);
     return !(jump > lim);
@@ -647,32 +737,29 @@ __device__ __forceinline__ bool normal_nb_ok(const float4 *pix, const float *dep
 // Normal of pixel k: a toward column + 1 (wrapping), b toward row + 1, each replaced by the
 // opposite neighbour with the sign flipped when unusable; n = a x b, normalised, toward the
 // sensor; (0, 0, 0, 0) when there is none.
-template <bool kCg>
-__device__ __forceinline__ float4 normal_pixel(const float4 *pix, const float *depth, const upslam_pano &pp,
-                                               const upslam_normal_params &np, int k) {
+template <typename Acc>
+__device__ __forceinline__ float4 normal_pixel(const Acc &px, const upslam_pano &pp, const upslam_normal_params &np,
+                                               int k) {
     const int H = pp.rows, W = pp.cols;
-    const float4 c = ld_front<kCg>(pix + k);
+    const float4 c = px.point(k);
     float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
     if (c.w == 0.0f) return out;
     const int v = k / W, u = k - v * W;
-    const float d = ld_front<kCg>(depth + k);
+    const float d = px.range(k);
     const int kr = v * W + (u + 1 == W ? 0 : u + 1);
     const int kl = v * W + (u == 0 ? W - 1 : u - 1);
     float3 a, b;
-    if (normal_nb_ok<kCg>(pix, depth, kr, d, np)) {
-        const float4 q = ld_front<kCg>(pix + kr);
+    float4 q;
+    if (normal_nb_ok(px, kr, d, np, q)) {
         a = make_float3(q.x - c.x, q.y - c.y, q.z - c.z);
-    } else if (normal_nb_ok<kCg>(pix, depth, kl, d, np)) {
-        const float4 q = ld_front<kCg>(pix + kl);
+    } else if (normal_nb_ok(px, kl, d, np, q)) {
         a = make_float3(c.x - q.x, c.y - q.y, c.z - q.z);
     } else {
         return out;
     }
-    if (v + 1 < H && normal_nb_ok<kCg>(pix, depth, k + W, d, np)) {
-        const float4 q = ld_front<kCg>(pix + k + W);
+    if (v + 1 < H && normal_nb_ok(px, k + W, d, np, q)) {
         b = make_float3(q.x - c.x, q.y - c.y, q.z - c.z);
-    } else if (v >= 1 && normal_nb_ok<kCg>(pix, depth, k - W, d, np)) {
-        const float4 q = ld_front<kCg>(pix + k - W);
+    } else if (v >= 1 && normal_nb_ok(px, k - W, d, np, q)) {
         b = make_float3(c.x - q.x, c.y - q.y, c.z - q.z);
     } else {
         return out;

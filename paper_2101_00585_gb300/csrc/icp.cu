@@ -464,8 +464,11 @@ __device__ __forceinline__ void sum_records(const float *rec, int nrec, float (*
 // after the last makes every other CTA's writes visible (the caller's next
 // __syncthreads extends both to the whole CTA).  False when the count has not
 // reached target after kWaitCycles (the caller reports UPSLAM_ERR_TIMEOUT).
-__device__ __forceinline__ bool grid_arrive_wait(unsigned long long *ctr, unsigned long long target) {
+__device__ __forceinline__ void grid_arrive(unsigned long long *ctr) {
     asm volatile("red.release.gpu.global.add.u64 [%0], 1;" ::"l"(ctr) : "memory");
+}
+
+__device__ __forceinline__ bool grid_wait(unsigned long long *ctr, unsigned long long target) {
     const long long t0 = clock64();
     unsigned long long v;
     for (;;) {
@@ -475,6 +478,32 @@ __device__ __forceinline__ bool grid_arrive_wait(unsigned long long *ctr, unsign
     }
     asm volatile("fence.acq_rel.gpu;" ::: "memory");
     return true;
+}
+
+__device__ __forceinline__ bool grid_arrive_wait(unsigned long long *ctr, unsigned long long target) {
+    grid_arrive(ctr);
+    return grid_wait(ctr, target);
+}
+
+// Split-phase grid barrier: the CTA arrives (after everything it wrote), does other work,
+// then waits.  cta_grid_arrive must be reached by the whole CTA; so must cta_grid_await.
+__device__ __forceinline__ void cta_grid_arrive(IcpCtrl *ctrl) {
+    __syncthreads();
+    if (threadIdx.x == 0) grid_arrive(&ctrl->arrive64);
+}
+
+__device__ __forceinline__ bool cta_grid_await(IcpCtrl *ctrl, unsigned long long target, upslam_icp_stats *st,
+                                               int *flag_s) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        *flag_s = 0;
+        if (!grid_wait(&ctrl->arrive64, target)) {
+            *flag_s = 3;
+            st->status = UPSLAM_ERR_TIMEOUT;
+        }
+    }
+    __syncthreads();
+    return *flag_s != 3;
 }
 
 // A grid barrier for the whole CTA: thread 0 arrives and waits, the CTA follows.
@@ -547,23 +576,6 @@ __global__ void __launch_bounds__(kTileThreads, 1)
         __syncwarp();
     }
 
-    // ---- sweep front end (upslam_track_scan): project, barrier, resolve, barrier,
-    // normals; the barrier after the normals comes after the keyframe staging,
-    // which does not read the sweep, so staging hides its wait.
-    unsigned long long nbar = 0;  // grid barriers passed before the Gauss-Newton steps
-    if (fr.on) {
-        const int ns = a.sp.rows * a.sp.cols;
-        const int stride = gridDim.x * kTileThreads;
-        for (int i = blockIdx.x * kTileThreads + threadIdx.x; i < fr.n; i += stride)
-            project_point(fr.pts, i, a.sp, fr.zbuf);
-        if (!cta_grid_sync(ctrl, base + G * ++nbar, st, &flag)) return;
-        for (int k = blockIdx.x * kTileThreads + threadIdx.x; k < ns; k += stride)
-            resolve_pixel<true>(fr.pts, k, fr.zbuf, fr.depth, fr.idx, fr.pix);
-        if (!cta_grid_sync(ctrl, base + G * ++nbar, st, &flag)) return;
-        for (int k = blockIdx.x * kTileThreads + threadIdx.x; k < ns; k += stride)
-            store_nw(fr.nrm, k, fr.nrm_prec, normal_pixel<true>(fr.pix, fr.depth, a.sp, fr.np, k));
-    }
-
     // ---- stage the CTA's chunks into shared memory (once per launch).  Chunks of
     // 512 pixels are dealt round-robin (chunk q goes to CTA q mod gridDim), so every
     // CTA gets an even share of the rows that hold samples.  kStageGroup chunks are
@@ -571,74 +583,105 @@ __global__ void __launch_bounds__(kTileThreads, 1)
     // barrier: the per-warp counts are double-buffered by group parity.  A chunk
     // that no longer fits is left, with every later chunk of this CTA, to the
     // global-memory path.
-    int staged = 0, spill_q = nchunks;
-    for (int q0 = blockIdx.x, par = 0; q0 < nchunks; q0 += kStageGroup * gridDim.x, par ^= 1) {
-        float dg[kStageGroup];
-        float4 ng[kStageGroup];
-        float2 eg[kStageGroup], ag[kStageGroup];
+    int staged = 0, spill_q = nchunks, par = 0;
+    bool spilled = false;
+    const int my_chunks = blockIdx.x < nchunks ? (nchunks - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int my_groups = (my_chunks + kStageGroup - 1) / kStageGroup;
+    auto stage_groups = [&](int g_begin, int g_end) {
+        for (int gi = g_begin; gi < g_end && !spilled; ++gi, par ^= 1) {
+            const int q0 = blockIdx.x + gi * kStageGroup * gridDim.x;
+            float dg[kStageGroup];
+            float4 ng[kStageGroup];
+            float2 eg[kStageGroup], ag[kStageGroup];
 #pragma unroll
-        for (int g = 0; g < kStageGroup; ++g) {
-            const int k = (q0 + g * gridDim.x) * kTileThreads + threadIdx.x;
-            dg[g] = 0.0f;
-            ng[g] = make_float4(0.f, 0.f, 0.f, 0.f);
-            eg[g] = ag[g] = make_float2(0.f, 0.f);
-            if (q0 + g * (int)gridDim.x < nchunks && k < npx) {
-                const int v = k / W;
-                dg[g] = __ldg(a.kdepth + k);
-                ng[g] = load_nw(a.knw, k, a.kprec);
-                eg[g] = __ldg(reinterpret_cast<const float2 *>(a.kdirs) + v);
-                ag[g] = __ldg(reinterpret_cast<const float2 *>(a.kdirs + 2 * a.kp.rows) + (k - v * W));
+            for (int g = 0; g < kStageGroup; ++g) {
+                const int k = (q0 + g * gridDim.x) * kTileThreads + threadIdx.x;
+                dg[g] = 0.0f;
+                ng[g] = make_float4(0.f, 0.f, 0.f, 0.f);
+                eg[g] = ag[g] = make_float2(0.f, 0.f);
+                if (q0 + g * (int)gridDim.x < nchunks && k < npx) {
+                    const int v = k / W;
+                    dg[g] = __ldg(a.kdepth + k);
+                    ng[g] = load_nw(a.knw, k, a.kprec);
+                    eg[g] = __ldg(reinterpret_cast<const float2 *>(a.kdirs) + v);
+                    ag[g] = __ldg(reinterpret_cast<const float2 *>(a.kdirs + 2 * a.kp.rows) + (k - v * W));
+                }
+            }
+            unsigned bal[kStageGroup];
+#pragma unroll
+            for (int g = 0; g < kStageGroup; ++g) {
+                const float4 n4 = ng[g];
+                const bool ok = dg[g] > 0.0f && __fadd_rn(__fadd_rn(__fmul_rn(n4.x, n4.x), __fmul_rn(n4.y, n4.y)),
+                                                          __fmul_rn(n4.z, n4.z)) > 0.25f;
+                bal[g] = __ballot_sync(0xffffffffu, ok);
+                if (lane == 0) wcnt[par][g][warp] = __popc(bal[g]);
+            }
+            __syncthreads();
+            // every thread derives the same offsets and totals from the counts
+            int fit = kStageGroup;
+            int off[kStageGroup];
+            int total = staged;
+#pragma unroll
+            for (int g = 0; g < kStageGroup; ++g) {
+                int o = total;
+                for (int w = 0; w < kTileWarps; ++w) {
+                    const int c = wcnt[par][g][w];
+                    o += w < warp ? c : 0;
+                    total += c;
+                }
+                off[g] = o + __popc(bal[g] & ((1u << lane) - 1u));
+                if (fit == kStageGroup && total > cap) fit = g;
+                if (fit == kStageGroup) staged = total;
+            }
+#pragma unroll
+            for (int g = 0; g < kStageGroup; ++g) {
+                if (g >= fit || !((bal[g] >> lane) & 1u)) continue;
+                const int k = (q0 + g * gridDim.x) * kTileThreads + threadIdx.x;
+                const int slot = off[g];
+                const float d = dg[g];
+                sx[slot] = __fmul_rn(d, __fmul_rn(eg[g].x, ag[g].x));
+                sy[slot] = __fmul_rn(d, __fmul_rn(eg[g].x, ag[g].y));
+                sz[slot] = __fmul_rn(d, eg[g].y);
+                snx[slot] = ng[g].x;
+                sny[slot] = ng[g].y;
+                snz[slot] = ng[g].z;
+                sw8[slot] = ng[g].w;
+                sd[slot] = d;
+                sk[slot] = k;
+            }
+            if (fit < kStageGroup) {  // uniform across the CTA: the counts are shared
+                spill_q = q0 + fit * gridDim.x;
+                spilled = true;
             }
         }
-        unsigned bal[kStageGroup];
-#pragma unroll
-        for (int g = 0; g < kStageGroup; ++g) {
-            const float4 n4 = ng[g];
-            const bool ok = dg[g] > 0.0f && __fadd_rn(__fadd_rn(__fmul_rn(n4.x, n4.x), __fmul_rn(n4.y, n4.y)),
-                                                      __fmul_rn(n4.z, n4.z)) > 0.25f;
-            bal[g] = __ballot_sync(0xffffffffu, ok);
-            if (lane == 0) wcnt[par][g][warp] = __popc(bal[g]);
+    };
+
+    // ---- sweep front end (upslam_track_scan): project; arrive; stage the first half of
+    // the keyframe while the other CTAs finish projecting; wait; resolve the z-buffer and
+    // form the normals from it in one pass; arrive; stage the rest; wait; reset the words.
+    // The keyframe does not depend on the sweep, so its loads fill both barrier waits.
+    unsigned long long nbar = 0;  // grid barriers passed before the Gauss-Newton steps
+    if (fr.on) {
+        const int ns = a.sp.rows * a.sp.cols;
+        const int stride = gridDim.x * kTileThreads;
+        for (int i = blockIdx.x * kTileThreads + threadIdx.x; i < fr.n; i += stride)
+            project_point(fr.pts, i, a.sp, fr.zbuf);
+        cta_grid_arrive(ctrl);
+        stage_groups(0, my_groups / 2);
+        if (!cta_grid_await(ctrl, base + G * ++nbar, st, &flag)) return;
+        const PixZbuf zb{fr.pts, fr.zbuf};
+        for (int k = blockIdx.x * kTileThreads + threadIdx.x; k < ns; k += stride) {
+            resolve_pixel<true, false>(fr.pts, k, fr.zbuf, fr.depth, fr.idx, fr.pix);
+            store_nw(fr.nrm, k, fr.nrm_prec, normal_pixel(zb, a.sp, fr.np, k));
         }
+        cta_grid_arrive(ctrl);
+        stage_groups(my_groups / 2, my_groups);
+        if (!cta_grid_await(ctrl, base + G * ++nbar, st, &flag)) return;
+        for (int k = blockIdx.x * kTileThreads + threadIdx.x; k < ns; k += stride) fr.zbuf[k] = kEmptyKey;
+    } else {
+        stage_groups(0, my_groups);
         __syncthreads();
-        // every thread derives the same offsets and totals from the counts
-        int fit = kStageGroup;
-        int off[kStageGroup];
-        int total = staged;
-#pragma unroll
-        for (int g = 0; g < kStageGroup; ++g) {
-            int o = total;
-            for (int w = 0; w < kTileWarps; ++w) {
-                const int c = wcnt[par][g][w];
-                o += w < warp ? c : 0;
-                total += c;
-            }
-            off[g] = o + __popc(bal[g] & ((1u << lane) - 1u));
-            if (fit == kStageGroup && total > cap) fit = g;
-            if (fit == kStageGroup) staged = total;
-        }
-#pragma unroll
-        for (int g = 0; g < kStageGroup; ++g) {
-            if (g >= fit || !((bal[g] >> lane) & 1u)) continue;
-            const int k = (q0 + g * gridDim.x) * kTileThreads + threadIdx.x;
-            const int slot = off[g];
-            const float d = dg[g];
-            sx[slot] = __fmul_rn(d, __fmul_rn(eg[g].x, ag[g].x));
-            sy[slot] = __fmul_rn(d, __fmul_rn(eg[g].x, ag[g].y));
-            sz[slot] = __fmul_rn(d, eg[g].y);
-            snx[slot] = ng[g].x;
-            sny[slot] = ng[g].y;
-            snz[slot] = ng[g].z;
-            sw8[slot] = ng[g].w;
-            sd[slot] = d;
-            sk[slot] = k;
-        }
-        if (fit < kStageGroup) {  // uniform across the CTA: the counts are shared
-            spill_q = q0 + fit * gridDim.x;
-            break;
-        }
     }
-    __syncthreads();
-    if (fr.on && !cta_grid_sync(ctrl, base + G * ++nbar, st, &flag)) return;
 
     // convergence thresholds, squared once per launch (read by warp 0 only)
     const double er2 = warp == 0 ? ip.eps_rot * ip.eps_rot : 0.0, et2 = warp == 0 ? ip.eps_trans * ip.eps_trans : 0.0;

@@ -17,7 +17,7 @@ __global__ void __launch_bounds__(256) normals_kernel(const float4 *__restrict__
                                                       int precision) {
     const int npx = pp.rows * pp.cols;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < npx; k += gridDim.x * blockDim.x)
-        store_nw(nrm, k, precision, normal_pixel<false>(pix, depth, pp, np, k));
+        store_nw(nrm, k, precision, normal_pixel(PixArrays<false>{pix, depth}, pp, np, k));
 }
 
 }  // namespace upslam
