@@ -237,10 +237,13 @@ upslam_status upslam_icp_step(const upslam_keyframe *kf, const upslam_sweep *sw,
 
 /*
  * Up to ip->max_iters Gauss-Newton steps in ONE persistent cooperative launch
- * (one CTA group resident per SM; a bounded grid-wide barrier per step; the
- * last CTA to arrive solves in FP64).  Stops early on convergence or a
- * degenerate system.  stats.iters counts the steps taken.  A barrier that
- * waits longer than about a second gives up and sets stats.status = 5.
+ * (one CTA per SM; a bounded grid-wide barrier per step).  Each CTA adds its
+ * share of the step's J^T J, J^T r and counts into integer accumulators in the
+ * workspace as exact fixed-point numbers, so the totals do not depend on the
+ * order of the CTAs; every CTA reads them and solves in FP64, getting the same
+ * pose.  Stops early on convergence or a degenerate system.  stats.iters counts
+ * the steps taken.  A barrier that waits longer than about a second gives up and
+ * sets stats.status = 5; the workspace must then be zeroed again before reuse.
  */
 upslam_status upslam_icp(const upslam_keyframe *kf, const upslam_sweep *sw, double *d_pose12,
                          const upslam_icp_params *ip, upslam_icp_stats *d_stats, void *d_ws, size_t ws_bytes,

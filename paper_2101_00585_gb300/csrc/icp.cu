@@ -35,7 +35,9 @@ constexpr int kIcpWarps = kIcpThreads / 32;
 // Per-CTA partial: 28 FP32 sums and their Neumaier compensations, then the
 // inlier and valid counts as integers (64 words = 256 bytes per CTA).
 constexpr int kSlots = 64;
-constexpr size_t kCtrlBytes = 256;
+constexpr size_t kCtrlBytes = 4096;  // IcpCtrl, then the persistent form's exact accumulators
+constexpr size_t kAccOffset = 256;   // three buffers of kAccWords 64-bit integers
+constexpr int kAccWords = 96;        // 28 sums x 3 chunks, inliers, valid (86 used)
 constexpr long long kWaitCycles = 4000000000ll;  // about 2 s at 2 GHz
 
 struct IcpArgs {
@@ -353,109 +355,28 @@ __device__ __forceinline__ void accumulate_entry(const IcpArgs &a, const PoseF &
     inl += ok ? 1 : 0;
 }
 
-// CTA partial record (64 words): sums [0, 28), inliers [28], valid [29], compensations [32, 60).
-__device__ __forceinline__ void tile_partial(float acc[28], int inl, int valid, float *partial, float (*sh)[32],
-                                             int (*shi)[2], float (*sg)[4][32]) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+// The CTA's contribution to one step's sums, exact: each warp's 28 sums (warp
+// reduce-scatter) go into shared 64-bit integer accumulators as fixed-point
+// chunks, the inlier and valid counts as integers.
+__device__ __forceinline__ void tile_fx(float acc[28], int inl, int valid, unsigned long long *fxs) {
+    const int lane = threadIdx.x & 31;
     float v[32];
 #pragma unroll
     for (int i = 0; i < 32; ++i) v[i] = i < 28 ? acc[i] : 0.0f;
     const float s = warp_reduce_scatter(v);  // lane i: the warp's sum of acc[i]
-    if (lane < 28) sh[warp][lane] = s;
+    if (lane < 28) {
+        long long c[3];
+        fx_chunks(s, c);
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            if (c[k]) atomicAdd(fxs + 3 * lane + k, (unsigned long long)c[k]);
+    }
     const int si = __reduce_add_sync(0xffffffffu, inl);
     const int sv = __reduce_add_sync(0xffffffffu, valid);
     if (lane == 0) {
-        shi[warp][0] = si;
-        shi[warp][1] = sv;
+        if (si) atomicAdd(fxs + 84, (unsigned long long)si);
+        if (sv) atomicAdd(fxs + 85, (unsigned long long)sv);
     }
-    __syncthreads();
-    // the 16 warp sums in two compensated levels: 4 groups of 4 warps, then the groups
-    if (warp < 4 && lane < 28) {
-        float t = 0.0f, c = 0.0f;
-#pragma unroll
-        for (int w = 4 * warp; w < 4 * warp + 4; ++w) kadd(t, c, sh[w][lane]);
-        sg[0][warp][lane] = t;
-        sg[1][warp][lane] = c;
-    }
-    __syncthreads();
-    if (threadIdx.x < 28) {
-        float t = 0.0f, c = 0.0f;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            kadd(t, c, sg[0][q][threadIdx.x]);
-            c += sg[1][q][threadIdx.x];
-        }
-        partial[threadIdx.x] = t;
-        partial[32 + threadIdx.x] = c;
-    } else if (threadIdx.x < 30) {
-        int t = 0;
-#pragma unroll
-        for (int w = 0; w < kTileWarps; ++w) t += shi[w][threadIdx.x - 28];
-        partial[threadIdx.x] = __int_as_float(t);
-    }
-}
-
-// Sum every CTA record of one step (compensated FP32, a fixed order, so every
-// CTA obtains bit-identical totals) into tot[0..27] (FP64) and the inlier and
-// valid counts into totn[0..1].
-__device__ __forceinline__ void sum_records(const float *rec, int nrec, float (*sh)[32], float (*shc)[32],
-                                            int (*shn)[32], float (*sg)[4][32], double *tot, long long *totn) {
-    const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
-    // two interleaved compensated chains per lane (even and odd records of the warp)
-    float s0 = 0.0f, c0 = 0.0f, s1 = 0.0f, c1 = 0.0f;
-    int n = 0;
-    constexpr int kBatch = 10;
-    for (int b0 = g; b0 < nrec; b0 += kTileWarps * kBatch) {
-        float x[kBatch], y[kBatch];
-#pragma unroll
-        for (int q = 0; q < kBatch; ++q) {
-            const int b = b0 + q * kTileWarps;
-            x[q] = b < nrec ? __ldcg(rec + (size_t)b * kSlots + lane) : 0.0f;
-            y[q] = b < nrec ? __ldcg(rec + (size_t)b * kSlots + 32 + lane) : 0.0f;
-        }
-#pragma unroll
-        for (int q = 0; q < kBatch; q += 2) {
-            if (lane < 28) {
-                kadd(s0, c0, x[q]);
-                c0 += y[q];
-                kadd(s1, c1, x[q + 1]);
-                c1 += y[q + 1];
-            } else if (lane < 30) {
-                n += __float_as_int(x[q]) + __float_as_int(x[q + 1]);
-            }
-        }
-    }
-    kadd(s0, c0, s1);
-    sh[g][lane] = s0;
-    shc[g][lane] = c0 + c1;
-    shn[g][lane] = n;
-    __syncthreads();
-    if (g < 4 && lane < 28) {
-        float t = 0.0f, cc = 0.0f;
-#pragma unroll
-        for (int w = 4 * g; w < 4 * g + 4; ++w) {
-            kadd(t, cc, sh[w][lane]);
-            cc += shc[w][lane];
-        }
-        sg[0][g][lane] = t;
-        sg[1][g][lane] = cc;
-    }
-    __syncthreads();
-    if (threadIdx.x < 28) {
-        float t = 0.0f, cc = 0.0f;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            kadd(t, cc, sg[0][q][threadIdx.x]);
-            cc += sg[1][q][threadIdx.x];
-        }
-        tot[threadIdx.x] = f2d(t) + f2d(cc);
-    } else if (threadIdx.x < 30) {
-        long long t = 0;
-#pragma unroll
-        for (int q = 0; q < kTileWarps; ++q) t += shn[q][threadIdx.x];
-        totn[threadIdx.x - 28] = t;
-    }
-    __syncthreads();
 }
 
 // Grid barrier on a monotonic 64-bit arrival counter, called by one thread per
@@ -537,13 +458,10 @@ __global__ void __launch_bounds__(kTileThreads, 1)
     float *snx = stage + 3 * cap, *sny = stage + 4 * cap, *snz = stage + 5 * cap;
     float *sw8 = stage + 6 * cap, *sd = stage + 7 * cap;
     int *sk = reinterpret_cast<int *>(stage + 8 * cap);
-    __shared__ float sh[kTileWarps][32];
-    __shared__ float shc[kTileWarps][32];
-    __shared__ int shn[kTileWarps][32];
-    __shared__ int shi[kTileWarps][2];
-    __shared__ float sg[2][4][32];
     __shared__ double tot[32];
     __shared__ long long totn[2];
+    __shared__ unsigned long long fxs[kAccWords];
+    __shared__ int gbm_s;
     __shared__ double Tsh[12];
     __shared__ double Tprev[12], Tmot[12];
     __shared__ float Tf[12];
@@ -557,7 +475,22 @@ __global__ void __launch_bounds__(kTileThreads, 1)
     const int W = a.kp.cols;
     const unsigned long long G = gridDim.x;
     unsigned long long base = 0;
-    if (threadIdx.x == 0) base = (*((volatile unsigned long long *)&ctrl->arrive64) / G) * G;
+    if (threadIdx.x == 0) {
+        base = (*((volatile unsigned long long *)&ctrl->arrive64) / G) * G;
+        gbm_s = (int)((base / G) % 3ull);
+    }
+    // exact step sums: barrier number j (counted over the whole workspace's life) adds into
+    // buffer j mod 3; CTA 0 clears buffer j - 1 once it has passed barrier j (all of its readers
+    // have then arrived at barrier j, and nobody adds into it before barrier j + 1 has passed)
+    unsigned long long *const acc_base =
+        reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(ctrl) + kAccOffset);
+    auto acc_buf = [&](unsigned long long j) { return acc_base + (size_t)((gbm_s + j) % 3ull) * kAccWords; };
+    auto clear_prev = [&](unsigned long long j) {  // after passing barrier j; warp 1 of CTA 0
+        if (blockIdx.x == 0 && warp == 1) {
+            unsigned long long *b = acc_buf(j + 2);  // = buffer j - 1
+            for (int i = lane; i < kAccWords; i += 32) b[i] = 0ull;
+        }
+    };
     if (pr.mode == 0) {
         if (threadIdx.x < 12) Tsh[threadIdx.x] = __ldcg(pose + threadIdx.x);
     } else if (warp == 0) {
@@ -669,6 +602,7 @@ __global__ void __launch_bounds__(kTileThreads, 1)
         cta_grid_arrive(ctrl);
         stage_groups(0, my_groups / 2);
         if (!cta_grid_await(ctrl, base + G * ++nbar, st, &flag)) return;
+        clear_prev(nbar);
         const PixZbuf zb{fr.pts, fr.zbuf};
         for (int k = blockIdx.x * kTileThreads + threadIdx.x; k < ns; k += stride) {
             resolve_pixel<true, false>(fr.pts, k, fr.zbuf, fr.depth, fr.idx, fr.pix);
@@ -677,6 +611,7 @@ __global__ void __launch_bounds__(kTileThreads, 1)
         cta_grid_arrive(ctrl);
         stage_groups(my_groups / 2, my_groups);
         if (!cta_grid_await(ctrl, base + G * ++nbar, st, &flag)) return;
+        clear_prev(nbar);
         for (int k = blockIdx.x * kTileThreads + threadIdx.x; k < ns; k += stride) fr.zbuf[k] = kEmptyKey;
     } else {
         stage_groups(0, my_groups);
@@ -689,6 +624,7 @@ __global__ void __launch_bounds__(kTileThreads, 1)
     for (; it < ip.max_iters; ++it) {
         // the pose in FP32: converted once per CTA (FP64 conversions are slow on GB300), read by all
         if (threadIdx.x < 12) Tf[threadIdx.x] = (float)Tsh[threadIdx.x];
+        if (threadIdx.x < kAccWords) fxs[threadIdx.x] = 0ull;
         __syncthreads();
         PoseF T;
 #pragma unroll
@@ -706,20 +642,35 @@ __global__ void __launch_bounds__(kTileThreads, 1)
             if (k < npx) accumulate_pixel<L1>(a, T, k, acc, inl);
         }
         const int valid = it == 0 ? count_valid(a) : 0;
-        float *rec = partials + (size_t)(it & 1) * gridDim.x * kSlots;
-        tile_partial(acc, inl, valid, rec + (size_t)blockIdx.x * kSlots, sh, shi, sg);
+        tile_fx(acc, inl, valid, fxs);
+        __syncthreads();
+        const unsigned long long jb = nbar + (unsigned long long)(it + 1);  // this step's barrier
+        unsigned long long *const buf = acc_buf(jb);
+        if (threadIdx.x < 86) {
+            const unsigned long long v = fxs[threadIdx.x];
+            if (v) asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(buf + threadIdx.x), "l"(v) : "memory");
+        }
         __syncthreads();
         if (threadIdx.x == 0) {
             flag = 0;
-            if (!grid_arrive_wait(&ctrl->arrive64, base + G * (nbar + (unsigned long long)(it + 1)))) {
+            if (!grid_arrive_wait(&ctrl->arrive64, base + G * jb)) {
                 flag = 3;
                 st->status = UPSLAM_ERR_TIMEOUT;
             }
         }
         __syncthreads();
         if (flag == 3) return;
-        sum_records(rec, gridDim.x, sh, shc, shn, sg, tot, totn);
+        clear_prev(jb);
         if (warp == 0) {
+            // the step's totals: one L2 round trip for the 86 words every CTA added into
+            if (lane < 28) {
+                const long long s0 = (long long)__ldcg(buf + 3 * lane), s1 = (long long)__ldcg(buf + 3 * lane + 1),
+                                s2 = (long long)__ldcg(buf + 3 * lane + 2);
+                tot[lane] = fx_value(s0, s1, s2);
+            } else if (lane < 30) {
+                totn[lane - 28] = (long long)__ldcg(buf + 84 + (lane - 28));
+            }
+            __syncwarp();
             const long long inliers = totn[0];
             double xi[6] = {0, 0, 0, 0, 0, 0};
             int status = UPSLAM_OK, conv = 0;
@@ -800,6 +751,7 @@ __global__ void __launch_bounds__(kTileThreads, 1)
         }
         __syncthreads();
         if (flag == 3) return;
+        clear_prev(nbar + (unsigned long long)(it + 1));
         if (acc_ok) {
             // hole fill, second pass: the winning sweep pixel writes the keyframe pixel
             for (int j = blockIdx.x * kTileThreads + threadIdx.x; j < ns; j += gridDim.x * kTileThreads) {
