@@ -479,3 +479,32 @@ def test_track_scan_one_launch_equals_separate_launches():
     d_ref, i_ref = oracle.project(seq.scan(5), seq.sweep)
     assert np.array_equal(host(a.sw.idx), i_ref)
     assert np.array_equal(host(a.sw.depth).view(np.uint32), d_ref.view(np.uint32))
+
+
+def test_persistent_steps_keep_the_exact_association():
+    """After the first step the persistent kernel reuses each sample's previous sweep pixel where a
+    certified test proves the exact FP32 rule gives it again.  Step k's record must equal the oracle's
+    normal equations at the pose the kernel reached after k - 1 steps (inliers within the gate's
+    near-ties, J^T J 1e-5), for the tunnel workload at full size."""
+    seq = configs.tunnel_sequence(n_scans=3)
+    prm = oracle.Params(accept_quality=0.1)
+    kf_ref = oracle.Keyframe(seq.kf)
+    sp0, sn0, _, _ = oracle.sweep_frame(seq.scan(0), seq.sweep, prm)
+    oracle.fuse(kf_ref, sp0, sn0, seq.sweep, IDENTITY, prm)
+    sp4, sn4, _, _ = oracle.sweep_frame(seq.scan(2), seq.sweep, prm)
+    kd, kn = kf_ref.depth_f32(), kf_ref.nrm4_f32()
+    kf = _kf_buffers(kd, kn, seq.kf)
+    sw = _sweep_buffers(sp4, sn4, seq.sweep)
+    T0 = synth.perturb(synth.relative(seq.poses[0], seq.poses[2]), np.random.default_rng(29), 0.03, 0.01)
+    prev = T0
+    for k in range(1, 6):
+        state = up.IcpState(kf)
+        state.pose.copy_(pose_dev(T0))
+        up.icp(kf, sw, state, up.Params(max_iters=k, eps_rot=0.0, eps_trans=0.0))
+        st = state.read_stats()
+        assert st["iters"] == k
+        ref = oracle.normal_equations(kd, kn, seq.kf, sp4, sn4, seq.sweep, prev, prm)
+        A, A_ref = _upper_to_full(st["A"]), _upper_to_full(ref["A"])
+        assert abs(st["inliers"] - ref["inliers"]) <= 3, (k, st["inliers"], ref["inliers"])
+        assert np.linalg.norm(A - A_ref) <= 1e-5 * np.linalg.norm(A_ref), k
+        prev = pose_host(state.pose)
