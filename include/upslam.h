@@ -449,14 +449,20 @@ upslam_status upslam_keyframe_consistency(const upslam_keyframe *kf_a, const ups
  * Parameters: one FP32 array of upslam_cnn_param_count() values in the order
  * w0 b0 w1 b1 w2 b2 w3 b3 wf bf (conv weights [C_out][3][3][C_in] for
  * 8->32->64->128->128 channels, head wf [6][128]).  Convolutions run as BF16
- * tensor-core GEMMs (mma.sync m16n8k16) with FP32 accumulation.
+ * tensor-core GEMMs (tcgen05.mma, FP32 accumulators in tensor memory).
  * d_ws: upslam_cnn_workspace_bytes(batch) bytes, 256-byte aligned; it keeps
  *   the activations of the last forward call, which upslam_cnn_backward reads.
  * d_x must be 16-byte aligned.  A null pointer, batch <= 0, a short or
  * misaligned workspace returns UPSLAM_ERR_INVALID_ARG before any launch.
+ * Every wait of the tensor-core kernels is bounded: one that gives up (the
+ * tensor cores never signalled) stops its CTA, leaves that call's outputs
+ * incomplete and stores a nonzero int32 at byte upslam_cnn_error_offset(batch)
+ * of d_ws.  The library never clears that word: zero the workspace once after
+ * allocating it and read the word at the caller's next synchronisation.
  */
 size_t upslam_cnn_param_count(void);
 size_t upslam_cnn_workspace_bytes(int32_t batch);
+size_t upslam_cnn_error_offset(int32_t batch);
 upslam_status upslam_cnn_forward(const float *d_params, const void *d_x, int32_t batch, float *d_out, void *d_ws,
                                  size_t ws_bytes, void *stream);
 /* Loss sum_b sum_i w_i (out - target)^2 / batch into *d_loss and every parameter's gradient into d_grads

@@ -108,6 +108,7 @@ SIGNATURES = {
                                                    _vp, ctypes.c_size_t, _vp, _vp]),
     "upslam_cnn_param_count": (ctypes.c_size_t, []),
     "upslam_cnn_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int32]),
+    "upslam_cnn_error_offset": (ctypes.c_size_t, [ctypes.c_int32]),
     "upslam_cnn_forward": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, _vp, _vp, ctypes.c_size_t, _vp]),
     "upslam_cnn_backward": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_size_t,
                                            _vp]),

@@ -8,15 +8,17 @@
 //   x0 [B, 64, 256, 8] --conv3x3/s2+ReLU--> [B,32,128,32] --> [B,16,64,64]
 //      --> [B,8,32,128] --> [B,4,16,128] --mean--> [B,128] --linear--> [B,6]
 //
-// Convolutions are GEMMs over im2col columns (reduction index (ky*3+kx)*Cin+ci):
-//   forward  Y[M,N]  = cols[M,K] . W[N,K]^T          (+ bias, ReLU, BF16 out)
-//   dW[N,K] += dY[M,N]^T . cols[M,K]                 (split-K, FP32 atomics)
-//   dcols    = dY[M,N] . W[N,K]  -> col2im -> x ReLU mask -> dY of the layer below
-// The GEMM is one kernel: 64x64x32 CTA tiles, four warps of 32x32, BF16
-// operands staged in shared memory, mma.sync.m16n8k16 with FP32 accumulators.
+// Each convolution is a GEMM whose im2col operand (reduction index
+// f = (ky*3+kx)*Cin+ci over pixel p) is gathered straight from the NHWC
+// activation while it is staged, so no column matrix is ever stored:
+//   forward  Y[p, n]  = sum_f cols(p, f) W[n, f]        (+ bias, ReLU, BF16 out)
+//   dW[n, f]         += sum_p cols(p, f) dY[p, n]       (split over p, FP32 red)
+//   dcols[p, f]       = sum_n dY[p, n] W[n, f]  -> col2im -> x ReLU mask
+// All three run on one persistent kernel on the fifth-generation tensor cores
+// (tcgen05.mma, FP32 accumulators in tensor memory); see gemm_tc_kernel.
 // Parameters live as one FP32 master array (w0 b0 w1 b1 w2 b2 w3 b3 wf bf,
 // weights [C_out][3][3][C_in], head [6][128]); BF16 copies of the conv weights
-// (K padded to a multiple of 32) are what the GEMMs read.
+// are what the GEMMs read.
 #include <string.h>
 
 #include "common.cuh"
@@ -27,173 +29,309 @@ constexpr int kCnnCh[5] = {8, 32, 64, 128, 128};
 constexpr int kCnnH = 64, kCnnW = 256;
 
 __host__ __device__ constexpr int cnn_k(int l) { return 9 * (l == 0 ? 8 : (l == 1 ? 32 : (l == 2 ? 64 : 128))); }
-__host__ __device__ constexpr int cnn_kp(int l) { return (cnn_k(l) + 31) / 32 * 32; }
 __host__ __device__ constexpr int cnn_co(int l) { return l == 0 ? 32 : (l == 1 ? 64 : 128); }
 
-// ----------------------------------------------------------------------------- GEMM
+// ----------------------------------------------------------------------------- tcgen05 GEMM
+//
+// C(m, n) = sum_k A(m, k) B(n, k).  Work is cut into units of one 128 x BN
+// output tile and one slice of K (split-K); each CTA (four warps) walks the
+// units blockIdx.x, blockIdx.x + gridDim.x, ... and, inside each, K in steps of
+// 64, as one continuous pipeline of S shared-memory stages:
+//   * every thread copies its share of the operand chunks of step s + S - 1
+//     with 16-byte cp.async (zero-filled outside the matrix), so loads run
+//     S - 1 steps ahead of the tensor cores, across unit boundaries too;
+//   * one thread issues the step's tcgen05.mma.kind::f16 (BF16 in, FP32
+//     accumulate, K = 16 each) and commits them to the stage's mbarrier, which
+//     frees the stage for refilling;
+//   * after a unit's last step the four warps read their 32 accumulator rows
+//     with tcgen05.ld and apply the epilogue.
+// An operand tile is R rows (along M or N) x 64 (along K) in the no-swizzle
+// canonical layout: 8 x 8 core matrices of 128 contiguous bytes, core matrix
+// (row group g, k group h) at g * 1024 + h * 128 bytes.  Inside a core matrix
+// a K-major operand holds 8 rows of 8 consecutive k, an MN-major one 8 k of 8
+// consecutive rows (instruction descriptor bits 15/16 say which).  A 16-byte
+// chunk is (a, f): a indexes one row of a K-major operand (8 consecutive k = f)
+// or one k of an MN-major operand (8 consecutive rows = f).  The sources:
+//   dense:  X[a * ld + f];
+//   im2col: pixel p and feature f of a 3x3 stride-2 pad-1 convolution over an
+//           NHWC activation [B][H][W][C] (H, W, C powers of two):
+//           x[b][2oy+ky-1][2ox+kx-1][ci..ci+7], zero outside the image.
+// Every wait is bounded; a wait that gives up sets *err and the CTA stops.
 
-enum { EPI_BIAS_RELU_BF16 = 0, EPI_F32 = 1, EPI_F32_ATOMIC = 2 };
+enum { EPI_BIAS_RELU_BF16 = 0, EPI_F32 = 1, EPI_F32_RED_T = 2 };
+enum { LD_DENSE_K = 0, LD_IM2COL_K = 1, LD_DENSE_MN = 2, LD_IM2COL_MN = 3 };
 
-struct GemmArgs {
-    const __nv_bfloat16 *A;
-    long long sam, sak;  // A(m, k) = A[m * sam + k * sak]
-    const __nv_bfloat16 *B;
-    long long sbn, sbk;  // B(n, k) = B[n * sbn + k * sbk]
+struct TcOperand {
+    const __nv_bfloat16 *p;
+    long long ld;    // dense: elements between consecutive a
+    int rows;        // extent along M (operand A) or N (operand B)
+    int hs, ws, cs;  // im2col: log2 of the input's H, W, C
+};
+
+struct TcGemm {
+    TcOperand a, b;
     int M, N, K;
-    int k_split;  // K per grid.z slice (multiple of 32)
+    int k_split;      // K per unit (multiple of 64)
+    int mt, nt, units;
     void *C;
-    long long ldc;
+    long long ldc;    // EPI_F32_RED_T: C[n * ldc + m]; otherwise C[m * ldc + n]
     const float *bias;
 };
 
-__device__ __forceinline__ void mma_bf16(float c[4], const unsigned a[4], const unsigned b[2]) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+constexpr int kTcBM = 128, kTcBK = 64;
+constexpr unsigned kTcWaitIters = 1u << 26;
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+// UMMA shared-memory descriptor, no swizzle: start, leading (K) and stride (M/N) byte offsets.
+__device__ __forceinline__ unsigned long long umma_desc(unsigned addr, unsigned lbo, unsigned sbo) {
+    return (unsigned long long)((addr >> 4) & 0x3FFFu) | ((unsigned long long)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((unsigned long long)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
-template <int EPI>
-__global__ void __launch_bounds__(128) gemm_bf16_kernel(GemmArgs g) {
-    constexpr int BM = 64, BN = 64, BK = 32, LD = BK + 8;
-    __shared__ __align__(16) __nv_bfloat16 As[BM][LD];
-    __shared__ __align__(16) __nv_bfloat16 Bs[BN][LD];
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-    const int kbeg = blockIdx.z * g.k_split, kend = min(g.K, kbeg + g.k_split);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-    const int grp = lane >> 2, tg = lane & 3;
-    float acc[2][4][4];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) acc[i][j][c] = 0.0f;
-    const __nv_bfloat16 zero = __float2bfloat16(0.0f);
-    for (int k0 = kbeg; k0 < kend; k0 += BK) {
-        // stage the A and B tiles (generic strides; 8-wide vector loads when K is contiguous and aligned)
-        if (g.sak == 1 && (g.sam % 8) == 0 && k0 + BK <= kend) {
-            for (int i = tid; i < BM * (BK / 8); i += 128) {
-                const int r = i / (BK / 8), c8 = (i % (BK / 8)) * 8;
-                const int m = m0 + r;
-                uint4 v = make_uint4(0, 0, 0, 0);
-                if (m < g.M) v = *reinterpret_cast<const uint4 *>(g.A + (long long)m * g.sam + k0 + c8);
-                *reinterpret_cast<uint4 *>(&As[r][c8]) = v;
-            }
-        } else if (g.sam == 1 && (g.sak % 8) == 0 && m0 + BM <= g.M && k0 + BK <= kend) {
-            // M contiguous: 8 consecutive rows of one column per 16-byte load, transposed into the tile
-            for (int i = tid; i < (BM / 8) * BK; i += 128) {
-                const int c = i / (BM / 8), r8 = (i % (BM / 8)) * 8;
-                const uint4 v = *reinterpret_cast<const uint4 *>(g.A + (long long)(k0 + c) * g.sak + m0 + r8);
-                const __nv_bfloat16 *e = reinterpret_cast<const __nv_bfloat16 *>(&v);
-#pragma unroll
-                for (int q = 0; q < 8; ++q) As[r8 + q][c] = e[q];
-            }
-        } else {
-            for (int i = tid; i < BM * BK; i += 128) {
-                const int r = i / BK, c = i % BK;
-                const int m = m0 + r, k = k0 + c;
-                As[r][c] = (m < g.M && k < kend) ? g.A[(long long)m * g.sam + (long long)k * g.sak] : zero;
-            }
-        }
-        if (g.sbk == 1 && (g.sbn % 8) == 0 && k0 + BK <= kend) {
-            for (int i = tid; i < BN * (BK / 8); i += 128) {
-                const int r = i / (BK / 8), c8 = (i % (BK / 8)) * 8;
-                const int n = n0 + r;
-                uint4 v = make_uint4(0, 0, 0, 0);
-                if (n < g.N) v = *reinterpret_cast<const uint4 *>(g.B + (long long)n * g.sbn + k0 + c8);
-                *reinterpret_cast<uint4 *>(&Bs[r][c8]) = v;
-            }
-        } else if (g.sbn == 1 && (g.sbk % 8) == 0 && n0 + BN <= g.N && k0 + BK <= kend) {
-            // N contiguous: 8 consecutive columns of one k per 16-byte load, transposed into the tile
-            for (int i = tid; i < (BN / 8) * BK; i += 128) {
-                const int c = i / (BN / 8), r8 = (i % (BN / 8)) * 8;
-                const uint4 v = *reinterpret_cast<const uint4 *>(g.B + (long long)(k0 + c) * g.sbk + n0 + r8);
-                const __nv_bfloat16 *e = reinterpret_cast<const __nv_bfloat16 *>(&v);
-#pragma unroll
-                for (int q = 0; q < 8; ++q) Bs[r8 + q][c] = e[q];
-            }
-        } else {
-            for (int i = tid; i < BN * BK; i += 128) {
-                const int r = i / BK, c = i % BK;
-                const int n = n0 + r, k = k0 + c;
-                Bs[r][c] = (n < g.N && k < kend) ? g.B[(long long)n * g.sbn + (long long)k * g.sbk] : zero;
-            }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < BK; kk += 16) {
-            unsigned af[2][4], bf[4][2];
-#pragma unroll
-            for (int i = 0; i < 2; ++i) {
-                const int r = wm + i * 16 + grp;
-                af[i][0] = *reinterpret_cast<const unsigned *>(&As[r][kk + 2 * tg]);
-                af[i][1] = *reinterpret_cast<const unsigned *>(&As[r + 8][kk + 2 * tg]);
-                af[i][2] = *reinterpret_cast<const unsigned *>(&As[r][kk + 2 * tg + 8]);
-                af[i][3] = *reinterpret_cast<const unsigned *>(&As[r + 8][kk + 2 * tg + 8]);
-            }
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int n = wn + j * 8 + grp;
-                bf[j][0] = *reinterpret_cast<const unsigned *>(&Bs[n][kk + 2 * tg]);
-                bf[j][1] = *reinterpret_cast<const unsigned *>(&Bs[n][kk + 2 * tg + 8]);
-            }
-#pragma unroll
-            for (int i = 0; i < 2; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], af[i], bf[j]);
-        }
-        __syncthreads();
+__device__ __forceinline__ bool mbar_wait(unsigned mbar, unsigned parity) {
+    for (unsigned it = 0; it < kTcWaitIters; ++it) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (done) return true;
     }
-    // epilogue: acc[i][j][c] is row wm + i*16 + grp (+8 for c >= 2), column wn + j*8 + 2*tg + (c & 1)
+    return false;
+}
+
+template <bool L1>
+__device__ __forceinline__ void cp_async16(unsigned dst, const void *src, bool ok) {
+    if (L1)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(ok ? 16 : 0) : "memory");
+    else
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(ok ? 16 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Issue the copies of one R x 64 operand tile: rows [r0, r0 + R), k [k0, k0 + 64), zero where k >= kend
+// or a row >= o.rows.  A warp takes 8 consecutive a by 4 consecutive f chunks: the 8 a land in the 8
+// distinct 16-byte rows of a core matrix (no shared-memory bank conflict) and the 4 chunks of one a are
+// contiguous in a dense source.
+template <int LD, int R>
+__device__ __forceinline__ void tc_load(unsigned tile, const TcOperand &o, int r0, int k0, int kend) {
+    constexpr bool MN = LD == LD_DENSE_MN || LD == LD_IM2COL_MN;
+    constexpr bool IM = LD == LD_IM2COL_K || LD == LD_IM2COL_MN;
+    constexpr int NA8 = MN ? kTcBK / 8 : R / 8;  // groups of 8 along a
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const int m = m0 + wm + i * 16 + grp + (c >= 2 ? 8 : 0);
-                const int n = n0 + wn + j * 8 + 2 * tg + (c & 1);
-                if (m >= g.M || n >= g.N) continue;
-                const float v = acc[i][j][c];
-                if (EPI == EPI_BIAS_RELU_BF16) {
-                    reinterpret_cast<__nv_bfloat16 *>(g.C)[(long long)m * g.ldc + n] =
-                        __float2bfloat16(fmaxf(v + g.bias[n], 0.0f));
-                } else if (EPI == EPI_F32) {
-                    reinterpret_cast<float *>(g.C)[(long long)m * g.ldc + n] = v;
-                } else {
-                    atomicAdd(reinterpret_cast<float *>(g.C) + (long long)m * g.ldc + n, v);
-                }
+    for (int it = 0; it < R / 16; ++it) {
+        const int q = it * 4 + warp;
+        const int i = (q % NA8) * 8 + (lane & 7);
+        const int j = (q / NA8) * 4 + (lane >> 3);
+        int a, f;
+        bool ok;
+        if (MN) {
+            a = k0 + i;
+            f = r0 + 8 * j;
+            ok = a < kend && f < o.rows;
+        } else {
+            a = r0 + i;
+            f = k0 + 8 * j;
+            ok = a < o.rows && f < kend;
+        }
+        const __nv_bfloat16 *src = o.p;
+        if (IM) {
+            const int wo = o.ws - 1, ho = o.hs - 1;
+            const int ox = a & ((1 << wo) - 1), oy = (a >> wo) & ((1 << ho) - 1), b = a >> (wo + ho);
+            const int tap = f >> o.cs, ci = f & ((1 << o.cs) - 1);
+            const int ky = tap / 3, kx = tap - 3 * ky;
+            const int y = 2 * oy + ky - 1, x = 2 * ox + kx - 1;
+            ok = ok && (unsigned)y < (1u << o.hs) && (unsigned)x < (1u << o.ws);
+            if (ok) src = o.p + ((((((long long)b << o.hs) + y) << o.ws) + x) << o.cs) + ci;
+        } else if (ok) {
+            src = o.p + (long long)a * o.ld + f;
+        }
+        const unsigned off = MN ? j * 1024 + (i >> 3) * 128 : (i >> 3) * 1024 + j * 128;
+        cp_async16<IM>(tile + off + (i & 7) * 16, src, ok);
+    }
+}
+
+template <int BN>
+__device__ __forceinline__ void tc_unit(const TcGemm &g, int u, int &r0a, int &r0b, int &kbeg, int &kend, int &nkt) {
+    const int nt = u % g.nt, rest = u / g.nt;
+    r0a = (rest % g.mt) * kTcBM;
+    r0b = nt * BN;
+    kbeg = (rest / g.mt) * g.k_split;
+    kend = min(g.K, kbeg + g.k_split);
+    nkt = (kend - kbeg + kTcBK - 1) / kTcBK;
+}
+
+template <int BN>
+constexpr int tc_stages() { return BN == 128 ? 3 : 4; }
+template <int BN>
+constexpr int tc_smem_bytes() { return tc_stages<BN>() * (kTcBM + BN) * kTcBK * 2; }
+
+template <int EPI, int BN, int LA, int LB>
+__global__ void __launch_bounds__(128, 2) gemm_tc_kernel(TcGemm g, int *err) {
+    constexpr int S = tc_stages<BN>();
+    constexpr int kA = kTcBM * kTcBK * 2, kStage = (kTcBM + BN) * kTcBK * 2;
+    constexpr bool A_MN = LA == LD_DENSE_MN || LA == LD_IM2COL_MN;
+    constexpr bool B_MN = LB == LD_DENSE_MN || LB == LD_IM2COL_MN;
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    __shared__ __align__(8) unsigned long long mbar[S];
+    __shared__ unsigned tmem_base;
+    const unsigned smem0 = smem_u32(tc_smem);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(BN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < S; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[i])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const unsigned tmem = tmem_base;
+    // instruction descriptor: FP32 accumulator, BF16 A and B, majors, N = BN, M = 128
+    const unsigned idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((A_MN ? 1u : 0u) << 15) | ((B_MN ? 1u : 0u) << 16) |
+                           ((unsigned)(BN >> 3) << 17) | ((unsigned)(kTcBM >> 4) << 24);
+
+    // producer cursor: unit pu, step pk inside it
+    int pu = blockIdx.x, pk = 0;
+    auto produce = [&](int stage) {
+        if (pu < g.units) {
+            int r0a, r0b, kbeg, kend, nkt;
+            tc_unit<BN>(g, pu, r0a, r0b, kbeg, kend, nkt);
+            const int k0 = kbeg + pk * kTcBK;
+            tc_load<LA, kTcBM>(smem0 + stage * kStage, g.a, r0a, k0, kend);
+            tc_load<LB, BN>(smem0 + stage * kStage + kA, g.b, r0b, k0, kend);
+            if (++pk == nkt) {
+                pk = 0;
+                pu += gridDim.x;
             }
+        }
+        cp_async_commit();
+    };
+#pragma unroll
+    for (int i = 0; i < S - 1; ++i) produce(i);
+
+    bool bad = false;
+    int s = 0;  // consumer step
+    int last_commit = -1;
+    for (int cu = blockIdx.x; cu < g.units; cu += gridDim.x) {
+        int r0a, r0b, kbeg, kend, nkt;
+        tc_unit<BN>(g, cu, r0a, r0b, kbeg, kend, nkt);
+        for (int ck = 0; ck < nkt; ++ck, ++s) {
+            const int st = s % S;
+            cp_async_wait<S - 2>();
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            if (__syncthreads_or(bad)) goto done;
+            if (threadIdx.x == 0) {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const unsigned a0 = smem0 + st * kStage, b0 = a0 + kA;
+                const int k0 = kbeg + ck * kTcBK;
+                const int nk = min(kTcBK / 16, (kend - k0 + 15) / 16);
+                for (int kk = 0; kk < nk; ++kk) {
+                    const unsigned long long ad = umma_desc(a0 + kk * 256, 128, 1024);
+                    const unsigned long long bd = umma_desc(b0 + kk * 256, 128, 1024);
+                    const unsigned acc = (ck > 0 || kk > 0) ? 1u : 0u;
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                        "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                        : "memory");
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 smem_u32(&mbar[st]))
+                             : "memory");
+            }
+            last_commit = s;
+            if (ck + 1 == nkt) {
+                // the unit's last commit covers all its MMAs
+                bad = bad || !mbar_wait(smem_u32(&mbar[st]), (unsigned)((s / S) & 1));
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                if (!bad) {
+                    const int m = r0a + warp * 32 + lane;
+                    constexpr int CW = BN < 32 ? BN : 32;  // columns per tensor-memory wait
+#pragma unroll
+                    for (int c0 = 0; c0 < BN; c0 += CW) {
+                        unsigned v[CW];
+#pragma unroll
+                        for (int q = 0; q < CW / 8; ++q)
+                            asm volatile(
+                                "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                                : "=r"(v[8 * q]), "=r"(v[8 * q + 1]), "=r"(v[8 * q + 2]), "=r"(v[8 * q + 3]),
+                                  "=r"(v[8 * q + 4]), "=r"(v[8 * q + 5]), "=r"(v[8 * q + 6]), "=r"(v[8 * q + 7])
+                                : "r"(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(c0 + 8 * q)));
+                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                        if (m < g.M) {
+#pragma unroll
+                            for (int q = 0; q < CW / 8; ++q) {
+                                const int n = r0b + c0 + 8 * q;
+                                const unsigned *w = v + 8 * q;
+                                if (n >= g.N) continue;
+                                if (EPI == EPI_BIAS_RELU_BF16) {
+                                    uint4 o;
+                                    unsigned *ow = &o.x;
+#pragma unroll
+                                    for (int jj = 0; jj < 4; ++jj) {
+                                        const __nv_bfloat162 h = __floats2bfloat162_rn(
+                                            fmaxf(__uint_as_float(w[2 * jj]) + __ldg(g.bias + n + 2 * jj), 0.0f),
+                                            fmaxf(__uint_as_float(w[2 * jj + 1]) + __ldg(g.bias + n + 2 * jj + 1),
+                                                  0.0f));
+                                        ow[jj] = *reinterpret_cast<const unsigned *>(&h);
+                                    }
+                                    *reinterpret_cast<uint4 *>(reinterpret_cast<__nv_bfloat16 *>(g.C) +
+                                                               (long long)m * g.ldc + n) = o;
+                                } else if (EPI == EPI_F32) {
+                                    float4 *o = reinterpret_cast<float4 *>(reinterpret_cast<float *>(g.C) +
+                                                                           (long long)m * g.ldc + n);
+                                    o[0] = make_float4(__uint_as_float(w[0]), __uint_as_float(w[1]),
+                                                       __uint_as_float(w[2]), __uint_as_float(w[3]));
+                                    o[1] = make_float4(__uint_as_float(w[4]), __uint_as_float(w[5]),
+                                                       __uint_as_float(w[6]), __uint_as_float(w[7]));
+                                } else {
+#pragma unroll
+                                    for (int jj = 0; jj < 8; ++jj)
+                                        if (n + jj < g.N)
+                                            atomicAdd(reinterpret_cast<float *>(g.C) + (long long)(n + jj) * g.ldc + m,
+                                                      __uint_as_float(w[jj]));
+                                }
+                            }
+                        }
+                    }
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            }
+            // refill the stage of step s - 1 (its MMAs must be done) with step s + S - 1
+            if (s >= 1 && !bad) bad = !mbar_wait(smem_u32(&mbar[(s - 1) % S]), (unsigned)(((s - 1) / S) & 1));
+            if (!bad) produce((s + S - 1) % S);
+            else cp_async_commit();
+        }
+    }
+done:
+    cp_async_wait<0>();
+    if (bad) {
+        // wait (bounded) for the last committed MMAs before the accumulator is freed
+        if (threadIdx.x == 0) {
+            atomicExch(err, 1);
+            if (last_commit >= 0) mbar_wait(smem_u32(&mbar[last_commit % S]), (unsigned)((last_commit / S) & 1));
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
 }
 
 // ----------------------------------------------------------------------------- layout kernels
 
-// [B,H,W,C] BF16 -> [B*H/2*W/2, Kp] BF16 columns of a 3x3 stride-2 pad-1 convolution (zero K padding).
-__global__ void im2col_kernel(const __nv_bfloat16 *__restrict__ x, int B, int H, int W, int C, int Kp,
-                              __nv_bfloat16 *__restrict__ cols) {
-    const int Ho = H / 2, Wo = W / 2;
-    const long long total = (long long)B * Ho * Wo * Kp;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int k = (int)(i % Kp);
-        const long long m = i / Kp;
-        __nv_bfloat16 v = __float2bfloat16(0.0f);
-        if (k < 9 * C) {
-            const int ci = k % C, tap = k / C, ky = tap / 3, kx = tap % 3;
-            const int ox = (int)(m % Wo), oy = (int)((m / Wo) % Ho), b = (int)(m / ((long long)Wo * Ho));
-            const int y = 2 * oy + ky - 1, xx = 2 * ox + kx - 1;
-            if (y >= 0 && y < H && xx >= 0 && xx < W) v = x[(((long long)b * H + y) * W + xx) * C + ci];
-        }
-        cols[i] = v;
-    }
-}
-
 // Adjoint of im2col followed by the ReLU mask of the layer's input (activation > 0):
 // dy_in[b,y,x,c] = (x_in > 0) * sum over the (output pixel, tap) pairs that read (y, x) of dcols.
-__global__ void col2im_mask_kernel(const float *__restrict__ dcols, int B, int H, int W, int C, int Kp,
+__global__ void col2im_mask_kernel(const float *__restrict__ dcols, int B, int H, int W, int C, int ldk,
                                    const __nv_bfloat16 *__restrict__ x_in, __nv_bfloat16 *__restrict__ dy_in) {
     const int Ho = H / 2, Wo = W / 2;
     const long long total = (long long)B * H * W * C;
@@ -215,7 +353,7 @@ __global__ void col2im_mask_kernel(const float *__restrict__ dcols, int B, int H
                     if (u < 0 || (u & 1) || (u >> 1) >= Wo) continue;
                     const int ox = u >> 1;
                     const long long m = ((long long)b * Ho + oy) * Wo + ox;
-                    s += dcols[m * Kp + (ky * 3 + kx) * C + c];
+                    s += dcols[m * ldk + (ky * 3 + kx) * C + c];
                 }
             }
         }
@@ -280,20 +418,9 @@ __global__ void bias_grad_kernel(const __nv_bfloat16 *__restrict__ dy, int M, in
     }
 }
 
-// FP32 master weights -> BF16 conv weights with K padded to a multiple of 32.
-__global__ void pack_weights_kernel(const float *w, int N, int K, int Kp, __nv_bfloat16 *wb) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N * Kp; i += gridDim.x * blockDim.x) {
-        const int n = i / Kp, k = i % Kp;
-        wb[i] = __float2bfloat16(k < K ? w[n * K + k] : 0.0f);
-    }
-}
-
-// Padded FP32 weight gradient [N][Kp] -> the master layout [N][K], added.
-__global__ void unpad_grad_kernel(const float *gp, int N, int K, int Kp, float *gw) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N * K; i += gridDim.x * blockDim.x) {
-        const int n = i / K, k = i % K;
-        gw[i] += gp[n * Kp + k];
-    }
+// FP32 master conv weights [N][K] -> the BF16 copy the GEMMs read.
+__global__ void pack_weights_kernel(const float *w, int n, __nv_bfloat16 *wb) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) wb[i] = __float2bfloat16(w[i]);
 }
 
 // Adam (Kingma & Ba) on the FP32 master parameters, bias-corrected.
@@ -367,9 +494,9 @@ static CnnLayout cnn_layout() {
 struct CnnWs {
     __nv_bfloat16 *wb[4];
     __nv_bfloat16 *act[4];  // outputs of the four conv layers
-    __nv_bfloat16 *cols;
     __nv_bfloat16 *dy[4];
-    float *dcols, *dwpad, *g, *out;
+    float *dcols, *g, *out;
+    int *err;               // nonzero once a tensor-core wait gave up
 };
 
 static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -382,34 +509,30 @@ static size_t cnn_ws_layout(int B, CnnWs *w, char *base) {
         return p;
     };
     int H = kCnnH, W = kCnnW;
-    size_t max_cols = 0, max_dcols = 0, max_dw = 0;
+    size_t max_dcols = 0;
     for (int l = 0; l < 4; ++l) {
         const size_t M = (size_t)B * (H / 2) * (W / 2);
-        if (w) w->wb[l] = reinterpret_cast<__nv_bfloat16 *>(take((size_t)cnn_co(l) * cnn_kp(l) * 2));
-        else take((size_t)cnn_co(l) * cnn_kp(l) * 2);
+        void *wb = take((size_t)cnn_co(l) * cnn_k(l) * 2);
         void *a = take(M * cnn_co(l) * 2);
         void *d = take(M * cnn_co(l) * 2);
         if (w) {
+            w->wb[l] = reinterpret_cast<__nv_bfloat16 *>(wb);
             w->act[l] = reinterpret_cast<__nv_bfloat16 *>(a);
             w->dy[l] = reinterpret_cast<__nv_bfloat16 *>(d);
         }
-        max_cols = max_cols > M * cnn_kp(l) ? max_cols : M * cnn_kp(l);
-        max_dcols = max_dcols > M * cnn_kp(l) ? max_dcols : M * cnn_kp(l);
-        max_dw = max_dw > (size_t)cnn_co(l) * cnn_kp(l) ? max_dw : (size_t)cnn_co(l) * cnn_kp(l);
+        if (l > 0) max_dcols = max_dcols > M * cnn_k(l) ? max_dcols : M * cnn_k(l);
         H /= 2;
         W /= 2;
     }
-    void *c = take(max_cols * 2);
     void *dc = take(max_dcols * 4);
-    void *dw = take(max_dw * 4);
     void *g = take((size_t)B * 128 * 4);
     void *out = take((size_t)B * 6 * 4);
+    void *err = take(256);
     if (w) {
-        w->cols = reinterpret_cast<__nv_bfloat16 *>(c);
         w->dcols = reinterpret_cast<float *>(dc);
-        w->dwpad = reinterpret_cast<float *>(dw);
         w->g = reinterpret_cast<float *>(g);
         w->out = reinterpret_cast<float *>(out);
+        w->err = reinterpret_cast<int *>(err);
     }
     return o;
 }
@@ -420,13 +543,51 @@ static int grid1d(long long n, int t = 256) {
     return (int)(b < 1 ? 1 : (b < cap ? b : cap));
 }
 
-template <int EPI>
-static void gemm(const GemmArgs &g0, cudaStream_t s, int splits = 1) {
-    GemmArgs g = g0;
-    const int per = ((g.K + splits - 1) / splits + 31) / 32 * 32;
-    g.k_split = per;
-    dim3 grid((g.N + 63) / 64, (g.M + 63) / 64, (g.K + per - 1) / per);
-    gemm_bf16_kernel<EPI><<<grid, 128, 0, s>>>(g);
+static int ilog2(int v) {
+    int r = 0;
+    while ((1 << r) < v) ++r;
+    return r;
+}
+
+// The operands of the layer whose input is [B][H][W][C].
+static TcOperand op_im2col(const __nv_bfloat16 *x, int H, int W, int C) {
+    TcOperand o;
+    o.p = x;
+    o.ld = 0;
+    o.rows = 0;
+    o.hs = ilog2(H);
+    o.ws = ilog2(W);
+    o.cs = ilog2(C);
+    return o;
+}
+
+static TcOperand op_dense(const __nv_bfloat16 *x, long long ld) {
+    TcOperand o;
+    o.p = x;
+    o.ld = ld;
+    o.rows = 0;
+    o.hs = o.ws = o.cs = 0;
+    return o;
+}
+
+// C(m, n) = sum_k A(m, k) B(n, k) on the tensor cores, K cut into `splits` slices (rounded to 64).
+template <int EPI, int BN, int LA, int LB>
+static void gemm(TcGemm g, int *err, cudaStream_t s, int splits = 1) {
+    constexpr int smem = tc_smem_bytes<BN>();
+    static bool attr = false;  // per process; every GB300 of a box takes the same value
+    if (!attr) {
+        cudaFuncSetAttribute(gemm_tc_kernel<EPI, BN, LA, LB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        attr = true;
+    }
+    g.a.rows = g.M;
+    g.b.rows = g.N;
+    g.k_split = ((g.K + splits - 1) / splits + kTcBK - 1) / kTcBK * kTcBK;
+    const int z = (g.K + g.k_split - 1) / g.k_split;
+    g.mt = (g.M + kTcBM - 1) / kTcBM;
+    g.nt = (g.N + BN - 1) / BN;
+    g.units = g.mt * g.nt * z;
+    const int cap = 2 * upslam_sm_count();  // two CTAs per SM by shared memory
+    gemm_tc_kernel<EPI, BN, LA, LB><<<g.units < cap ? g.units : cap, 128, smem, s>>>(g, err);
 }
 
 }  // namespace upslam
@@ -438,6 +599,11 @@ extern "C" size_t upslam_cnn_param_count(void) { return cnn_layout().count; }
 extern "C" size_t upslam_cnn_workspace_bytes(int32_t batch) {
     if (batch <= 0) return 0;
     return cnn_ws_layout(batch, nullptr, nullptr);
+}
+
+extern "C" size_t upslam_cnn_error_offset(int32_t batch) {
+    if (batch <= 0) return 0;
+    return cnn_ws_layout(batch, nullptr, nullptr) - 256;  // the last block of the layout
 }
 
 extern "C" upslam_status upslam_cnn_forward(const float *d_params, const void *d_x, int32_t batch, float *d_out,
@@ -452,24 +618,20 @@ extern "C" upslam_status upslam_cnn_forward(const float *d_params, const void *d
     const __nv_bfloat16 *x = reinterpret_cast<const __nv_bfloat16 *>(d_x);
     int H = kCnnH, W = kCnnW;
     for (int l = 0; l < 4; ++l) {
-        const int C = kCnnCh[l], N = cnn_co(l), K = cnn_k(l), Kp = cnn_kp(l);
-        pack_weights_kernel<<<grid1d((long long)N * Kp), 256, 0, s>>>(d_params + L.off_w[l], N, K, Kp, w.wb[l]);
-        const long long M = (long long)batch * (H / 2) * (W / 2);
-        im2col_kernel<<<grid1d(M * Kp), 256, 0, s>>>(x, batch, H, W, C, Kp, w.cols);
-        GemmArgs g;
-        g.A = w.cols;
-        g.sam = Kp;
-        g.sak = 1;
-        g.B = w.wb[l];
-        g.sbn = Kp;
-        g.sbk = 1;
-        g.M = (int)M;
+        const int C = kCnnCh[l], N = cnn_co(l), K = cnn_k(l);
+        pack_weights_kernel<<<grid1d((long long)N * K), 256, 0, s>>>(d_params + L.off_w[l], N * K, w.wb[l]);
+        TcGemm g;
+        g.a = op_im2col(x, H, W, C);
+        g.b = op_dense(w.wb[l], K);
+        g.M = batch * (H / 2) * (W / 2);
         g.N = N;
-        g.K = Kp;
+        g.K = K;
         g.C = w.act[l];
         g.ldc = N;
         g.bias = d_params + L.off_b[l];
-        gemm<EPI_BIAS_RELU_BF16>(g, s);
+        if (N == 32) gemm<EPI_BIAS_RELU_BF16, 32, LD_IM2COL_K, LD_DENSE_K>(g, w.err, s);
+        else if (N == 64) gemm<EPI_BIAS_RELU_BF16, 64, LD_IM2COL_K, LD_DENSE_K>(g, w.err, s);
+        else gemm<EPI_BIAS_RELU_BF16, 128, LD_IM2COL_K, LD_DENSE_K>(g, w.err, s);
         x = w.act[l];
         H /= 2;
         W /= 2;
@@ -497,60 +659,45 @@ extern "C" upslam_status upslam_cnn_backward(const float *d_params, const void *
     // head: loss, d wf, d bf, and the gradient entering the last feature map (masked by its ReLU)
     head_backward_kernel<<<batch, 128, 0, s>>>(d_out, d_target, d_wloss6, batch, w.g, d_params + L.off_wf, w.act[3],
                                                4 * 16, 128, d_grads + L.off_wf, d_grads + L.off_bf, w.dy[3], d_loss);
-    int Hs[4], Ws[4];
-    {
-        int H = kCnnH, W = kCnnW;
-        for (int l = 0; l < 4; ++l) {
-            Hs[l] = H;
-            Ws[l] = W;
-            H /= 2;
-            W /= 2;
-        }
-    }
+    const int sms = upslam_sm_count();
     for (int l = 3; l >= 0; --l) {
-        const int C = kCnnCh[l], N = cnn_co(l), K = cnn_k(l), Kp = cnn_kp(l);
-        const int H = Hs[l], W = Ws[l];
-        const long long M = (long long)batch * (H / 2) * (W / 2);
+        const int C = kCnnCh[l], N = cnn_co(l), K = cnn_k(l);
+        const int H = kCnnH >> l, W = kCnnW >> l;
+        const int P = batch * (H / 2) * (W / 2);
         const __nv_bfloat16 *xin = l == 0 ? reinterpret_cast<const __nv_bfloat16 *>(d_x) : w.act[l - 1];
-        im2col_kernel<<<grid1d(M * Kp), 256, 0, s>>>(xin, batch, H, W, C, Kp, w.cols);
-        // d W (padded layout) = dY^T cols, split over the M reduction
-        if (cudaMemsetAsync(w.dwpad, 0, (size_t)N * Kp * sizeof(float), s) != cudaSuccess) return UPSLAM_ERR_CUDA;
-        GemmArgs gw;
-        gw.A = w.dy[l];
-        gw.sam = 1;
-        gw.sak = N;
-        gw.B = w.cols;
-        gw.sbn = 1;
-        gw.sbk = Kp;
-        gw.M = N;
-        gw.N = Kp;
-        gw.K = (int)M;
-        gw.C = w.dwpad;
-        gw.ldc = Kp;
+        // dW[n][f] += sum_p cols(p, f) dY[p][n]: M = f (im2col, MN-major), N = n (dY, MN-major), K = p
+        TcGemm gw;
+        gw.a = op_im2col(xin, H, W, C);
+        gw.b = op_dense(w.dy[l], N);
+        gw.M = K;
+        gw.N = N;
+        gw.K = P;
+        gw.C = d_grads + L.off_w[l];
+        gw.ldc = K;
         gw.bias = nullptr;
-        const int tiles = ((N + 63) / 64) * ((Kp + 63) / 64);
-        int splits = (upslam_sm_count() * 4 + tiles - 1) / tiles;
-        if ((long long)splits * 256 > M) splits = (int)((M + 255) / 256);
-        gemm<EPI_F32_ATOMIC>(gw, s, splits < 1 ? 1 : splits);
-        unpad_grad_kernel<<<grid1d((long long)N * K), 256, 0, s>>>(w.dwpad, N, K, Kp, d_grads + L.off_w[l]);
-        bias_grad_kernel<<<upslam_sm_count() * 2, 128, 0, s>>>(w.dy[l], (int)M, N, d_grads + L.off_b[l]);
+        // enough slices for two CTAs per SM, each at least 16 K tiles deep
+        const int tiles = (K + kTcBM - 1) / kTcBM;
+        const int ktiles = (P + kTcBK - 1) / kTcBK;
+        int splits = (2 * sms + tiles - 1) / tiles;
+        if (splits > ktiles / 16) splits = ktiles / 16;
+        if (splits < 1) splits = 1;
+        if (N == 32) gemm<EPI_F32_RED_T, 32, LD_IM2COL_MN, LD_DENSE_MN>(gw, w.err, s, splits);
+        else if (N == 64) gemm<EPI_F32_RED_T, 64, LD_IM2COL_MN, LD_DENSE_MN>(gw, w.err, s, splits);
+        else gemm<EPI_F32_RED_T, 128, LD_IM2COL_MN, LD_DENSE_MN>(gw, w.err, s, splits);
+        bias_grad_kernel<<<sms * 2, 128, 0, s>>>(w.dy[l], P, N, d_grads + L.off_b[l]);
         if (l > 0) {
-            // d cols = dY W, then col2im with the input activation's ReLU mask
-            GemmArgs gd;
-            gd.A = w.dy[l];
-            gd.sam = N;
-            gd.sak = 1;
-            gd.B = w.wb[l];
-            gd.sbn = 1;
-            gd.sbk = Kp;
-            gd.M = (int)M;
-            gd.N = Kp;
+            // dcols[p][f] = sum_n dY[p][n] W[n][f] (W read MN-major), then col2im with the input's ReLU mask
+            TcGemm gd;
+            gd.a = op_dense(w.dy[l], N);
+            gd.b = op_dense(w.wb[l], K);
+            gd.M = P;
+            gd.N = K;
             gd.K = N;
             gd.C = w.dcols;
-            gd.ldc = Kp;
+            gd.ldc = K;
             gd.bias = nullptr;
-            gemm<EPI_F32>(gd, s);
-            col2im_mask_kernel<<<grid1d((long long)batch * H * W * C), 256, 0, s>>>(w.dcols, batch, H, W, C, Kp,
+            gemm<EPI_F32, 128, LD_DENSE_K, LD_DENSE_MN>(gd, w.err, s);
+            col2im_mask_kernel<<<grid1d((long long)batch * H * W * C), 256, 0, s>>>(w.dcols, batch, H, W, C, K,
                                                                                     w.act[l - 1], w.dy[l - 1]);
         }
     }

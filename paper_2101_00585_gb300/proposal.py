@@ -81,6 +81,7 @@ class PoseNet:
         self.device = device
         self.ws_bytes = int(L.upslam_cnn_workspace_bytes(self.batch))
         self.ws = torch.zeros(self.ws_bytes, dtype=torch.uint8, device=device)
+        self._batches: set = set()  # batch sizes used so far: each has its own error word in ws
         self.params = (params.to(device=device, dtype=torch.float32).clone() if params is not None
                        else self.init_params(seed, device))
         assert self.params.numel() == self.count
@@ -109,6 +110,7 @@ class PoseNet:
         """x: BF16 [B, 64, 256, 8], B <= batch -> FP32 [B, 6] (a view of an internal buffer)."""
         B = x.shape[0]
         assert x.dtype == torch.bfloat16 and x.is_contiguous() and B <= self.batch
+        self._batches.add(B)
         _abi.check("upslam_cnn_forward", _abi.lib().upslam_cnn_forward(_p(self.params), _p(x), B, _p(self.out),
                                                                        _p(self.ws), self.ws_bytes, _stream()))
         return self.out[:B]
@@ -126,6 +128,14 @@ class PoseNet:
         self.step += 1
         _abi.check("upslam_cnn_adam", _abi.lib().upslam_cnn_adam(_p(self.params), _p(self.grads), _p(self.m),
                                                                  _p(self.v), self.step, float(lr), _stream()))
+
+    def check(self) -> None:
+        """Raise if a tensor-core wait of any call so far gave up (its outputs were left incomplete)."""
+        L = _abi.lib()
+        for b in sorted(self._batches):
+            off = int(L.upslam_cnn_error_offset(b))
+            if int(self.ws[off:off + 4].view(torch.int32).item()) != 0:
+                raise RuntimeError(f"pose network: a tensor-core wait gave up (batch {b})")
 
     def train_step(self, x: torch.Tensor, target: torch.Tensor, lr: float) -> torch.Tensor:
         self.forward(x)
@@ -276,6 +286,7 @@ def train(net: PoseNet, x: torch.Tensor, xi: torch.Tensor, epochs: int = 3, lr: 
             tot += net.train_step(x[idx].contiguous(), xi[idx], rate)[0]
             s += 1
         hist.append(float(tot) / max(1, n // B))
+        net.check()
         if log:
             log(f"epoch {ep}: loss {hist[-1]:.5f}")
     return hist
