@@ -329,35 +329,53 @@ done:
 
 // ----------------------------------------------------------------------------- layout kernels
 
-// Adjoint of im2col followed by the ReLU mask of the layer's input (activation > 0):
+// Adjoint of im2col followed by the ReLU mask of the layer's input (activation > 0), 8 channels per thread:
 // dy_in[b,y,x,c] = (x_in > 0) * sum over the (output pixel, tap) pairs that read (y, x) of dcols.
-__global__ void col2im_mask_kernel(const float *__restrict__ dcols, int B, int H, int W, int C, int ldk,
-                                   const __nv_bfloat16 *__restrict__ x_in, __nv_bfloat16 *__restrict__ dy_in) {
-    const int Ho = H / 2, Wo = W / 2;
-    const long long total = (long long)B * H * W * C;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int c = (int)(i % C);
-        const int xx = (int)((i / C) % W), y = (int)((i / ((long long)C * W)) % H);
-        const int b = (int)(i / ((long long)C * W * H));
-        float s = 0.0f;
-        if (__bfloat162float(x_in[i]) > 0.0f) {
+// H = 2^hs, W = 2^ws, C = 2^cs (C >= 8); dcols rows are ldk floats (a multiple of 8).
+__global__ void __launch_bounds__(256) col2im_mask_kernel(const float *__restrict__ dcols, int B, int hs, int ws,
+                                                          int cs, int ldk, const __nv_bfloat16 *__restrict__ x_in,
+                                                          __nv_bfloat16 *__restrict__ dy_in) {
+    const int Ho = 1 << (hs - 1), Wo = 1 << (ws - 1), C = 1 << cs;
+    const int total = (B << (hs + ws)) << (cs - 3);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        const int c = (i & ((1 << (cs - 3)) - 1)) << 3;
+        const int pix = i >> (cs - 3);
+        const int x = pix & ((1 << ws) - 1), y = (pix >> ws) & ((1 << hs) - 1), b = pix >> (hs + ws);
+        const uint4 xm = __ldg(reinterpret_cast<const uint4 *>(x_in + ((long long)pix << cs) + c));
+        float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-            for (int ky = 0; ky < 3; ++ky) {
-                const int t = y + 1 - ky;
-                if (t < 0 || (t & 1) || (t >> 1) >= Ho) continue;
-                const int oy = t >> 1;
+        for (int ky = 0; ky < 3; ++ky) {
+            const int t = y + 1 - ky;
+            if (t < 0 || (t & 1) || (t >> 1) >= Ho) continue;
 #pragma unroll
-                for (int kx = 0; kx < 3; ++kx) {
-                    const int u = xx + 1 - kx;
-                    if (u < 0 || (u & 1) || (u >> 1) >= Wo) continue;
-                    const int ox = u >> 1;
-                    const long long m = ((long long)b * Ho + oy) * Wo + ox;
-                    s += dcols[m * ldk + (ky * 3 + kx) * C + c];
-                }
+            for (int kx = 0; kx < 3; ++kx) {
+                const int u = x + 1 - kx;
+                if (u < 0 || (u & 1) || (u >> 1) >= Wo) continue;
+                const int m = ((b * Ho + (t >> 1)) * Wo) + (u >> 1);
+                const float4 *src =
+                    reinterpret_cast<const float4 *>(dcols + (long long)m * ldk + (ky * 3 + kx) * C + c);
+                const float4 lo = __ldcs(src), hi = __ldcs(src + 1);
+                acc[0] += lo.x;
+                acc[1] += lo.y;
+                acc[2] += lo.z;
+                acc[3] += lo.w;
+                acc[4] += hi.x;
+                acc[5] += hi.y;
+                acc[6] += hi.z;
+                acc[7] += hi.w;
             }
         }
-        dy_in[i] = __float2bfloat16(s);
+        const __nv_bfloat162 *xh = reinterpret_cast<const __nv_bfloat162 *>(&xm);
+        uint4 o;
+        unsigned *ow = &o.x;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float2 xv = __bfloat1622float2(xh[q]);
+            const __nv_bfloat162 h =
+                __floats2bfloat162_rn(xv.x > 0.0f ? acc[2 * q] : 0.0f, xv.y > 0.0f ? acc[2 * q + 1] : 0.0f);
+            ow[q] = *reinterpret_cast<const unsigned *>(&h);
+        }
+        *reinterpret_cast<uint4 *>(dy_in + ((long long)pix << cs) + c) = o;
     }
 }
 
@@ -380,42 +398,104 @@ __global__ void pool_head_kernel(const __nv_bfloat16 *__restrict__ x, int B, int
     }
 }
 
-// Loss and the head's backward: dout = 2 w (out - t) / B; d wf += dout^T g; d bf += dout;
-// dy4 = (dout wf) / HW broadcast over the last feature map, masked by its ReLU.
-__global__ void head_backward_kernel(const float *out, const float *target, const float *w6, int B, const float *g,
-                                     const float *wf, const __nv_bfloat16 *__restrict__ x4, int HW, int C,
-                                     float *dwf, float *dbf, __nv_bfloat16 *__restrict__ dy4, float *loss) {
-    const int b = blockIdx.x;
-    __shared__ float dout[6], dg[128];
-    if (threadIdx.x < 6) {
-        const float diff = out[b * 6 + threadIdx.x] - target[b * 6 + threadIdx.x];
-        dout[threadIdx.x] = 2.0f * w6[threadIdx.x] * diff / B;
-        atomicAdd(loss, w6[threadIdx.x] * diff * diff / B);
-        atomicAdd(dbf + threadIdx.x, dout[threadIdx.x]);
-    }
+// Loss and the head's backward for kHeadB samples per block (C = 128 threads):
+// dout = 2 w (out - t) / B; loss += sum w (out - t)^2 / B; d bf += dout; d wf += dout^T g (summed over the
+// block's samples before one atomic per weight); dg[b][c] = (dout wf)[c] / HW, the gradient of every pixel
+// of the last feature map before its ReLU mask.
+constexpr int kHeadB = 8;
+__global__ void __launch_bounds__(128) head_backward_kernel(const float *out, const float *target, const float *w6,
+                                                            int B, const float *g, const float *wf, int HW,
+                                                            float *dwf, float *dbf, float *dg, float *loss) {
+    constexpr int C = 128;
+    const int b0 = blockIdx.x * kHeadB;
+    __shared__ float dout[kHeadB][6];
+    __shared__ float lsum;
+    const int t = threadIdx.x;
+    if (t == 0) lsum = 0.0f;
     __syncthreads();
-    for (int c = threadIdx.x; c < C; c += blockDim.x) {
-        float s = 0.0f;
-        for (int i = 0; i < 6; ++i) {
-            s += dout[i] * wf[i * C + c];
-            atomicAdd(dwf + i * C + c, dout[i] * g[b * C + c]);
+    if (t < kHeadB * 6) {
+        const int j = t / 6, i = t % 6, b = b0 + j;
+        float d = 0.0f, l = 0.0f;
+        if (b < B) {
+            const float diff = out[b * 6 + i] - target[b * 6 + i];
+            d = 2.0f * w6[i] * diff / B;
+            l = w6[i] * diff * diff / B;
         }
-        dg[c] = s / HW;
+        dout[j][i] = d;
+        atomicAdd(&lsum, l);
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < HW * C; i += blockDim.x) {
-        const long long idx = (long long)b * HW * C + i;
-        dy4[idx] = __float2bfloat16(__bfloat162float(x4[idx]) > 0.0f ? dg[i % C] : 0.0f);
+    if (t == 0) atomicAdd(loss, lsum);
+    if (t < 6) {
+        float sb = 0.0f;
+        for (int j = 0; j < kHeadB; ++j) sb += dout[j][t];
+        atomicAdd(dbf + t, sb);
+    }
+    float sw[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int j = 0; j < kHeadB && b0 + j < B; ++j) {
+        const float gv = g[(b0 + j) * C + t];
+        float s = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            sw[i] += dout[j][i] * gv;
+            s += dout[j][i] * wf[i * C + t];
+        }
+        dg[(b0 + j) * C + t] = s / HW;
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) atomicAdd(dwf + i * C + t, sw[i]);
+}
+
+// dy4[b][p][c] = (x4[b][p][c] > 0) * dg[b][c], 8 channels per thread (C = 128).
+__global__ void __launch_bounds__(256) head_dy_kernel(const float *__restrict__ dg, const __nv_bfloat16 *__restrict__ x4,
+                                                      int B, int HW, __nv_bfloat16 *__restrict__ dy4) {
+    const int total = B * HW * 16;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        const int c = (i & 15) << 3, pix = i >> 4, b = pix / HW;
+        const uint4 xm = __ldg(reinterpret_cast<const uint4 *>(x4) + i);
+        const float4 lo = __ldg(reinterpret_cast<const float4 *>(dg + b * 128 + c));
+        const float4 hi = __ldg(reinterpret_cast<const float4 *>(dg + b * 128 + c) + 1);
+        const float v[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+        const __nv_bfloat162 *xh = reinterpret_cast<const __nv_bfloat162 *>(&xm);
+        uint4 o;
+        unsigned *ow = &o.x;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float2 xv = __bfloat1622float2(xh[q]);
+            const __nv_bfloat162 h =
+                __floats2bfloat162_rn(xv.x > 0.0f ? v[2 * q] : 0.0f, xv.y > 0.0f ? v[2 * q + 1] : 0.0f);
+            ow[q] = *reinterpret_cast<const unsigned *>(&h);
+        }
+        reinterpret_cast<uint4 *>(dy4)[i] = o;
     }
 }
 
-// Column sums of dy [M, N] (BF16) added to db [N] (FP32).
-__global__ void bias_grad_kernel(const __nv_bfloat16 *__restrict__ dy, int M, int N, float *db) {
-    for (int col = threadIdx.x; col < N; col += blockDim.x) {
-        float s = 0.0f;
-        for (int m = blockIdx.x; m < M; m += gridDim.x) s += __bfloat162float(dy[(long long)m * N + col]);
-        atomicAdd(db + col, s);
+// Column sums of dy [P][N] (BF16, N in {32, 64, 128}) added to db [N] (FP32): each thread streams 16-byte
+// chunks of one column group, the block folds its partial sums in shared memory and adds them with one
+// atomic per column.
+__global__ void __launch_bounds__(256) bias_grad_kernel(const __nv_bfloat16 *__restrict__ dy, int P, int N, float *db) {
+    __shared__ float part[128];
+    const int cpr = N >> 3, rpp = 256 / cpr;  // chunks per row, rows per pass
+    const int c = threadIdx.x % cpr, r = threadIdx.x / cpr;
+    for (int n = threadIdx.x; n < N; n += blockDim.x) part[n] = 0.0f;
+    __syncthreads();
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const long long stride = (long long)gridDim.x * rpp;
+#pragma unroll 4
+    for (long long p = (long long)blockIdx.x * rpp + r; p < P; p += stride) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(dy + p * N) + c);
+        const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&v);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float2 f = __bfloat1622float2(h[q]);
+            acc[2 * q] += f.x;
+            acc[2 * q + 1] += f.y;
+        }
     }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) atomicAdd(&part[c * 8 + q], acc[q]);
+    __syncthreads();
+    for (int n = threadIdx.x; n < N; n += blockDim.x) atomicAdd(db + n, part[n]);
 }
 
 // FP32 master conv weights [N][K] -> the BF16 copy the GEMMs read.
@@ -495,7 +575,7 @@ struct CnnWs {
     __nv_bfloat16 *wb[4];
     __nv_bfloat16 *act[4];  // outputs of the four conv layers
     __nv_bfloat16 *dy[4];
-    float *dcols, *g, *out;
+    float *dcols, *g, *dg, *out;
     int *err;               // nonzero once a tensor-core wait gave up
 };
 
@@ -526,11 +606,13 @@ static size_t cnn_ws_layout(int B, CnnWs *w, char *base) {
     }
     void *dc = take(max_dcols * 4);
     void *g = take((size_t)B * 128 * 4);
+    void *dg = take((size_t)B * 128 * 4);
     void *out = take((size_t)B * 6 * 4);
     void *err = take(256);
     if (w) {
         w->dcols = reinterpret_cast<float *>(dc);
         w->g = reinterpret_cast<float *>(g);
+        w->dg = reinterpret_cast<float *>(dg);
         w->out = reinterpret_cast<float *>(out);
         w->err = reinterpret_cast<int *>(err);
     }
@@ -657,8 +739,11 @@ extern "C" upslam_status upslam_cnn_backward(const float *d_params, const void *
         cudaMemsetAsync(d_loss, 0, sizeof(float), s) != cudaSuccess)
         return UPSLAM_ERR_CUDA;
     // head: loss, d wf, d bf, and the gradient entering the last feature map (masked by its ReLU)
-    head_backward_kernel<<<batch, 128, 0, s>>>(d_out, d_target, d_wloss6, batch, w.g, d_params + L.off_wf, w.act[3],
-                                               4 * 16, 128, d_grads + L.off_wf, d_grads + L.off_bf, w.dy[3], d_loss);
+    head_backward_kernel<<<(batch + kHeadB - 1) / kHeadB, 128, 0, s>>>(d_out, d_target, d_wloss6, batch, w.g,
+                                                                       d_params + L.off_wf, 4 * 16,
+                                                                       d_grads + L.off_wf, d_grads + L.off_bf, w.dg,
+                                                                       d_loss);
+    head_dy_kernel<<<grid1d((long long)batch * 64 * 16), 256, 0, s>>>(w.dg, w.act[3], batch, 4 * 16, w.dy[3]);
     const int sms = upslam_sm_count();
     for (int l = 3; l >= 0; --l) {
         const int C = kCnnCh[l], N = cnn_co(l), K = cnn_k(l);
@@ -684,7 +769,7 @@ extern "C" upslam_status upslam_cnn_backward(const float *d_params, const void *
         if (N == 32) gemm<EPI_F32_RED_T, 32, LD_IM2COL_MN, LD_DENSE_MN>(gw, w.err, s, splits);
         else if (N == 64) gemm<EPI_F32_RED_T, 64, LD_IM2COL_MN, LD_DENSE_MN>(gw, w.err, s, splits);
         else gemm<EPI_F32_RED_T, 128, LD_IM2COL_MN, LD_DENSE_MN>(gw, w.err, s, splits);
-        bias_grad_kernel<<<sms * 2, 128, 0, s>>>(w.dy[l], P, N, d_grads + L.off_b[l]);
+        bias_grad_kernel<<<sms * 2, 256, 0, s>>>(w.dy[l], P, N, d_grads + L.off_b[l]);
         if (l > 0) {
             // dcols[p][f] = sum_n dY[p][n] W[n][f] (W read MN-major), then col2im with the input's ReLU mask
             TcGemm gd;
@@ -697,8 +782,8 @@ extern "C" upslam_status upslam_cnn_backward(const float *d_params, const void *
             gd.ldc = K;
             gd.bias = nullptr;
             gemm<EPI_F32, 128, LD_DENSE_K, LD_DENSE_MN>(gd, w.err, s);
-            col2im_mask_kernel<<<grid1d((long long)batch * H * W * C), 256, 0, s>>>(w.dcols, batch, H, W, C, K,
-                                                                                    w.act[l - 1], w.dy[l - 1]);
+            col2im_mask_kernel<<<grid1d((long long)batch * H * W * C / 8), 256, 0, s>>>(
+                w.dcols, batch, ilog2(H), ilog2(W), ilog2(C), K, w.act[l - 1], w.dy[l - 1]);
         }
     }
     UPSLAM_CHECK_LAUNCH();
