@@ -13,7 +13,9 @@
 // activation while it is staged, so no column matrix is ever stored:
 //   forward  Y[p, n]  = sum_f cols(p, f) W[n, f]        (+ bias, ReLU, BF16 out)
 //   dW[n, f]         += sum_p cols(p, f) dY[p, n]       (split over p, FP32 red)
-//   dcols[p, f]       = sum_n dY[p, n] W[n, f]  -> col2im -> x ReLU mask
+//   dX[p', c]         = (x > 0) sum over the taps t that read input pixel p'
+//                       of sum_n dY[p_t, n] W[n, t C + c]  (one GEMM per parity
+//                       class of p', ReLU mask and BF16 store in the epilogue)
 // All three run on one persistent kernel on the fifth-generation tensor cores
 // (tcgen05.mma, FP32 accumulators in tensor memory); see gemm_tc_kernel.
 // Parameters live as one FP32 master array (w0 b0 w1 b1 w2 b2 w3 b3 wf bf,
@@ -58,14 +60,14 @@ __host__ __device__ constexpr int cnn_co(int l) { return l == 0 ? 32 : (l == 1 ?
 //           x[b][2oy+ky-1][2ox+kx-1][ci..ci+7], zero outside the image.
 // Every wait is bounded; a wait that gives up sets *err and the CTA stops.
 
-enum { EPI_BIAS_RELU_BF16 = 0, EPI_F32 = 1, EPI_F32_RED_T = 2 };
-enum { LD_DENSE_K = 0, LD_IM2COL_K = 1, LD_DENSE_MN = 2, LD_IM2COL_MN = 3 };
+enum { EPI_BIAS_RELU_BF16 = 0, EPI_F32_RED_T = 1, EPI_DGRAD_MASK_BF16 = 2 };
+enum { LD_DENSE_K = 0, LD_IM2COL_K = 1, LD_DENSE_MN = 2, LD_IM2COL_MN = 3, LD_DY_TAPS_K = 4, LD_W_TAPS_MN = 5 };
 
 struct TcOperand {
     const __nv_bfloat16 *p;
-    long long ld;    // dense: elements between consecutive a
+    long long ld;    // dense and LD_W_TAPS_MN: elements between consecutive a
     int rows;        // extent along M (operand A) or N (operand B)
-    int hs, ws, cs;  // im2col: log2 of the input's H, W, C
+    int hs, ws, cs;  // im2col: log2 of the input's H, W, C; LD_DY_TAPS_K: log2 of dY's H, W, C
 };
 
 struct TcGemm {
@@ -76,6 +78,7 @@ struct TcGemm {
     void *C;
     long long ldc;    // EPI_F32_RED_T: C[n * ldc + m]; otherwise C[m * ldc + n]
     const float *bias;
+    const __nv_bfloat16 *mask;  // EPI_DGRAD_MASK_BF16: the layer input, whose ReLU masks dX
 };
 
 constexpr int kTcBM = 128, kTcBK = 64;
@@ -117,9 +120,22 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // or a row >= o.rows.  A warp takes 8 consecutive a by 4 consecutive f chunks: the 8 a land in the 8
 // distinct 16-byte rows of a core matrix (no shared-memory bank conflict) and the 4 chunks of one a are
 // contiguous in a dense source.
+// The data gradient of a 3x3 stride-2 pad-1 convolution, without the column matrix: an input pixel
+// (y, x) = (2i + py, 2j + px) is read by the taps ky = 1 (py = 0) or ky in {0, 2} (py = 1), and likewise kx,
+// from output pixel ((y + 1 - ky) / 2, (x + 1 - kx) / 2).  Parity class q = 2 py + px has
+// taps(q) = (1 + py)(1 + px) taps; its GEMM runs over i, j (M = B H/2 W/2) with k = t N + n (tap t of the
+// class, output channel n):  dX(y, x, c) = sum_k dY(oy_t, ox_t, n) W[n][(3 ky_t + kx_t) C + c].
+__device__ __forceinline__ int class_taps(int q) { return (1 + (q >> 1)) * (1 + (q & 1)); }
+__device__ __forceinline__ void class_tap(int q, int t, int &ky, int &kx) {
+    const int py = q >> 1, px = q & 1;
+    const int ty = px ? (t >> 1) : t, tx = px ? (t & 1) : 0;
+    ky = py ? 2 * ty : 1;
+    kx = px ? 2 * tx : 1;
+}
+
 template <int LD, int R>
-__device__ __forceinline__ void tc_load(unsigned tile, const TcOperand &o, int r0, int k0, int kend) {
-    constexpr bool MN = LD == LD_DENSE_MN || LD == LD_IM2COL_MN;
+__device__ __forceinline__ void tc_load(unsigned tile, const TcOperand &o, int r0, int k0, int kend, int cls) {
+    constexpr bool MN = LD == LD_DENSE_MN || LD == LD_IM2COL_MN || LD == LD_W_TAPS_MN;
     constexpr bool IM = LD == LD_IM2COL_K || LD == LD_IM2COL_MN;
     constexpr int NA8 = MN ? kTcBK / 8 : R / 8;  // groups of 8 along a
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -148,6 +164,19 @@ __device__ __forceinline__ void tc_load(unsigned tile, const TcOperand &o, int r
             const int y = 2 * oy + ky - 1, x = 2 * ox + kx - 1;
             ok = ok && (unsigned)y < (1u << o.hs) && (unsigned)x < (1u << o.ws);
             if (ok) src = o.p + ((((((long long)b << o.hs) + y) << o.ws) + x) << o.cs) + ci;
+        } else if (LD == LD_DY_TAPS_K) {
+            // a: input pixel (b, i, j) of class cls; f = t N + n
+            int ky, kx;
+            class_tap(cls, f >> o.cs, ky, kx);
+            const int j2 = a & ((1 << o.ws) - 1), i2 = (a >> o.ws) & ((1 << o.hs) - 1), b = a >> (o.ws + o.hs);
+            const int oy = (2 * i2 + (cls >> 1) + 1 - ky) >> 1, ox = (2 * j2 + (cls & 1) + 1 - kx) >> 1;
+            ok = ok && oy < (1 << o.hs) && ox < (1 << o.ws);
+            if (ok) src = o.p + ((((((long long)b << o.hs) + oy) << o.ws) + ox) << o.cs) + (f & ((1 << o.cs) - 1));
+        } else if (LD == LD_W_TAPS_MN) {
+            // a = t N + n (o.cs = log2 N), f = input channel c (o.rows = C)
+            int ky, kx;
+            class_tap(cls, a >> o.cs, ky, kx);
+            if (ok) src = o.p + (long long)(a & ((1 << o.cs) - 1)) * o.ld + (3 * ky + kx) * o.rows + f;
         } else if (ok) {
             src = o.p + (long long)a * o.ld + f;
         }
@@ -156,14 +185,30 @@ __device__ __forceinline__ void tc_load(unsigned tile, const TcOperand &o, int r
     }
 }
 
-template <int BN>
-__device__ __forceinline__ void tc_unit(const TcGemm &g, int u, int &r0a, int &r0b, int &kbeg, int &kend, int &nkt) {
-    const int nt = u % g.nt, rest = u / g.nt;
-    r0a = (rest % g.mt) * kTcBM;
-    r0b = nt * BN;
-    kbeg = (rest / g.mt) * g.k_split;
-    kend = min(g.K, kbeg + g.k_split);
-    nkt = (kend - kbeg + kTcBK - 1) / kTcBK;
+struct TcUnit {
+    int r0a, r0b, kbeg, kend, nkt, cls;
+};
+
+// Unit u: output tile (and class, for the data gradient) and its slice of K.
+template <int EPI, int BN>
+__device__ __forceinline__ TcUnit tc_unit(const TcGemm &g, int u) {
+    TcUnit t;
+    if (EPI == EPI_DGRAD_MASK_BF16) {
+        t.cls = u / g.mt;  // class-major: a CTA's units mix the classes
+        t.r0a = (u % g.mt) * kTcBM;
+        t.r0b = 0;
+        t.kbeg = 0;
+        t.kend = class_taps(t.cls) * g.K;
+    } else {
+        const int nt = u % g.nt, rest = u / g.nt;
+        t.cls = 0;
+        t.r0a = (rest % g.mt) * kTcBM;
+        t.r0b = nt * BN;
+        t.kbeg = (rest / g.mt) * g.k_split;
+        t.kend = min(g.K, t.kbeg + g.k_split);
+    }
+    t.nkt = (t.kend - t.kbeg + kTcBK - 1) / kTcBK;
+    return t;
 }
 
 template <int BN>
@@ -176,7 +221,7 @@ __global__ void __launch_bounds__(128, 2) gemm_tc_kernel(TcGemm g, int *err) {
     constexpr int S = tc_stages<BN>();
     constexpr int kA = kTcBM * kTcBK * 2, kStage = (kTcBM + BN) * kTcBK * 2;
     constexpr bool A_MN = LA == LD_DENSE_MN || LA == LD_IM2COL_MN;
-    constexpr bool B_MN = LB == LD_DENSE_MN || LB == LD_IM2COL_MN;
+    constexpr bool B_MN = LB == LD_DENSE_MN || LB == LD_IM2COL_MN || LB == LD_W_TAPS_MN;
     extern __shared__ __align__(1024) unsigned char tc_smem[];
     __shared__ __align__(8) unsigned long long mbar[S];
     __shared__ unsigned tmem_base;
@@ -204,12 +249,11 @@ __global__ void __launch_bounds__(128, 2) gemm_tc_kernel(TcGemm g, int *err) {
     int pu = blockIdx.x, pk = 0;
     auto produce = [&](int stage) {
         if (pu < g.units) {
-            int r0a, r0b, kbeg, kend, nkt;
-            tc_unit<BN>(g, pu, r0a, r0b, kbeg, kend, nkt);
-            const int k0 = kbeg + pk * kTcBK;
-            tc_load<LA, kTcBM>(smem0 + stage * kStage, g.a, r0a, k0, kend);
-            tc_load<LB, BN>(smem0 + stage * kStage + kA, g.b, r0b, k0, kend);
-            if (++pk == nkt) {
+            const TcUnit t = tc_unit<EPI, BN>(g, pu);
+            const int k0 = t.kbeg + pk * kTcBK;
+            tc_load<LA, kTcBM>(smem0 + stage * kStage, g.a, t.r0a, k0, t.kend, t.cls);
+            tc_load<LB, BN>(smem0 + stage * kStage + kA, g.b, t.r0b, k0, t.kend, t.cls);
+            if (++pk == t.nkt) {
                 pk = 0;
                 pu += gridDim.x;
             }
@@ -223,8 +267,8 @@ __global__ void __launch_bounds__(128, 2) gemm_tc_kernel(TcGemm g, int *err) {
     int s = 0;  // consumer step
     int last_commit = -1;
     for (int cu = blockIdx.x; cu < g.units; cu += gridDim.x) {
-        int r0a, r0b, kbeg, kend, nkt;
-        tc_unit<BN>(g, cu, r0a, r0b, kbeg, kend, nkt);
+        const TcUnit cur = tc_unit<EPI, BN>(g, cu);
+        const int r0a = cur.r0a, r0b = cur.r0b, kbeg = cur.kbeg, kend = cur.kend, nkt = cur.nkt;
         for (int ck = 0; ck < nkt; ++ck, ++s) {
             const int st = s % S;
             cp_async_wait<S - 2>();
@@ -287,13 +331,29 @@ __global__ void __launch_bounds__(128, 2) gemm_tc_kernel(TcGemm g, int *err) {
                                     }
                                     *reinterpret_cast<uint4 *>(reinterpret_cast<__nv_bfloat16 *>(g.C) +
                                                                (long long)m * g.ldc + n) = o;
-                                } else if (EPI == EPI_F32) {
-                                    float4 *o = reinterpret_cast<float4 *>(reinterpret_cast<float *>(g.C) +
-                                                                           (long long)m * g.ldc + n);
-                                    o[0] = make_float4(__uint_as_float(w[0]), __uint_as_float(w[1]),
-                                                       __uint_as_float(w[2]), __uint_as_float(w[3]));
-                                    o[1] = make_float4(__uint_as_float(w[4]), __uint_as_float(w[5]),
-                                                       __uint_as_float(w[6]), __uint_as_float(w[7]));
+                                } else if (EPI == EPI_DGRAD_MASK_BF16) {
+                                    // row m = (b, i, j) of class cur.cls -> input pixel (b, 2i + py, 2j + px)
+                                    const int hs = g.a.hs, ws = g.a.ws;
+                                    const int j2 = m & ((1 << ws) - 1), i2 = (m >> ws) & ((1 << hs) - 1);
+                                    const int b = m >> (ws + hs);
+                                    const long long pix =
+                                        ((((long long)b << (hs + 1)) + 2 * i2 + (cur.cls >> 1)) << (ws + 1)) + 2 * j2 +
+                                        (cur.cls & 1);
+                                    const uint4 xm =
+                                        __ldg(reinterpret_cast<const uint4 *>(g.mask + pix * g.ldc + n));
+                                    const __nv_bfloat162 *xh = reinterpret_cast<const __nv_bfloat162 *>(&xm);
+                                    uint4 o;
+                                    unsigned *ow = &o.x;
+#pragma unroll
+                                    for (int jj = 0; jj < 4; ++jj) {
+                                        const float2 xv = __bfloat1622float2(xh[jj]);
+                                        const __nv_bfloat162 h = __floats2bfloat162_rn(
+                                            xv.x > 0.0f ? __uint_as_float(w[2 * jj]) : 0.0f,
+                                            xv.y > 0.0f ? __uint_as_float(w[2 * jj + 1]) : 0.0f);
+                                        ow[jj] = *reinterpret_cast<const unsigned *>(&h);
+                                    }
+                                    *reinterpret_cast<uint4 *>(reinterpret_cast<__nv_bfloat16 *>(g.C) + pix * g.ldc +
+                                                               n) = o;
                                 } else {
 #pragma unroll
                                     for (int jj = 0; jj < 8; ++jj)
@@ -328,56 +388,6 @@ done:
 }
 
 // ----------------------------------------------------------------------------- layout kernels
-
-// Adjoint of im2col followed by the ReLU mask of the layer's input (activation > 0), 8 channels per thread:
-// dy_in[b,y,x,c] = (x_in > 0) * sum over the (output pixel, tap) pairs that read (y, x) of dcols.
-// H = 2^hs, W = 2^ws, C = 2^cs (C >= 8); dcols rows are ldk floats (a multiple of 8).
-__global__ void __launch_bounds__(256) col2im_mask_kernel(const float *__restrict__ dcols, int B, int hs, int ws,
-                                                          int cs, int ldk, const __nv_bfloat16 *__restrict__ x_in,
-                                                          __nv_bfloat16 *__restrict__ dy_in) {
-    const int Ho = 1 << (hs - 1), Wo = 1 << (ws - 1), C = 1 << cs;
-    const int total = (B << (hs + ws)) << (cs - 3);
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
-        const int c = (i & ((1 << (cs - 3)) - 1)) << 3;
-        const int pix = i >> (cs - 3);
-        const int x = pix & ((1 << ws) - 1), y = (pix >> ws) & ((1 << hs) - 1), b = pix >> (hs + ws);
-        const uint4 xm = __ldg(reinterpret_cast<const uint4 *>(x_in + ((long long)pix << cs) + c));
-        float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-        for (int ky = 0; ky < 3; ++ky) {
-            const int t = y + 1 - ky;
-            if (t < 0 || (t & 1) || (t >> 1) >= Ho) continue;
-#pragma unroll
-            for (int kx = 0; kx < 3; ++kx) {
-                const int u = x + 1 - kx;
-                if (u < 0 || (u & 1) || (u >> 1) >= Wo) continue;
-                const int m = ((b * Ho + (t >> 1)) * Wo) + (u >> 1);
-                const float4 *src =
-                    reinterpret_cast<const float4 *>(dcols + (long long)m * ldk + (ky * 3 + kx) * C + c);
-                const float4 lo = __ldcs(src), hi = __ldcs(src + 1);
-                acc[0] += lo.x;
-                acc[1] += lo.y;
-                acc[2] += lo.z;
-                acc[3] += lo.w;
-                acc[4] += hi.x;
-                acc[5] += hi.y;
-                acc[6] += hi.z;
-                acc[7] += hi.w;
-            }
-        }
-        const __nv_bfloat162 *xh = reinterpret_cast<const __nv_bfloat162 *>(&xm);
-        uint4 o;
-        unsigned *ow = &o.x;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const float2 xv = __bfloat1622float2(xh[q]);
-            const __nv_bfloat162 h =
-                __floats2bfloat162_rn(xv.x > 0.0f ? acc[2 * q] : 0.0f, xv.y > 0.0f ? acc[2 * q + 1] : 0.0f);
-            ow[q] = *reinterpret_cast<const unsigned *>(&h);
-        }
-        *reinterpret_cast<uint4 *>(dy_in + ((long long)pix << cs) + c) = o;
-    }
-}
 
 // Global mean over [B, HW, C] (BF16) -> g [B, C] (FP32), then the linear head out = g W^T + b.
 __global__ void pool_head_kernel(const __nv_bfloat16 *__restrict__ x, int B, int HW, int C, const float *wf,
@@ -575,7 +585,7 @@ struct CnnWs {
     __nv_bfloat16 *wb[4];
     __nv_bfloat16 *act[4];  // outputs of the four conv layers
     __nv_bfloat16 *dy[4];
-    float *dcols, *g, *dg, *out;
+    float *g, *dg, *out;
     int *err;               // nonzero once a tensor-core wait gave up
 };
 
@@ -589,7 +599,6 @@ static size_t cnn_ws_layout(int B, CnnWs *w, char *base) {
         return p;
     };
     int H = kCnnH, W = kCnnW;
-    size_t max_dcols = 0;
     for (int l = 0; l < 4; ++l) {
         const size_t M = (size_t)B * (H / 2) * (W / 2);
         void *wb = take((size_t)cnn_co(l) * cnn_k(l) * 2);
@@ -600,17 +609,14 @@ static size_t cnn_ws_layout(int B, CnnWs *w, char *base) {
             w->act[l] = reinterpret_cast<__nv_bfloat16 *>(a);
             w->dy[l] = reinterpret_cast<__nv_bfloat16 *>(d);
         }
-        if (l > 0) max_dcols = max_dcols > M * cnn_k(l) ? max_dcols : M * cnn_k(l);
         H /= 2;
         W /= 2;
     }
-    void *dc = take(max_dcols * 4);
     void *g = take((size_t)B * 128 * 4);
     void *dg = take((size_t)B * 128 * 4);
     void *out = take((size_t)B * 6 * 4);
     void *err = take(256);
     if (w) {
-        w->dcols = reinterpret_cast<float *>(dc);
         w->g = reinterpret_cast<float *>(g);
         w->dg = reinterpret_cast<float *>(dg);
         w->out = reinterpret_cast<float *>(out);
@@ -667,7 +673,7 @@ static void gemm(TcGemm g, int *err, cudaStream_t s, int splits = 1) {
     const int z = (g.K + g.k_split - 1) / g.k_split;
     g.mt = (g.M + kTcBM - 1) / kTcBM;
     g.nt = (g.N + BN - 1) / BN;
-    g.units = g.mt * g.nt * z;
+    g.units = EPI == EPI_DGRAD_MASK_BF16 ? 4 * g.mt : g.mt * g.nt * z;  // four parity classes
     const int cap = 2 * upslam_sm_count();  // two CTAs per SM by shared memory
     gemm_tc_kernel<EPI, BN, LA, LB><<<g.units < cap ? g.units : cap, 128, smem, s>>>(g, err);
 }
@@ -771,19 +777,24 @@ extern "C" upslam_status upslam_cnn_backward(const float *d_params, const void *
         else gemm<EPI_F32_RED_T, 128, LD_IM2COL_MN, LD_DENSE_MN>(gw, w.err, s, splits);
         bias_grad_kernel<<<sms * 2, 256, 0, s>>>(w.dy[l], P, N, d_grads + L.off_b[l]);
         if (l > 0) {
-            // dcols[p][f] = sum_n dY[p][n] W[n][f] (W read MN-major), then col2im with the input's ReLU mask
-            TcGemm gd;
+            // dY of the layer below = its ReLU mask x sum over the taps that read each input pixel of dY W,
+            // one GEMM per parity class of the input pixels (no column matrix)
+            TcGemm gd{};
             gd.a = op_dense(w.dy[l], N);
+            gd.a.hs = ilog2(H / 2);
+            gd.a.ws = ilog2(W / 2);
+            gd.a.cs = ilog2(N);
             gd.b = op_dense(w.wb[l], K);
+            gd.b.cs = ilog2(N);
             gd.M = P;
-            gd.N = K;
-            gd.K = N;
-            gd.C = w.dcols;
-            gd.ldc = K;
-            gd.bias = nullptr;
-            gemm<EPI_F32, 128, LD_DENSE_K, LD_DENSE_MN>(gd, w.err, s);
-            col2im_mask_kernel<<<grid1d((long long)batch * H * W * C / 8), 256, 0, s>>>(
-                w.dcols, batch, ilog2(H), ilog2(W), ilog2(C), K, w.act[l - 1], w.dy[l - 1]);
+            gd.N = C;
+            gd.K = N;  // per tap
+            gd.C = w.dy[l - 1];
+            gd.ldc = C;
+            gd.mask = w.act[l - 1];
+            if (C == 32) gemm<EPI_DGRAD_MASK_BF16, 32, LD_DY_TAPS_K, LD_W_TAPS_MN>(gd, w.err, s);
+            else if (C == 64) gemm<EPI_DGRAD_MASK_BF16, 64, LD_DY_TAPS_K, LD_W_TAPS_MN>(gd, w.err, s);
+            else gemm<EPI_DGRAD_MASK_BF16, 128, LD_DY_TAPS_K, LD_W_TAPS_MN>(gd, w.err, s);
         }
     }
     UPSLAM_CHECK_LAUNCH();
