@@ -795,7 +795,8 @@ def run_learned(args, local):
             "plain_pairs_per_s": round(res["plain_pairs_per_s"], 1),
             "gated_pairs_per_s": round(res["gated_pairs_per_s"], 1), "cnn_ms_per_pair": res["cnn_ms_per_pair"],
             "train": {"pairs": args.train_pairs, "epochs": args.epochs, "batch": net.batch, "loss": hist,
-                      "seconds": round(t_train, 2), "pairs_per_s": round(pairs_trained / t_train, 1),
+                      "seconds": round(t_train, 2), "ms_per_step": round(t_train * 1e3 / max(1, steps), 3),
+                      "pairs_per_s": round(pairs_trained / t_train, 1),
                       "tflops": round(flops / t_train / 1e12, 2),
                       "frac_of_bf16_peak": round(flops / t_train / 1e12 / peak, 5),
                       "pair_generation_s": round(t_gen, 1)},

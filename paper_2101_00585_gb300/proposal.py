@@ -269,22 +269,53 @@ def make_pairs(n_pairs: int, seed: int, device="cuda", keep_scans: bool = False,
 
 
 def train(net: PoseNet, x: torch.Tensor, xi: torch.Tensor, epochs: int = 3, lr: float = 1e-3, seed: int = 0,
-          log=None) -> list:
-    """Mini-batch Adam over (x, xi); the learning rate decays by 10x over the run.  Returns per-epoch mean losses."""
+          log=None, graph: bool = True) -> list:
+    """Mini-batch Adam over (x, xi); the learning rate decays by 10x over the run.  Returns per-epoch mean losses.
+
+    With graph=True the mini-batch gather, forward and backward of a step are captured once as a CUDA graph and
+    replayed (the batch indices live in a fixed device buffer); Adam, whose learning rate and bias corrections
+    change every step, is launched eagerly after each replay.
+    """
     n = x.shape[0]
     B = net.batch
     g = torch.Generator(device=x.device).manual_seed(seed)
     steps = epochs * (n // B)
+    idx = torch.zeros(B, dtype=torch.long, device=x.device)
+    xb = torch.empty((B,) + tuple(x.shape[1:]), dtype=x.dtype, device=x.device)
+    tb = torch.empty((B, 6), dtype=torch.float32, device=x.device)
+    xi32 = xi.to(torch.float32).contiguous()
+
+    def body():
+        torch.index_select(x, 0, idx, out=xb)
+        torch.index_select(xi32, 0, idx, out=tb)
+        net.forward(xb)
+        net.backward(xb, tb)
+
+    cg = None
+    if graph and steps > 0:
+        s = torch.cuda.Stream(device=x.device)
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            body()  # first launches (kernel attributes, module loading) outside the capture
+            cg = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(cg, stream=s):
+                body()
+        torch.cuda.current_stream().wait_stream(s)
     hist = []
-    s = 0
+    st = 0
     for ep in range(epochs):
         perm = torch.randperm(n, generator=g, device=x.device)
         tot = torch.zeros((), device=x.device)
         for b in range(n // B):
-            idx = perm[b * B:(b + 1) * B]
-            rate = lr * (0.1 ** (s / max(1, steps)))
-            tot += net.train_step(x[idx].contiguous(), xi[idx], rate)[0]
-            s += 1
+            idx.copy_(perm[b * B:(b + 1) * B])
+            rate = lr * (0.1 ** (st / max(1, steps)))
+            if cg is not None:
+                cg.replay()
+            else:
+                body()
+            net.adam(rate)
+            tot += net.loss[0]
+            st += 1
         hist.append(float(tot) / max(1, n // B))
         net.check()
         if log:

@@ -133,3 +133,23 @@ def test_learned_proposal_gains_over_plain_init():
     res = proposal.evaluate(net, xt, ext["motions"], ext["scans"])
     print("\nlearned proposal:", res, "train loss", [round(h, 4) for h in hist])
     assert res["gated_success"] > res["plain_success"]
+
+
+def test_train_graph_replay_matches_eager():
+    """The captured step (gather, forward, backward replayed as one CUDA graph, Adam eager) trains like the eager
+    step.  The weight gradients are FP32 atomic sums, whose order varies, so the runs agree to rounding."""
+    rng = np.random.default_rng(21)
+    n, B = 384, 64
+    x = torch.from_numpy((rng.uniform(-1, 1, (n, 64, 256, 8)) * (rng.random((n, 64, 256, 1)) < 0.7))
+                         .astype(np.float32)).to(torch.bfloat16).cuda()
+    xi = torch.from_numpy(rng.standard_normal((n, 6)) * 0.3).cuda()
+    flat = torch.from_numpy(ocnn.flatten(_flat_params(22)))
+    nets, hists = [], []
+    for graph in (False, True):
+        net = proposal.PoseNet(B, params=flat)
+        hists.append(proposal.train(net, x, xi, epochs=2, lr=2e-3, seed=23, graph=graph))
+        nets.append(net)
+    assert np.allclose(hists[0], hists[1], rtol=1e-3), hists
+    a, b = nets[0].params.cpu().numpy(), nets[1].params.cpu().numpy()
+    assert np.linalg.norm(a - b) <= 1e-3 * np.linalg.norm(a)
+    assert nets[1].step == 2 * (n // B)
