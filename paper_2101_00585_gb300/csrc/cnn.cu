@@ -92,19 +92,6 @@ __device__ __forceinline__ unsigned long long umma_desc(unsigned addr, unsigned 
            ((unsigned long long)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
-__device__ __forceinline__ bool mbar_wait(unsigned mbar, unsigned parity) {
-    for (unsigned it = 0; it < kTcWaitIters; ++it) {
-        unsigned done;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done)
-            : "r"(mbar), "r"(parity)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
-}
-
 template <bool L1>
 __device__ __forceinline__ void cp_async16(unsigned dst, const void *src, bool ok) {
     if (L1)
@@ -134,11 +121,12 @@ __device__ __forceinline__ void class_tap(int q, int t, int &ky, int &kx) {
 }
 
 template <int LD, int R>
-__device__ __forceinline__ void tc_load(unsigned tile, const TcOperand &o, int r0, int k0, int kend, int cls) {
+__device__ __forceinline__ void tc_load(unsigned tile, const TcOperand &o, int r0, int k0, int kend, int kread, int cls,
+                                        int ptid) {
     constexpr bool MN = LD == LD_DENSE_MN || LD == LD_IM2COL_MN || LD == LD_W_TAPS_MN;
     constexpr bool IM = LD == LD_IM2COL_K || LD == LD_IM2COL_MN;
     constexpr int NA8 = MN ? kTcBK / 8 : R / 8;  // groups of 8 along a
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = ptid & 31, warp = ptid >> 5;
 #pragma unroll
     for (int it = 0; it < R / 16; ++it) {
         const int q = it * 4 + warp;
@@ -155,6 +143,7 @@ __device__ __forceinline__ void tc_load(unsigned tile, const TcOperand &o, int r
             f = k0 + 8 * j;
             ok = a < o.rows && f < kend;
         }
+        if ((MN ? a : f) >= kread) continue;  // beyond the k the step's MMAs read: never touched
         const __nv_bfloat16 *src = o.p;
         if (IM) {
             const int wo = o.ws - 1, ho = o.hs - 1;
@@ -211,180 +200,283 @@ __device__ __forceinline__ TcUnit tc_unit(const TcGemm &g, int u) {
     return t;
 }
 
+// Stages that fit in about 100 KB of shared memory (two CTAs per SM), at most 8.
 template <int BN>
-constexpr int tc_stages() { return BN == 128 ? 3 : 4; }
+constexpr int tc_stages() {
+    return 102400 / ((kTcBM + BN) * kTcBK * 2) < 8 ? 102400 / ((kTcBM + BN) * kTcBK * 2) : 8;
+}
 template <int BN>
 constexpr int tc_smem_bytes() { return tc_stages<BN>() * (kTcBM + BN) * kTcBK * 2; }
 
+constexpr int kTcThreads = 288;  // warps 0-3 epilogue, 4-7 producers, 8 MMA issue
+
+struct TcSync {
+    unsigned long long full[8];   // producers -> MMA: a stage's copies landed (4 warp arrivals)
+    unsigned long long empty[8];  // MMA -> producers: the stage's MMAs are done (tcgen05.commit)
+    unsigned long long accf[2];   // MMA -> epilogue: an accumulator buffer holds a finished tile
+    unsigned long long acce[2];   // epilogue -> MMA: the buffer has been read (4 warp arrivals)
+    unsigned tmem_base;
+    int abort;
+};
+
+__device__ __forceinline__ void mbar_init(unsigned mbar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+__device__ __forceinline__ void tc_commit(unsigned mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
+}
+
+// Bounded wait for the phase of the given parity; gives up early once another role has aborted, and aborts
+// the CTA (error word set) when the bound runs out.
+__device__ __forceinline__ bool tc_wait(unsigned mbar, unsigned parity, volatile int *abort, int *err) {
+    for (unsigned it = 0; it < kTcWaitIters; ++it) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if ((it & 63) == 63 && *abort) return false;
+    }
+    *abort = 1;
+    atomicExch(err, 1);
+    return false;
+}
+
+// The epilogue of one 128 x BN tile from tensor-memory columns [acc, acc + BN): warp w owns rows 32w..32w+31.
+template <int EPI, int BN>
+__device__ __forceinline__ void tc_epilogue(const TcGemm &g, const TcUnit &cur, unsigned acc, int warp, int lane) {
+    const int m = cur.r0a + warp * 32 + lane;
+    long long pix = 0;
+    // the mask of up to 64 columns is loaded before the accumulator is read; wider tiles load the rest per group
+    constexpr int PF = EPI == EPI_DGRAD_MASK_BF16 ? (BN < 64 ? BN : 64) / 8 : 1;
+    uint4 xm[PF];
+    if (EPI == EPI_DGRAD_MASK_BF16) {
+        // row m = (b, i, j) of class cur.cls -> input pixel (b, 2i + py, 2j + px); its mask is loaded first
+        const int hs = g.a.hs, ws = g.a.ws;
+        const int j2 = m & ((1 << ws) - 1), i2 = (m >> ws) & ((1 << hs) - 1), b = m >> (ws + hs);
+        pix = ((((long long)b << (hs + 1)) + 2 * i2 + (cur.cls >> 1)) << (ws + 1)) + 2 * j2 + (cur.cls & 1);
+#pragma unroll
+        for (int q = 0; q < PF; ++q)
+            xm[q] = (m < g.M && cur.r0b + 8 * q < g.N)
+                        ? __ldg(reinterpret_cast<const uint4 *>(g.mask + pix * g.ldc + cur.r0b + 8 * q))
+                        : make_uint4(0, 0, 0, 0);
+    }
+    constexpr int CW = BN < 32 ? BN : 32;  // columns per tensor-memory wait
+#pragma unroll
+    for (int c0 = 0; c0 < BN; c0 += CW) {
+        unsigned v[CW];
+#pragma unroll
+        for (int q = 0; q < CW / 8; ++q)
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                : "=r"(v[8 * q]), "=r"(v[8 * q + 1]), "=r"(v[8 * q + 2]), "=r"(v[8 * q + 3]), "=r"(v[8 * q + 4]),
+                  "=r"(v[8 * q + 5]), "=r"(v[8 * q + 6]), "=r"(v[8 * q + 7])
+                : "r"(acc + ((unsigned)(warp * 32) << 16) + (unsigned)(c0 + 8 * q)));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (m >= g.M) continue;
+#pragma unroll
+        for (int q = 0; q < CW / 8; ++q) {
+            const int n = cur.r0b + c0 + 8 * q;
+            const unsigned *w = v + 8 * q;
+            if (n >= g.N) continue;
+            if (EPI == EPI_BIAS_RELU_BF16) {
+                uint4 o;
+                unsigned *ow = &o.x;
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) {
+                    const __nv_bfloat162 h = __floats2bfloat162_rn(
+                        fmaxf(__uint_as_float(w[2 * jj]) + __ldg(g.bias + n + 2 * jj), 0.0f),
+                        fmaxf(__uint_as_float(w[2 * jj + 1]) + __ldg(g.bias + n + 2 * jj + 1), 0.0f));
+                    ow[jj] = *reinterpret_cast<const unsigned *>(&h);
+                }
+                *reinterpret_cast<uint4 *>(reinterpret_cast<__nv_bfloat16 *>(g.C) + (long long)m * g.ldc + n) = o;
+            } else if (EPI == EPI_DGRAD_MASK_BF16) {
+                const uint4 mq = (c0 + 8 * q) / 8 < PF
+                                     ? xm[((c0 + 8 * q) / 8) % PF]
+                                     : __ldg(reinterpret_cast<const uint4 *>(g.mask + pix * g.ldc + n));
+                const __nv_bfloat162 *xh = reinterpret_cast<const __nv_bfloat162 *>(&mq);
+                uint4 o;
+                unsigned *ow = &o.x;
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) {
+                    const float2 xv = __bfloat1622float2(xh[jj]);
+                    const __nv_bfloat162 h =
+                        __floats2bfloat162_rn(xv.x > 0.0f ? __uint_as_float(w[2 * jj]) : 0.0f,
+                                              xv.y > 0.0f ? __uint_as_float(w[2 * jj + 1]) : 0.0f);
+                    ow[jj] = *reinterpret_cast<const unsigned *>(&h);
+                }
+                *reinterpret_cast<uint4 *>(reinterpret_cast<__nv_bfloat16 *>(g.C) + pix * g.ldc + n) = o;
+            } else {
+#pragma unroll
+                for (int jj = 0; jj < 8; ++jj)
+                    if (n + jj < g.N)
+                        atomicAdd(reinterpret_cast<float *>(g.C) + (long long)(n + jj) * g.ldc + m,
+                                  __uint_as_float(w[jj]));
+            }
+        }
+    }
+}
+
+// Warp-specialised persistent GEMM, one CTA per SM.  Producers (warps 4-7) fill the S-stage ring with
+// cp.async and, once a stage's copies have landed (cp.async.wait_group, then a proxy fence), arrive on its
+// full barrier; the MMA thread (warp 8, lane 0) waits for full, issues the stage's MMAs into one of two
+// tensor-memory accumulators and commits them to the stage's empty barrier, and after a unit's last step to
+// the accumulator's full barrier; the epilogue warps (0-3) drain one accumulator while the MMAs of the next
+// unit fill the other, then arrive on its empty barrier.
 template <int EPI, int BN, int LA, int LB>
-__global__ void __launch_bounds__(128, 2) gemm_tc_kernel(TcGemm g, int *err) {
+__global__ void __launch_bounds__(kTcThreads, 2) gemm_tc_kernel(TcGemm g, int *err) {
     constexpr int S = tc_stages<BN>();
+    // cp.async groups a producer keeps in flight before it signals a stage full: all but one stage, which
+    // still cannot deadlock (the stage refilled at step it was consumed at it - S, signalled at it - 1)
+    constexpr int kTcLag = S - 2;
+    static_assert(S >= 2 && S <= 8, "stage ring");
     constexpr int kA = kTcBM * kTcBK * 2, kStage = (kTcBM + BN) * kTcBK * 2;
     constexpr bool A_MN = LA == LD_DENSE_MN || LA == LD_IM2COL_MN;
     constexpr bool B_MN = LB == LD_DENSE_MN || LB == LD_IM2COL_MN || LB == LD_W_TAPS_MN;
     extern __shared__ __align__(1024) unsigned char tc_smem[];
-    __shared__ __align__(8) unsigned long long mbar[S];
-    __shared__ unsigned tmem_base;
+    __shared__ __align__(8) TcSync sy;
     const unsigned smem0 = smem_u32(tc_smem);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    volatile int *abort = &sy.abort;
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
-                     "r"(BN)
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sy.tmem_base)),
+                     "r"(2 * BN)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    if (threadIdx.x == 0) {
-        for (int i = 0; i < S; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[i])) : "memory");
+    if (threadIdx.x == 32) {
+        for (int i = 0; i < S; ++i) {
+            mbar_init(smem_u32(&sy.full[i]), 4);
+            mbar_init(smem_u32(&sy.empty[i]), 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(smem_u32(&sy.accf[i]), 1);
+            mbar_init(smem_u32(&sy.acce[i]), 4);
+        }
+        sy.abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const unsigned tmem = tmem_base;
-    // instruction descriptor: FP32 accumulator, BF16 A and B, majors, N = BN, M = 128
-    const unsigned idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((A_MN ? 1u : 0u) << 15) | ((B_MN ? 1u : 0u) << 16) |
-                           ((unsigned)(BN >> 3) << 17) | ((unsigned)(kTcBM >> 4) << 24);
+    const unsigned tmem = sy.tmem_base;
 
-    // producer cursor: unit pu, step pk inside it
-    int pu = blockIdx.x, pk = 0;
-    auto produce = [&](int stage) {
-        if (pu < g.units) {
-            const TcUnit t = tc_unit<EPI, BN>(g, pu);
-            const int k0 = t.kbeg + pk * kTcBK;
-            tc_load<LA, kTcBM>(smem0 + stage * kStage, g.a, t.r0a, k0, t.kend, t.cls);
-            tc_load<LB, BN>(smem0 + stage * kStage + kA, g.b, t.r0b, k0, t.kend, t.cls);
-            if (++pk == t.nkt) {
-                pk = 0;
-                pu += gridDim.x;
+    if (warp >= 4 && warp < 8) {
+        // ---- producers
+        const int ptid = threadIdx.x - 128;
+        int it = 0;
+        bool ok = true;
+        for (int u = blockIdx.x; ok && u < g.units; u += gridDim.x) {
+            const TcUnit t = tc_unit<EPI, BN>(g, u);
+            for (int k = 0; k < t.nkt; ++k, ++it) {
+                const int st = it % S;
+                if (it >= S && !tc_wait(smem_u32(&sy.empty[st]), (unsigned)(((it / S) - 1) & 1), abort, err)) {
+                    ok = false;
+                    break;
+                }
+                const int k0 = t.kbeg + k * kTcBK;
+                const int kread = k0 + 16 * min(kTcBK / 16, (t.kend - k0 + 15) / 16);
+                tc_load<LA, kTcBM>(smem0 + st * kStage, g.a, t.r0a, k0, t.kend, kread, t.cls, ptid);
+                tc_load<LB, BN>(smem0 + st * kStage + kA, g.b, t.r0b, k0, t.kend, kread, t.cls, ptid);
+                cp_async_commit();
+                if (it >= kTcLag) {
+                    cp_async_wait<kTcLag>();
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(smem_u32(&sy.full[(it - kTcLag) % S]));
+                }
             }
         }
-        cp_async_commit();
-    };
-#pragma unroll
-    for (int i = 0; i < S - 1; ++i) produce(i);
-
-    bool bad = false;
-    int s = 0;  // consumer step
-    int last_commit = -1;
-    for (int cu = blockIdx.x; cu < g.units; cu += gridDim.x) {
-        const TcUnit cur = tc_unit<EPI, BN>(g, cu);
-        const int r0a = cur.r0a, r0b = cur.r0b, kbeg = cur.kbeg, kend = cur.kend, nkt = cur.nkt;
-        for (int ck = 0; ck < nkt; ++ck, ++s) {
-            const int st = s % S;
-            cp_async_wait<S - 2>();
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            if (__syncthreads_or(bad)) goto done;
-            if (threadIdx.x == 0) {
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const unsigned a0 = smem0 + st * kStage, b0 = a0 + kA;
-                const int k0 = kbeg + ck * kTcBK;
-                const int nk = min(kTcBK / 16, (kend - k0 + 15) / 16);
-                for (int kk = 0; kk < nk; ++kk) {
-                    const unsigned long long ad = umma_desc(a0 + kk * 256, 128, 1024);
-                    const unsigned long long bd = umma_desc(b0 + kk * 256, 128, 1024);
-                    const unsigned acc = (ck > 0 || kk > 0) ? 1u : 0u;
-                    asm volatile(
-                        "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
-                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                        "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
-                        : "memory");
+        cp_async_wait<0>();
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (ok && lane == 0)
+            for (int j = it > kTcLag ? it - kTcLag : 0; j < it; ++j) mbar_arrive(smem_u32(&sy.full[j % S]));
+    } else if (warp == 8) {
+        // ---- MMA issue
+        if (lane == 0) {
+            // instruction descriptor: FP32 accumulator, BF16 A and B, majors, N = BN, M = 128
+            const unsigned idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((A_MN ? 1u : 0u) << 15) |
+                                   ((B_MN ? 1u : 0u) << 16) | ((unsigned)(BN >> 3) << 17) |
+                                   ((unsigned)(kTcBM >> 4) << 24);
+            int it = 0, uc = 0;
+            unsigned last_bar = 0, last_par = 0;
+            bool ok = true;
+            for (int u = blockIdx.x; ok && u < g.units; u += gridDim.x, ++uc) {
+                const TcUnit t = tc_unit<EPI, BN>(g, u);
+                const int b = uc & 1;
+                if (uc >= 2 && !tc_wait(smem_u32(&sy.acce[b]), (unsigned)(((uc >> 1) - 1) & 1), abort, err)) {
+                    ok = false;
+                    break;
                 }
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                                 smem_u32(&mbar[st]))
-                             : "memory");
-            }
-            last_commit = s;
-            if (ck + 1 == nkt) {
-                // the unit's last commit covers all its MMAs
-                bad = bad || !mbar_wait(smem_u32(&mbar[st]), (unsigned)((s / S) & 1));
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                if (!bad) {
-                    const int m = r0a + warp * 32 + lane;
-                    constexpr int CW = BN < 32 ? BN : 32;  // columns per tensor-memory wait
-#pragma unroll
-                    for (int c0 = 0; c0 < BN; c0 += CW) {
-                        unsigned v[CW];
-#pragma unroll
-                        for (int q = 0; q < CW / 8; ++q)
-                            asm volatile(
-                                "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-                                : "=r"(v[8 * q]), "=r"(v[8 * q + 1]), "=r"(v[8 * q + 2]), "=r"(v[8 * q + 3]),
-                                  "=r"(v[8 * q + 4]), "=r"(v[8 * q + 5]), "=r"(v[8 * q + 6]), "=r"(v[8 * q + 7])
-                                : "r"(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(c0 + 8 * q)));
-                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                        if (m < g.M) {
-#pragma unroll
-                            for (int q = 0; q < CW / 8; ++q) {
-                                const int n = r0b + c0 + 8 * q;
-                                const unsigned *w = v + 8 * q;
-                                if (n >= g.N) continue;
-                                if (EPI == EPI_BIAS_RELU_BF16) {
-                                    uint4 o;
-                                    unsigned *ow = &o.x;
-#pragma unroll
-                                    for (int jj = 0; jj < 4; ++jj) {
-                                        const __nv_bfloat162 h = __floats2bfloat162_rn(
-                                            fmaxf(__uint_as_float(w[2 * jj]) + __ldg(g.bias + n + 2 * jj), 0.0f),
-                                            fmaxf(__uint_as_float(w[2 * jj + 1]) + __ldg(g.bias + n + 2 * jj + 1),
-                                                  0.0f));
-                                        ow[jj] = *reinterpret_cast<const unsigned *>(&h);
-                                    }
-                                    *reinterpret_cast<uint4 *>(reinterpret_cast<__nv_bfloat16 *>(g.C) +
-                                                               (long long)m * g.ldc + n) = o;
-                                } else if (EPI == EPI_DGRAD_MASK_BF16) {
-                                    // row m = (b, i, j) of class cur.cls -> input pixel (b, 2i + py, 2j + px)
-                                    const int hs = g.a.hs, ws = g.a.ws;
-                                    const int j2 = m & ((1 << ws) - 1), i2 = (m >> ws) & ((1 << hs) - 1);
-                                    const int b = m >> (ws + hs);
-                                    const long long pix =
-                                        ((((long long)b << (hs + 1)) + 2 * i2 + (cur.cls >> 1)) << (ws + 1)) + 2 * j2 +
-                                        (cur.cls & 1);
-                                    const uint4 xm =
-                                        __ldg(reinterpret_cast<const uint4 *>(g.mask + pix * g.ldc + n));
-                                    const __nv_bfloat162 *xh = reinterpret_cast<const __nv_bfloat162 *>(&xm);
-                                    uint4 o;
-                                    unsigned *ow = &o.x;
-#pragma unroll
-                                    for (int jj = 0; jj < 4; ++jj) {
-                                        const float2 xv = __bfloat1622float2(xh[jj]);
-                                        const __nv_bfloat162 h = __floats2bfloat162_rn(
-                                            xv.x > 0.0f ? __uint_as_float(w[2 * jj]) : 0.0f,
-                                            xv.y > 0.0f ? __uint_as_float(w[2 * jj + 1]) : 0.0f);
-                                        ow[jj] = *reinterpret_cast<const unsigned *>(&h);
-                                    }
-                                    *reinterpret_cast<uint4 *>(reinterpret_cast<__nv_bfloat16 *>(g.C) + pix * g.ldc +
-                                                               n) = o;
-                                } else {
-#pragma unroll
-                                    for (int jj = 0; jj < 8; ++jj)
-                                        if (n + jj < g.N)
-                                            atomicAdd(reinterpret_cast<float *>(g.C) + (long long)(n + jj) * g.ldc + m,
-                                                      __uint_as_float(w[jj]));
-                                }
-                            }
-                        }
+                const unsigned acc = tmem + (unsigned)(b * BN);
+                for (int k = 0; k < t.nkt; ++k, ++it) {
+                    const int st = it % S;
+                    if (!tc_wait(smem_u32(&sy.full[st]), (unsigned)((it / S) & 1), abort, err)) {
+                        ok = false;
+                        break;
                     }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const unsigned a0 = smem0 + st * kStage, b0 = a0 + kA;
+                    const int k0 = t.kbeg + k * kTcBK;
+                    const int nk = min(kTcBK / 16, (t.kend - k0 + 15) / 16);
+                    for (int kk = 0; kk < nk; ++kk) {
+                        const unsigned long long ad = umma_desc(a0 + kk * 256, 128, 1024);
+                        const unsigned long long bd = umma_desc(b0 + kk * 256, 128, 1024);
+                        const unsigned accum = (k > 0 || kk > 0) ? 1u : 0u;
+                        asm volatile(
+                            "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(acc),
+                            "l"(ad), "l"(bd), "r"(idesc), "r"(accum)
+                            : "memory");
+                    }
+                    tc_commit(smem_u32(&sy.empty[st]));
+                    last_bar = smem_u32(&sy.empty[st]);
+                    last_par = (unsigned)((it / S) & 1);
                 }
-                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                if (!ok) break;
+                tc_commit(smem_u32(&sy.accf[b]));
             }
-            // refill the stage of step s - 1 (its MMAs must be done) with step s + S - 1
-            if (s >= 1 && !bad) bad = !mbar_wait(smem_u32(&mbar[(s - 1) % S]), (unsigned)(((s - 1) / S) & 1));
-            if (!bad) produce((s + S - 1) % S);
-            else cp_async_commit();
+            // after an abort, let the MMAs already issued finish before the accumulators are freed
+            if (!ok && last_bar) {
+                for (unsigned w = 0; w < kTcWaitIters; ++w) {
+                    unsigned done;
+                    asm volatile(
+                        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                        " selp.u32 %0, 1, 0, p;\n}\n"
+                        : "=r"(done)
+                        : "r"(last_bar), "r"(last_par)
+                        : "memory");
+                    if (done) break;
+                }
+            }
         }
-    }
-done:
-    cp_async_wait<0>();
-    if (bad) {
-        // wait (bounded) for the last committed MMAs before the accumulator is freed
-        if (threadIdx.x == 0) {
-            atomicExch(err, 1);
-            if (last_commit >= 0) mbar_wait(smem_u32(&mbar[last_commit % S]), (unsigned)((last_commit / S) & 1));
+        __syncwarp();
+    } else {
+        // ---- epilogue
+        int uc = 0;
+        for (int u = blockIdx.x; u < g.units; u += gridDim.x, ++uc) {
+            const TcUnit t = tc_unit<EPI, BN>(g, u);
+            const int b = uc & 1;
+            if (!tc_wait(smem_u32(&sy.accf[b]), (unsigned)((uc >> 1) & 1), abort, err)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            tc_epilogue<EPI, BN>(g, t, tmem + (unsigned)(b * BN), warp, lane);
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&sy.acce[b]));
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * BN) : "memory");
 }
 
 // ----------------------------------------------------------------------------- layout kernels
@@ -674,8 +766,8 @@ static void gemm(TcGemm g, int *err, cudaStream_t s, int splits = 1) {
     g.mt = (g.M + kTcBM - 1) / kTcBM;
     g.nt = (g.N + BN - 1) / BN;
     g.units = EPI == EPI_DGRAD_MASK_BF16 ? 4 * g.mt : g.mt * g.nt * z;  // four parity classes
-    const int cap = 2 * upslam_sm_count();  // two CTAs per SM by shared memory
-    gemm_tc_kernel<EPI, BN, LA, LB><<<g.units < cap ? g.units : cap, 128, smem, s>>>(g, err);
+    const int cap = 2 * upslam_sm_count();  // persistent: two CTAs per SM
+    gemm_tc_kernel<EPI, BN, LA, LB><<<g.units < cap ? g.units : cap, kTcThreads, smem, s>>>(g, err);
 }
 
 }  // namespace upslam
