@@ -565,34 +565,66 @@ def run_atrous(args, seq, d_scans, device, up, hbm, hbm_src):
 
 
 def run_e2e(args, seq, h_scans, device, up):
-    """Public API from pinned host memory: H2D sweep, track, D2H pose + record, sync, every step."""
+    """Public API from pinned host memory, driven as a streaming caller would: every step copies its sweep
+    host -> device (on a copy stream, overlapping the previous sweep's tracking), tracks it, copies its pose and
+    record device -> host, and the host reads that result while the next sweep runs.  All copies of every step
+    are inside the timed region."""
     import torch
     K = min(args.e2e_steps, h_scans.shape[0] - 1)
     p = up.Params(accept_quality=0.1)
     trk = up.Tracker(seq.sweep, seq.kf, p, device=device, constant_velocity=True)
     n_kf = 2 + K // seq.kf_every
     pool = [trk.kf] + [up.KeyframeBuffer(seq.kf, device) for _ in range(n_kf)]
-    staging = torch.empty(h_scans.shape[1:], dtype=torch.float32, device=device)
-    out_pose = torch.empty(12, dtype=torch.float64).pin_memory()
-    out_stats = torch.empty(up._abi.STATS_BYTES, dtype=torch.uint8).pin_memory()
-    staging.copy_(h_scans[0], non_blocking=True)
-    trk.new_keyframe(staging)
+    staging = [torch.empty(h_scans.shape[1:], dtype=torch.float32, device=device) for _ in range(2)]
+    out_pose = [torch.empty(12, dtype=torch.float64).pin_memory() for _ in range(2)]
+    out_stats = [torch.empty(up._abi.STATS_BYTES, dtype=torch.uint8).pin_memory() for _ in range(2)]
+    ready = [torch.cuda.Event() for _ in range(2)]  # sweep copied into staging[b]
+    free = [torch.cuda.Event() for _ in range(2)]   # the sweep in staging[b] has been tracked
+    done = [torch.cuda.Event() for _ in range(2)]   # pose and record of the step in out_*[b]
+    cs = torch.cuda.Stream(device=device)
+    ms = torch.cuda.current_stream()
+    staging[0].copy_(h_scans[0], non_blocking=True)
+    trk.new_keyframe(staging[0])
     torch.cuda.synchronize()
+
+    def h2d(k):
+        b = k % 2
+        with torch.cuda.stream(cs):
+            if k >= 3:
+                cs.wait_event(free[b])
+            staging[b].copy_(h_scans[k], non_blocking=True)
+            ready[b].record(cs)
+
     pos = 0
+    checksum = 0.0
     t0 = time.perf_counter()
+    h2d(1)
     for k in range(1, K + 1):
-        staging.copy_(h_scans[k], non_blocking=True)
-        trk.track(staging)
+        b = k % 2
+        if k < K:
+            h2d(k + 1)
+        ms.wait_event(ready[b])
+        trk.track(staging[b])
+        free[b].record(ms)
         if k % seq.kf_every == 0:
             pos += 1
             trk.new_keyframe(buffer=pool[pos])
-        out_pose.copy_(trk.state.pose, non_blocking=True)
-        out_stats.copy_(trk.state.stats, non_blocking=True)
-        torch.cuda.current_stream().synchronize()
+        out_pose[b].copy_(trk.state.pose, non_blocking=True)
+        out_stats[b].copy_(trk.state.stats, non_blocking=True)
+        done[b].record(ms)
+        if k >= 2:  # the previous step's result, read while this step runs
+            done[1 - b].synchronize()
+            checksum += float(out_pose[1 - b][3])
+    done[K % 2].synchronize()
+    checksum += float(out_pose[K % 2][3])
     dt = time.perf_counter() - t0
     return {"value": round(K / dt, 2), "unit": UNIT, "steps": K,
             "h2d_bytes_per_step": int(h_scans[0].numel() * 4),
-            "d2h_bytes_per_step": int(12 * 8 + up._abi.STATS_BYTES)}
+            "d2h_bytes_per_step": int(12 * 8 + up._abi.STATS_BYTES),
+            "overlap": "sweep k+1 copied in on a second stream while sweep k tracks; step k's result read on "
+                       "the host while step k+1 runs",
+            "l2": "not flushed between steps: the keyframe stays cache-resident across sweeps, as for a "
+                  "streaming caller (the device-timed value flushes L2 before every step)"}
 
 
 # ----------------------------------------------------------------------------- oracle timing
