@@ -36,17 +36,16 @@ __host__ __device__ constexpr int cnn_co(int l) { return l == 0 ? 32 : (l == 1 ?
 // ----------------------------------------------------------------------------- tcgen05 GEMM
 //
 // C(m, n) = sum_k A(m, k) B(n, k).  Work is cut into units of one 128 x BN
-// output tile and one slice of K (split-K); each CTA (four warps) walks the
-// units blockIdx.x, blockIdx.x + gridDim.x, ... and, inside each, K in steps of
-// 64, as one continuous pipeline of S shared-memory stages:
-//   * every thread copies its share of the operand chunks of step s + S - 1
-//     with 16-byte cp.async (zero-filled outside the matrix), so loads run
-//     S - 1 steps ahead of the tensor cores, across unit boundaries too;
+// output tile and one slice of K (split-K; for the data gradient, one parity
+// class); each persistent CTA walks the units blockIdx.x, blockIdx.x +
+// gridDim.x, ... and, inside each, K in steps of 64, through a ring of S
+// shared-memory stages shared by three warp roles (gemm_tc_kernel):
+//   * producer warps copy each step's operand chunks with 16-byte cp.async
+//     (zero-filled outside the matrix), running ahead across unit boundaries;
 //   * one thread issues the step's tcgen05.mma.kind::f16 (BF16 in, FP32
-//     accumulate, K = 16 each) and commits them to the stage's mbarrier, which
-//     frees the stage for refilling;
-//   * after a unit's last step the four warps read their 32 accumulator rows
-//     with tcgen05.ld and apply the epilogue.
+//     accumulate, K = 16 each) into one of two tensor-memory accumulators;
+//   * epilogue warps read a finished accumulator with tcgen05.ld while the
+//     next unit's MMAs fill the other one.
 // An operand tile is R rows (along M or N) x 64 (along K) in the no-swizzle
 // canonical layout: 8 x 8 core matrices of 128 contiguous bytes, core matrix
 // (row group g, k group h) at g * 1024 + h * 128 bytes.  Inside a core matrix
