@@ -67,7 +67,12 @@ struct TcOperand {
     long long ld;    // dense and LD_W_TAPS_MN: elements between consecutive a
     int rows;        // extent along M (operand A) or N (operand B)
     int hs, ws, cs;  // im2col: log2 of the input's H, W, C; LD_DY_TAPS_K: log2 of dY's H, W, C
+    int ones_row;    // LD_IM2COL_MN: feature index whose every element reads 1 (or -1: none)
 };
+
+// A 16-byte chunk holding (1, 0, 0, 0, 0, 0, 0, 0) in BF16: the source of an appended feature of ones, which makes
+// the weight-gradient GEMM also produce the bias gradient sum_p dY[p][n].
+static __device__ __align__(16) const unsigned short kUnitChunk[8] = {0x3F80, 0, 0, 0, 0, 0, 0, 0};
 
 struct TcGemm {
     TcOperand a, b;
@@ -78,6 +83,7 @@ struct TcGemm {
     long long ldc;    // EPI_F32_RED_T: C[n * ldc + m]; otherwise C[m * ldc + n]
     const float *bias;
     const __nv_bfloat16 *mask;  // EPI_DGRAD_MASK_BF16: the layer input, whose ReLU masks dX
+    float *db;                  // EPI_F32_RED_T with a ones row: the bias gradient it feeds
 };
 
 constexpr int kTcBM = 128, kTcBK = 64;
@@ -144,7 +150,9 @@ __device__ __forceinline__ void tc_load(unsigned tile, const TcOperand &o, int r
         }
         if ((MN ? a : f) >= kread) continue;  // beyond the k the step's MMAs read: never touched
         const __nv_bfloat16 *src = o.p;
-        if (IM) {
+        if (LD == LD_IM2COL_MN && f == o.ones_row) {
+            if (ok) src = reinterpret_cast<const __nv_bfloat16 *>(kUnitChunk);
+        } else if (IM) {
             const int wo = o.ws - 1, ho = o.hs - 1;
             const int ox = a & ((1 << wo) - 1), oy = (a >> wo) & ((1 << ho) - 1), b = a >> (wo + ho);
             const int tap = f >> o.cs, ci = f & ((1 << o.cs) - 1);
@@ -310,6 +318,11 @@ __device__ __forceinline__ void tc_epilogue(const TcGemm &g, const TcUnit &cur, 
                     ow[jj] = *reinterpret_cast<const unsigned *>(&h);
                 }
                 *reinterpret_cast<uint4 *>(reinterpret_cast<__nv_bfloat16 *>(g.C) + pix * g.ldc + n) = o;
+            } else if (m == g.a.ones_row) {
+                // the appended feature of ones: sum_p dY[p][n], the bias gradient
+#pragma unroll
+                for (int jj = 0; jj < 8; ++jj)
+                    if (n + jj < g.N) atomicAdd(g.db + n + jj, __uint_as_float(w[jj]));
             } else {
 #pragma unroll
                 for (int jj = 0; jj < 8; ++jj)
@@ -571,34 +584,6 @@ __global__ void __launch_bounds__(256) head_dy_kernel(const float *__restrict__ 
     }
 }
 
-// Column sums of dy [P][N] (BF16, N in {32, 64, 128}) added to db [N] (FP32): each thread streams 16-byte
-// chunks of one column group, the block folds its partial sums in shared memory and adds them with one
-// atomic per column.
-__global__ void __launch_bounds__(256) bias_grad_kernel(const __nv_bfloat16 *__restrict__ dy, int P, int N, float *db) {
-    __shared__ float part[128];
-    const int cpr = N >> 3, rpp = 256 / cpr;  // chunks per row, rows per pass
-    const int c = threadIdx.x % cpr, r = threadIdx.x / cpr;
-    for (int n = threadIdx.x; n < N; n += blockDim.x) part[n] = 0.0f;
-    __syncthreads();
-    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    const long long stride = (long long)gridDim.x * rpp;
-#pragma unroll 4
-    for (long long p = (long long)blockIdx.x * rpp + r; p < P; p += stride) {
-        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(dy + p * N) + c);
-        const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&v);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const float2 f = __bfloat1622float2(h[q]);
-            acc[2 * q] += f.x;
-            acc[2 * q + 1] += f.y;
-        }
-    }
-#pragma unroll
-    for (int q = 0; q < 8; ++q) atomicAdd(&part[c * 8 + q], acc[q]);
-    __syncthreads();
-    for (int n = threadIdx.x; n < N; n += blockDim.x) atomicAdd(db + n, part[n]);
-}
-
 // FP32 master conv weights [N][K] -> the BF16 copy the GEMMs read.
 __global__ void pack_weights_kernel(const float *w, int n, __nv_bfloat16 *wb) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) wb[i] = __float2bfloat16(w[i]);
@@ -737,6 +722,7 @@ static TcOperand op_im2col(const __nv_bfloat16 *x, int H, int W, int C) {
     o.hs = ilog2(H);
     o.ws = ilog2(W);
     o.cs = ilog2(C);
+    o.ones_row = -1;
     return o;
 }
 
@@ -746,6 +732,7 @@ static TcOperand op_dense(const __nv_bfloat16 *x, long long ld) {
     o.ld = ld;
     o.rows = 0;
     o.hs = o.ws = o.cs = 0;
+    o.ones_row = -1;
     return o;
 }
 
@@ -799,7 +786,7 @@ extern "C" upslam_status upslam_cnn_forward(const float *d_params, const void *d
     for (int l = 0; l < 4; ++l) {
         const int C = kCnnCh[l], N = cnn_co(l), K = cnn_k(l);
         pack_weights_kernel<<<grid1d((long long)N * K), 256, 0, s>>>(d_params + L.off_w[l], N * K, w.wb[l]);
-        TcGemm g;
+        TcGemm g{};
         g.a = op_im2col(x, H, W, C);
         g.b = op_dense(w.wb[l], K);
         g.M = batch * (H / 2) * (W / 2);
@@ -847,18 +834,21 @@ extern "C" upslam_status upslam_cnn_backward(const float *d_params, const void *
         const int H = kCnnH >> l, W = kCnnW >> l;
         const int P = batch * (H / 2) * (W / 2);
         const __nv_bfloat16 *xin = l == 0 ? reinterpret_cast<const __nv_bfloat16 *>(d_x) : w.act[l - 1];
-        // dW[n][f] += sum_p cols(p, f) dY[p][n]: M = f (im2col, MN-major), N = n (dY, MN-major), K = p
-        TcGemm gw;
+        // dW[n][f] += sum_p cols(p, f) dY[p][n]: M = f (im2col, MN-major), N = n (dY, MN-major), K = p;
+        // an appended feature f = K of ones yields db[n] = sum_p dY[p][n] in the same GEMM
+        TcGemm gw{};
         gw.a = op_im2col(xin, H, W, C);
+        gw.a.ones_row = K;
+        gw.db = d_grads + L.off_b[l];
         gw.b = op_dense(w.dy[l], N);
-        gw.M = K;
+        gw.M = K + 1;
         gw.N = N;
         gw.K = P;
         gw.C = d_grads + L.off_w[l];
         gw.ldc = K;
         gw.bias = nullptr;
         // enough slices for two CTAs per SM, each at least 16 K tiles deep
-        const int tiles = (K + kTcBM - 1) / kTcBM;
+        const int tiles = (K + 1 + kTcBM - 1) / kTcBM;
         const int ktiles = (P + kTcBK - 1) / kTcBK;
         int splits = (2 * sms + tiles - 1) / tiles;
         if (splits > ktiles / 16) splits = ktiles / 16;
@@ -866,7 +856,6 @@ extern "C" upslam_status upslam_cnn_backward(const float *d_params, const void *
         if (N == 32) gemm<EPI_F32_RED_T, 32, LD_IM2COL_MN, LD_DENSE_MN>(gw, w.err, s, splits);
         else if (N == 64) gemm<EPI_F32_RED_T, 64, LD_IM2COL_MN, LD_DENSE_MN>(gw, w.err, s, splits);
         else gemm<EPI_F32_RED_T, 128, LD_IM2COL_MN, LD_DENSE_MN>(gw, w.err, s, splits);
-        bias_grad_kernel<<<sms * 2, 256, 0, s>>>(w.dy[l], P, N, d_grads + L.off_b[l]);
         if (l > 0) {
             // dY of the layer below = its ReLU mask x sum over the taps that read each input pixel of dY W,
             // one GEMM per parity class of the input pixels (no column matrix)

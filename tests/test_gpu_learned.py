@@ -36,10 +36,12 @@ def _flat_params(seed):
     return p
 
 
-@pytest.mark.parametrize("B", [4, 3, 40])
+@pytest.mark.parametrize("B", [4, 3, 1, 40])
 def test_forward_backward_match_oracle(B):
-    """B = 3 leaves ragged tensor-core tiles (the last layer's 192 rows are 1.5 tiles of 128); B = 40 gives the
-    first layer 1280 output tiles, so every persistent CTA runs several tiles through one load pipeline."""
+    """B = 3 leaves ragged tensor-core tiles (the last layer's 192 rows are 1.5 tiles of 128); B = 1 gives the
+    last layer a single half-empty tile and each weight gradient one K slice; B = 40 gives the first layer 1280
+    output tiles, so every persistent CTA runs several tiles through one load pipeline.  The bias gradients
+    come out of the weight-gradient GEMM (an appended feature of ones) and are checked with the rest."""
     rng = np.random.default_rng(5 + B)
     x = rng.uniform(-1, 1, size=(B, 64, 256, 8)) * (rng.random((B, 64, 256, 1)) < 0.7)
     xb = _bf16(x)
