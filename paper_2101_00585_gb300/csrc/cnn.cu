@@ -236,10 +236,20 @@ __device__ __forceinline__ void tc_commit(unsigned mbar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
 }
 
-// Bounded wait for the phase of the given parity; gives up early once another role has aborted, and aborts
-// the CTA (error word set) when the bound runs out.
+// Bounded wait for the phase of the given parity: gives up early once another role has aborted, and aborts
+// the CTA (error word set) after kTcTimeoutNs of global time.  (A suspend-time hint on try_wait, letting
+// waiting warps sleep, measured no different from polling.)
+constexpr unsigned long long kTcTimeoutNs = 2000000000ull;
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 __device__ __forceinline__ bool tc_wait(unsigned mbar, unsigned parity, volatile int *abort, int *err) {
-    for (unsigned it = 0; it < kTcWaitIters; ++it) {
+    unsigned long long t0 = 0;
+    for (unsigned it = 0;; ++it) {
         unsigned done;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -247,11 +257,18 @@ __device__ __forceinline__ bool tc_wait(unsigned mbar, unsigned parity, volatile
             : "r"(mbar), "r"(parity)
             : "memory");
         if (done) return true;
-        if ((it & 63) == 63 && *abort) return false;
+        if ((it & 63) == 63) {
+            if (*abort) return false;
+            const unsigned long long t = global_ns();
+            if (t0 == 0) {
+                t0 = t;
+            } else if (t - t0 > kTcTimeoutNs) {
+                *abort = 1;
+                atomicExch(err, 1);
+                return false;
+            }
+        }
     }
-    *abort = 1;
-    atomicExch(err, 1);
-    return false;
 }
 
 // The epilogue of one 128 x BN tile from tensor-memory columns [acc, acc + BN): warp w owns rows 32w..32w+31.
