@@ -125,7 +125,14 @@ __device__ __forceinline__ void class_tap(int q, int t, int &ky, int &kx) {
     kx = px ? 2 * tx : 1;
 }
 
-template <int LD, int R>
+// Producer warps per CTA: the weight gradient streams long K (pixel) ranges through the MN-major loaders and
+// is bound by their issue rate, so it takes eight; the other GEMMs are not and take four.
+template <int LA>
+constexpr int tc_prod() { return LA == LD_IM2COL_MN ? 8 : 4; }
+template <int LA>
+constexpr int tc_threads() { return 32 * (4 + tc_prod<LA>() + 1); }  // epilogue, producers, MMA issue
+
+template <int LD, int R, int NPROD>
 __device__ __forceinline__ void tc_load(unsigned tile, const TcOperand &o, int r0, int k0, int kend, int kread, int cls,
                                         int ptid) {
     constexpr bool MN = LD == LD_DENSE_MN || LD == LD_IM2COL_MN || LD == LD_W_TAPS_MN;
@@ -133,8 +140,8 @@ __device__ __forceinline__ void tc_load(unsigned tile, const TcOperand &o, int r
     constexpr int NA8 = MN ? kTcBK / 8 : R / 8;  // groups of 8 along a
     const int lane = ptid & 31, warp = ptid >> 5;
 #pragma unroll
-    for (int it = 0; it < R / 16; ++it) {
-        const int q = it * 4 + warp;
+    for (int it = 0; it < R / (4 * NPROD); ++it) {
+        const int q = it * NPROD + warp;
         const int i = (q % NA8) * 8 + (lane & 7);
         const int j = (q / NA8) * 4 + (lane >> 3);
         int a, f;
@@ -215,7 +222,6 @@ constexpr int tc_stages() {
 template <int BN>
 constexpr int tc_smem_bytes() { return tc_stages<BN>() * (kTcBM + BN) * kTcBK * 2; }
 
-constexpr int kTcThreads = 288;  // warps 0-3 epilogue, 4-7 producers, 8 MMA issue
 
 struct TcSync {
     unsigned long long full[8];   // producers -> MMA: a stage's copies landed (4 warp arrivals)
@@ -351,14 +357,15 @@ __device__ __forceinline__ void tc_epilogue(const TcGemm &g, const TcUnit &cur, 
     }
 }
 
-// Warp-specialised persistent GEMM, one CTA per SM.  Producers (warps 4-7) fill the S-stage ring with
-// cp.async and, once a stage's copies have landed (cp.async.wait_group, then a proxy fence), arrive on its
-// full barrier; the MMA thread (warp 8, lane 0) waits for full, issues the stage's MMAs into one of two
+// Warp-specialised persistent GEMM, two CTAs per SM.  Producers (warps 4 .. 3 + kProd) fill the S-stage ring
+// with cp.async and, once a stage's copies have landed (cp.async.wait_group, then a proxy fence), arrive on its
+// full barrier; the MMA thread (the last warp, lane 0) waits for full, issues the stage's MMAs into one of two
 // tensor-memory accumulators and commits them to the stage's empty barrier, and after a unit's last step to
 // the accumulator's full barrier; the epilogue warps (0-3) drain one accumulator while the MMAs of the next
 // unit fill the other, then arrive on its empty barrier.
 template <int EPI, int BN, int LA, int LB>
-__global__ void __launch_bounds__(kTcThreads, 2) gemm_tc_kernel(TcGemm g, int *err) {
+__global__ void __launch_bounds__(tc_threads<LA>(), 2) gemm_tc_kernel(TcGemm g, int *err) {
+    constexpr int kProd = tc_prod<LA>();
     constexpr int S = tc_stages<BN>();
     // cp.async groups a producer keeps in flight before it signals a stage full: all but one stage, which
     // still cannot deadlock (the stage refilled at step it was consumed at it - S, signalled at it - 1)
@@ -380,7 +387,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) gemm_tc_kernel(TcGemm g, int *e
     }
     if (threadIdx.x == 32) {
         for (int i = 0; i < S; ++i) {
-            mbar_init(smem_u32(&sy.full[i]), 4);
+            mbar_init(smem_u32(&sy.full[i]), kProd);
             mbar_init(smem_u32(&sy.empty[i]), 1);
         }
         for (int i = 0; i < 2; ++i) {
@@ -395,7 +402,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) gemm_tc_kernel(TcGemm g, int *e
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const unsigned tmem = sy.tmem_base;
 
-    if (warp >= 4 && warp < 8) {
+    if (warp >= 4 && warp < 4 + kProd) {
         // ---- producers
         const int ptid = threadIdx.x - 128;
         int it = 0;
@@ -410,8 +417,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) gemm_tc_kernel(TcGemm g, int *e
                 }
                 const int k0 = t.kbeg + k * kTcBK;
                 const int kread = k0 + 16 * min(kTcBK / 16, (t.kend - k0 + 15) / 16);
-                tc_load<LA, kTcBM>(smem0 + st * kStage, g.a, t.r0a, k0, t.kend, kread, t.cls, ptid);
-                tc_load<LB, BN>(smem0 + st * kStage + kA, g.b, t.r0b, k0, t.kend, kread, t.cls, ptid);
+                tc_load<LA, kTcBM, kProd>(smem0 + st * kStage, g.a, t.r0a, k0, t.kend, kread, t.cls, ptid);
+                tc_load<LB, BN, kProd>(smem0 + st * kStage + kA, g.b, t.r0b, k0, t.kend, kread, t.cls, ptid);
                 cp_async_commit();
                 if (it >= kTcLag) {
                     cp_async_wait<kTcLag>();
@@ -426,7 +433,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) gemm_tc_kernel(TcGemm g, int *e
         __syncwarp();
         if (ok && lane == 0)
             for (int j = it > kTcLag ? it - kTcLag : 0; j < it; ++j) mbar_arrive(smem_u32(&sy.full[j % S]));
-    } else if (warp == 8) {
+    } else if (warp == 4 + kProd) {
         // ---- MMA issue
         if (lane == 0) {
             // instruction descriptor: FP32 accumulator, BF16 A and B, majors, N = BN, M = 128
@@ -770,7 +777,7 @@ static void gemm(TcGemm g, int *err, cudaStream_t s, int splits = 1) {
     g.nt = (g.N + BN - 1) / BN;
     g.units = EPI == EPI_DGRAD_MASK_BF16 ? 4 * g.mt : g.mt * g.nt * z;  // four parity classes
     const int cap = 2 * upslam_sm_count();  // persistent: two CTAs per SM
-    gemm_tc_kernel<EPI, BN, LA, LB><<<g.units < cap ? g.units : cap, kTcThreads, smem, s>>>(g, err);
+    gemm_tc_kernel<EPI, BN, LA, LB><<<g.units < cap ? g.units : cap, tc_threads<LA>(), smem, s>>>(g, err);
 }
 
 }  // namespace upslam
