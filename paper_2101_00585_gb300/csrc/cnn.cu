@@ -197,8 +197,13 @@ template <int EPI, int BN>
 __device__ __forceinline__ TcUnit tc_unit(const TcGemm &g, int u) {
     TcUnit t;
     if (EPI == EPI_DGRAD_MASK_BF16) {
-        t.cls = u / g.mt;  // class-major: a CTA's units mix the classes
-        t.r0a = (u % g.mt) * kTcBM;
+        // the four classes of one row tile are consecutive units, so neighbouring CTAs write both halves of
+        // each output line at about the same time; the class order rotates with the tile (by a function of the
+        // tile alone, so the four units still cover the four classes) so that each CTA's units, gridDim.x
+        // apart, cycle through the classes and their 1, 2, 2 or 4 taps of work
+        const int tile = u >> 2;
+        t.cls = ((u & 3) + (int)((4ll * tile) / gridDim.x)) & 3;
+        t.r0a = tile * kTcBM;
         t.r0b = 0;
         t.kbeg = 0;
         t.kend = class_taps(t.cls) * g.K;
