@@ -21,6 +21,8 @@
 // Parameters live as one FP32 master array (w0 b0 w1 b1 w2 b2 w3 b3 wf bf,
 // weights [C_out][3][3][C_in], head [6][128]); BF16 copies of the conv weights
 // are what the GEMMs read.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <string.h>
 
 #include "common.cuh"
@@ -68,6 +70,8 @@ struct TcOperand {
     int rows;        // extent along M (operand A) or N (operand B)
     int hs, ws, cs;  // im2col: log2 of the input's H, W, C; LD_DY_TAPS_K: log2 of dY's H, W, C
     int ones_row;    // LD_IM2COL_MN: feature index whose every element reads 1 (or -1: none)
+    int kf;          // im2col: number of features (9 C)
+    int nb;          // im2col and LD_DY_TAPS_K: number of images (a chunk loaded at image nb reads zeros)
 };
 
 // A 16-byte chunk holding (1, 0, 0, 0, 0, 0, 0, 0) in BF16: the source of an appended feature of ones, which makes
@@ -97,46 +101,43 @@ __device__ __forceinline__ unsigned long long umma_desc(unsigned addr, unsigned 
            ((unsigned long long)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
-template <bool L1>
-__device__ __forceinline__ void cp_async16(unsigned dst, const void *src, bool ok) {
-    if (L1)
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(ok ? 16 : 0) : "memory");
-    else
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(ok ? 16 : 0) : "memory");
+__device__ __forceinline__ void mbar_expect_tx(unsigned mbar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+
+// One TMA tile load of a 4-D tensor map into shared memory, completing on mbar (transaction bytes).
+__device__ __forceinline__ void tma_load4(unsigned dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
+                                          unsigned mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}],"
+        " [%6];" ::"r"(dst),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(mbar)
+        : "memory");
+}
+
+__device__ __forceinline__ void cp_async16_ca(unsigned dst, const void *src, bool ok) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(ok ? 16 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async16_cg(unsigned dst, const void *src, bool ok) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(ok ? 16 : 0) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-// Issue the copies of one R x 64 operand tile: rows [r0, r0 + R), k [k0, k0 + 64), zero where k >= kend
-// or a row >= o.rows.  A warp takes 8 consecutive a by 4 consecutive f chunks: the 8 a land in the 8
-// distinct 16-byte rows of a core matrix (no shared-memory bank conflict) and the 4 chunks of one a are
-// contiguous in a dense source.
-// The data gradient of a 3x3 stride-2 pad-1 convolution, without the column matrix: an input pixel
-// (y, x) = (2i + py, 2j + px) is read by the taps ky = 1 (py = 0) or ky in {0, 2} (py = 1), and likewise kx,
-// from output pixel ((y + 1 - ky) / 2, (x + 1 - kx) / 2).  Parity class q = 2 py + px has
-// taps(q) = (1 + py)(1 + px) taps; its GEMM runs over i, j (M = B H/2 W/2) with k = t N + n (tap t of the
-// class, output channel n):  dX(y, x, c) = sum_k dY(oy_t, ox_t, n) W[n][(3 ky_t + kx_t) C + c].
-__device__ __forceinline__ int class_taps(int q) { return (1 + (q >> 1)) * (1 + (q & 1)); }
-__device__ __forceinline__ void class_tap(int q, int t, int &ky, int &kx) {
-    const int py = q >> 1, px = q & 1;
-    const int ty = px ? (t >> 1) : t, tx = px ? (t & 1) : 0;
-    ky = py ? 2 * ty : 1;
-    kx = px ? 2 * tx : 1;
-}
-
-// Producer warps per CTA: eight.  Once the epilogue is cheap, every GEMM here is bound by the rate at which
-// the producers compute addresses and issue 16-byte copies (measured with per-role timestamps: the MMA
-// thread waits on full stages, the epilogue on finished accumulators).
-template <int LA>
-constexpr int tc_prod() { return 8; }
-template <int LA>
-constexpr int tc_threads() { return 32 * (4 + tc_prod<LA>() + 1); }  // epilogue, producers, MMA issue
-
+// The forward and weight-gradient operands are gathered by NPROD producer warps with 16-byte cp.async,
+// zero-filled outside the matrix, into the no-swizzle layout with core matrix (row group g, k group h) at
+// g * 1024 + h * 128 bytes (LBO 128, SBO 1024).  A chunk (a, f) is 8 consecutive k of row a (K-major) or 8
+// consecutive rows f at k a (MN-major):
+//   LD_IM2COL_K  (forward A):  row a = output pixel, k f = feature (one 8-channel chunk of one tap);
+//   LD_IM2COL_MN (wgrad A):    k a = output pixel, row f = feature (feature o.ones_row reads 1);
+//   LD_DENSE_K   (forward B):  X[a * ld + f], the weights;  LD_DENSE_MN (wgrad B): X[a * ld + f], dY.
+// A warp takes 8 consecutive a by 4 consecutive f chunks: the 8 a land in the 8 distinct 16-byte rows of a
+// core matrix (no bank conflict).  Chunks at or past kread (beyond what the step's MMAs read) are skipped.
 template <int LD, int R, int NPROD>
-__device__ __forceinline__ void tc_load(unsigned tile, const TcOperand &o, int r0, int k0, int kend, int kread, int cls,
-                                        int ptid) {
-    constexpr bool MN = LD == LD_DENSE_MN || LD == LD_IM2COL_MN || LD == LD_W_TAPS_MN;
+__device__ __forceinline__ void tc_gather(unsigned tile, const TcOperand &o, int r0, int k0, int kend, int kread,
+                                          int ptid) {
+    constexpr bool MN = LD == LD_IM2COL_MN || LD == LD_DENSE_MN;
     constexpr bool IM = LD == LD_IM2COL_K || LD == LD_IM2COL_MN;
     constexpr int NA8 = MN ? kTcBK / 8 : R / 8;  // groups of 8 along a
     const int lane = ptid & 31, warp = ptid >> 5;
@@ -156,11 +157,13 @@ __device__ __forceinline__ void tc_load(unsigned tile, const TcOperand &o, int r
             f = k0 + 8 * j;
             ok = a < o.rows && f < kend;
         }
-        if ((MN ? a : f) >= kread) continue;  // beyond the k the step's MMAs read: never touched
+        if ((MN ? a : f) >= kread) continue;
         const __nv_bfloat16 *src = o.p;
-        if (LD == LD_IM2COL_MN && f == o.ones_row) {
+        if (!IM) {
+            if (ok) src = o.p + (long long)a * o.ld + f;
+        } else if (MN && f == o.ones_row) {
             if (ok) src = reinterpret_cast<const __nv_bfloat16 *>(kUnitChunk);
-        } else if (IM) {
+        } else {
             const int wo = o.ws - 1, ho = o.hs - 1;
             const int ox = a & ((1 << wo) - 1), oy = (a >> wo) & ((1 << ho) - 1), b = a >> (wo + ho);
             const int tap = f >> o.cs, ci = f & ((1 << o.cs) - 1);
@@ -168,26 +171,35 @@ __device__ __forceinline__ void tc_load(unsigned tile, const TcOperand &o, int r
             const int y = 2 * oy + ky - 1, x = 2 * ox + kx - 1;
             ok = ok && (unsigned)y < (1u << o.hs) && (unsigned)x < (1u << o.ws);
             if (ok) src = o.p + ((((((long long)b << o.hs) + y) << o.ws) + x) << o.cs) + ci;
-        } else if (LD == LD_DY_TAPS_K) {
-            // a: input pixel (b, i, j) of class cls; f = t N + n
-            int ky, kx;
-            class_tap(cls, f >> o.cs, ky, kx);
-            const int j2 = a & ((1 << o.ws) - 1), i2 = (a >> o.ws) & ((1 << o.hs) - 1), b = a >> (o.ws + o.hs);
-            const int oy = (2 * i2 + (cls >> 1) + 1 - ky) >> 1, ox = (2 * j2 + (cls & 1) + 1 - kx) >> 1;
-            ok = ok && oy < (1 << o.hs) && ox < (1 << o.ws);
-            if (ok) src = o.p + ((((((long long)b << o.hs) + oy) << o.ws) + ox) << o.cs) + (f & ((1 << o.cs) - 1));
-        } else if (LD == LD_W_TAPS_MN) {
-            // a = t N + n (o.cs = log2 N), f = input channel c (o.rows = C)
-            int ky, kx;
-            class_tap(cls, a >> o.cs, ky, kx);
-            if (ok) src = o.p + (long long)(a & ((1 << o.cs) - 1)) * o.ld + (3 * ky + kx) * o.rows + f;
-        } else if (ok) {
-            src = o.p + (long long)a * o.ld + f;
         }
         const unsigned off = MN ? j * 1024 + (i >> 3) * 128 : (i >> 3) * 1024 + j * 128;
-        cp_async16<IM>(tile + off + (i & 7) * 16, src, ok);
+        if (IM) cp_async16_ca(tile + off + (i & 7) * 16, src, ok);
+        else cp_async16_cg(tile + off + (i & 7) * 16, src, ok);
     }
 }
+
+// The data gradient of a 3x3 stride-2 pad-1 convolution, without the column matrix: an input pixel
+// (y, x) = (2i + py, 2j + px) is read by the taps ky = 1 (py = 0) or ky in {0, 2} (py = 1), and likewise kx,
+// from output pixel ((y + 1 - ky) / 2, (x + 1 - kx) / 2).  Parity class q = 2 py + px has
+// taps(q) = (1 + py)(1 + px) taps; its GEMM runs over i, j (M = B H/2 W/2) with k = t N + n (tap t of the
+// class, output channel n):  dX(y, x, c) = sum_k dY(oy_t, ox_t, n) W[n][(3 ky_t + kx_t) C + c].
+__device__ __forceinline__ int class_taps(int q) { return (1 + (q >> 1)) * (1 + (q & 1)); }
+__device__ __forceinline__ void class_tap(int q, int t, int &ky, int &kx) {
+    const int py = q >> 1, px = q & 1;
+    const int ty = px ? (t >> 1) : t, tx = px ? (t & 1) : 0;
+    ky = py ? 2 * ty : 1;
+    kx = px ? 2 * tx : 1;
+}
+
+// Warps: 0-3 epilogue, then the producers, then one MMA-issue warp.  The data gradient is loaded by one TMA
+// thread; the forward and weight-gradient operands by eight cp.async warps (their address arithmetic and copy
+// issue set the pace).
+template <int LA>
+constexpr bool tc_a_tma() { return LA == LD_DY_TAPS_K; }
+template <int LA>
+constexpr int tc_prod() { return tc_a_tma<LA>() ? 1 : 8; }
+template <int LA>
+constexpr int tc_threads() { return 32 * (4 + tc_prod<LA>() + 1); }
 
 struct TcUnit {
     int r0a, r0b, kbeg, kend, nkt, cls;
@@ -218,6 +230,36 @@ __device__ __forceinline__ TcUnit tc_unit(const TcGemm &g, int u) {
     }
     t.nkt = (t.kend - t.kbeg + kTcBK - 1) / kTcBK;
     return t;
+}
+
+// TMA loads of one K step of the data gradient (tensor maps built on the host; one 16-byte-wide box per chunk
+// of 8; coordinates past the tensor read as zeros):
+//   A, LD_DY_TAPS_K: class pixels (b, i, j) from t.r0a by (tap, n) from k0, K-major chunk j = [128 rows][16 B]
+//     at j * 2048 (LBO 2048, SBO 128); a tap's offset pixels past dY read zeros;
+//   B, LD_W_TAPS_MN, at stage + 16 KB: chunk j (8 channels) = [64 k][16 B] at j * 1024 (LBO 128, SBO 1024).
+// With these dense boxes TMA beats the cp.async gather; for the im2col operands (8-channel boxes stepping 2
+// pixels) it measured slower, so the forward and weight-gradient GEMMs gather with cp.async.
+__device__ __forceinline__ void tc_tma_a(unsigned stage, unsigned mbar, const TcOperand &a, const CUtensorMap *ma,
+                                         const TcUnit &t, int k0) {
+    int ky, kx;
+    class_tap(t.cls, k0 >> a.cs, ky, kx);
+    const int doy = ((t.cls >> 1) + 1 - ky) >> 1, dox = ((t.cls & 1) + 1 - kx) >> 1;
+    const int j0 = t.r0a & ((1 << a.ws) - 1), i0 = (t.r0a >> a.ws) & ((1 << a.hs) - 1), b0 = t.r0a >> (a.ws + a.hs);
+    const int n0 = k0 & ((1 << a.cs) - 1);
+#pragma unroll 1
+    for (int j = 0; j < 8; ++j) tma_load4(stage + j * 2048, ma, n0 + 8 * j, j0 + dox, i0 + doy, b0, mbar);
+}
+
+template <int BN>
+__device__ __forceinline__ void tc_tma_b(unsigned sb, unsigned mbar, const TcOperand &b, const CUtensorMap *mb,
+                                         const TcUnit &t, int k0) {
+    // W[n][(3 ky + kx) C + c]: k = (tap, n) from k0, rows = c from t.r0b in chunks of 8
+    int ky, kx;
+    class_tap(t.cls, k0 >> b.cs, ky, kx);
+    const int n0 = k0 & ((1 << b.cs) - 1);
+#pragma unroll 1
+    for (int j = 0; j < BN / 8; ++j)
+        tma_load4(sb + j * 1024, mb, (3 * ky + kx) * b.rows + t.r0b + 8 * j, n0, 0, 0, mbar);
 }
 
 // Stages that fit in about 100 KB of shared memory (two CTAs per SM), at most 8.
@@ -366,23 +408,28 @@ __device__ __forceinline__ void tc_epilogue(const TcGemm &g, const TcUnit &cur, 
     }
 }
 
-// Warp-specialised persistent GEMM, two CTAs per SM.  Producers (warps 4 .. 3 + kProd) fill the S-stage ring
-// with cp.async and, once a stage's copies have landed (cp.async.wait_group, then a proxy fence), arrive on its
-// full barrier; the MMA thread (the last warp, lane 0) waits for full, issues the stage's MMAs into one of two
-// tensor-memory accumulators and commits them to the stage's empty barrier, and after a unit's last step to
-// the accumulator's full barrier; the epilogue warps (0-3) drain one accumulator while the MMAs of the next
-// unit fill the other, then arrive on its empty barrier.
+// Warp-specialised persistent GEMM, two CTAs per SM.  One producer thread (warp 4) issues each step's TMA
+// loads into the S-stage ring, announcing the step's bytes on its full barrier; the MMA thread (warp 5, lane 0)
+// waits for full, issues the stage's MMAs into one of two tensor-memory accumulators and commits them to the
+// stage's empty barrier, and after a unit's last step to the accumulator's full barrier; the epilogue warps
+// (0-3) drain one accumulator while the MMAs of the next unit fill the other, then arrive on its empty barrier.
 template <int EPI, int BN, int LA, int LB>
-__global__ void __launch_bounds__(tc_threads<LA>(), 2) gemm_tc_kernel(TcGemm g, int *err) {
-    constexpr int kProd = tc_prod<LA>();
+__global__ void __launch_bounds__(tc_threads<LA>(), 2)
+    gemm_tc_kernel(TcGemm g, int *err, const __grid_constant__ CUtensorMap tma_a,
+                   const __grid_constant__ CUtensorMap tma_b) {
     constexpr int S = tc_stages<BN>();
-    // cp.async groups a producer keeps in flight before it signals a stage full: all but one stage, which
-    // still cannot deadlock (the stage refilled at step it was consumed at it - S, signalled at it - 1)
-    constexpr int kTcLag = S - 2;
     static_assert(S >= 2 && S <= 8, "stage ring");
+    constexpr bool A_TMA = tc_a_tma<LA>();
+    constexpr int kProd = tc_prod<LA>();
+    constexpr int kLag = S - 2;  // cp.async groups a gather thread keeps in flight before signalling a stage
     constexpr int kA = kTcBM * kTcBK * 2, kStage = (kTcBM + BN) * kTcBK * 2;
-    constexpr bool A_MN = LA == LD_DENSE_MN || LA == LD_IM2COL_MN;
-    constexpr bool B_MN = LB == LD_DENSE_MN || LB == LD_IM2COL_MN || LB == LD_W_TAPS_MN;
+    constexpr unsigned kTxBytes = (unsigned)kStage;  // TMA boxes are written in full (zeros outside)
+    constexpr bool A_MN = LA == LD_IM2COL_MN;
+    constexpr bool B_MN = LB == LD_DENSE_MN || LB == LD_W_TAPS_MN;
+    // descriptor byte offsets (leading = along K, stride = along M/N); an MMA (16 k) advances two core
+    // matrices along K
+    constexpr unsigned kALbo = A_TMA ? 2048 : 128, kASbo = A_TMA ? 128 : 1024;
+    constexpr unsigned kBLbo = 128, kBSbo = 1024;
     extern __shared__ __align__(1024) unsigned char tc_smem[];
     __shared__ __align__(8) TcSync sy;
     __shared__ float sbias[EPI == EPI_BIAS_RELU_BF16 ? BN : 1];
@@ -397,7 +444,7 @@ __global__ void __launch_bounds__(tc_threads<LA>(), 2) gemm_tc_kernel(TcGemm g, 
     }
     if (threadIdx.x == 32) {
         for (int i = 0; i < S; ++i) {
-            mbar_init(smem_u32(&sy.full[i]), kProd);
+            mbar_init(smem_u32(&sy.full[i]), A_TMA ? 1 : kProd);
             mbar_init(smem_u32(&sy.empty[i]), 1);
         }
         for (int i = 0; i < 2; ++i) {
@@ -415,34 +462,62 @@ __global__ void __launch_bounds__(tc_threads<LA>(), 2) gemm_tc_kernel(TcGemm g, 
     if (warp >= 4 && warp < 4 + kProd) {
         // ---- producers
         const int ptid = threadIdx.x - 128;
+        const bool tma_thread = warp == 4 && lane == 0;
         int it = 0;
         bool ok = true;
-        for (int u = blockIdx.x; ok && u < g.units; u += gridDim.x) {
-            const TcUnit t = tc_unit<EPI, BN>(g, u);
-            for (int k = 0; k < t.nkt; ++k, ++it) {
-                const int st = it % S;
-                if (it >= S && !tc_wait(smem_u32(&sy.empty[st]), (unsigned)(((it / S) - 1) & 1), abort, err)) {
-                    ok = false;
-                    break;
-                }
-                const int k0 = t.kbeg + k * kTcBK;
-                const int kread = k0 + 16 * min(kTcBK / 16, (t.kend - k0 + 15) / 16);
-                tc_load<LA, kTcBM, kProd>(smem0 + st * kStage, g.a, t.r0a, k0, t.kend, kread, t.cls, ptid);
-                tc_load<LB, BN, kProd>(smem0 + st * kStage + kA, g.b, t.r0b, k0, t.kend, kread, t.cls, ptid);
-                cp_async_commit();
-                if (it >= kTcLag) {
-                    cp_async_wait<kTcLag>();
-                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(smem_u32(&sy.full[(it - kTcLag) % S]));
+        if (!A_TMA || tma_thread) {
+            for (int u = blockIdx.x; ok && u < g.units; u += gridDim.x) {
+                const TcUnit t = tc_unit<EPI, BN>(g, u);
+                for (int k = 0; k < t.nkt; ++k, ++it) {
+                    const int st = it % S;
+                    if (it >= S && !tc_wait(smem_u32(&sy.empty[st]), (unsigned)(((it / S) - 1) & 1), abort, err)) {
+                        ok = false;
+                        break;
+                    }
+                    const unsigned stage = smem0 + st * kStage, fb = smem_u32(&sy.full[st]);
+                    const int k0 = t.kbeg + k * kTcBK;
+                    if (A_TMA) {
+                        mbar_expect_tx(fb, kTxBytes);
+                        tc_tma_a(stage, fb, g.a, &tma_a, t, k0);
+                        tc_tma_b<BN>(stage + kA, fb, g.b, &tma_b, t, k0);
+                    } else {
+                        const int kread = k0 + 16 * min(kTcBK / 16, (t.kend - k0 + 15) / 16);
+                        tc_gather<LA, kTcBM, kProd>(stage, g.a, t.r0a, k0, t.kend, kread, ptid);
+                        tc_gather<LB, BN, kProd>(stage + kA, g.b, t.r0b, k0, t.kend, kread, ptid);
+                        cp_async_commit();
+                        if (it >= kLag) {
+                            cp_async_wait<kLag>();
+                            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                            __syncwarp();
+                            if (lane == 0) mbar_arrive(smem_u32(&sy.full[(it - kLag) % S]));
+                        }
+                    }
                 }
             }
         }
-        cp_async_wait<0>();
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        if (!A_TMA) {
+            // signal the steps still in flight
+            cp_async_wait<0>();
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0)
+                for (int j = it > kLag ? it - kLag : 0; j < it; ++j) mbar_arrive(smem_u32(&sy.full[j % S]));
+        }
+        if (A_TMA && tma_thread && !ok) {
+            // let the loads already issued land before the CTA's shared memory goes away
+            for (int j = it > S ? it - S : 0; j < it; ++j)
+                for (unsigned w = 0; w < kTcWaitIters; ++w) {
+                    unsigned done;
+                    asm volatile(
+                        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                        " selp.u32 %0, 1, 0, p;\n}\n"
+                        : "=r"(done)
+                        : "r"(smem_u32(&sy.full[j % S])), "r"((unsigned)((j / S) & 1))
+                        : "memory");
+                    if (done) break;
+                }
+        }
         __syncwarp();
-        if (ok && lane == 0)
-            for (int j = it > kTcLag ? it - kTcLag : 0; j < it; ++j) mbar_arrive(smem_u32(&sy.full[j % S]));
     } else if (warp == 4 + kProd) {
         // ---- MMA issue
         if (lane == 0) {
@@ -473,8 +548,8 @@ __global__ void __launch_bounds__(tc_threads<LA>(), 2) gemm_tc_kernel(TcGemm g, 
                     const int k0 = t.kbeg + k * kTcBK;
                     const int nk = min(kTcBK / 16, (t.kend - k0 + 15) / 16);
                     for (int kk = 0; kk < nk; ++kk) {
-                        const unsigned long long ad = umma_desc(a0 + kk * 256, 128, 1024);
-                        const unsigned long long bd = umma_desc(b0 + kk * 256, 128, 1024);
+                        const unsigned long long ad = umma_desc(a0 + kk * 2 * kALbo, kALbo, kASbo);
+                        const unsigned long long bd = umma_desc(b0 + kk * 2 * kBLbo, kBLbo, kBSbo);
                         const unsigned accum = (k > 0 || kk > 0) ? 1u : 0u;
                         asm volatile(
                             "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
@@ -763,6 +838,8 @@ static TcOperand op_im2col(const __nv_bfloat16 *x, int H, int W, int C) {
     o.ws = ilog2(W);
     o.cs = ilog2(C);
     o.ones_row = -1;
+    o.kf = 9 * C;
+    o.nb = 0;
     return o;
 }
 
@@ -773,12 +850,58 @@ static TcOperand op_dense(const __nv_bfloat16 *x, long long ld) {
     o.rows = 0;
     o.hs = o.ws = o.cs = 0;
     o.ones_row = -1;
+    o.kf = 0;
+    o.nb = 0;
     return o;
 }
 
+// ----------------------------------------------------------------------------- tensor maps
+
+static PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// A 4-D BF16 tensor map: dims innermost first, byte strides of dims 1..3, box and element strides; out-of-range
+// elements read as zeros.
+static bool tmap4(CUtensorMap *m, const void *base, unsigned long long d0, unsigned long long d1, unsigned long long d2,
+                  unsigned long long d3, unsigned long long s1, unsigned long long s2, unsigned long long s3,
+                  const unsigned box[4], const unsigned estr[4]) {
+    const PFN_cuTensorMapEncodeTiled_v12000 enc = tmap_encoder();
+    if (!enc) return false;
+    const cuuint64_t dims[4] = {d0, d1, d2, d3};
+    const cuuint64_t strides[3] = {s1, s2, s3};
+    const cuuint32_t bx[4] = {box[0], box[1], box[2], box[3]}, es[4] = {estr[0], estr[1], estr[2], estr[3]};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(base), dims, strides, bx, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// dY [B][Ho][Wo][N] in boxes of 128 consecutive pixels by 8 channels.
+static bool tmap_dy_tiles(CUtensorMap *m, const TcOperand &o) {
+    const int Ho = 1 << o.hs, Wo = 1 << o.ws, N = 1 << o.cs;
+    const int wb = Wo < 128 ? Wo : 128, hb = Ho < 128 / wb ? Ho : 128 / wb, nb = 128 / (wb * hb);
+    const unsigned box[4] = {8u, (unsigned)wb, (unsigned)hb, (unsigned)nb}, estr[4] = {1, 1, 1, 1};
+    return tmap4(m, o.p, N, Wo, Ho, o.nb, 2ull * N, 2ull * N * Wo, 2ull * N * Wo * Ho, box, estr);
+}
+
+// A row-major matrix [rows][cols] (cols contiguous) in boxes of `box_rows` rows by 8 columns.
+static bool tmap_matrix(CUtensorMap *m, const void *p, long long rows, long long cols, int box_rows) {
+    const unsigned box[4] = {8u, (unsigned)box_rows, 1, 1}, estr[4] = {1, 1, 1, 1};
+    return tmap4(m, p, cols, rows, 1, 1, 2ull * cols, 2ull * cols * rows, 2ull * cols * rows, box, estr);
+}
+
 // C(m, n) = sum_k A(m, k) B(n, k) on the tensor cores, K cut into `splits` slices (rounded to 64).
+// False when a tensor map cannot be built (nothing is launched then).
 template <int EPI, int BN, int LA, int LB>
-static void gemm(TcGemm g, int *err, cudaStream_t s, int splits = 1) {
+static bool gemm(TcGemm g, int *err, cudaStream_t s, int splits = 1) {
     constexpr int smem = tc_smem_bytes<BN>();
     static bool attr = false;  // per process; every GB300 of a box takes the same value
     if (!attr) {
@@ -792,8 +915,17 @@ static void gemm(TcGemm g, int *err, cudaStream_t s, int splits = 1) {
     g.mt = (g.M + kTcBM - 1) / kTcBM;
     g.nt = (g.N + BN - 1) / BN;
     g.units = EPI == EPI_DGRAD_MASK_BF16 ? 4 * g.mt : g.mt * g.nt * z;  // four parity classes
+    CUtensorMap ma, mb;
+    if (tc_a_tma<LA>()) {
+        // data gradient: dY in 128-pixel tiles, W [N_out][9 C] in 64-row boxes
+        if (!tmap_dy_tiles(&ma, g.a) || !tmap_matrix(&mb, g.b.p, 1 << g.b.cs, g.b.ld, kTcBK)) return false;
+    } else {
+        memset(&ma, 0, sizeof(ma));  // unused: these operands are gathered with cp.async
+        mb = ma;
+    }
     const int cap = 2 * upslam_sm_count();  // persistent: two CTAs per SM
-    gemm_tc_kernel<EPI, BN, LA, LB><<<g.units < cap ? g.units : cap, tc_threads<LA>(), smem, s>>>(g, err);
+    gemm_tc_kernel<EPI, BN, LA, LB><<<g.units < cap ? g.units : cap, tc_threads<LA>(), smem, s>>>(g, err, ma, mb);
+    return true;
 }
 
 }  // namespace upslam
@@ -828,6 +960,7 @@ extern "C" upslam_status upslam_cnn_forward(const float *d_params, const void *d
         pack_weights_kernel<<<grid1d((long long)N * K), 256, 0, s>>>(d_params + L.off_w[l], N * K, w.wb[l]);
         TcGemm g{};
         g.a = op_im2col(x, H, W, C);
+        g.a.nb = batch;
         g.b = op_dense(w.wb[l], K);
         g.M = batch * (H / 2) * (W / 2);
         g.N = N;
@@ -836,9 +969,10 @@ extern "C" upslam_status upslam_cnn_forward(const float *d_params, const void *d
         g.ldc = N;
         g.bias = d_params + L.off_b[l];
         // the staged-bias epilogue needs one column tile: BN = N
-        if (N == 32) gemm<EPI_BIAS_RELU_BF16, 32, LD_IM2COL_K, LD_DENSE_K>(g, w.err, s);
-        else if (N == 64) gemm<EPI_BIAS_RELU_BF16, 64, LD_IM2COL_K, LD_DENSE_K>(g, w.err, s);
-        else gemm<EPI_BIAS_RELU_BF16, 128, LD_IM2COL_K, LD_DENSE_K>(g, w.err, s);
+        const bool ok = N == 32   ? gemm<EPI_BIAS_RELU_BF16, 32, LD_IM2COL_K, LD_DENSE_K>(g, w.err, s)
+                        : N == 64 ? gemm<EPI_BIAS_RELU_BF16, 64, LD_IM2COL_K, LD_DENSE_K>(g, w.err, s)
+                                  : gemm<EPI_BIAS_RELU_BF16, 128, LD_IM2COL_K, LD_DENSE_K>(g, w.err, s);
+        if (!ok) return UPSLAM_ERR_CUDA;
         x = w.act[l];
         H /= 2;
         W /= 2;
@@ -879,6 +1013,7 @@ extern "C" upslam_status upslam_cnn_backward(const float *d_params, const void *
         // an appended feature f = K of ones yields db[n] = sum_p dY[p][n] in the same GEMM
         TcGemm gw{};
         gw.a = op_im2col(xin, H, W, C);
+        gw.a.nb = batch;
         gw.a.ones_row = K;
         gw.db = d_grads + L.off_b[l];
         gw.b = op_dense(w.dy[l], N);
@@ -894,14 +1029,16 @@ extern "C" upslam_status upslam_cnn_backward(const float *d_params, const void *
         int splits = (2 * sms + tiles - 1) / tiles;
         if (splits > ktiles / 16) splits = ktiles / 16;
         if (splits < 1) splits = 1;
-        if (N == 32) gemm<EPI_F32_RED_T, 32, LD_IM2COL_MN, LD_DENSE_MN>(gw, w.err, s, splits);
-        else if (N == 64) gemm<EPI_F32_RED_T, 64, LD_IM2COL_MN, LD_DENSE_MN>(gw, w.err, s, splits);
-        else gemm<EPI_F32_RED_T, 128, LD_IM2COL_MN, LD_DENSE_MN>(gw, w.err, s, splits);
+        const bool okw = N == 32   ? gemm<EPI_F32_RED_T, 32, LD_IM2COL_MN, LD_DENSE_MN>(gw, w.err, s, splits)
+                         : N == 64 ? gemm<EPI_F32_RED_T, 64, LD_IM2COL_MN, LD_DENSE_MN>(gw, w.err, s, splits)
+                                   : gemm<EPI_F32_RED_T, 128, LD_IM2COL_MN, LD_DENSE_MN>(gw, w.err, s, splits);
+        if (!okw) return UPSLAM_ERR_CUDA;
         if (l > 0) {
             // dY of the layer below = its ReLU mask x sum over the taps that read each input pixel of dY W,
             // one GEMM per parity class of the input pixels (no column matrix)
             TcGemm gd{};
             gd.a = op_dense(w.dy[l], N);
+            gd.a.nb = batch;
             gd.a.hs = ilog2(H / 2);
             gd.a.ws = ilog2(W / 2);
             gd.a.cs = ilog2(N);
@@ -913,9 +1050,10 @@ extern "C" upslam_status upslam_cnn_backward(const float *d_params, const void *
             gd.C = w.dy[l - 1];
             gd.ldc = C;
             gd.mask = w.act[l - 1];
-            if (C == 32) gemm<EPI_DGRAD_MASK_BF16, 32, LD_DY_TAPS_K, LD_W_TAPS_MN>(gd, w.err, s);
-            else if (C == 64) gemm<EPI_DGRAD_MASK_BF16, 64, LD_DY_TAPS_K, LD_W_TAPS_MN>(gd, w.err, s);
-            else gemm<EPI_DGRAD_MASK_BF16, 128, LD_DY_TAPS_K, LD_W_TAPS_MN>(gd, w.err, s);
+            const bool okd = C == 32   ? gemm<EPI_DGRAD_MASK_BF16, 32, LD_DY_TAPS_K, LD_W_TAPS_MN>(gd, w.err, s)
+                             : C == 64 ? gemm<EPI_DGRAD_MASK_BF16, 64, LD_DY_TAPS_K, LD_W_TAPS_MN>(gd, w.err, s)
+                                       : gemm<EPI_DGRAD_MASK_BF16, 128, LD_DY_TAPS_K, LD_W_TAPS_MN>(gd, w.err, s);
+            if (!okd) return UPSLAM_ERR_CUDA;
         }
     }
     UPSLAM_CHECK_LAUNCH();
