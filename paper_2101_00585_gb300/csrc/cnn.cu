@@ -608,22 +608,38 @@ __global__ void __launch_bounds__(tc_threads<LA>(), 2)
 
 // ----------------------------------------------------------------------------- layout kernels
 
-// Global mean over [B, HW, C] (BF16) -> g [B, C] (FP32), then the linear head out = g W^T + b.
-__global__ void pool_head_kernel(const __nv_bfloat16 *__restrict__ x, int B, int HW, int C, const float *wf,
-                                 const float *bf, float *g, float *out) {
-    const int b = blockIdx.x;
+// Global mean over [B, HW, C = 128] (BF16) -> g [B, C] (FP32), then the linear head out = g W^T + b.
+// 128 threads per sample: thread t sums channels 8 (t % 16) .. + 7 over pixels t / 16, t / 16 + 8, ... with
+// 16-byte loads; the eight partial sums of each channel are folded in shared memory.
+__global__ void __launch_bounds__(128) pool_head_kernel(const __nv_bfloat16 *__restrict__ x, int B, int HW, int C,
+                                                        const float *wf, const float *bf, float *g, float *out) {
+    const int b = blockIdx.x, t = threadIdx.x, c8 = (t & 15) * 8, p0 = t >> 4;
+    __shared__ float part[8][128];
     __shared__ float gs[128];
-    for (int c = threadIdx.x; c < C; c += blockDim.x) {
-        float s = 0.0f;
-        for (int p = 0; p < HW; ++p) s += __bfloat162float(x[((long long)b * HW + p) * C + c]);
-        gs[c] = s / HW;
-        g[b * C + c] = s / HW;
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int p = p0; p < HW; p += 8) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(x + ((long long)b * HW + p) * C + c8));
+        const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&v);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float2 f = __bfloat1622float2(h[q]);
+            acc[2 * q] += f.x;
+            acc[2 * q + 1] += f.y;
+        }
     }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) part[p0][c8 + q] = acc[q];
     __syncthreads();
-    if (threadIdx.x < 6) {
-        float o = bf[threadIdx.x];
-        for (int c = 0; c < C; ++c) o += wf[threadIdx.x * C + c] * gs[c];
-        out[b * 6 + threadIdx.x] = o;
+    float sum = 0.0f;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) sum += part[r][t];
+    gs[t] = sum / HW;
+    g[b * C + t] = sum / HW;
+    __syncthreads();
+    if (t < 6) {
+        float o = bf[t];
+        for (int c = 0; c < C; ++c) o += wf[t * C + c] * gs[c];
+        out[b * 6 + t] = o;
     }
 }
 
