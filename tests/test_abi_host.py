@@ -118,3 +118,16 @@ def test_product_path_has_no_oracle_or_cpu_fallback():
             _abi.lib(build_if_missing=False)
         finally:
             _abi._lib, _abi.LIB_PATH = saved
+
+
+def test_cnn_workspace_and_error_word_offsets():
+    """The pose network's workspace size grows with the batch and its error word is the last 256-byte block."""
+    L = up.lib()
+    assert L.upslam_cnn_workspace_bytes(0) == 0 and L.upslam_cnn_error_offset(0) == 0
+    prev = 0
+    for b in (1, 3, 64, 256):
+        ws = L.upslam_cnn_workspace_bytes(b)
+        off = L.upslam_cnn_error_offset(b)
+        assert ws > prev and ws % 256 == 0
+        assert off == ws - 256 and off % 256 == 0
+        prev = ws
