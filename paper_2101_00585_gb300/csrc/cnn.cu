@@ -101,6 +101,13 @@ __device__ __forceinline__ unsigned long long umma_desc(unsigned addr, unsigned 
            ((unsigned long long)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
+// The same for a K-major tile written by TMA with the 128-byte swizzle (rows of 64 BF16, 8-row groups 1024
+// bytes apart, tile 1024-byte aligned): layout type 2 in bits 61-63, the leading offset unused.
+__device__ __forceinline__ unsigned long long umma_desc_sw128(unsigned addr) {
+    return (unsigned long long)((addr >> 4) & 0x3FFFu) | (1ull << 16) | ((unsigned long long)(1024 >> 4) << 32) |
+           (1ull << 46) | (2ull << 61);
+}
+
 __device__ __forceinline__ void mbar_expect_tx(unsigned mbar, unsigned bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
 }
@@ -234,8 +241,9 @@ __device__ __forceinline__ TcUnit tc_unit(const TcGemm &g, int u) {
 
 // TMA loads of one K step of the data gradient (tensor maps built on the host; one 16-byte-wide box per chunk
 // of 8; coordinates past the tensor read as zeros):
-//   A, LD_DY_TAPS_K: class pixels (b, i, j) from t.r0a by (tap, n) from k0, K-major chunk j = [128 rows][16 B]
-//     at j * 2048 (LBO 2048, SBO 128); a tap's offset pixels past dY read zeros;
+//   A, LD_DY_TAPS_K: class pixels (b, i, j) from t.r0a by (tap, n) from k0: one box [128 rows][128 B] in the
+//     128-byte-swizzled K-major layout (SBO 1024; an MMA's 16 k start 32 bytes further along the row); a tap's
+//     offset pixels past dY read zeros;
 //   B, LD_W_TAPS_MN, at stage + 16 KB: chunk j (8 channels) = [64 k][16 B] at j * 1024 (LBO 128, SBO 1024).
 // With these dense boxes TMA beats the cp.async gather; for the im2col operands (8-channel boxes stepping 2
 // pixels) it measured slower, so the forward and weight-gradient GEMMs gather with cp.async.
@@ -246,8 +254,7 @@ __device__ __forceinline__ void tc_tma_a(unsigned stage, unsigned mbar, const Tc
     const int doy = ((t.cls >> 1) + 1 - ky) >> 1, dox = ((t.cls & 1) + 1 - kx) >> 1;
     const int j0 = t.r0a & ((1 << a.ws) - 1), i0 = (t.r0a >> a.ws) & ((1 << a.hs) - 1), b0 = t.r0a >> (a.ws + a.hs);
     const int n0 = k0 & ((1 << a.cs) - 1);
-#pragma unroll 1
-    for (int j = 0; j < 8; ++j) tma_load4(stage + j * 2048, ma, n0 + 8 * j, j0 + dox, i0 + doy, b0, mbar);
+    tma_load4(stage, ma, n0, j0 + dox, i0 + doy, b0, mbar);
 }
 
 template <int BN>
@@ -548,7 +555,8 @@ __global__ void __launch_bounds__(tc_threads<LA>(), 2)
                     const int k0 = t.kbeg + k * kTcBK;
                     const int nk = min(kTcBK / 16, (t.kend - k0 + 15) / 16);
                     for (int kk = 0; kk < nk; ++kk) {
-                        const unsigned long long ad = umma_desc(a0 + kk * 2 * kALbo, kALbo, kASbo);
+                        const unsigned long long ad =
+                            A_TMA ? umma_desc_sw128(a0 + kk * 32) : umma_desc(a0 + kk * 2 * kALbo, kALbo, kASbo);
                         const unsigned long long bd = umma_desc(b0 + kk * 2 * kBLbo, kBLbo, kBSbo);
                         const unsigned accum = (k > 0 || kk > 0) ? 1u : 0u;
                         asm volatile(
@@ -889,23 +897,26 @@ static PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
 // elements read as zeros.
 static bool tmap4(CUtensorMap *m, const void *base, unsigned long long d0, unsigned long long d1, unsigned long long d2,
                   unsigned long long d3, unsigned long long s1, unsigned long long s2, unsigned long long s3,
-                  const unsigned box[4], const unsigned estr[4]) {
+                  const unsigned box[4], const unsigned estr[4],
+                  CUtensorMapSwizzle swz = CU_TENSOR_MAP_SWIZZLE_NONE) {
     const PFN_cuTensorMapEncodeTiled_v12000 enc = tmap_encoder();
     if (!enc) return false;
     const cuuint64_t dims[4] = {d0, d1, d2, d3};
     const cuuint64_t strides[3] = {s1, s2, s3};
     const cuuint32_t bx[4] = {box[0], box[1], box[2], box[3]}, es[4] = {estr[0], estr[1], estr[2], estr[3]};
     return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(base), dims, strides, bx, es,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// dY [B][Ho][Wo][N] in boxes of 128 consecutive pixels by 8 channels.
+// dY [B][Ho][Wo][N] in boxes of 128 consecutive pixels by 64 channels (one 128-byte row per pixel), written
+// with the 128-byte swizzle: one request per pixel row instead of eight.
 static bool tmap_dy_tiles(CUtensorMap *m, const TcOperand &o) {
     const int Ho = 1 << o.hs, Wo = 1 << o.ws, N = 1 << o.cs;
     const int wb = Wo < 128 ? Wo : 128, hb = Ho < 128 / wb ? Ho : 128 / wb, nb = 128 / (wb * hb);
-    const unsigned box[4] = {8u, (unsigned)wb, (unsigned)hb, (unsigned)nb}, estr[4] = {1, 1, 1, 1};
-    return tmap4(m, o.p, N, Wo, Ho, o.nb, 2ull * N, 2ull * N * Wo, 2ull * N * Wo * Ho, box, estr);
+    const unsigned box[4] = {64u, (unsigned)wb, (unsigned)hb, (unsigned)nb}, estr[4] = {1, 1, 1, 1};
+    return tmap4(m, o.p, N, Wo, Ho, o.nb, 2ull * N, 2ull * N * Wo, 2ull * N * Wo * Ho, box, estr,
+                 CU_TENSOR_MAP_SWIZZLE_128B);
 }
 
 // A row-major matrix [rows][cols] (cols contiguous) in boxes of `box_rows` rows by 8 columns.
