@@ -101,11 +101,12 @@ __device__ __forceinline__ unsigned long long umma_desc(unsigned addr, unsigned 
            ((unsigned long long)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
-// The same for a K-major tile written by TMA with the 128-byte swizzle (rows of 64 BF16, 8-row groups 1024
-// bytes apart, tile 1024-byte aligned): layout type 2 in bits 61-63, the leading offset unused.
-__device__ __forceinline__ unsigned long long umma_desc_sw128(unsigned addr) {
-    return (unsigned long long)((addr >> 4) & 0x3FFFu) | (1ull << 16) | ((unsigned long long)(1024 >> 4) << 32) |
-           (1ull << 46) | (2ull << 61);
+// The same for a tile written by TMA with a swizzle (layout type in bits 61-63: 2 = 128-byte, 4 = 64-byte;
+// tile aligned to the swizzle atom).  K-major: rows of 64 BF16, 8-row groups `sbo` apart, the leading offset
+// unused.  MN-major: rows along K of 64 (or 32) BF16, 8-row K groups `sbo` apart, atoms along M/N `lbo` apart.
+__device__ __forceinline__ unsigned long long umma_desc_sw(unsigned addr, unsigned lbo, unsigned sbo, unsigned type) {
+    return (unsigned long long)((addr >> 4) & 0x3FFFu) | ((unsigned long long)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((unsigned long long)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46) | ((unsigned long long)type << 61);
 }
 
 __device__ __forceinline__ void mbar_expect_tx(unsigned mbar, unsigned bytes) {
@@ -244,7 +245,8 @@ __device__ __forceinline__ TcUnit tc_unit(const TcGemm &g, int u) {
 //   A, LD_DY_TAPS_K: class pixels (b, i, j) from t.r0a by (tap, n) from k0: one box [128 rows][128 B] in the
 //     128-byte-swizzled K-major layout (SBO 1024; an MMA's 16 k start 32 bytes further along the row); a tap's
 //     offset pixels past dY read zeros;
-//   B, LD_W_TAPS_MN, at stage + 16 KB: chunk j (8 channels) = [64 k][16 B] at j * 1024 (LBO 128, SBO 1024).
+//   B, LD_W_TAPS_MN, at stage + 16 KB: per 64 channels one box [64 k][128 B] (128-byte swizzle), or for
+//     BN = 32 one box [64 k][64 B] (64-byte swizzle).
 // With these dense boxes TMA beats the cp.async gather; for the im2col operands (8-channel boxes stepping 2
 // pixels) it measured slower, so the forward and weight-gradient GEMMs gather with cp.async.
 __device__ __forceinline__ void tc_tma_a(unsigned stage, unsigned mbar, const TcOperand &a, const CUtensorMap *ma,
@@ -260,13 +262,14 @@ __device__ __forceinline__ void tc_tma_a(unsigned stage, unsigned mbar, const Tc
 template <int BN>
 __device__ __forceinline__ void tc_tma_b(unsigned sb, unsigned mbar, const TcOperand &b, const CUtensorMap *mb,
                                          const TcUnit &t, int k0) {
-    // W[n][(3 ky + kx) C + c]: k = (tap, n) from k0, rows = c from t.r0b in chunks of 8
+    // W[n][(3 ky + kx) C + c]: k = (tap, n) from k0, rows = c from t.r0b; boxes of 64 n by 64 c (32 c when
+    // BN = 32), swizzled rows along k, one box per 64 channels
     int ky, kx;
     class_tap(t.cls, k0 >> b.cs, ky, kx);
     const int n0 = k0 & ((1 << b.cs) - 1);
 #pragma unroll 1
-    for (int j = 0; j < BN / 8; ++j)
-        tma_load4(sb + j * 1024, mb, (3 * ky + kx) * b.rows + t.r0b + 8 * j, n0, 0, 0, mbar);
+    for (int h = 0; h < (BN + 63) / 64; ++h)
+        tma_load4(sb + h * 8192, mb, (3 * ky + kx) * b.rows + t.r0b + 64 * h, n0, 0, 0, mbar);
 }
 
 // Stages that fit in about 100 KB of shared memory (two CTAs per SM), at most 8.
@@ -555,9 +558,15 @@ __global__ void __launch_bounds__(tc_threads<LA>(), 2)
                     const int k0 = t.kbeg + k * kTcBK;
                     const int nk = min(kTcBK / 16, (t.kend - k0 + 15) / 16);
                     for (int kk = 0; kk < nk; ++kk) {
+                        // TMA tiles: A K-major 128-byte swizzle (an MMA's 16 k start 32 bytes along the row); B
+                        // MN-major, 128-byte swizzle (BN >= 64: 8-row K groups 1024 B apart, 64-channel atoms
+                        // 8 KB apart) or 64-byte swizzle (BN = 32: K groups 512 B apart); an MMA spans two K groups
                         const unsigned long long ad =
-                            A_TMA ? umma_desc_sw128(a0 + kk * 32) : umma_desc(a0 + kk * 2 * kALbo, kALbo, kASbo);
-                        const unsigned long long bd = umma_desc(b0 + kk * 2 * kBLbo, kBLbo, kBSbo);
+                            A_TMA ? umma_desc_sw(a0 + kk * 32, 16, 1024, 2) : umma_desc(a0 + kk * 2 * kALbo, kALbo, kASbo);
+                        const unsigned long long bd =
+                            !A_TMA ? umma_desc(b0 + kk * 2 * kBLbo, kBLbo, kBSbo)
+                            : BN == 32 ? umma_desc_sw(b0 + kk * 1024, 512, 512, 4)
+                                       : umma_desc_sw(b0 + kk * 2048, 8192, 1024, 2);
                         const unsigned accum = (k > 0 || kk > 0) ? 1u : 0u;
                         asm volatile(
                             "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
@@ -919,10 +928,11 @@ static bool tmap_dy_tiles(CUtensorMap *m, const TcOperand &o) {
                  CU_TENSOR_MAP_SWIZZLE_128B);
 }
 
-// A row-major matrix [rows][cols] (cols contiguous) in boxes of `box_rows` rows by 8 columns.
-static bool tmap_matrix(CUtensorMap *m, const void *p, long long rows, long long cols, int box_rows) {
-    const unsigned box[4] = {8u, (unsigned)box_rows, 1, 1}, estr[4] = {1, 1, 1, 1};
-    return tmap4(m, p, cols, rows, 1, 1, 2ull * cols, 2ull * cols * rows, 2ull * cols * rows, box, estr);
+// A row-major matrix [rows][cols] (cols contiguous) in boxes of `box_rows` rows by `box_cols` columns.
+static bool tmap_matrix(CUtensorMap *m, const void *p, long long rows, long long cols, int box_rows, int box_cols,
+                        CUtensorMapSwizzle swz) {
+    const unsigned box[4] = {(unsigned)box_cols, (unsigned)box_rows, 1, 1}, estr[4] = {1, 1, 1, 1};
+    return tmap4(m, p, cols, rows, 1, 1, 2ull * cols, 2ull * cols * rows, 2ull * cols * rows, box, estr, swz);
 }
 
 // C(m, n) = sum_k A(m, k) B(n, k) on the tensor cores, K cut into `splits` slices (rounded to 64).
@@ -945,7 +955,11 @@ static bool gemm(TcGemm g, int *err, cudaStream_t s, int splits = 1) {
     CUtensorMap ma, mb;
     if (tc_a_tma<LA>()) {
         // data gradient: dY in 128-pixel tiles, W [N_out][9 C] in 64-row boxes
-        if (!tmap_dy_tiles(&ma, g.a) || !tmap_matrix(&mb, g.b.p, 1 << g.b.cs, g.b.ld, kTcBK)) return false;
+        const bool narrow = BN < 64;
+        if (!tmap_dy_tiles(&ma, g.a) ||
+            !tmap_matrix(&mb, g.b.p, 1 << g.b.cs, g.b.ld, kTcBK, narrow ? 32 : 64,
+                         narrow ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B))
+            return false;
     } else {
         memset(&ma, 0, sizeof(ma));  // unused: these operands are gathered with cp.async
         mb = ma;
