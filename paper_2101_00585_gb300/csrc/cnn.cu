@@ -62,7 +62,16 @@ __host__ __device__ constexpr int cnn_co(int l) { return l == 0 ? 32 : (l == 1 ?
 // Every wait is bounded; a wait that gives up sets *err and the CTA stops.
 
 enum { EPI_BIAS_RELU_BF16 = 0, EPI_F32_RED_T = 1, EPI_DGRAD_MASK_BF16 = 2 };
-enum { LD_DENSE_K = 0, LD_IM2COL_K = 1, LD_DENSE_MN = 2, LD_IM2COL_MN = 3, LD_DY_TAPS_K = 4, LD_W_TAPS_MN = 5 };
+enum {
+    LD_DENSE_K = 0,
+    LD_IM2COL_K = 1,
+    LD_DENSE_MN = 2,
+    LD_IM2COL_MN = 3,
+    LD_DY_TAPS_K = 4,   // TMA: dY rows of one tap (data gradient)
+    LD_W_TAPS_MN = 5,   // TMA: W per tap, MN-major (data gradient)
+    LD_IM2COL_KT = 6,   // TMA: im2col of an input with C >= 64, one tap's 64 channels per K step (forward)
+    LD_DENSE_KT = 7     // TMA: weights [N][K], K-major (forward)
+};
 
 struct TcOperand {
     const __nv_bfloat16 *p;
@@ -203,7 +212,7 @@ __device__ __forceinline__ void class_tap(int q, int t, int &ky, int &kx) {
 // thread; the forward and weight-gradient operands by eight cp.async warps (their address arithmetic and copy
 // issue set the pace).
 template <int LA>
-constexpr bool tc_a_tma() { return LA == LD_DY_TAPS_K; }
+constexpr bool tc_a_tma() { return LA == LD_DY_TAPS_K || LA == LD_IM2COL_KT; }
 template <int LA>
 constexpr int tc_prod() { return tc_a_tma<LA>() ? 1 : 8; }
 template <int LA>
@@ -249,8 +258,18 @@ __device__ __forceinline__ TcUnit tc_unit(const TcGemm &g, int u) {
 //     BN = 32 one box [64 k][64 B] (64-byte swizzle).
 // With these dense boxes TMA beats the cp.async gather; for the im2col operands (8-channel boxes stepping 2
 // pixels) it measured slower, so the forward and weight-gradient GEMMs gather with cp.async.
+template <int LA>
 __device__ __forceinline__ void tc_tma_a(unsigned stage, unsigned mbar, const TcOperand &a, const CUtensorMap *ma,
                                          const TcUnit &t, int k0) {
+    if (LA == LD_IM2COL_KT) {
+        // rows: 128 output pixels from t.r0a (whole output rows); k: 64 channels of one tap (C >= 64), read as
+        // one box stepping 2 along W and H from (2 ox0 + kx - 1, 2 oy0 + ky - 1); the padding reads zeros
+        const int wo = a.ws - 1, ho = a.hs - 1;
+        const int ox0 = t.r0a & ((1 << wo) - 1), oy0 = (t.r0a >> wo) & ((1 << ho) - 1), b0 = t.r0a >> (wo + ho);
+        const int tap = k0 >> a.cs, ky = tap / 3, kx = tap - 3 * ky;
+        tma_load4(stage, ma, k0 & ((1 << a.cs) - 1), 2 * ox0 + kx - 1, 2 * oy0 + ky - 1, b0, mbar);
+        return;
+    }
     int ky, kx;
     class_tap(t.cls, k0 >> a.cs, ky, kx);
     const int doy = ((t.cls >> 1) + 1 - ky) >> 1, dox = ((t.cls & 1) + 1 - kx) >> 1;
@@ -259,9 +278,14 @@ __device__ __forceinline__ void tc_tma_a(unsigned stage, unsigned mbar, const Tc
     tma_load4(stage, ma, n0, j0 + dox, i0 + doy, b0, mbar);
 }
 
-template <int BN>
+template <int LB, int BN>
 __device__ __forceinline__ void tc_tma_b(unsigned sb, unsigned mbar, const TcOperand &b, const CUtensorMap *mb,
                                          const TcUnit &t, int k0) {
+    if (LB == LD_DENSE_KT) {
+        // weights [N][K]: BN rows from t.r0b by 64 k from k0, one 128-byte-swizzled box
+        tma_load4(sb, mb, k0, t.r0b, 0, 0, mbar);
+        return;
+    }
     // W[n][(3 ky + kx) C + c]: k = (tap, n) from k0, rows = c from t.r0b; boxes of 64 n by 64 c (32 c when
     // BN = 32), swizzled rows along k, one box per 64 channels
     int ky, kx;
@@ -488,8 +512,8 @@ __global__ void __launch_bounds__(tc_threads<LA>(), 2)
                     const int k0 = t.kbeg + k * kTcBK;
                     if (A_TMA) {
                         mbar_expect_tx(fb, kTxBytes);
-                        tc_tma_a(stage, fb, g.a, &tma_a, t, k0);
-                        tc_tma_b<BN>(stage + kA, fb, g.b, &tma_b, t, k0);
+                        tc_tma_a<LA>(stage, fb, g.a, &tma_a, t, k0);
+                        tc_tma_b<LB, BN>(stage + kA, fb, g.b, &tma_b, t, k0);
                     } else {
                         const int kread = k0 + 16 * min(kTcBK / 16, (t.kend - k0 + 15) / 16);
                         tc_gather<LA, kTcBM, kProd>(stage, g.a, t.r0a, k0, t.kend, kread, ptid);
@@ -564,9 +588,10 @@ __global__ void __launch_bounds__(tc_threads<LA>(), 2)
                         const unsigned long long ad =
                             A_TMA ? umma_desc_sw(a0 + kk * 32, 16, 1024, 2) : umma_desc(a0 + kk * 2 * kALbo, kALbo, kASbo);
                         const unsigned long long bd =
-                            !A_TMA ? umma_desc(b0 + kk * 2 * kBLbo, kBLbo, kBSbo)
-                            : BN == 32 ? umma_desc_sw(b0 + kk * 1024, 512, 512, 4)
-                                       : umma_desc_sw(b0 + kk * 2048, 8192, 1024, 2);
+                            !A_TMA                ? umma_desc(b0 + kk * 2 * kBLbo, kBLbo, kBSbo)
+                            : LB == LD_DENSE_KT  ? umma_desc_sw(b0 + kk * 32, 16, 1024, 2)
+                            : BN == 32           ? umma_desc_sw(b0 + kk * 1024, 512, 512, 4)
+                                                 : umma_desc_sw(b0 + kk * 2048, 8192, 1024, 2);
                         const unsigned accum = (k > 0 || kk > 0) ? 1u : 0u;
                         asm volatile(
                             "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
@@ -928,6 +953,16 @@ static bool tmap_dy_tiles(CUtensorMap *m, const TcOperand &o) {
                  CU_TENSOR_MAP_SWIZZLE_128B);
 }
 
+// An NHWC input [B][H][W][C] (C >= 64) seen by a 3x3 stride-2 convolution: boxes of 128 consecutive output
+// pixels (whole output rows) by 64 channels, stepping 2 along W and H, written with the 128-byte swizzle.
+static bool tmap_im2col_wide(CUtensorMap *m, const TcOperand &o) {
+    const int H = 1 << o.hs, W = 1 << o.ws, C = 1 << o.cs, Ho = H / 2, Wo = W / 2;
+    const int wb = Wo < 128 ? Wo : 128, hb = Ho < 128 / wb ? Ho : 128 / wb, nb = 128 / (wb * hb);
+    const unsigned box[4] = {64u, 2u * wb, 2u * hb, (unsigned)nb}, estr[4] = {1, 2, 2, 1};
+    return tmap4(m, o.p, C, W, H, o.nb, 2ull * C, 2ull * C * W, 2ull * C * W * H, box, estr,
+                 CU_TENSOR_MAP_SWIZZLE_128B);
+}
+
 // A row-major matrix [rows][cols] (cols contiguous) in boxes of `box_rows` rows by `box_cols` columns.
 static bool tmap_matrix(CUtensorMap *m, const void *p, long long rows, long long cols, int box_rows, int box_cols,
                         CUtensorMapSwizzle swz) {
@@ -953,7 +988,12 @@ static bool gemm(TcGemm g, int *err, cudaStream_t s, int splits = 1) {
     g.nt = (g.N + BN - 1) / BN;
     g.units = EPI == EPI_DGRAD_MASK_BF16 ? 4 * g.mt : g.mt * g.nt * z;  // four parity classes
     CUtensorMap ma, mb;
-    if (tc_a_tma<LA>()) {
+    if (LA == LD_IM2COL_KT) {
+        // forward with C >= 64: the input in 128-pixel boxes of 64 channels, the weights [N][9 C] in BN-row boxes
+        if (!tmap_im2col_wide(&ma, g.a) ||
+            !tmap_matrix(&mb, g.b.p, g.N, g.b.ld, BN, 64, CU_TENSOR_MAP_SWIZZLE_128B))
+            return false;
+    } else if (tc_a_tma<LA>()) {
         // data gradient: dY in 128-pixel tiles, W [N_out][9 C] in 64-row boxes
         const bool narrow = BN < 64;
         if (!tmap_dy_tiles(&ma, g.a) ||
@@ -1010,9 +1050,10 @@ extern "C" upslam_status upslam_cnn_forward(const float *d_params, const void *d
         g.ldc = N;
         g.bias = d_params + L.off_b[l];
         // the staged-bias epilogue needs one column tile: BN = N
-        const bool ok = N == 32   ? gemm<EPI_BIAS_RELU_BF16, 32, LD_IM2COL_K, LD_DENSE_K>(g, w.err, s)
-                        : N == 64 ? gemm<EPI_BIAS_RELU_BF16, 64, LD_IM2COL_K, LD_DENSE_K>(g, w.err, s)
-                                  : gemm<EPI_BIAS_RELU_BF16, 128, LD_IM2COL_K, LD_DENSE_K>(g, w.err, s);
+        // layers with C >= 64 (N = 128) load through TMA; the 8- and 32-channel inputs are gathered
+        const bool ok = C >= 64   ? gemm<EPI_BIAS_RELU_BF16, 128, LD_IM2COL_KT, LD_DENSE_KT>(g, w.err, s)
+                        : N == 32 ? gemm<EPI_BIAS_RELU_BF16, 32, LD_IM2COL_K, LD_DENSE_K>(g, w.err, s)
+                                  : gemm<EPI_BIAS_RELU_BF16, 64, LD_IM2COL_K, LD_DENSE_K>(g, w.err, s);
         if (!ok) return UPSLAM_ERR_CUDA;
         x = w.act[l];
         H /= 2;
