@@ -70,7 +70,9 @@ enum {
     LD_DY_TAPS_K = 4,   // TMA: dY rows of one tap (data gradient)
     LD_W_TAPS_MN = 5,   // TMA: W per tap, MN-major (data gradient)
     LD_IM2COL_KT = 6,   // TMA: im2col of an input with C >= 64, one tap's 64 channels per K step (forward)
-    LD_DENSE_KT = 7     // TMA: weights [N][K], K-major (forward)
+    LD_DENSE_KT = 7,    // TMA: weights [N][K], K-major (forward)
+    LD_IM2COL_MNT = 8,  // TMA: im2col of an input with C >= 64, MN-major (weight gradient)
+    LD_DENSE_MNT = 9    // TMA: dY [P][N], MN-major (weight gradient)
 };
 
 struct TcOperand {
@@ -86,6 +88,15 @@ struct TcOperand {
 // A 16-byte chunk holding (1, 0, 0, 0, 0, 0, 0, 0) in BF16: the source of an appended feature of ones, which makes
 // the weight-gradient GEMM also produce the bias gradient sum_p dY[p][n].
 static __device__ __align__(16) const unsigned short kUnitChunk[8] = {0x3F80, 0, 0, 0, 0, 0, 0, 0};
+
+// The same feature for the TMA weight gradient: 64 pixels by 64 features, feature 0 = 1, as one box.
+struct OnesBox {
+    unsigned short v[64 * 64];
+    constexpr OnesBox() : v() {
+        for (int i = 0; i < 64; ++i) v[64 * i] = 0x3F80;
+    }
+};
+static __device__ __align__(1024) const OnesBox kOnesBox;
 
 struct TcGemm {
     TcOperand a, b;
@@ -212,7 +223,7 @@ __device__ __forceinline__ void class_tap(int q, int t, int &ky, int &kx) {
 // thread; the forward and weight-gradient operands by eight cp.async warps (their address arithmetic and copy
 // issue set the pace).
 template <int LA>
-constexpr bool tc_a_tma() { return LA == LD_DY_TAPS_K || LA == LD_IM2COL_KT; }
+constexpr bool tc_a_tma() { return LA == LD_DY_TAPS_K || LA == LD_IM2COL_KT || LA == LD_IM2COL_MNT; }
 template <int LA>
 constexpr int tc_prod() { return tc_a_tma<LA>() ? 1 : 8; }
 template <int LA>
@@ -260,7 +271,31 @@ __device__ __forceinline__ TcUnit tc_unit(const TcGemm &g, int u) {
 // pixels) it measured slower, so the forward and weight-gradient GEMMs gather with cp.async.
 template <int LA>
 __device__ __forceinline__ void tc_tma_a(unsigned stage, unsigned mbar, const TcOperand &a, const CUtensorMap *ma,
-                                         const TcUnit &t, int k0) {
+                                         const CUtensorMap *mo, const TcUnit &t, int k0) {
+    if (LA == LD_IM2COL_MNT) {
+        // k: 64 pixels from k0; rows: features t.r0a.. as two 64-channel boxes, [64 k][128 B] each, 8 KB apart
+        // (the appended feature of ones from mo; features past it read zeros from image nb)
+        const int wo = a.ws - 1, ho = a.hs - 1;
+        const int ox0 = k0 & ((1 << wo) - 1), oy0 = (k0 >> wo) & ((1 << ho) - 1), b0 = k0 >> (wo + ho);
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+            const int f = t.r0a + 64 * h;
+            if (f == a.ones_row) {
+                tma_load4(stage + h * 8192, mo, 0, 0, 0, 0, mbar);
+                continue;
+            }
+            int c0 = 0, c1 = 0, c2 = 0, c3 = a.nb;
+            if (f < a.kf) {
+                const int tap = f >> a.cs, ky = tap / 3, kx = tap - 3 * ky;
+                c0 = f & ((1 << a.cs) - 1);
+                c1 = 2 * ox0 + kx - 1;
+                c2 = 2 * oy0 + ky - 1;
+                c3 = b0;
+            }
+            tma_load4(stage + h * 8192, ma, c0, c1, c2, c3, mbar);
+        }
+        return;
+    }
     if (LA == LD_IM2COL_KT) {
         // rows: 128 output pixels from t.r0a (whole output rows); k: 64 channels of one tap (C >= 64), read as
         // one box stepping 2 along W and H from (2 ox0 + kx - 1, 2 oy0 + ky - 1); the padding reads zeros
@@ -284,6 +319,12 @@ __device__ __forceinline__ void tc_tma_b(unsigned sb, unsigned mbar, const TcOpe
     if (LB == LD_DENSE_KT) {
         // weights [N][K]: BN rows from t.r0b by 64 k from k0, one 128-byte-swizzled box
         tma_load4(sb, mb, k0, t.r0b, 0, 0, mbar);
+        return;
+    }
+    if (LB == LD_DENSE_MNT) {
+        // dY [P][N]: k = 64 pixels from k0, rows = channels from t.r0b in 64-channel boxes 8 KB apart
+#pragma unroll 1
+        for (int h = 0; h < BN / 64; ++h) tma_load4(sb + h * 8192, mb, t.r0b + 64 * h, k0, 0, 0, mbar);
         return;
     }
     // W[n][(3 ky + kx) C + c]: k = (tap, n) from k0, rows = c from t.r0b; boxes of 64 n by 64 c (32 c when
@@ -450,7 +491,7 @@ __device__ __forceinline__ void tc_epilogue(const TcGemm &g, const TcUnit &cur, 
 template <int EPI, int BN, int LA, int LB>
 __global__ void __launch_bounds__(tc_threads<LA>(), 2)
     gemm_tc_kernel(TcGemm g, int *err, const __grid_constant__ CUtensorMap tma_a,
-                   const __grid_constant__ CUtensorMap tma_b) {
+                   const __grid_constant__ CUtensorMap tma_b, const __grid_constant__ CUtensorMap tma_one) {
     constexpr int S = tc_stages<BN>();
     static_assert(S >= 2 && S <= 8, "stage ring");
     constexpr bool A_TMA = tc_a_tma<LA>();
@@ -458,8 +499,8 @@ __global__ void __launch_bounds__(tc_threads<LA>(), 2)
     constexpr int kLag = S - 2;  // cp.async groups a gather thread keeps in flight before signalling a stage
     constexpr int kA = kTcBM * kTcBK * 2, kStage = (kTcBM + BN) * kTcBK * 2;
     constexpr unsigned kTxBytes = (unsigned)kStage;  // TMA boxes are written in full (zeros outside)
-    constexpr bool A_MN = LA == LD_IM2COL_MN;
-    constexpr bool B_MN = LB == LD_DENSE_MN || LB == LD_W_TAPS_MN;
+    constexpr bool A_MN = LA == LD_IM2COL_MN || LA == LD_IM2COL_MNT;
+    constexpr bool B_MN = LB == LD_DENSE_MN || LB == LD_W_TAPS_MN || LB == LD_DENSE_MNT;
     // descriptor byte offsets (leading = along K, stride = along M/N); an MMA (16 k) advances two core
     // matrices along K
     constexpr unsigned kALbo = A_TMA ? 2048 : 128, kASbo = A_TMA ? 128 : 1024;
@@ -512,7 +553,7 @@ __global__ void __launch_bounds__(tc_threads<LA>(), 2)
                     const int k0 = t.kbeg + k * kTcBK;
                     if (A_TMA) {
                         mbar_expect_tx(fb, kTxBytes);
-                        tc_tma_a<LA>(stage, fb, g.a, &tma_a, t, k0);
+                        tc_tma_a<LA>(stage, fb, g.a, &tma_a, &tma_one, t, k0);
                         tc_tma_b<LB, BN>(stage + kA, fb, g.b, &tma_b, t, k0);
                     } else {
                         const int kread = k0 + 16 * min(kTcBK / 16, (t.kend - k0 + 15) / 16);
@@ -586,10 +627,13 @@ __global__ void __launch_bounds__(tc_threads<LA>(), 2)
                         // MN-major, 128-byte swizzle (BN >= 64: 8-row K groups 1024 B apart, 64-channel atoms
                         // 8 KB apart) or 64-byte swizzle (BN = 32: K groups 512 B apart); an MMA spans two K groups
                         const unsigned long long ad =
-                            A_TMA ? umma_desc_sw(a0 + kk * 32, 16, 1024, 2) : umma_desc(a0 + kk * 2 * kALbo, kALbo, kASbo);
+                            !A_TMA               ? umma_desc(a0 + kk * 2 * kALbo, kALbo, kASbo)
+                            : LA == LD_IM2COL_MNT ? umma_desc_sw(a0 + kk * 2048, 8192, 1024, 2)
+                                                  : umma_desc_sw(a0 + kk * 32, 16, 1024, 2);
                         const unsigned long long bd =
                             !A_TMA                ? umma_desc(b0 + kk * 2 * kBLbo, kBLbo, kBSbo)
                             : LB == LD_DENSE_KT  ? umma_desc_sw(b0 + kk * 32, 16, 1024, 2)
+                            : LB == LD_DENSE_MNT ? umma_desc_sw(b0 + kk * 2048, 8192, 1024, 2)
                             : BN == 32           ? umma_desc_sw(b0 + kk * 1024, 512, 512, 4)
                                                  : umma_desc_sw(b0 + kk * 2048, 8192, 1024, 2);
                         const unsigned accum = (k > 0 || kk > 0) ? 1u : 0u;
@@ -954,10 +998,11 @@ static bool tmap_dy_tiles(CUtensorMap *m, const TcOperand &o) {
 }
 
 // An NHWC input [B][H][W][C] (C >= 64) seen by a 3x3 stride-2 convolution: boxes of 128 consecutive output
-// pixels (whole output rows) by 64 channels, stepping 2 along W and H, written with the 128-byte swizzle.
-static bool tmap_im2col_wide(CUtensorMap *m, const TcOperand &o) {
+// pixels (128 for the forward, 64 for the weight gradient; whole output rows or part of one) by 64 channels,
+// stepping 2 along W and H, written with the 128-byte swizzle.
+static bool tmap_im2col_wide(CUtensorMap *m, const TcOperand &o, int pix) {
     const int H = 1 << o.hs, W = 1 << o.ws, C = 1 << o.cs, Ho = H / 2, Wo = W / 2;
-    const int wb = Wo < 128 ? Wo : 128, hb = Ho < 128 / wb ? Ho : 128 / wb, nb = 128 / (wb * hb);
+    const int wb = Wo < pix ? Wo : pix, hb = Ho < pix / wb ? Ho : pix / wb, nb = pix / (wb * hb);
     const unsigned box[4] = {64u, 2u * wb, 2u * hb, (unsigned)nb}, estr[4] = {1, 2, 2, 1};
     return tmap4(m, o.p, C, W, H, o.nb, 2ull * C, 2ull * C * W, 2ull * C * W * H, box, estr,
                  CU_TENSOR_MAP_SWIZZLE_128B);
@@ -968,6 +1013,19 @@ static bool tmap_matrix(CUtensorMap *m, const void *p, long long rows, long long
                         CUtensorMapSwizzle swz) {
     const unsigned box[4] = {(unsigned)box_cols, (unsigned)box_rows, 1, 1}, estr[4] = {1, 1, 1, 1};
     return tmap4(m, p, cols, rows, 1, 1, 2ull * cols, 2ull * cols * rows, 2ull * cols * rows, box, estr, swz);
+}
+
+// The ones box's device address, per device (host code must not take the symbol itself as an address).
+static const void *ones_box_address() {
+    static const void *addr[64] = {nullptr};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    if (!addr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, kOnesBox) != cudaSuccess) return nullptr;
+        addr[dev] = p;
+    }
+    return addr[dev];
 }
 
 // C(m, n) = sum_k A(m, k) B(n, k) on the tensor cores, K cut into `splits` slices (rounded to 64).
@@ -987,10 +1045,19 @@ static bool gemm(TcGemm g, int *err, cudaStream_t s, int splits = 1) {
     g.mt = (g.M + kTcBM - 1) / kTcBM;
     g.nt = (g.N + BN - 1) / BN;
     g.units = EPI == EPI_DGRAD_MASK_BF16 ? 4 * g.mt : g.mt * g.nt * z;  // four parity classes
-    CUtensorMap ma, mb;
-    if (LA == LD_IM2COL_KT) {
+    CUtensorMap ma, mb, mo;
+    memset(&mo, 0, sizeof(mo));
+    if (LA == LD_IM2COL_MNT) {
+        // weight gradient with C >= 64: the input in 64-pixel boxes of 64 channels, dY [P][N] in 64-pixel boxes
+        // of 64 channels, the appended feature of ones from a constant box
+        const void *ones = ones_box_address();
+        if (!ones || !tmap_im2col_wide(&ma, g.a, kTcBK) ||
+            !tmap_matrix(&mb, g.b.p, g.K, g.b.ld, kTcBK, 64, CU_TENSOR_MAP_SWIZZLE_128B) ||
+            !tmap_matrix(&mo, ones, 64, 64, 64, 64, CU_TENSOR_MAP_SWIZZLE_128B))
+            return false;
+    } else if (LA == LD_IM2COL_KT) {
         // forward with C >= 64: the input in 128-pixel boxes of 64 channels, the weights [N][9 C] in BN-row boxes
-        if (!tmap_im2col_wide(&ma, g.a) ||
+        if (!tmap_im2col_wide(&ma, g.a, kTcBM) ||
             !tmap_matrix(&mb, g.b.p, g.N, g.b.ld, BN, 64, CU_TENSOR_MAP_SWIZZLE_128B))
             return false;
     } else if (tc_a_tma<LA>()) {
@@ -1005,7 +1072,7 @@ static bool gemm(TcGemm g, int *err, cudaStream_t s, int splits = 1) {
         mb = ma;
     }
     const int cap = 2 * upslam_sm_count();  // persistent: two CTAs per SM
-    gemm_tc_kernel<EPI, BN, LA, LB><<<g.units < cap ? g.units : cap, tc_threads<LA>(), smem, s>>>(g, err, ma, mb);
+    gemm_tc_kernel<EPI, BN, LA, LB><<<g.units < cap ? g.units : cap, tc_threads<LA>(), smem, s>>>(g, err, ma, mb, mo);
     return true;
 }
 
@@ -1111,9 +1178,10 @@ extern "C" upslam_status upslam_cnn_backward(const float *d_params, const void *
         int splits = (2 * sms + tiles - 1) / tiles;
         if (splits > ktiles / 16) splits = ktiles / 16;
         if (splits < 1) splits = 1;
-        const bool okw = N == 32   ? gemm<EPI_F32_RED_T, 32, LD_IM2COL_MN, LD_DENSE_MN>(gw, w.err, s, splits)
-                         : N == 64 ? gemm<EPI_F32_RED_T, 64, LD_IM2COL_MN, LD_DENSE_MN>(gw, w.err, s, splits)
-                                   : gemm<EPI_F32_RED_T, 128, LD_IM2COL_MN, LD_DENSE_MN>(gw, w.err, s, splits);
+        // layers with C >= 64 (N = 128) load through TMA; the 8- and 32-channel inputs are gathered
+        const bool okw = C >= 64   ? gemm<EPI_F32_RED_T, 128, LD_IM2COL_MNT, LD_DENSE_MNT>(gw, w.err, s, splits)
+                         : N == 32 ? gemm<EPI_F32_RED_T, 32, LD_IM2COL_MN, LD_DENSE_MN>(gw, w.err, s, splits)
+                                   : gemm<EPI_F32_RED_T, 64, LD_IM2COL_MN, LD_DENSE_MN>(gw, w.err, s, splits);
         if (!okw) return UPSLAM_ERR_CUDA;
         if (l > 0) {
             // dY of the layer below = its ReLU mask x sum over the taps that read each input pixel of dY W,
