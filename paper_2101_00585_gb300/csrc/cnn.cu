@@ -72,8 +72,14 @@ enum {
     LD_IM2COL_KT = 6,   // TMA: im2col of an input with C >= 64, one tap's 64 channels per K step (forward)
     LD_DENSE_KT = 7,    // TMA: weights [N][K], K-major (forward)
     LD_IM2COL_MNT = 8,  // TMA: im2col of an input with C >= 64, MN-major (weight gradient)
-    LD_DENSE_MNT = 9    // TMA: dY [P][N], MN-major (weight gradient)
+    LD_DENSE_MNT = 9,   // TMA: dY [P][N], MN-major (weight gradient)
+    LD_IM2COL_KT32 = 10,  // TMA: as LD_IM2COL_KT for C = 32 (two taps per K step, 64-byte swizzle)
+    LD_IM2COL_MNT32 = 11  // TMA: as LD_IM2COL_MNT for C = 32 (64-byte swizzle)
 };
+
+// Channels per im2col TMA box: 64 (128-byte swizzle) or 32 (64-byte swizzle).
+template <int LD>
+constexpr int tma_cb() { return LD == LD_IM2COL_KT32 || LD == LD_IM2COL_MNT32 ? 32 : 64; }
 
 struct TcOperand {
     const __nv_bfloat16 *p;
@@ -223,7 +229,10 @@ __device__ __forceinline__ void class_tap(int q, int t, int &ky, int &kx) {
 // thread; the forward and weight-gradient operands by eight cp.async warps (their address arithmetic and copy
 // issue set the pace).
 template <int LA>
-constexpr bool tc_a_tma() { return LA == LD_DY_TAPS_K || LA == LD_IM2COL_KT || LA == LD_IM2COL_MNT; }
+constexpr bool tc_a_tma() {
+    return LA == LD_DY_TAPS_K || LA == LD_IM2COL_KT || LA == LD_IM2COL_MNT || LA == LD_IM2COL_KT32 ||
+           LA == LD_IM2COL_MNT32;
+}
 template <int LA>
 constexpr int tc_prod() { return tc_a_tma<LA>() ? 1 : 8; }
 template <int LA>
@@ -272,16 +281,17 @@ __device__ __forceinline__ TcUnit tc_unit(const TcGemm &g, int u) {
 template <int LA>
 __device__ __forceinline__ void tc_tma_a(unsigned stage, unsigned mbar, const TcOperand &a, const CUtensorMap *ma,
                                          const CUtensorMap *mo, const TcUnit &t, int k0) {
-    if (LA == LD_IM2COL_MNT) {
-        // k: 64 pixels from k0; rows: features t.r0a.. as two 64-channel boxes, [64 k][128 B] each, 8 KB apart
-        // (the appended feature of ones from mo; features past it read zeros from image nb)
+    if (LA == LD_IM2COL_MNT || LA == LD_IM2COL_MNT32) {
+        // k: 64 pixels from k0; rows: features t.r0a.. as boxes of CB channels, [64 k][2 CB bytes] each, 128 CB
+        // bytes apart (the appended feature of ones from mo; features past it read zeros from image nb)
+        constexpr int CB = tma_cb<LA>();
         const int wo = a.ws - 1, ho = a.hs - 1;
         const int ox0 = k0 & ((1 << wo) - 1), oy0 = (k0 >> wo) & ((1 << ho) - 1), b0 = k0 >> (wo + ho);
 #pragma unroll 1
-        for (int h = 0; h < 2; ++h) {
-            const int f = t.r0a + 64 * h;
+        for (int h = 0; h < kTcBM / CB; ++h) {
+            const int f = t.r0a + CB * h;
             if (f == a.ones_row) {
-                tma_load4(stage + h * 8192, mo, 0, 0, 0, 0, mbar);
+                tma_load4(stage + h * CB * 128, mo, 0, 0, 0, 0, mbar);
                 continue;
             }
             int c0 = 0, c1 = 0, c2 = 0, c3 = a.nb;
@@ -292,17 +302,30 @@ __device__ __forceinline__ void tc_tma_a(unsigned stage, unsigned mbar, const Tc
                 c2 = 2 * oy0 + ky - 1;
                 c3 = b0;
             }
-            tma_load4(stage + h * 8192, ma, c0, c1, c2, c3, mbar);
+            tma_load4(stage + h * CB * 128, ma, c0, c1, c2, c3, mbar);
         }
         return;
     }
-    if (LA == LD_IM2COL_KT) {
-        // rows: 128 output pixels from t.r0a (whole output rows); k: 64 channels of one tap (C >= 64), read as
-        // one box stepping 2 along W and H from (2 ox0 + kx - 1, 2 oy0 + ky - 1); the padding reads zeros
+    if (LA == LD_IM2COL_KT || LA == LD_IM2COL_KT32) {
+        // rows: 128 output pixels from t.r0a (whole output rows); k: 64 features as boxes of CB channels of one
+        // tap ([128 rows][2 CB bytes], 8 KB apart when CB = 32), each stepping 2 along W and H from
+        // (2 ox0 + kx - 1, 2 oy0 + ky - 1); the padding and features past 9 C read zeros
+        constexpr int CB = tma_cb<LA>();
         const int wo = a.ws - 1, ho = a.hs - 1;
         const int ox0 = t.r0a & ((1 << wo) - 1), oy0 = (t.r0a >> wo) & ((1 << ho) - 1), b0 = t.r0a >> (wo + ho);
-        const int tap = k0 >> a.cs, ky = tap / 3, kx = tap - 3 * ky;
-        tma_load4(stage, ma, k0 & ((1 << a.cs) - 1), 2 * ox0 + kx - 1, 2 * oy0 + ky - 1, b0, mbar);
+#pragma unroll 1
+        for (int h = 0; h < kTcBK / CB; ++h) {
+            const int f = k0 + CB * h;
+            int c0 = 0, c1 = 0, c2 = 0, c3 = a.nb;
+            if (f < a.kf) {
+                const int tap = f >> a.cs, ky = tap / 3, kx = tap - 3 * ky;
+                c0 = f & ((1 << a.cs) - 1);
+                c1 = 2 * ox0 + kx - 1;
+                c2 = 2 * oy0 + ky - 1;
+                c3 = b0;
+            }
+            tma_load4(stage + h * 8192, ma, c0, c1, c2, c3, mbar);
+        }
         return;
     }
     int ky, kx;
@@ -499,7 +522,7 @@ __global__ void __launch_bounds__(tc_threads<LA>(), 2)
     constexpr int kLag = S - 2;  // cp.async groups a gather thread keeps in flight before signalling a stage
     constexpr int kA = kTcBM * kTcBK * 2, kStage = (kTcBM + BN) * kTcBK * 2;
     constexpr unsigned kTxBytes = (unsigned)kStage;  // TMA boxes are written in full (zeros outside)
-    constexpr bool A_MN = LA == LD_IM2COL_MN || LA == LD_IM2COL_MNT;
+    constexpr bool A_MN = LA == LD_IM2COL_MN || LA == LD_IM2COL_MNT || LA == LD_IM2COL_MNT32;
     constexpr bool B_MN = LB == LD_DENSE_MN || LB == LD_W_TAPS_MN || LB == LD_DENSE_MNT;
     // descriptor byte offsets (leading = along K, stride = along M/N); an MMA (16 k) advances two core
     // matrices along K
@@ -629,6 +652,10 @@ __global__ void __launch_bounds__(tc_threads<LA>(), 2)
                         const unsigned long long ad =
                             !A_TMA               ? umma_desc(a0 + kk * 2 * kALbo, kALbo, kASbo)
                             : LA == LD_IM2COL_MNT ? umma_desc_sw(a0 + kk * 2048, 8192, 1024, 2)
+                            // 64-byte swizzle: MN-major 8-row K groups 512 B apart, 32-feature atoms 4 KB apart;
+                            // K-major: two 64-byte-row sub-tiles 8 KB apart, an MMA's 16 k 32 bytes along the row
+                            : LA == LD_IM2COL_MNT32 ? umma_desc_sw(a0 + kk * 1024, 4096, 512, 4)
+                            : LA == LD_IM2COL_KT32  ? umma_desc_sw(a0 + (kk >> 1) * 8192 + (kk & 1) * 32, 16, 512, 4)
                                                   : umma_desc_sw(a0 + kk * 32, 16, 1024, 2);
                         const unsigned long long bd =
                             !A_TMA                ? umma_desc(b0 + kk * 2 * kBLbo, kBLbo, kBSbo)
@@ -997,15 +1024,15 @@ static bool tmap_dy_tiles(CUtensorMap *m, const TcOperand &o) {
                  CU_TENSOR_MAP_SWIZZLE_128B);
 }
 
-// An NHWC input [B][H][W][C] (C >= 64) seen by a 3x3 stride-2 convolution: boxes of 128 consecutive output
-// pixels (128 for the forward, 64 for the weight gradient; whole output rows or part of one) by 64 channels,
-// stepping 2 along W and H, written with the 128-byte swizzle.
-static bool tmap_im2col_wide(CUtensorMap *m, const TcOperand &o, int pix) {
+// An NHWC input [B][H][W][C] (C >= cb) seen by a 3x3 stride-2 convolution: boxes of 128 consecutive output
+// pixels (128 for the forward, 64 for the weight gradient; whole output rows or part of one) by cb channels
+// (64 or 32), stepping 2 along W and H, written with the 128-byte or 64-byte swizzle.
+static bool tmap_im2col_wide(CUtensorMap *m, const TcOperand &o, int pix, int cb) {
     const int H = 1 << o.hs, W = 1 << o.ws, C = 1 << o.cs, Ho = H / 2, Wo = W / 2;
     const int wb = Wo < pix ? Wo : pix, hb = Ho < pix / wb ? Ho : pix / wb, nb = pix / (wb * hb);
-    const unsigned box[4] = {64u, 2u * wb, 2u * hb, (unsigned)nb}, estr[4] = {1, 2, 2, 1};
+    const unsigned box[4] = {(unsigned)cb, 2u * wb, 2u * hb, (unsigned)nb}, estr[4] = {1, 2, 2, 1};
     return tmap4(m, o.p, C, W, H, o.nb, 2ull * C, 2ull * C * W, 2ull * C * W * H, box, estr,
-                 CU_TENSOR_MAP_SWIZZLE_128B);
+                 cb == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B);
 }
 
 // A row-major matrix [rows][cols] (cols contiguous) in boxes of `box_rows` rows by `box_cols` columns.
@@ -1047,17 +1074,19 @@ static bool gemm(TcGemm g, int *err, cudaStream_t s, int splits = 1) {
     g.units = EPI == EPI_DGRAD_MASK_BF16 ? 4 * g.mt : g.mt * g.nt * z;  // four parity classes
     CUtensorMap ma, mb, mo;
     memset(&mo, 0, sizeof(mo));
-    if (LA == LD_IM2COL_MNT) {
-        // weight gradient with C >= 64: the input in 64-pixel boxes of 64 channels, dY [P][N] in 64-pixel boxes
+    constexpr int CB = tma_cb<LA>();
+    constexpr CUtensorMapSwizzle kSwzA = CB == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
+    if (LA == LD_IM2COL_MNT || LA == LD_IM2COL_MNT32) {
+        // weight gradient with C >= 32: the input in 64-pixel boxes of CB channels, dY [P][N] in 64-pixel boxes
         // of 64 channels, the appended feature of ones from a constant box
         const void *ones = ones_box_address();
-        if (!ones || !tmap_im2col_wide(&ma, g.a, kTcBK) ||
+        if (!ones || !tmap_im2col_wide(&ma, g.a, kTcBK, CB) ||
             !tmap_matrix(&mb, g.b.p, g.K, g.b.ld, kTcBK, 64, CU_TENSOR_MAP_SWIZZLE_128B) ||
-            !tmap_matrix(&mo, ones, 64, 64, 64, 64, CU_TENSOR_MAP_SWIZZLE_128B))
+            !tmap_matrix(&mo, ones, 64, 64, 64, CB, kSwzA))
             return false;
-    } else if (LA == LD_IM2COL_KT) {
-        // forward with C >= 64: the input in 128-pixel boxes of 64 channels, the weights [N][9 C] in BN-row boxes
-        if (!tmap_im2col_wide(&ma, g.a, kTcBM) ||
+    } else if (LA == LD_IM2COL_KT || LA == LD_IM2COL_KT32) {
+        // forward with C >= 32: the input in 128-pixel boxes of CB channels, the weights [N][9 C] in BN-row boxes
+        if (!tmap_im2col_wide(&ma, g.a, kTcBM, CB) ||
             !tmap_matrix(&mb, g.b.p, g.N, g.b.ld, BN, 64, CU_TENSOR_MAP_SWIZZLE_128B))
             return false;
     } else if (tc_a_tma<LA>()) {
@@ -1117,10 +1146,10 @@ extern "C" upslam_status upslam_cnn_forward(const float *d_params, const void *d
         g.ldc = N;
         g.bias = d_params + L.off_b[l];
         // the staged-bias epilogue needs one column tile: BN = N
-        // layers with C >= 64 (N = 128) load through TMA; the 8- and 32-channel inputs are gathered
+        // layers with C >= 32 load through TMA (128- or 64-byte swizzle); the 8-channel input is gathered
         const bool ok = C >= 64   ? gemm<EPI_BIAS_RELU_BF16, 128, LD_IM2COL_KT, LD_DENSE_KT>(g, w.err, s)
-                        : N == 32 ? gemm<EPI_BIAS_RELU_BF16, 32, LD_IM2COL_K, LD_DENSE_K>(g, w.err, s)
-                                  : gemm<EPI_BIAS_RELU_BF16, 64, LD_IM2COL_K, LD_DENSE_K>(g, w.err, s);
+                        : C == 32 ? gemm<EPI_BIAS_RELU_BF16, 64, LD_IM2COL_KT32, LD_DENSE_KT>(g, w.err, s)
+                                  : gemm<EPI_BIAS_RELU_BF16, 32, LD_IM2COL_K, LD_DENSE_K>(g, w.err, s);
         if (!ok) return UPSLAM_ERR_CUDA;
         x = w.act[l];
         H /= 2;
@@ -1178,10 +1207,10 @@ extern "C" upslam_status upslam_cnn_backward(const float *d_params, const void *
         int splits = (2 * sms + tiles - 1) / tiles;
         if (splits > ktiles / 16) splits = ktiles / 16;
         if (splits < 1) splits = 1;
-        // layers with C >= 64 (N = 128) load through TMA; the 8- and 32-channel inputs are gathered
+        // layers with C >= 32 load through TMA (128- or 64-byte swizzle); the 8-channel input is gathered
         const bool okw = C >= 64   ? gemm<EPI_F32_RED_T, 128, LD_IM2COL_MNT, LD_DENSE_MNT>(gw, w.err, s, splits)
-                         : N == 32 ? gemm<EPI_F32_RED_T, 32, LD_IM2COL_MN, LD_DENSE_MN>(gw, w.err, s, splits)
-                                   : gemm<EPI_F32_RED_T, 64, LD_IM2COL_MN, LD_DENSE_MN>(gw, w.err, s, splits);
+                         : C == 32 ? gemm<EPI_F32_RED_T, 64, LD_IM2COL_MNT32, LD_DENSE_MNT>(gw, w.err, s, splits)
+                                   : gemm<EPI_F32_RED_T, 32, LD_IM2COL_MN, LD_DENSE_MN>(gw, w.err, s, splits);
         if (!okw) return UPSLAM_ERR_CUDA;
         if (l > 0) {
             // dY of the layer below = its ReLU mask x sum over the taps that read each input pixel of dY W,
