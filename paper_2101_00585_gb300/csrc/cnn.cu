@@ -829,8 +829,19 @@ __global__ void __launch_bounds__(256) head_dy_kernel(const float *__restrict__ 
 }
 
 // FP32 master conv weights [N][K] -> the BF16 copy the GEMMs read.
-__global__ void pack_weights_kernel(const float *w, int n, __nv_bfloat16 *wb) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) wb[i] = __float2bfloat16(w[i]);
+// The four layers' FP32 master weights -> their BF16 copies, in one launch.
+struct PackArgs {
+    const float *src[4];
+    __nv_bfloat16 *dst[4];
+    int n[4];
+};
+__global__ void pack_weights_kernel(PackArgs a) {
+    const int total = a.n[0] + a.n[1] + a.n[2] + a.n[3];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        int l = 0, k = i;
+        while (k >= a.n[l]) k -= a.n[l++];
+        a.dst[l][k] = __float2bfloat16(a.src[l][k]);
+    }
 }
 
 // Adam (Kingma & Ba) on the FP32 master parameters, bias-corrected.
@@ -1131,10 +1142,18 @@ extern "C" upslam_status upslam_cnn_forward(const float *d_params, const void *d
     cnn_ws_layout(batch, &w, reinterpret_cast<char *>(d_ws));
     const CnnLayout L = cnn_layout();
     const __nv_bfloat16 *x = reinterpret_cast<const __nv_bfloat16 *>(d_x);
+    PackArgs pk;
+    int n_w = 0;
+    for (int l = 0; l < 4; ++l) {
+        pk.src[l] = d_params + L.off_w[l];
+        pk.dst[l] = w.wb[l];
+        pk.n[l] = cnn_co(l) * cnn_k(l);
+        n_w += pk.n[l];
+    }
+    pack_weights_kernel<<<grid1d(n_w), 256, 0, s>>>(pk);
     int H = kCnnH, W = kCnnW;
     for (int l = 0; l < 4; ++l) {
         const int C = kCnnCh[l], N = cnn_co(l), K = cnn_k(l);
-        pack_weights_kernel<<<grid1d((long long)N * K), 256, 0, s>>>(d_params + L.off_w[l], N * K, w.wb[l]);
         TcGemm g{};
         g.a = op_im2col(x, H, W, C);
         g.a.nb = batch;
