@@ -312,18 +312,31 @@ constexpr int kTileThreads = 512;
 constexpr int kTileWarps = kTileThreads / 32;
 constexpr int kStageGroup = 4;  // keyframe chunks staged per memory round trip
 
-// One staged correspondence, branch-free: a rejected pair contributes zeros.
-template <int L1>
-__device__ __forceinline__ void accumulate_entry(const IcpArgs &a, const PoseF &T, float3 s, float3 n, float acc[28],
-                                                 int &inl) {
+// The sweep pixel a staged keyframe point lands in: its point and normal,
+// gathered from L2, and whether the point binned at all.
+struct SweepHit {
+    float4 P, m;
+    bool binned;
+};
+
+__device__ __forceinline__ SweepHit gather_entry(const IcpArgs &a, const PoseF &T, float3 s) {
     const float3 q = xform_inv(T, s.x, s.y, s.z);
     int jv = 0, ju = 0;
     float rr;
-    bool ok = bin_point(q.x, q.y, q.z, a.sp, jv, ju, rr);
-    const int j = ok ? jv * a.sp.cols + ju : 0;
-    const float4 P = __ldcg(a.spix + j);
-    const float4 m = load_nw_cg(a.snrm, j, a.sprec);
-    ok = ok && P.w != 0.0f && m.w != 0.0f;
+    SweepHit h;
+    h.binned = bin_point(q.x, q.y, q.z, a.sp, jv, ju, rr);
+    const int j = h.binned ? jv * a.sp.cols + ju : 0;
+    h.P = __ldcg(a.spix + j);
+    h.m = load_nw_cg(a.snrm, j, a.sprec);
+    return h;
+}
+
+// One staged correspondence, branch-free: a rejected pair contributes zeros.
+template <int L1>
+__device__ __forceinline__ void accumulate_entry(const IcpArgs &a, const PoseF &T, float3 s, float3 n,
+                                                 const SweepHit &h, float acc[28], int &inl) {
+    const float4 P = h.P, m = h.m;
+    bool ok = h.binned && P.w != 0.0f && m.w != 0.0f;
     const float *r = T.r;
     const float px = fmaf(r[0], P.x, fmaf(r[1], P.y, fmaf(r[2], P.z, r[3])));
     const float py = fmaf(r[4], P.x, fmaf(r[5], P.y, fmaf(r[6], P.z, r[7])));
@@ -633,10 +646,20 @@ __global__ void __launch_bounds__(kTileThreads, 1)
 #pragma unroll
         for (int i = 0; i < 28; ++i) acc[i] = 0.0f;
         int inl = 0;
-#pragma unroll 2
-        for (int e = threadIdx.x; e < staged; e += kTileThreads)
-            accumulate_entry<L1>(a, T, make_float3(sx[e], sy[e], sz[e]), make_float3(snx[e], sny[e], snz[e]), acc,
-                                 inl);
+        // Software-pipelined: the gathers of a thread's next entry are issued
+        // before the current one is reduced, so each L2 round trip overlaps
+        // the previous entry's arithmetic.  The entries are still summed in
+        // the same order.
+        if (threadIdx.x < staged) {
+            SweepHit h = gather_entry(a, T, make_float3(sx[threadIdx.x], sy[threadIdx.x], sz[threadIdx.x]));
+            for (int e = threadIdx.x; e < staged; e += kTileThreads) {
+                const int e1 = min(e + kTileThreads, staged - 1);  // the last prefetch repeats an entry, unused
+                const SweepHit h1 = gather_entry(a, T, make_float3(sx[e1], sy[e1], sz[e1]));
+                accumulate_entry<L1>(a, T, make_float3(sx[e], sy[e], sz[e]), make_float3(snx[e], sny[e], snz[e]), h,
+                                     acc, inl);
+                h = h1;
+            }
+        }
         for (int q = spill_q; q < nchunks; q += gridDim.x) {
             const int k = q * kTileThreads + threadIdx.x;
             if (k < npx) accumulate_pixel<L1>(a, T, k, acc, inl);
