@@ -388,9 +388,9 @@ upslam_status upslam_track_scan(const upslam_keyframe *kf, const float *d_pts4, 
                                 size_t ws_bytes, uint64_t *d_zbuf_kf, void *stream);
 
 /*
- * Loop-closure grid search (Sec. III-C): candidate transformations are scored
- * by low-resolution projective alignment checks and the best is promoted to a
- * full-resolution ICP registration.  A candidate's score is its number of
+ * Loop-closure grid search (Sec. III-C): each candidate pose gets a cheap
+ * projective score on a subsampled keyframe, and the winner is refined by ICP
+ * at full resolution afterwards.  A candidate's score is its number of
  * inliers of the ICP association (keyframe pixel -> sweep pixel under T^-1,
  * the FP32 binning rule, Omega with ip->d_max and ip->cos_theta_max) over the
  * keyframe pixels (stride i, stride j).

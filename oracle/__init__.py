@@ -318,8 +318,8 @@ def residual(v, u, kf_depth, kf_nrm4, kp, sp4, sn4, sw, T, prm: Params = Params(
 
 
 def grid_score(kf_depth, kf_nrm4, kp, sp4, sn4, sw, poses, stride: int, prm: Params = Params()):
-    """Sec. III-C loop closure: a grid search evaluates several hundred candidate transformations with
-    low-resolution projective alignment checks and promotes the best to full-resolution ICP.
+    """Sec. III-C loop closure: a grid of a few hundred candidate poses, each scored by a cheap projective
+    check at reduced resolution; the winner is then refined by ICP at full resolution.
 
     Reading: the check is the ICP association of this oracle (keyframe pixel -> sweep pixel, filter
     Omega) on the keyframe sampled every ``stride`` rows and columns; a candidate's score is its number

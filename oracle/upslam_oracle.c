@@ -7,12 +7,12 @@
  *
  * It restates, step by step, what the paper's per-sweep path computes
  * (UPSLAM, arXiv 2101.00585):
- *   - Sec. III-A "Data Intake": points are projected into a panoramic image, and a
+ *   - Sec. III-A "Data Intake": the points are binned into a panoramic image, and a
  *     normal is the cross product of the vectors from a pixel's point to two
  *     image neighbours;
  *   - Sec. III-B "Motion Estimation", Eq. 1: point-to-plane ICP over projective
  *     correspondences C filtered by the similarity test Omega_{d,theta};
- *   - Sec. III-C "Keyframe Update": every keyframe pixel is projected onto the
+ *   - Sec. III-C "Keyframe Update": every keyframe pixel is carried over to the
  *     sweep image, gated by the same kind of similarity test, and averaged in
  *     with a per-pixel sample count saturated at 10; the registration quality
  *     is inliers / valid sweep measurements.
@@ -392,7 +392,7 @@ int orc_solve6(const double *Aup, const double *rhs, double pivot_eps, double *x
 /*
  * Projective correspondence of one keyframe pixel k = (v, u) under T (Eq. 1's set
  * C and filter Omega, Sec. III-B).  As in the keyframe update (Sec. III-C), the
- * keyframe pixel is projected onto the sweep depth image: its point s1 = d_k dir_k
+ * keyframe pixel is carried over to the sweep's depth image: its point s1 = d_k dir_k
  * goes to the sweep frame by T^-1 and is binned (FP32 decision) into sweep pixel
  * j; s2 = P_j.  Returns 1 for an inlier and fills r = (T s2 - s1) . N(s1) and
  * J = d r / d xi for the left update T <- exp(xi^) T, xi = (omega, v).
@@ -517,7 +517,7 @@ int orc_icp_residual(int32_t v, int32_t u, const float *kf_depth, const float *k
  * Keyframe update (Sec. III-C) with the keyframe-from-sweep pose T.
  *
  * Gather: each keyframe pixel k holding a sample (w_k > 0) is put at its FP32
- * point d_k * dir_k, taken into the sweep frame, and projected onto the sweep
+ * point d_k * dir_k, taken into the sweep frame, and binned into the sweep
  * panorama.  If the sweep pixel j there holds a point with a normal, and the two
  * pass the similarity test (distance <= d_max and normal cosine >= cos_theta_max,
  * in the keyframe frame), the keyframe pixel averages in the sweep sample:

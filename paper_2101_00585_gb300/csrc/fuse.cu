@@ -1,7 +1,7 @@
 // Keyframe update (UPSLAM Sec. III-C).
 //
-// With the optimised T, every keyframe pixel holding a sample is projected onto
-// the sweep depth image (the same keyframe-to-sweep correspondence as the ICP
+// With the optimised T, every keyframe pixel holding a sample is carried over to
+// the sweep's depth image (the same keyframe-to-sweep correspondence as the ICP
 // step).  When the similarity gate keeps the pair, the pixel averages the sweep
 // sample in with its sample count as weight, and the count saturates at w_max:
 //   d <- (w d + |T s2|) / (w + 1),  n <- unit(w n + R m),  w <- min(w + 1, w_max).

@@ -1,6 +1,6 @@
-// Loop-closure grid search (UPSLAM Sec. III-C): several hundred candidate
-// transformations are evaluated with low-resolution projective alignment
-// checks and the best is promoted to a full-resolution ICP registration.
+// Loop-closure grid search (UPSLAM Sec. III-C): a few hundred candidate poses
+// each get a cheap projective score on a subsampled keyframe, and the winner
+// is then refined by ICP at full resolution.
 //
 // The check is the ICP association of the registration kernels (keyframe pixel
 // -> sweep pixel under T^-1 with the FP32 binning rule, filter Omega on the

@@ -1,5 +1,5 @@
-"""Pins of the loop-closure grid search oracle (Sec. III-C: several hundred candidate transformations
-evaluated by low-resolution projective alignment checks, the best promoted to full-resolution ICP).
+"""Pins of the loop-closure grid search oracle (Sec. III-C: a few hundred candidate poses, each scored by
+a cheap projective check at reduced resolution; the winner is refined by ICP at full resolution).
 
 * On an exact room (noise-free sweep, rendered keyframe) the true pose wins a grid of candidates
   around it, and candidates a metre or more away score far lower;
