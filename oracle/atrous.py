@@ -1,9 +1,9 @@
 """FP64 reference of the edge-avoiding a-trous normal smoothing (TEST INFRASTRUCTURE ONLY).
 
-UPSLAM Sec. III-A says the cross-product normals of the sweep are very noisy and are smoothed
-with an edge-sensitive filter, naming the a-trous wavelet filter of Dammertz et al. (2010).
-Sec. III-B adds that the sweep normals may end up slightly over-smoothed, which helps ICP
-converge.  The paper gives no filter parameters.  The reading used here, restated from the
+Per UPSLAM Sec. III-A, normals built from cross products of neighbouring pixels carry a lot of
+noise, so they are smoothed by a filter that stops at edges: the a-trous wavelet filter of
+Dammertz et al. (2010).  Per Sec. III-B, a little too much smoothing of the sweep normals is
+harmless and even helps ICP converge.  The paper gives no filter parameters.  The reading used here, restated from the
 published method and not from any code:
 
 * Level l = 0 .. levels-1 convolves with the separable B3-spline taps [1, 4, 6, 4, 1] / 16

@@ -1,7 +1,7 @@
-// Edge-avoiding a-trous smoothing of a normal image (UPSLAM Sec. III-A: the
-// cross-product normals are very noisy and are smoothed by an edge-sensitive
-// filter, the a-trous wavelet filter of Dammertz et al. 2010; Sec. III-B: the
-// smoothing helps ICP converge).
+// Edge-avoiding a-trous smoothing of a normal image (UPSLAM Sec. III-A: normals
+// from neighbour cross products carry much noise and are smoothed by a filter
+// that stops at edges, the a-trous wavelet filter of Dammertz et al. 2010;
+// Sec. III-B: the smoothing helps ICP converge).
 //
 // Level l (step s = 2^l) sets every valid pixel p to the normalised sum over the
 // 5 x 5 taps q = p + s (dy, dx), dy, dx in -2..2, of
