@@ -443,8 +443,9 @@ def run_ours(args, ws, rank, local):
         k_fuse = min(kf_every - 1, n_scans - 1)  # a sweep registered against the first keyframe
         out["extra_kernels"] = {"atrous_kernel": run_atrous(args, seq, d_scans, device, up, hbm, hbm_src),
                                 "grid_score_kernel": run_grid(trk, device, up, hbm, hbm_src),
-                                "consistency_kernels": run_consistency(pool, hist_pose[kf_every].clone(), device, up, hbm,
-                                                                       hbm_src),
+                                "consistency_kernels": (run_consistency(pool, hist_pose[kf_every].clone(), device, up,
+                                                                        hbm, hbm_src) if n_scans > kf_every else
+                                                        {"skipped": "the run opened no second keyframe"}),
                                 "fuse_kernels": run_fuse(pool[0], seq, d_scans[k_fuse], hist_pose[k_fuse].clone(),
                                                          device, up, hbm, hbm_src)}
     if dist:
