@@ -91,8 +91,10 @@ def _load():
     global _lib
     if _lib is not None:
         return _lib
-    build()
-    lib = ctypes.CDLL(_SO)
+    # UPSLAM_ORACLE_LIB names another build of upslam_oracle.c: the planted-mistake
+    # tests load deliberately broken copies through it to show that the pins fail.
+    path = os.environ.get("UPSLAM_ORACLE_LIB") or build()
+    lib = ctypes.CDLL(path)
     P = ctypes.POINTER
     sig = {
         "orc_atan2p": (ctypes.c_float, [ctypes.c_float, ctypes.c_float]),

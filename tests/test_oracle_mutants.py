@@ -1,0 +1,113 @@
+"""Planted mistakes in the FP64 oracle must fail its pins (no GPU).
+
+Each case copies ``oracle/upslam_oracle.c``, plants one plausible mistake (a
+flipped sign, a dropped term, a transposed operand, a wrong index or gate),
+compiles the copy with the oracle's own flags and runs the pin tests against it
+in a child process (``UPSLAM_ORACLE_LIB``).  The pins pass on the real oracle; a
+case passes here only when some pin fails on the broken copy.  This shows that
+the pins are tied to the paper and the mathematics tightly enough to catch
+mistakes of these kinds anywhere in the oracle.
+"""
+from __future__ import annotations
+
+import concurrent.futures as cf
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "upslam_oracle.c")
+
+PINS = ["tests/test_oracle_pins.py", "tests/test_oracle_consistency_pins.py", "tests/test_oracle_grid_pins.py",
+        "tests/test_oracle_irls_pins.py"]
+# the two slow pins (a 10 s tracking run and a 7 s per-pixel re-assembly) are left to the main suite
+SLOW = ["tests/test_oracle_pins.py::test_sequence_tracks_tunnel",
+        "tests/test_oracle_irls_pins.py::test_weighted_normal_equations_match_per_pixel_definition"]
+
+# (name, text in upslam_oracle.c, planted replacement)
+MUTANTS = [
+    # a1: binning (Sec. III-A)
+    ("atan2_reflection_sign", "    if (x < 0.0f) a = ORC_PI_F - a;", "    if (x < 0.0f) a = ORC_PI_F + a;"),
+    ("atan2_octant_sign", "    if (ay > ax) a = ORC_HALF_PI_F - a;", "    if (ay > ax) a = ORC_HALF_PI_F + a;"),
+    ("elevation_sign", "    float fr = (pp->el_top - el) * pp->s_el;", "    float fr = (pp->el_top + el) * pp->s_el;"),
+    ("azimuth_mirrored", "    float fc = (ORC_PI_F - az) * pp->s_az;", "    float fc = (ORC_PI_F + az) * pp->s_az;"),
+    ("inverse_not_transposed",
+     "    *qx = (r[0] * dx + r[4] * dy) + r[8] * dz;\n"
+     "    *qy = (r[1] * dx + r[5] * dy) + r[9] * dz;\n"
+     "    *qz = (r[2] * dx + r[6] * dy) + r[10] * dz;",
+     "    *qx = (r[0] * dx + r[1] * dy) + r[2] * dz;\n"
+     "    *qy = (r[4] * dx + r[5] * dy) + r[6] * dz;\n"
+     "    *qz = (r[8] * dx + r[9] * dy) + r[10] * dz;"),
+    ("zbuffer_first_come",
+     "        int64_t k = (int64_t)v * pp->cols + u;\n        if (key < best[k]) best[k] = key;",
+     "        int64_t k = (int64_t)v * pp->cols + u;\n        if (best[k] == UINT64_MAX) best[k] = key;"),
+    # a2: normals (Sec. III-A)
+    ("normal_cross_component",
+     "double n[3] = { a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0] };",
+     "double n[3] = { a[1] * b[2] - a[2] * b[1], a[0] * b[2] - a[2] * b[0], a[0] * b[1] - a[1] * b[0] };"),
+    ("normal_orientation",
+     "double s = (n[0] * P[0] + n[1] * P[1] + n[2] * P[2]) > 0.0 ? -1.0 / nn : 1.0 / nn;",
+     "double s = (n[0] * P[0] + n[1] * P[1] + n[2] * P[2]) < 0.0 ? -1.0 / nn : 1.0 / nn;"),
+    ("normal_jump_absolute_term", "    float lim = np->jump_rel * d + np->jump_abs;", "    float lim = np->jump_rel * d;"),
+    # SE(3) and the 6x6 solve
+    ("se3_rotation_transposed", "        R[i] = I + A * W[i] + B * W2[i];", "        R[i] = I - A * W[i] + B * W2[i];"),
+    ("se3_v_coefficient", "        V[i] = I + B * W[i] + C * W2[i];", "        V[i] = I + A * W[i] + C * W2[i];"),
+    ("solve_back_substitution_index", "        for (int k = i + 1; k < 6; ++k) s -= L[6 * k + i] * x[k];",
+     "        for (int k = i + 1; k < 6; ++k) s -= L[6 * i + k] * x[k];"),
+    # a3: Eq. 1, filter Omega, Gauss-Newton (Sec. III-B)
+    ("jacobian_rotation_sign", "    J[0] = p[1] * n[2] - p[2] * n[1];", "    J[0] = p[2] * n[1] - p[1] * n[2];"),
+    ("residual_dropped_term", "    *r_out = e[0] * n[0] + e[1] * n[1] + e[2] * n[2];", "    *r_out = e[0] * n[0] + e[1] * n[1];"),
+    ("omega_normal_gate_dropped", "    if (!(cs >= (double)ip->cos_theta_max)) return 0;", "    (void)cs;"),
+    ("omega_distance_gate_dropped", "    if (!(dist <= (double)ip->d_max)) return 0;", "    (void)dist;"),
+    ("gauss_newton_rhs_sign", "    for (int i = 0; i < 6; ++i) nb[i] = -st->b[i];", "    for (int i = 0; i < 6; ++i) nb[i] = st->b[i];"),
+    ("irls_weight_constant", "                w = 1.0 / (ar > (double)ip->loss_delta ? ar : (double)ip->loss_delta);",
+     "                w = 1.0 / (double)ip->loss_delta;"),
+    ("normal_equations_unweighted", "                for (int c = a; c < 6; ++c) st->A[p++] += w * J[a] * J[c];",
+     "                for (int c = a; c < 6; ++c) st->A[p++] += J[a] * J[c];"),
+    # a4: keyframe update (Sec. III-C)
+    ("fusion_weights_swapped", "            kf_depth[k] = (w * kf_depth[k] + dm) / (w + 1.0);",
+     "            kf_depth[k] = (kf_depth[k] + w * dm) / (w + 1.0);"),
+    ("fusion_count_unsaturated", "            kf_w[k] = (w + 1.0 < (double)fp->w_max) ? w + 1.0 : (double)fp->w_max;",
+     "            kf_w[k] = w + 1.0;"),
+    ("fusion_distance_gate_dropped",
+     "            if (!(sqrt(e0 * e0 + e1 * e1 + e2 * e2) <= (double)fp->d_max)) continue;",
+     "            (void)e0; (void)e1; (void)e2;"),
+    ("hole_fill_farthest",
+     "        if (!was_empty[k]) continue;\n        uint32_t rb;\n        memcpy(&rb, &r, 4);\n"
+     "        uint64_t key = ((uint64_t)rb << 32) | (uint32_t)j;\n        if (key < best[k]) best[k] = key;",
+     "        if (!was_empty[k]) continue;\n        uint32_t rb;\n        memcpy(&rb, &r, 4);\n"
+     "        uint64_t key = ((uint64_t)rb << 32) | (uint32_t)j;\n"
+     "        if (best[k] == UINT64_MAX || key > best[k]) best[k] = key;"),
+    # keyframe mutual consistency (Sec. III-C) and the fixed-order inverse
+    ("consistency_test_inverted", "                    if (dn > 0.0f && !(dn > lim)) {",
+     "                    if (dn > 0.0f && (dn > lim)) {"),
+    ("pose_inverse_sign", "        out[4 * i + 3] = -((T[i] * T[3] + T[4 + i] * T[7]) + T[8 + i] * T[11]);",
+     "        out[4 * i + 3] = ((T[i] * T[3] + T[4 + i] * T[7]) + T[8 + i] * T[11]);"),
+]
+
+
+def _survives(name, old, new, workdir):
+    """True when every pin passes on the oracle with this mistake planted."""
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"{name}: the text to mutate must occur exactly once"
+    mutant_c = os.path.join(workdir, f"{name}.c")
+    mutant_so = os.path.join(workdir, f"{name}.so")
+    with open(mutant_c, "w") as fh:
+        fh.write(src.replace(old, new))
+    subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", mutant_c,
+                           "-o", mutant_so, "-lm"])
+    env = dict(os.environ, UPSLAM_ORACLE_LIB=mutant_so)
+    cmd = [sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *PINS]
+    for s in SLOW:
+        cmd += ["--deselect", s]
+    r = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
+    assert r.returncode in (0, 1), f"{name}: pytest ended with status {r.returncode}:\n{r.stdout[-1500:]}"
+    return r.returncode == 0
+
+
+def test_pins_fail_on_every_planted_mistake(tmp_path):
+    workers = max(1, min(len(MUTANTS), os.cpu_count() or 1))
+    with cf.ThreadPoolExecutor(max_workers=workers) as ex:
+        results = list(ex.map(lambda m: (m[0], _survives(*m, str(tmp_path))), MUTANTS))
+    survivors = [name for name, alive in results if alive]
+    assert not survivors, f"planted mistakes that passed every pin: {survivors}"

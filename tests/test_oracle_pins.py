@@ -218,6 +218,29 @@ def test_normal_discontinuity_and_fallback():
     assert not val2[:, 4].any()
 
 
+def test_normal_discontinuity_threshold_has_both_terms():
+    """The neighbour test |r_nb - r| > 0.05 r + 0.1 m (reading of Sec. III-A): at r = 1 m a step of
+    0.12 m is within the limit (0.15 m, most of it the absolute term) and a step of 0.17 m is not."""
+    pp = tiny_pano(4, 8)
+    dirs = pp.pixel_dirs()
+    for step, right_usable in ((0.12, True), (0.17, False)):
+        depth = np.full((4, 8), 1.0, np.float32)
+        depth[:, 5] = np.float32(1.0 + step)
+        pts = np.zeros((4, 8, 4), np.float32)
+        pts[..., :3] = (dirs * depth[..., None]).astype(np.float32)
+        pts[..., 3] = 1
+        n, val = oracle.normals(pts, depth, pp)
+        assert val[1, 4]
+        P = pts[1, 4, :3].astype(np.float64)
+        a = pts[1, 5, :3] - P if right_usable else P - pts[1, 3, :3]
+        b = pts[2, 4, :3].astype(np.float64) - P
+        want = np.cross(a, b)
+        want /= np.linalg.norm(want)
+        if want @ P > 0:
+            want = -want
+        assert np.allclose(n[1, 4], want, atol=1e-12), step
+
+
 # ----------------------------------------------------------------------------- a3: ICP
 
 
