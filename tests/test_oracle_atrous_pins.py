@@ -8,11 +8,17 @@
 * seeded noise on a plane is reduced;
 * rolling the panorama by whole columns commutes with the filter (the azimuth wraps).
 """
+import math
+
 import numpy as np
 import pytest
 from scipy import ndimage
 
-from oracle.atrous import TAPS, atrous
+from oracle.atrous import atrous
+
+# the cubic B-spline smoothing kernel of the a-trous transform: the binomial row C(4, k) / 2^4, taken
+# from its definition here rather than from the oracle
+B3 = np.array([math.comb(4, k) for k in range(5)], np.float64) / 16.0
 
 H, W = 12, 40
 
@@ -38,7 +44,7 @@ def _noisy_plane_normals(rng, sigma=0.1):
 def _dilated_kernel(level):
     s = 1 << level
     k1 = np.zeros(4 * s + 1)
-    k1[::s] = TAPS
+    k1[::s] = B3
     return np.outer(k1, k1)
 
 

@@ -66,3 +66,20 @@ def test_adam_first_step_closed_form():
     # bias-corrected first moments equal g and second moments g^2: the step is lr * g / (|g| + eps)
     want = np.array([1.0, -2.0, 3.0]) - 0.1 * g["a"] / (np.abs(g["a"]) + 1e-8)
     assert np.allclose(p["a"], want, rtol=1e-12)
+
+
+def test_downsample_means_only_the_pixels_holding_samples():
+    """Each cell is the mean of (depth / scale, nx, ny, nz) over its pixels that hold a sample (depth > 0 and a
+    normal flagged valid); cells without one are zero."""
+    depth = np.zeros((4, 8), np.float32)
+    nrm4 = np.zeros((4, 8, 4), np.float32)
+    depth[0:2, 0:2] = 6.0  # cell (0, 0): four samples facing +x
+    nrm4[0:2, 0:2] = (1, 0, 0, 1)
+    depth[0, 2], nrm4[0, 2] = 2.0, (0, 1, 0, 1)  # cell (0, 1): two samples ...
+    depth[1, 3], nrm4[1, 3] = 4.0, (0, 0, 1, 1)
+    depth[0, 3], nrm4[0, 3] = 100.0, (1, 1, 1, 0)  # ... a depth without a valid normal ...
+    nrm4[1, 2] = (1, 0, 0, 1)  # ... and a normal without a depth
+    out = cnn.downsample(depth, nrm4, 2, 4, depth_scale=2.0)
+    assert np.allclose(out[0, 0], [3.0, 1.0, 0.0, 0.0], atol=0, rtol=1e-15)
+    assert np.allclose(out[0, 1], [1.5, 0.0, 0.5, 0.5], atol=0, rtol=1e-15)
+    assert not out[1].any() and not out[0, 2:].any()

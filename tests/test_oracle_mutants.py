@@ -3,7 +3,9 @@
 Each case copies ``oracle/upslam_oracle.c``, plants one plausible mistake (a
 flipped sign, a dropped term, a transposed operand, a wrong index or gate),
 compiles the copy with the oracle's own flags and runs the pin tests against it
-in a child process (``UPSLAM_ORACLE_LIB``).  The pins pass on the real oracle; a
+in a child process (``UPSLAM_ORACLE_LIB``).  The NumPy parts of the oracle
+(a-trous smoothing, pose network, downsampling) are mutated the same way in a
+copy of the source tree.  The pins pass on the real oracle; a
 case passes here only when some pin fails on the broken copy.  This shows that
 the pins are tied to the paper and the mathematics tightly enough to catch
 mistakes of these kinds anywhere in the oracle.
@@ -86,6 +88,62 @@ MUTANTS = [
 ]
 
 
+# (name, file under oracle/, text, planted replacement): the NumPy parts of the oracle
+PY_PINS = ["tests/test_oracle_atrous_pins.py", "tests/test_oracle_cnn_pins.py"]
+PY_MUTANTS = [
+    # a-trous smoothing (Sec. III-A)
+    ("atrous_linear_dilation", "atrous.py", "        s = 1 << lev", "        s = lev + 1"),
+    ("atrous_tap_set", "atrous.py", "TAPS = np.array([1.0, 4.0, 6.0, 4.0, 1.0]) / 16.0",
+     "TAPS = np.array([1.0, 2.0, 6.0, 2.0, 1.0]) / 12.0"),
+    ("atrous_rows_wrap", "atrous.py", "    out = np.full_like(A, fill)\n    rolled = np.roll(A, -dc, axis=1)",
+     "    return np.roll(np.roll(A, -dc, axis=1), -dr, axis=0)\n    rolled = np.roll(A, -dc, axis=1)"),
+    ("atrous_plane_distance_sign", "atrous.py", "dpl = np.sum(N * (Pq - P), axis=-1)",
+     "dpl = np.sum(N * (Pq + P), axis=-1)"),
+    ("atrous_no_normalisation", "atrous.py",
+     "        N = np.where(V[..., None], acc / np.where(norm > 0, norm, 1.0)[..., None], 0.0)",
+     "        N = np.where(V[..., None], acc, 0.0)"),
+    ("atrous_normal_weight_unscaled", "atrous.py", "np.exp(-dn2 * inv_sn2)", "np.exp(-dn2)"),
+    # pose network (no counterpart in the paper)
+    ("cnn_im2col_taps_swapped", "cnn.py", "cols[:, :, :, ky, kx, :] = xp[:, ky:ky + 2 * Ho:2, kx:kx + 2 * Wo:2, :]",
+     "cols[:, :, :, ky, kx, :] = xp[:, kx:kx + 2 * Ho:2, ky:ky + 2 * Wo:2, :]"),
+    ("cnn_col2im_taps_swapped", "cnn.py", "+= d[:, :, :, ky, kx, :]", "+= d[:, :, :, kx, ky, :]"),
+    ("cnn_relu_mask_dropped", "cnn.py", "        dy = da.reshape(-1, co) * (cache[f\"pre{l}\"] > 0)",
+     "        dy = da.reshape(-1, co)"),
+    ("cnn_pool_scale_dropped", "cnn.py", "dg[:, None, None, :] / (H * W)", "dg[:, None, None, :]"),
+    ("cnn_loss_gradient_factor", "cnn.py", "    return L, 2.0 * weights * diff / B", "    return L, weights * diff / B"),
+    ("cnn_bias_gradient_mean", "cnn.py", "\"bf\": dout.sum(axis=0)", "\"bf\": dout.mean(axis=0)"),
+    ("adam_no_bias_correction", "cnn.py", "        mh = m[k] / (1 - b1 ** t)", "        mh = m[k]"),
+    ("downsample_counts_empty_pixels", "cnn.py", "                out[r, c, 0] = d[m].mean() / depth_scale",
+     "                out[r, c, 0] = d.mean() / depth_scale"),
+    ("downsample_depth_test_dropped", "cnn.py",
+     "            m = (d > 0) & (n[..., 3] != 0) & (np.abs(n[..., :3]).sum(-1) > 0)",
+     "            m = (n[..., 3] != 0) & (np.abs(n[..., :3]).sum(-1) > 0)"),
+]
+
+
+def _survives_py(name, fname, old, new, workdir):
+    """True when the NumPy oracle's pins all pass with this mistake planted in a copy of the tree."""
+    import shutil
+    tree = os.path.join(workdir, name)
+    ignore = shutil.ignore_patterns("__pycache__", "*.so", "*.o")
+    for d in ("oracle", "synth", "tests"):
+        shutil.copytree(os.path.join(ROOT, d), os.path.join(tree, d), ignore=ignore)
+    path = os.path.join(tree, "oracle", fname)
+    src = open(path).read()
+    assert src.count(old) == 1, f"{name}: the text to mutate must occur exactly once"
+    mutated = src.replace(old, new)
+    compile(mutated, path, "exec")  # a planted mistake must still be a valid program
+    with open(path, "w") as fh:
+        fh.write(mutated)
+    cmd = [sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *PY_PINS]
+    r = subprocess.run(cmd, cwd=tree, capture_output=True, text=True, timeout=900)
+    assert r.returncode in (0, 1), f"{name}: pytest ended with status {r.returncode}:\n{r.stdout[-1500:]}"
+    # a mutant counts as caught only through a failing pin, never through an import or collection error
+    summary = [ln for ln in r.stdout.splitlines() if ln.strip()][-1]
+    assert r.returncode == 0 or ("failed" in summary and "error" not in summary), f"{name}: {summary}"
+    return r.returncode == 0
+
+
 def _survives(name, old, new, workdir):
     """True when every pin passes on the oracle with this mistake planted."""
     src = open(SRC).read()
@@ -102,6 +160,9 @@ def _survives(name, old, new, workdir):
         cmd += ["--deselect", s]
     r = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
     assert r.returncode in (0, 1), f"{name}: pytest ended with status {r.returncode}:\n{r.stdout[-1500:]}"
+    # a mutant counts as caught only through a failing pin, never through an import or collection error
+    summary = [ln for ln in r.stdout.splitlines() if ln.strip()][-1]
+    assert r.returncode == 0 or ("failed" in summary and "error" not in summary), f"{name}: {summary}"
     return r.returncode == 0
 
 
@@ -109,5 +170,13 @@ def test_pins_fail_on_every_planted_mistake(tmp_path):
     workers = max(1, min(len(MUTANTS), os.cpu_count() or 1))
     with cf.ThreadPoolExecutor(max_workers=workers) as ex:
         results = list(ex.map(lambda m: (m[0], _survives(*m, str(tmp_path))), MUTANTS))
+    survivors = [name for name, alive in results if alive]
+    assert not survivors, f"planted mistakes that passed every pin: {survivors}"
+
+
+def test_numpy_oracle_pins_fail_on_every_planted_mistake(tmp_path):
+    workers = max(1, min(len(PY_MUTANTS), os.cpu_count() or 1))
+    with cf.ThreadPoolExecutor(max_workers=workers) as ex:
+        results = list(ex.map(lambda m: (m[0], _survives_py(*m, str(tmp_path))), PY_MUTANTS))
     survivors = [name for name, alive in results if alive]
     assert not survivors, f"planted mistakes that passed every pin: {survivors}"
