@@ -3,9 +3,9 @@
 Each case copies ``oracle/upslam_oracle.c``, plants one plausible mistake (a
 flipped sign, a dropped term, a transposed operand, a wrong index or gate),
 compiles the copy with the oracle's own flags and runs the pin tests against it
-in a child process (``UPSLAM_ORACLE_LIB``).  The NumPy parts of the oracle
-(a-trous smoothing, pose network, downsampling) are mutated the same way in a
-copy of the source tree.  The pins pass on the real oracle; a
+in a child process (``UPSLAM_ORACLE_LIB``).  The Python parts of the oracle
+(a-trous smoothing, pose network, downsampling, the grid-search and consistency
+glue) are mutated the same way in a copy of the source tree.  The pins pass on the real oracle; a
 case passes here only when some pin fails on the broken copy.  This shows that
 the pins are tied to the paper and the mathematics tightly enough to catch
 mistakes of these kinds anywhere in the oracle.
@@ -88,7 +88,7 @@ MUTANTS = [
 ]
 
 
-# (name, file under oracle/, text, planted replacement): the NumPy parts of the oracle
+# (name, file under oracle/, text, planted replacement): the Python parts of the oracle
 PY_PINS = ["tests/test_oracle_atrous_pins.py", "tests/test_oracle_cnn_pins.py"]
 PY_MUTANTS = [
     # a-trous smoothing (Sec. III-A)
@@ -115,14 +115,19 @@ PY_MUTANTS = [
     ("adam_no_bias_correction", "cnn.py", "        mh = m[k] / (1 - b1 ** t)", "        mh = m[k]"),
     ("downsample_counts_empty_pixels", "cnn.py", "                out[r, c, 0] = d[m].mean() / depth_scale",
      "                out[r, c, 0] = d.mean() / depth_scale"),
+    # the Python glue of the oracle: grid search (Sec. III-C) and the two-way consistency check
+    ("grid_not_subsampled", "__init__.py", "    kd[::stride, ::stride] = np.asarray(kf_depth, np.float32)[::stride, ::stride]",
+     "    kd[:, :] = np.asarray(kf_depth, np.float32)"),
+    ("consistency_second_pose_not_inverted", "__init__.py",
+     "    Tba = np.ascontiguousarray(pose_inv_fixed(Tab).reshape(12))", "    Tba = Tab"),
     ("downsample_depth_test_dropped", "cnn.py",
      "            m = (d > 0) & (n[..., 3] != 0) & (np.abs(n[..., :3]).sum(-1) > 0)",
      "            m = (n[..., 3] != 0) & (np.abs(n[..., :3]).sum(-1) > 0)"),
 ]
 
 
-def _survives_py(name, fname, old, new, workdir):
-    """True when the NumPy oracle's pins all pass with this mistake planted in a copy of the tree."""
+def _survives_py(name, fname, old, new, workdir, oracle_lib):
+    """True when every pin passes with this mistake planted in a copy of the oracle's Python source."""
     import shutil
     tree = os.path.join(workdir, name)
     ignore = shutil.ignore_patterns("__pycache__", "*.so", "*.o")
@@ -135,8 +140,11 @@ def _survives_py(name, fname, old, new, workdir):
     compile(mutated, path, "exec")  # a planted mistake must still be a valid program
     with open(path, "w") as fh:
         fh.write(mutated)
-    cmd = [sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *PY_PINS]
-    r = subprocess.run(cmd, cwd=tree, capture_output=True, text=True, timeout=900)
+    cmd = [sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *PY_PINS, *PINS]
+    for s in SLOW:
+        cmd += ["--deselect", s]
+    env = dict(os.environ, UPSLAM_ORACLE_LIB=oracle_lib)
+    r = subprocess.run(cmd, cwd=tree, env=env, capture_output=True, text=True, timeout=900)
     assert r.returncode in (0, 1), f"{name}: pytest ended with status {r.returncode}:\n{r.stdout[-1500:]}"
     # a mutant counts as caught only through a failing pin, never through an import or collection error
     summary = [ln for ln in r.stdout.splitlines() if ln.strip()][-1]
@@ -175,8 +183,11 @@ def test_pins_fail_on_every_planted_mistake(tmp_path):
 
 
 def test_numpy_oracle_pins_fail_on_every_planted_mistake(tmp_path):
+    sys.path.insert(0, ROOT)
+    import oracle
+    lib = oracle.build()  # the unmodified C part, shared by every copy
     workers = max(1, min(len(PY_MUTANTS), os.cpu_count() or 1))
     with cf.ThreadPoolExecutor(max_workers=workers) as ex:
-        results = list(ex.map(lambda m: (m[0], _survives_py(*m, str(tmp_path))), PY_MUTANTS))
+        results = list(ex.map(lambda m: (m[0], _survives_py(*m, str(tmp_path), lib)), PY_MUTANTS))
     survivors = [name for name, alive in results if alive]
     assert not survivors, f"planted mistakes that passed every pin: {survivors}"
