@@ -131,3 +131,73 @@ def test_cnn_workspace_and_error_word_offsets():
         assert ws > prev and ws % 256 == 0
         assert off == ws - 256 and off % 256 == 0
         prev = ws
+
+
+def test_fused_batched_and_added_entry_points_reject_bad_arguments():
+    """The fused per-sweep launches, the batched form, the next rows and the pose network check their
+    arguments on the host too: each bad call returns INVALID_ARG before any CUDA call."""
+    L = up.lib()
+    INV = _abi.ERR_INVALID_ARG
+    pp = _pano()
+    fake = ctypes.c_void_p(256)
+    ks = _abi.Keyframe(pp, 256, 256, 0, 256)
+    ss = _abi.Sweep(pp, 256, 256, 0)
+    ip = _abi.IcpParams(0.5, 0.86, 10, 6, 1e-6, 1e-6, 1e-12)
+    fp = _abi.FuseParams(0.2, 0.86, 10.0, 0.3)
+    ws = int(L.upslam_icp_workspace_bytes(ctypes.byref(ks)))
+    K, S, I, F = (ctypes.byref(x) for x in (ks, ss, ip, fp))
+    # motion prior: mode out of range, or a mode that needs a buffer that is missing
+    for prior, prev, motion in ((3, fake, fake), (-1, fake, fake), (1, None, fake), (2, fake, None)):
+        assert L.upslam_register(K, S, prev, motion, fake, prior, I, fake, fake, ws, None) == INV
+        assert L.upslam_track(K, S, prev, motion, fake, prior, I, F, fake, fake, ws, fake, None) == INV
+    # track: a bad keyframe-update parameter, no keyframe z-buffer, no iterations
+    assert L.upslam_track(K, S, None, None, fake, 0, I, ctypes.byref(_abi.FuseParams(0.2, 0.86, 0.5, 0.3)), fake,
+                          fake, ws, fake, None) == INV
+    assert L.upslam_track(K, S, None, None, fake, 0, I, F, fake, fake, ws, None, None) == INV
+    assert L.upslam_track(K, S, None, None, fake, 0, ctypes.byref(_abi.IcpParams(0.5, 0.86, 0, 6, 1e-6, 1e-6, 1e-12)),
+                          F, fake, fake, ws, fake, None) == INV
+    # whole-sweep launch: points missing, buffers missing, a misaligned point array
+    sb = _abi.SweepBuffers(pp, 256, 256, 256, 256, 256, 0)
+    npar = _abi.NormalParams(0.05, 0.1, 1e-4)
+    SB, NP = ctypes.byref(sb), ctypes.byref(npar)
+    assert L.upslam_track_scan(K, None, 10, SB, NP, None, None, fake, 0, I, F, fake, fake, ws, fake, None) == INV
+    assert L.upslam_track_scan(K, fake, 10, None, NP, None, None, fake, 0, I, F, fake, fake, ws, fake, None) == INV
+    assert L.upslam_track_scan(K, ctypes.c_void_p(260), 10, SB, NP, None, None, fake, 0, I, F, fake, fake, ws, fake,
+                               None) == INV
+    assert L.upslam_track_scan(K, fake, -1, SB, NP, None, None, fake, 0, I, F, fake, fake, ws, fake, None) == INV
+    # the allocation-free form needs its stats record
+    assert L.upslam_icp_noalloc(K, S, fake, I, None, None) == INV
+    # batched form: no keyframes, no hypotheses, too many keyframes
+    tiles = ctypes.byref(_abi.BatchTiles(512, 512))
+    for n_kf, n_hyp in ((0, 8), (4, 0), (257, 1)):
+        assert L.upslam_icp_batched(fake, K, n_kf, S, n_hyp, fake, I, fake, fake, 1 << 20, tiles, None) == INV
+    # grid search: no candidates, a zero stride, a negative count
+    assert L.upslam_grid_score(K, S, fake, 0, 4, I, fake, fake, fake, None) == INV
+    assert L.upslam_grid_score(K, S, fake, 9, 0, I, fake, fake, fake, None) == INV
+    assert L.upslam_grid_candidates(fake, fake, -1, fake, None) == INV
+    assert L.upslam_grid_candidates(fake, fake, 0, fake, None) == _abi.OK  # nothing to do, nothing launched
+    # consistency: a keyframe against itself in place, a negative tolerance, a misaligned workspace
+    kb = _abi.Keyframe(pp, 512, 512, 0, 512)
+    KB = ctypes.byref(kb)
+    cws = int(L.upslam_consistency_workspace_bytes(K, KB))
+    assert L.upslam_keyframe_consistency(K, K, fake, 0.05, 0.2, fake, cws, None, None) == INV
+    assert L.upslam_keyframe_consistency(K, KB, fake, -0.05, 0.2, fake, cws, None, None) == INV
+    assert L.upslam_keyframe_consistency(K, KB, fake, 0.05, 0.2, ctypes.c_void_p(264), cws, None, None) == INV
+    assert L.upslam_keyframe_consistency(K, KB, fake, 0.05, 0.2, fake, 0, None, None) == INV
+    # pose network: an empty batch, a misaligned workspace, a missing loss, Adam before step 1
+    nws = int(L.upslam_cnn_workspace_bytes(4))
+    assert L.upslam_cnn_forward(fake, fake, 0, fake, fake, nws, None) == INV
+    assert L.upslam_cnn_forward(fake, fake, 4, fake, ctypes.c_void_p(264), nws, None) == INV
+    assert L.upslam_cnn_backward(fake, fake, 4, fake, fake, fake, fake, None, fake, nws, None) == INV
+    assert L.upslam_cnn_adam(fake, fake, fake, fake, 0, ctypes.c_float(1e-3), None) == INV
+    # network input: cells that do not divide the panorama, a non-positive depth scale, a bad precision
+    big = _abi.Pano(64, 256, 0.5, 256 / 6.283185307, 64.0, 0.1, 100.0)
+    BP = ctypes.byref(big)
+    assert L.upslam_downsample(fake, fake, 0, BP, 60, 256, ctypes.c_float(20.0), fake, 8, 0, None) == INV
+    assert L.upslam_downsample(fake, fake, 0, BP, 64, 256, ctypes.c_float(0.0), fake, 8, 0, None) == INV
+    assert L.upslam_downsample(fake, fake, 3, BP, 64, 256, ctypes.c_float(20.0), fake, 8, 0, None) == INV
+    assert L.upslam_downsample(fake, fake, 0, BP, 64, 256, ctypes.c_float(20.0), fake, 8, 5, None) == INV
+    # twists to poses, and keyframe points
+    assert L.upslam_se3_exp(fake, -1, fake, None) == INV
+    assert L.upslam_se3_exp(fake, 0, fake, None) == _abi.OK
+    assert L.upslam_unproject(fake, ctypes.byref(pp), fake, ctypes.c_void_p(264), None) == INV
