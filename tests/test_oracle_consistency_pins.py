@@ -70,3 +70,35 @@ def test_pose_inverse():
     Ti = oracle.pose_inv_fixed(T)
     M = np.vstack([T, [0, 0, 0, 1]])
     assert np.abs(np.vstack([Ti, [0, 0, 0, 1]]) - np.linalg.inv(M)).max() < 1e-14
+
+
+def _tiny():
+    from tests.helpers import tiny_pano
+    return tiny_pano(8, 16)
+
+
+def test_margin_has_relative_and_absolute_parts():
+    """At the identity a sample at r = 1 m is seen through only when every depth around it in the other
+    keyframe lies beyond r + (0.05 r + 0.2 m) = 1.25 m."""
+    pp = _tiny()
+    da = np.full((8, 16), 1.0, np.float32)
+    for other, flagged in ((1.1, False), (1.2, False), (1.3, True)):
+        db = np.full((8, 16), other, np.float32)
+        fa, _ = oracle.consistency(da, pp, db, pp, IDENTITY, rel=0.05, abs_m=0.2)
+        assert fa.all() if flagged else not fa.any(), other
+
+
+def test_neighbourhood_covers_the_rows_above_and_below():
+    """A sample stays when any depth-holding pixel of the other keyframe's 3 x 3 neighbourhood around it
+    lies within the margin, even though the centre pixel saw through it."""
+    pp = _tiny()
+    da = np.zeros((8, 16), np.float32)
+    da[4, 8] = 1.0
+    db = np.full((8, 16), 5.0, np.float32)
+    fa, _ = oracle.consistency(da, pp, db, pp, IDENTITY)
+    assert fa[4, 8]
+    for dv, du in ((-1, 0), (1, 0), (-1, -1), (1, 1), (0, 1), (0, -1)):
+        db2 = db.copy()
+        db2[4 + dv, 8 + du] = 1.0
+        fa2, _ = oracle.consistency(da, pp, db2, pp, IDENTITY)
+        assert not fa2[4, 8], (dv, du)

@@ -85,6 +85,25 @@ MUTANTS = [
      "                    if (dn > 0.0f && (dn > lim)) {"),
     ("pose_inverse_sign", "        out[4 * i + 3] = -((T[i] * T[3] + T[4 + i] * T[7]) + T[8 + i] * T[11]);",
      "        out[4 * i + 3] = ((T[i] * T[3] + T[4 + i] * T[7]) + T[8 + i] * T[11]);"),
+    # second batch: thresholds, counts and the less-travelled branches
+    ("se3_c_coefficient_power", "C = (th - sin(th)) / (th2 * th);", "C = (th - sin(th)) / th2;"),
+    ("solve_pivot_threshold_dropped", "if (!(s > pivot_eps * dmax)) return 3;", "if (!(s > 0.0)) return 3;"),
+    ("range_minimum_dropped", "if (!(r >= pp->r_min && r <= pp->r_max)) return 0;", "if (!(r <= pp->r_max)) return 0;"),
+    ("normal_degeneracy_test_dropped", "if (!(nn >= (double)np->min_cross * na * nb) || nn == 0.0) continue;",
+     "if (nn == 0.0) continue;"),
+    ("keyframe_normal_validity_dropped",
+     "if (!(nk[0] * nk[0] + nk[1] * nk[1] + nk[2] * nk[2] > 0.25f)) return 0;", "(void)nk;"),
+    ("sse_not_squared", "st->sse += w * r * r;", "st->sse += w * r;"),
+    ("valid_counts_every_pixel", "st->valid += sp4[4 * j + 3] != 0.0f;", "st->valid += 1;"),
+    ("convergence_either_norm", "st->converged = (wn < ip->eps_rot && vn < ip->eps_trans) ? 1 : 0;",
+     "st->converged = (wn < ip->eps_rot || vn < ip->eps_trans) ? 1 : 0;"),
+    ("fusion_normal_weights_swapped", "double nn[3] = { w * n[0] + Rm[0], w * n[1] + Rm[1], w * n[2] + Rm[2] };",
+     "double nn[3] = { n[0] + w * Rm[0], n[1] + w * Rm[1], n[2] + w * Rm[2] };"),
+    ("fusion_range_in_sweep_frame", "double dm = sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);",
+     "double dm = sqrt((double)P[0] * P[0] + (double)P[1] * P[1] + (double)P[2] * P[2]);"),
+    ("consistency_centre_row_only", "for (int dv = -1; dv <= 1 && seen_through; ++dv) {",
+     "for (int dv = 0; dv <= 0 && seen_through; ++dv) {"),
+    ("consistency_absolute_margin_dropped", "float lim = (rel * r + abs_m) + r;", "float lim = rel * r + r;"),
 ]
 
 

@@ -487,3 +487,117 @@ def test_sequence_tracks_tunnel():
         assert acc
     dt, dr = synth.pose_error(T, synth.relative(seq.poses[0], seq.poses[11]))
     assert dt < 0.03 and dr < math.radians(0.3)
+
+
+# ----------------------------------------------------------------------------- thresholds and branches
+
+def test_points_outside_the_range_interval_are_not_binned():
+    """a1: a point is binned only when its range lies in [r_min, r_max]."""
+    pp = tiny_pano(4, 8, r_min=0.5, r_max=10.0)
+    rt, ct = oracle.dir_table(pp)
+    el_c, el_s, az_c, az_s = rt[2], rt[3], ct[6], ct[7]  # centre of pixel (1, 3)
+    d = np.array([el_c * az_c, el_c * az_s, el_s], np.float64)
+    for r, inside in ((0.4, False), (0.6, True), (9.0, True), (11.0, False)):
+        got = oracle.bin_point((d * r).astype(np.float32), pp)
+        assert (got is not None) == inside, (r, got)
+        if inside:
+            assert got[:2] == (1, 3)
+
+
+def test_nearly_collinear_neighbours_give_no_normal():
+    """a2 reading: |a x b| < min_cross |a| |b| leaves the pixel without a normal (here 1e-5 < 1e-4)."""
+    pts = np.zeros((4, 8, 4), np.float32)
+    depth = np.zeros((4, 8), np.float32)
+    for (v, u), p in (((1, 1), (2.0, 0.0, 0.0)), ((1, 2), (2.0, 0.1, 0.0)), ((2, 1), (2.0, 0.2, 2e-6))):
+        pts[v, u] = (*p, 1.0)
+        depth[v, u] = np.linalg.norm(p)
+    _, val = oracle.normals(pts, depth, tiny_pano(4, 8))
+    assert not val[1, 1]
+    pts[2, 1, 2] = 0.1  # b now leaves the line of a: a proper normal
+    _, val = oracle.normals(pts, depth, tiny_pano(4, 8))
+    assert val[1, 1]
+
+
+def test_solve6_rejects_a_pivot_below_the_relative_threshold():
+    """Degenerate-solve reading: a Cholesky pivot at or below pivot_eps * max diagonal is rank deficiency."""
+    iu = np.triu_indices(6)
+    st, _ = oracle.solve6(np.diag([1.0, 1.0, 1.0, 1.0, 1.0, 1e-14])[iu], np.ones(6), 1e-12)
+    assert st == oracle.DEGENERATE
+    st, x = oracle.solve6(np.diag([1.0, 1.0, 1.0, 1.0, 1.0, 1e-10])[iu], np.ones(6), 1e-12)
+    assert st == 0 and np.allclose(x, [1, 1, 1, 1, 1, 1e10], rtol=1e-12)
+
+
+def test_keyframe_pixels_without_a_normal_are_not_correspondences():
+    """Eq. 1 pairs keyframe samples (a depth and a normal).  With the normal gate opened (cos = -1), a
+    pixel whose normal is missing must still not pair: the normal equations equal those of the same
+    keyframe with that pixel's depth removed as well."""
+    c, prm, sp4, sn4, kd, kn4 = room_sweep_and_keyframe(noise=False)
+    open_gate = oracle.Params(cos_theta_max=-1.0)
+    kn_b = kn4.copy()
+    kn_b[::3, ::2] = 0.0
+    kd_b = kd.copy()
+    kd_b[::3, ::2] = 0.0
+    a = oracle.normal_equations(kd, kn_b, c.kf, sp4, sn4, c.sweep, c.T_true, open_gate)
+    b = oracle.normal_equations(kd_b, kn_b, c.kf, sp4, sn4, c.sweep, c.T_true, open_gate)
+    assert a["inliers"] == b["inliers"] > 1000
+    assert np.array_equal(a["A"], b["A"]) and np.array_equal(a["b"], b["b"])
+
+
+def test_convergence_needs_both_rotation_and_translation_small():
+    """Convergence reading: a step converges when |omega| < eps_rot and |v| < eps_trans, both.  With one
+    threshold made trivial (1 rad or 1 m) and the other unreachable (1e-12), the first step from a 5 cm /
+    2 degree offset must not report convergence; with both at their defaults the run converges with
+    both norms small."""
+    c = configs.room_case(noise=False)
+    sp4, sn4, _, _ = oracle.sweep_frame(c.scan, c.sweep, oracle.Params())
+    kd, kn4 = rendered_keyframe(c.scene, c.kf, c.P_w_kf)
+    for eps_rot, eps_trans in ((1.0, 1e-12), (1e-12, 1.0)):
+        prm = oracle.Params(eps_rot=eps_rot, eps_trans=eps_trans)
+        _, st = oracle.icp_step(kd, kn4, c.kf, sp4, sn4, c.sweep, IDENTITY, prm)
+        xi = np.asarray(st["xi"])
+        assert np.linalg.norm(xi[:3]) < 1.0 and np.linalg.norm(xi[3:]) < 1.0
+        assert not st["converged"], (eps_rot, eps_trans)
+    prm = oracle.Params(max_iters=40)
+    _, st, iters = oracle.icp(kd, kn4, c.kf, sp4, sn4, c.sweep, IDENTITY, prm)
+    xi = np.asarray(st["xi"])
+    assert st["converged"] and iters < 40
+    assert np.linalg.norm(xi[:3]) < prm.eps_rot and np.linalg.norm(xi[3:]) < prm.eps_trans
+
+
+def test_fusion_blends_normals_with_the_sample_count():
+    """Sec. III-C with the fusion reading: n <- unit(w n + R m).  Every keyframe normal is n0 with count 2
+    and every sweep normal is m (20 degrees apart, inside the gate), at the identity pose: each averaged
+    pixel must hold unit(2 n0 + m) with count 3."""
+    c = configs.room_case(noise=False)
+    prm = oracle.Params()
+    sp4, sn4, _, _ = oracle.sweep_frame(c.scan, c.sweep, prm)
+    d, _, _ = synth.render_keyframe(c.scene, c.kf, c.P_w_s)  # keyframe at the sweep's own pose
+    n0 = np.array([0.0, 0.0, 1.0])
+    m = np.array([math.sin(math.radians(20.0)), 0.0, math.cos(math.radians(20.0))])
+    sn = sn4.copy()
+    sn[sn[..., 3] != 0, :3] = m
+    has = d > 0
+    kf = oracle.Keyframe(c.kf, d, np.where(has[..., None], n0, 0.0), np.where(has, 2.0, 0.0))
+    fused, _ = oracle.fuse(kf, sp4, sn, c.sweep, IDENTITY, prm)
+    averaged = kf.w == 3.0
+    assert fused == averaged.sum() > 1000
+    want = 2.0 * n0 + m.astype(np.float32)  # sweep normals are stored in FP32
+    want /= np.linalg.norm(want)
+    assert np.abs(kf.nrm[averaged] - want).max() < 1e-12
+
+
+def test_fusion_measures_depth_in_the_keyframe_frame():
+    """Sec. III-C: the averaged-in depth is the sweep sample's range seen from the keyframe, |T P|.  An
+    exact sweep from 0.5 m / 10 degrees away, fused with the true pose into an exact keyframe, leaves the
+    keyframe depths where the geometry puts them."""
+    c = configs.room_case(noise=False, trans_m=0.5, rot_deg=10.0)
+    prm = oracle.Params()
+    sp4, sn4, _, _ = oracle.sweep_frame(c.scan, c.sweep, prm)
+    kd, kn4 = rendered_keyframe(c.scene, c.kf, c.P_w_kf)
+    has = kd > 0
+    kf = oracle.Keyframe(c.kf, kd.astype(np.float64), kn4[..., :3].astype(np.float64), np.where(has, 1.0, 0.0))
+    fused, _ = oracle.fuse(kf, sp4, sn4, c.sweep, c.T_true, prm)
+    averaged = kf.w == 2.0
+    assert fused == averaged.sum() > 500
+    err = np.abs(kf.depth[averaged] - kd[averaged])
+    assert np.median(err) < 0.01 and err.max() < 0.1, (np.median(err), err.max())
