@@ -76,3 +76,14 @@ def test_stride_is_a_subsample():
             hits += int(ok)
     s4, _ = oracle.grid_score(kd, kn, c.kf, sp4, sn4, c.sweep, [T], 4, prm)
     assert s4[0] == hits
+
+
+def test_ties_go_to_the_first_candidate():
+    """Grid reading: the first candidate with the largest score wins, so equal candidates resolve to the
+    earliest one."""
+    c, sp4, sn4, kd, kn = _exact_room()
+    prm = oracle.Params(d_max=0.1)
+    far = synth.pose_mul(synth.pose(np.eye(3), [1.5, -1.0, 0.0]), c.T_true)
+    scores, best = oracle.grid_score(kd, kn, c.kf, sp4, sn4, c.sweep, [far, c.T_true, c.T_true, far], 2, prm)
+    assert scores[1] == scores[2] > scores[0] == scores[3]
+    assert best == 1

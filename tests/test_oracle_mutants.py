@@ -104,6 +104,8 @@ MUTANTS = [
     ("consistency_centre_row_only", "for (int dv = -1; dv <= 1 && seen_through; ++dv) {",
      "for (int dv = 0; dv <= 0 && seen_through; ++dv) {"),
     ("consistency_absolute_margin_dropped", "float lim = (rel * r + abs_m) + r;", "float lim = rel * r + r;"),
+    ("irls_weight_sum", "                w = 1.0 / (ar > (double)ip->loss_delta ? ar : (double)ip->loss_delta);",
+     "                w = 1.0 / (ar + (double)ip->loss_delta);"),
 ]
 
 
@@ -137,6 +139,8 @@ PY_MUTANTS = [
     # the Python glue of the oracle: grid search (Sec. III-C) and the two-way consistency check
     ("grid_not_subsampled", "__init__.py", "    kd[::stride, ::stride] = np.asarray(kf_depth, np.float32)[::stride, ::stride]",
      "    kd[:, :] = np.asarray(kf_depth, np.float32)"),
+    ("grid_last_best", "__init__.py", "    return scores, int(np.argmax(scores)) if len(scores) else -1",
+     "    return scores, int(len(scores) - 1 - np.argmax(scores[::-1])) if len(scores) else -1"),
     ("consistency_second_pose_not_inverted", "__init__.py",
      "    Tba = np.ascontiguousarray(pose_inv_fixed(Tab).reshape(12))", "    Tba = Tab"),
     ("downsample_depth_test_dropped", "cnn.py",
