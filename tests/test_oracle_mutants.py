@@ -134,6 +134,13 @@ PY_MUTANTS = [
     ("cnn_loss_gradient_factor", "cnn.py", "    return L, 2.0 * weights * diff / B", "    return L, weights * diff / B"),
     ("cnn_bias_gradient_mean", "cnn.py", "\"bf\": dout.sum(axis=0)", "\"bf\": dout.mean(axis=0)"),
     ("adam_no_bias_correction", "cnn.py", "        mh = m[k] / (1 - b1 ** t)", "        mh = m[k]"),
+    ("adam_no_second_moment_correction", "cnn.py", "        vh = v[k] / (1 - b2 ** t)", "        vh = v[k]"),
+    ("adam_step_sign", "cnn.py", "        p[k] = p[k] - lr * mh / (np.sqrt(vh) + eps)",
+     "        p[k] = p[k] + lr * mh / (np.sqrt(vh) + eps)"),
+    ("cnn_forward_relu_dropped", "cnn.py", "        a = np.maximum(y, 0.0).reshape(B, H // 2, W // 2, co)",
+     "        a = y.reshape(B, H // 2, W // 2, co)"),
+    ("cnn_pool_sum", "cnn.py", "    g = x.mean(axis=(1, 2))", "    g = x.sum(axis=(1, 2))"),
+    ("cnn_head_bias_dropped", "cnn.py", "    out = g @ p[\"wf\"].T + p[\"bf\"]", "    out = g @ p[\"wf\"].T"),
     ("downsample_counts_empty_pixels", "cnn.py", "                out[r, c, 0] = d[m].mean() / depth_scale",
      "                out[r, c, 0] = d.mean() / depth_scale"),
     # the Python glue of the oracle: grid search (Sec. III-C) and the two-way consistency check
