@@ -26,6 +26,9 @@ PINS = ["tests/test_oracle_pins.py", "tests/test_oracle_consistency_pins.py", "t
 SLOW = ["tests/test_oracle_pins.py::test_sequence_tracks_tunnel",
         "tests/test_oracle_irls_pins.py::test_weighted_normal_equations_match_per_pixel_definition"]
 
+# each child runs single-threaded; the children run side by side
+ONE_THREAD = {"OMP_NUM_THREADS": "1", "OPENBLAS_NUM_THREADS": "1", "MKL_NUM_THREADS": "1"}
+
 # (name, text in upslam_oracle.c, planted replacement)
 MUTANTS = [
     # a1: binning (Sec. III-A)
@@ -173,7 +176,7 @@ def _survives_py(name, fname, old, new, workdir, oracle_lib):
     cmd = [sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *PY_PINS, *PINS]
     for s in SLOW:
         cmd += ["--deselect", s]
-    env = dict(os.environ, UPSLAM_ORACLE_LIB=oracle_lib)
+    env = dict(os.environ, UPSLAM_ORACLE_LIB=oracle_lib, **ONE_THREAD)
     r = subprocess.run(cmd, cwd=tree, env=env, capture_output=True, text=True, timeout=900)
     assert r.returncode in (0, 1), f"{name}: pytest ended with status {r.returncode}:\n{r.stdout[-1500:]}"
     # a mutant counts as caught only through a failing pin, never through an import or collection error
@@ -192,7 +195,7 @@ def _survives(name, old, new, workdir):
         fh.write(src.replace(old, new))
     subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", mutant_c,
                            "-o", mutant_so, "-lm"])
-    env = dict(os.environ, UPSLAM_ORACLE_LIB=mutant_so)
+    env = dict(os.environ, UPSLAM_ORACLE_LIB=mutant_so, **ONE_THREAD)
     cmd = [sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *PINS]
     for s in SLOW:
         cmd += ["--deselect", s]
