@@ -150,11 +150,11 @@ typedef struct {
     const float *d_dirs; /* direction table from upslam_pano_dirs */
 } upslam_keyframe;
 
-/* Size in floats of a panorama's direction table: 2*rows + 2*cols. */
+/* Size in floats of a panorama's direction table (Sec. III-A panoramas): 2*rows + 2*cols. */
 size_t upslam_pano_dirs_floats(const upslam_pano *pp);
 
 /*
- * Direction table of a panorama: cos/sin of every row-centre elevation and
+ * Direction table of a panorama (Sec. III-A): cos/sin of every row-centre elevation and
  * column-centre azimuth, computed in FP64 and rounded to FP32
  * (d_dirs[2v], d_dirs[2v+1] = cos, sin of el_v; then d_dirs[2*rows + 2u],
  * [.. + 1] = cos, sin of az_u).  The FP32 point of pixel (v, u) at depth d is
@@ -175,7 +175,8 @@ upslam_status upslam_pano_dirs(const upslam_pano *pp, float *d_dirs, void *strea
 upslam_status upslam_project(const float *d_pts, int32_t n, const double *d_pose12, const upslam_pano *pp,
                              uint64_t *d_zbuf, float *d_depth, int32_t *d_idx, float *d_pix, void *stream);
 
-/* Keyframe pixel points d_pix float4 [rows*cols] = depth * dir (valid = depth > 0). */
+/* Keyframe pixel points (Sec. III: a keyframe is a depth panorama) d_pix float4 [rows*cols] = depth * dir
+ * (valid = depth > 0). */
 upslam_status upslam_unproject(const float *d_depth, const upslam_pano *pp, const float *d_dirs, float *d_pix,
                                void *stream);
 
@@ -206,6 +207,7 @@ typedef struct {
 } upslam_atrous_params;
 
 /*
+ * A-trous smoothing arguments (Sec. III-A).
  * d_pix float4 [rows*cols] pixel points (16-byte aligned); d_nrm_in and
  * d_nrm_out float4 or half4 [rows*cols] = (nx, ny, nz, valid) in `precision`;
  * d_tmp a scratch image of the same size, needed when levels >= 2 (else may be
@@ -217,7 +219,7 @@ upslam_status upslam_atrous_normals(const upslam_pano *pp, const float *d_pix, c
                                     void *d_nrm_out, void *d_tmp, int32_t precision,
                                     const upslam_atrous_params *ap, void *stream);
 
-/* Workspace bytes that upslam_icp_step / upslam_icp need for this keyframe. */
+/* Workspace bytes that upslam_icp_step / upslam_icp (Sec. III-B, Eq. 1) need for this keyframe. */
 size_t upslam_icp_workspace_bytes(const upslam_keyframe *kf);
 
 /*
@@ -236,7 +238,7 @@ upslam_status upslam_icp_step(const upslam_keyframe *kf, const upslam_sweep *sw,
                               void *stream);
 
 /*
- * Up to ip->max_iters Gauss-Newton steps in ONE persistent cooperative launch
+ * Up to ip->max_iters Gauss-Newton steps of Eq. 1 (Sec. III-B) in ONE persistent cooperative launch
  * (one CTA per SM; a bounded grid-wide barrier per step).  Each CTA adds its
  * share of the step's J^T J, J^T r and counts into integer accumulators in the
  * workspace as exact fixed-point numbers, so the totals do not depend on the
@@ -267,7 +269,7 @@ upslam_status upslam_register(const upslam_keyframe *kf, const upslam_sweep *sw,
                               upslam_icp_stats *d_stats, void *d_ws, size_t ws_bytes, void *stream);
 
 /*
- * The whole registration and keyframe update of one sweep in ONE persistent
+ * The whole registration and keyframe update of one sweep (Sec. III-B, III-C) in ONE persistent
  * launch: upslam_register followed by upslam_fuse with the registered pose
  * (gated by the same acceptance test), reusing the keyframe samples the ICP
  * staged in shared memory.  Arguments as those two calls; ip->max_iters >= 1.
@@ -373,7 +375,7 @@ typedef struct {
 } upslam_sweep_buffers;
 
 /*
- * One whole sweep in ONE persistent cooperative launch: projection with the
+ * One whole sweep (Sec. III-A to III-C) in ONE persistent cooperative launch: projection with the
  * z-buffer, resolve and normals of the scan d_pts4 (float4 [n_pts], 16-byte
  * aligned) into the sweep buffers (as upslam_project with no pose followed by
  * upslam_normals, with the same results), then everything upslam_track does.
@@ -406,7 +408,7 @@ upslam_status upslam_grid_score(const upslam_keyframe *kf, const upslam_sweep *s
                                 int32_t stride, const upslam_icp_params *ip, uint64_t *d_scores, int32_t *d_best,
                                 double *d_best_pose12, void *stream);
 
-/* Candidate poses d_poses[i] = exp(xi_i^) * center (FP64 [n][12]) for FP32 twists
+/* Grid-search candidates (Sec. III-C): d_poses[i] = exp(xi_i^) * center (FP64 [n][12]) for FP32 twists
  * d_xi [n][6] = (omega, v), e.g. a grid of offsets around the current estimate. */
 upslam_status upslam_grid_candidates(const double *d_center12, const float *d_xi, int32_t n, double *d_poses,
                                      void *stream);
@@ -465,16 +467,18 @@ size_t upslam_cnn_workspace_bytes(int32_t batch);
 size_t upslam_cnn_error_offset(int32_t batch);
 upslam_status upslam_cnn_forward(const float *d_params, const void *d_x, int32_t batch, float *d_out, void *d_ws,
                                  size_t ws_bytes, void *stream);
-/* Loss sum_b sum_i w_i (out - target)^2 / batch into *d_loss and every parameter's gradient into d_grads
+/* Pose network (not in the paper), backward: loss sum_b sum_i w_i (out - target)^2 / batch into *d_loss and
+ * every parameter's gradient into d_grads
  * (overwritten), for the activations of the preceding upslam_cnn_forward on the same workspace. */
 upslam_status upslam_cnn_backward(const float *d_params, const void *d_x, int32_t batch, const float *d_out,
                                   const float *d_target, const float *d_wloss6, float *d_grads, float *d_loss,
                                   void *d_ws, size_t ws_bytes, void *stream);
-/* One Adam step (beta 0.9 / 0.999, eps 1e-8, bias-corrected for step >= 1) on the FP32 master parameters. */
+/* Pose network (not in the paper): one Adam step (beta 0.9 / 0.999, eps 1e-8, bias-corrected for step >= 1)
+ * on the FP32 master parameters. */
 upslam_status upslam_cnn_adam(float *d_params, const float *d_grads, float *d_m, float *d_v, int32_t step, float lr,
                               void *stream);
 /*
- * Downsample a panorama to out_rows x out_cols cells (rows and cols must
+ * Pose-network input (not in the paper): downsample a panorama to out_rows x out_cols cells (rows and cols must
  * divide evenly): per cell the mean over pixels holding a sample of
  * (depth / depth_scale, nx, ny, nz), zeros where none, written as BF16 to
  * d_out[cell * c_stride + c_off + 0..3].  d_nrm: float4 or half4
@@ -484,7 +488,8 @@ upslam_status upslam_downsample(const float *d_depth, const void *d_nrm, int32_t
                                 int32_t out_rows, int32_t out_cols, float depth_scale, void *d_out, int32_t c_stride,
                                 int32_t c_off, void *stream);
 
-/* Poses exp(xi^) (FP64 [n][12], row-major [R | t]) of n FP32 twists xi = (omega, v), e.g. network outputs. */
+/* Poses exp(xi^) (FP64 [n][12], row-major [R | t]) of n FP32 twists xi = (omega, v), e.g. the pose
+ * network's outputs (not in the paper), with the left update of the ICP step (Sec. III-B). */
 upslam_status upslam_se3_exp(const float *d_xi, int32_t n, double *d_poses, void *stream);
 
 /* Human-readable name of a status code (static storage). */
