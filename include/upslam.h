@@ -100,7 +100,12 @@ typedef struct {
 typedef enum { UPSLAM_LOSS_L2 = 0, UPSLAM_LOSS_L1 = 1 } upslam_loss;
 
 /* ICP (Sec. III-B, Eq. 1).  Omega keeps a correspondence when the points are
- * within d_max metres and the normals' cosine is >= cos_theta_max. */
+ * within d_max metres and the normals' cosine is >= cos_theta_max.  The paper
+ * gives no threshold; a coarse-to-fine gate (wide while a large initial error
+ * is taken out, then narrow) is selected by coarse_iters > 0: Gauss-Newton
+ * steps 0 .. coarse_iters - 1 of one multi-step call gate with d_max, later
+ * steps with d_max_fine.  coarse_iters = 0 gates every step with d_max.  A
+ * single upslam_icp_step always gates with d_max. */
 typedef struct {
     float d_max, cos_theta_max;
     int32_t max_iters;   /* iterations of upslam_icp */
@@ -109,6 +114,8 @@ typedef struct {
     double pivot_eps;          /* Cholesky pivot threshold relative to the largest diagonal */
     int32_t loss;              /* upslam_loss */
     float loss_delta;          /* metres; > 0 with UPSLAM_LOSS_L1 */
+    int32_t coarse_iters;      /* >= 0; steps gated with d_max before switching to d_max_fine */
+    float d_max_fine;          /* metres; > 0 when coarse_iters > 0 */
 } upslam_icp_params;
 
 /* Keyframe update (Sec. III-C). */
@@ -302,17 +309,23 @@ upslam_status upslam_fuse(const upslam_keyframe *kf, const upslam_sweep *sw, con
  * sweep deadline), a plugin whose host runtime owns the device allocator, or
  * code that may only use memory fixed at load time.  It runs exactly what
  * upslam_icp runs, but its workspace is a static device array inside the
- * library (upslam_icp_noalloc_capacity_bytes() bytes, 512.25 KiB, held on
- * every GPU that loads the library until the process exits) instead of d_ws.
- * The caller still provides the keyframe, sweep, pose and stats buffers.
+ * library (upslam_icp_noalloc_capacity_bytes() = 528384 bytes, 516 KiB: the
+ * control block plus 2048 per-CTA records, enough for devices of up to 1024
+ * SMs) instead of d_ws.  The caller still provides the keyframe, sweep, pose
+ * and stats buffers.
  * - Allocates nothing: no cudaMalloc / cudaFree, no allocating library call.
  *   The scratch's barrier counters are cleared with cudaMemsetAsync on the
  *   stream at every call.
- * - The first call on a device looks up the array's device address
- *   (cudaGetSymbolAddress) with that device current; make that first call
- *   before any stream capture.
+ * - The first call on a device is a warm-up: it looks up the array's device
+ *   address (cudaGetSymbolAddress) with that device current, and under lazy
+ *   module loading (the CUDA default) that lookup is what loads the library's
+ *   device code and its array onto the device, which can allocate and take a
+ *   driver lock.  Make that first call during set-up, before the real-time
+ *   loop and before any stream capture; later calls allocate nothing.  The
+ *   array then stays on every GPU the library was used on until the process
+ *   exits.
  * - Returns UPSLAM_ERR_CAPACITY when the launch this device needs would not fit
- *   the array (more than 2048 CTAs).
+ *   the array (more than 1024 SMs).
  * - Every call shares the one array: calls that overlap on the GPU (other
  *   streams, other threads) race and corrupt each other's results; serialise
  *   them on one stream.

@@ -22,6 +22,9 @@ Every function follows a passage of UPSLAM (arXiv 2101.00585):
 ``quality``            Sec. III-C: inliers / valid sweep measurements
 ``grid_score``         Sec. III-C: low-resolution alignment checks of candidate poses
 ``consistency``        Sec. III-C: mutual consistency of two keyframes (moving objects)
+``predict_pose``       Sec. IV-F footnote: zero-velocity / zero-acceleration prior
+``update_motion``      Sec. IV-F footnote: the last inter-sweep motion
+``track``              the per-sweep chain: prior, process_scan, motion update
 =====================  =============================================================
 
 Pins that tie it to the paper and to mathematics rather than to itself live in
@@ -32,7 +35,7 @@ from __future__ import annotations
 import ctypes
 import os
 import subprocess
-from dataclasses import dataclass
+from dataclasses import dataclass, replace
 
 import numpy as np
 
@@ -114,6 +117,9 @@ def _load():
         "orc_consistency_flags": (ctypes.c_int64, [_F, P(Pano), _F, P(Pano), _D, ctypes.c_float, ctypes.c_float,
                                                    _U8]),
         "orc_pose_inv_fixed": (None, [_D, _D]),
+        "orc_orthonormalise_rows": (None, [_D]),
+        "orc_predict_pose": (None, [_D, _D, _D]),
+        "orc_update_motion": (None, [_D, _D, _D]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -162,6 +168,10 @@ class Params:
     # weights 1 / max(|r|, loss_delta)
     loss: int = 0
     loss_delta: float = 0.01
+    # coarse-to-fine Omega gate of a whole registration (``icp``): steps 0 .. coarse_iters - 1 gate with
+    # d_max, later steps with d_max_fine; 0 steps gate every step with d_max
+    coarse_iters: int = 0
+    d_max_fine: float = 0.5
     # a-trous smoothing of the sweep normals (Sec. III-A); 0 levels = off
     atrous_levels: int = 0
     atrous_sigma_n: float = 0.5
@@ -292,12 +302,14 @@ def icp_step(kf_depth, kf_nrm4, kp, sp4, sn4, sw, T, prm: Params = Params()):
 
 
 def icp(kf_depth, kf_nrm4, kp, sp4, sn4, sw, T0, prm: Params = Params(), max_iters: int | None = None):
-    """Iterate icp_step until convergence, a degenerate system, or max_iters -> (T, last stats, steps)."""
+    """Iterate icp_step until convergence, a degenerate system, or max_iters -> (T, last stats, steps).
+    With prm.coarse_iters > 0, steps from coarse_iters on gate with d_max_fine instead of d_max."""
     T = np.ascontiguousarray(T0, np.float64).copy()
     iters = 0
     st = None
-    for _ in range(prm.max_iters if max_iters is None else max_iters):
-        Tn, st = icp_step(kf_depth, kf_nrm4, kp, sp4, sn4, sw, T, prm)
+    fine = replace(prm, d_max=prm.d_max_fine)
+    for i in range(prm.max_iters if max_iters is None else max_iters):
+        Tn, st = icp_step(kf_depth, kf_nrm4, kp, sp4, sn4, sw, T, fine if 0 < prm.coarse_iters <= i else prm)
         iters += 1
         if st["status"] == DEGENERATE:
             break
@@ -432,3 +444,39 @@ def process_scan(kf: Keyframe, scan4, sw, T0, prm: Params = Params()):
     if accepted:
         fuse(kf, sp4, sn4, sw, T, prm)
     return T, st, iters, accepted
+
+
+# ----------------------------------------------------------------------------- motion prior
+
+def _pose12(T) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(T, np.float64).reshape(12))
+
+
+def orthonormalise_rows(T) -> np.ndarray:
+    """Gram-Schmidt on the rotation rows of a 3x4 pose (r2 = r0 x r1)."""
+    out = _pose12(T).copy()
+    _load().orc_orthonormalise_rows(_d(out))
+    return out.reshape(3, 4)
+
+
+def predict_pose(T_prev, M=None) -> np.ndarray:
+    """Sec. IV-F footnote: the ICP initial guess.  M None: zero velocity (T_prev); else zero
+    acceleration, T_prev M with the rotation re-orthonormalised."""
+    out = np.empty(12)
+    _load().orc_predict_pose(_d(_pose12(T_prev)), None if M is None else _d(_pose12(M)), _d(out))
+    return out.reshape(3, 4)
+
+
+def update_motion(T_prev, T) -> np.ndarray:
+    """Sec. IV-F footnote: the last inter-sweep motion M = T_prev^-1 T, re-orthonormalised."""
+    out = np.empty(12)
+    _load().orc_update_motion(_d(_pose12(T_prev)), _d(_pose12(T)), _d(out))
+    return out.reshape(3, 4)
+
+
+def track(kf: Keyframe, scan4, sw, T_prev, M, prm: Params = Params(), constant_velocity: bool = True):
+    """One sweep of a tracked sequence: the prior from (T_prev, M), process_scan, then the motion
+    update.  -> (T, stats, iters, accepted, M_new); the next sweep's T_prev is T."""
+    T0 = predict_pose(T_prev, M if constant_velocity else None)
+    T, st, iters, accepted = process_scan(kf, scan4, sw, T0, prm)
+    return T, st, iters, accepted, update_motion(T_prev, T)

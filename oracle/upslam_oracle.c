@@ -15,7 +15,9 @@
  *   - Sec. III-C "Keyframe Update": every keyframe pixel is carried over to the
  *     sweep image, gated by the same kind of similarity test, and averaged in
  *     with a per-pixel sample count saturated at 10; the registration quality
- *     is inliers / valid sweep measurements.
+ *     is inliers / valid sweep measurements;
+ *   - Sec. IV-F footnote: the ICP initial guess from a zero-velocity or a
+ *     zero-acceleration motion prior.
  *
  * Arithmetic: values are FP64.  Where floating point decides an integer (the
  * pixel a point falls in, and the z-buffer winner), the decision is taken in
@@ -31,7 +33,9 @@
  * normals from the ray caster; identity gives zero residual; a known rigid
  * perturbation is recovered; a single plane is degenerate; the Jacobian against
  * finite differences; the 6x6 solve against LAPACK; SE(3) exp against the
- * matrix exponential; brute-force association; the fusion closed form.
+ * matrix exponential; brute-force association; the fusion closed form; the
+ * motion prior against constant-twist trajectories built by the matrix
+ * exponential.
  *
  * Build: gcc -O2 -ffp-contract=off -fno-fast-math -fPIC -shared upslam_oracle.c -lm
  */
@@ -693,4 +697,68 @@ void orc_pose_inv_fixed(const double *T, double *out) {
         for (int j = 0; j < 3; ++j) out[4 * i + j] = T[4 * j + i];
         out[4 * i + 3] = -((T[i] * T[3] + T[4 + i] * T[7]) + T[8 + i] * T[11]);
     }
+}
+
+/* ------------------------------------------------------------------ motion prior */
+
+/*
+ * Sec. IV-F footnote: the registration of a sweep starts from a motion prior,
+ * zero velocity by default (the previous sweep's pose) or zero acceleration
+ * (the previous pose carried on by the last inter-sweep motion).  Poses are
+ * 3x4 [R | t] maps sweep -> keyframe, so the sweep-to-sweep motion is
+ * M = T_prev^-1 T and the zero-acceleration guess is T_prev M.
+ *
+ * Reading: after each product the rotation is put back on SO(3) by
+ * Gram-Schmidt on its rows (r0 normalised, r1 minus its r0 component then
+ * normalised, r2 = r0 x r1), so that rounding cannot compound over a long
+ * sequence.  Plain FP64 with sqrt and division.
+ */
+static void pose_mul34(const double *A, const double *B, double *C) {
+    double t[12];
+    for (int i = 0; i < 3; ++i) {
+        for (int j = 0; j < 4; ++j) {
+            double s = 0.0;
+            for (int k = 0; k < 3; ++k) s += A[4 * i + k] * B[4 * k + j];
+            if (j == 3) s += A[4 * i + 3];
+            t[4 * i + j] = s;
+        }
+    }
+    memcpy(C, t, sizeof(t));
+}
+
+void orc_orthonormalise_rows(double *T) {
+    double *r0 = T, *r1 = T + 4, *r2 = T + 8;
+    double n0 = sqrt(r0[0] * r0[0] + r0[1] * r0[1] + r0[2] * r0[2]);
+    for (int i = 0; i < 3; ++i) r0[i] /= n0;
+    double d = r0[0] * r1[0] + r0[1] * r1[1] + r0[2] * r1[2];
+    for (int i = 0; i < 3; ++i) r1[i] -= d * r0[i];
+    double n1 = sqrt(r1[0] * r1[0] + r1[1] * r1[1] + r1[2] * r1[2]);
+    for (int i = 0; i < 3; ++i) r1[i] /= n1;
+    r2[0] = r0[1] * r1[2] - r0[2] * r1[1];
+    r2[1] = r0[2] * r1[0] - r0[0] * r1[2];
+    r2[2] = r0[0] * r1[1] - r0[1] * r1[0];
+}
+
+/* Initial guess: T_out = T_prev (M == NULL, zero velocity) or T_prev M re-orthonormalised. */
+void orc_predict_pose(const double *T_prev, const double *M, double *T_out) {
+    double t[12];
+    if (!M) {
+        memcpy(t, T_prev, sizeof(t));
+    } else {
+        pose_mul34(T_prev, M, t);
+        orc_orthonormalise_rows(t);
+    }
+    memcpy(T_out, t, sizeof(t));
+}
+
+/* Last inter-sweep motion: M = T_prev^-1 T (T_prev^-1 = [R^T | -R^T t]), re-orthonormalised. */
+void orc_update_motion(const double *T_prev, const double *T, double *M) {
+    double inv[12], t[12];
+    for (int i = 0; i < 3; ++i) {
+        for (int j = 0; j < 3; ++j) inv[4 * i + j] = T_prev[4 * j + i];
+        inv[4 * i + 3] = -(T_prev[i] * T_prev[3] + T_prev[4 + i] * T_prev[7] + T_prev[8 + i] * T_prev[11]);
+    }
+    pose_mul34(inv, T, t);
+    orc_orthonormalise_rows(t);
+    memcpy(M, t, sizeof(t));
 }

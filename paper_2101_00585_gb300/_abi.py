@@ -30,7 +30,8 @@ class NormalParams(ctypes.Structure):
 class IcpParams(ctypes.Structure):
     _fields_ = [("d_max", ctypes.c_float), ("cos_theta_max", ctypes.c_float), ("max_iters", ctypes.c_int32),
                 ("min_inliers", ctypes.c_int32), ("eps_rot", ctypes.c_double), ("eps_trans", ctypes.c_double),
-                ("pivot_eps", ctypes.c_double), ("loss", ctypes.c_int32), ("loss_delta", ctypes.c_float)]
+                ("pivot_eps", ctypes.c_double), ("loss", ctypes.c_int32), ("loss_delta", ctypes.c_float),
+                ("coarse_iters", ctypes.c_int32), ("d_max_fine", ctypes.c_float)]
 
 
 class FuseParams(ctypes.Structure):

@@ -53,6 +53,10 @@ class Params:
     # printed by IRLS with weights 1 / max(|r|, loss_delta)
     loss: int = 0
     loss_delta: float = 0.01
+    # coarse-to-fine Omega gate: the first coarse_iters steps of a multi-step call use d_max, later
+    # ones d_max_fine (0 steps: d_max throughout)
+    coarse_iters: int = 0
+    d_max_fine: float = 0.5
     fuse_d_max: float = 0.2
     fuse_cos_theta_max: float = math.cos(math.radians(30.0))
     w_max: float = 10.0
@@ -67,7 +71,8 @@ class Params:
 
     def icp(self):
         return _abi.IcpParams(self.d_max, self.cos_theta_max, self.max_iters, self.min_inliers, self.eps_rot,
-                              self.eps_trans, self.pivot_eps, self.loss, self.loss_delta)
+                              self.eps_trans, self.pivot_eps, self.loss, self.loss_delta, self.coarse_iters,
+                              self.d_max_fine)
 
     def fuse(self):
         return _abi.FuseParams(self.fuse_d_max, self.fuse_cos_theta_max, self.w_max, self.accept_quality)
@@ -472,14 +477,36 @@ class Batch:
         if getattr(self, "ws", None) is None or self.ws.numel() < self.ws_bytes:
             self.ws = torch.zeros(self.ws_bytes, dtype=torch.uint8, device=self.sw.pix.device)
 
-    def run(self, init_poses: torch.Tensor, params: Params = Params()) -> None:
-        self.poses.copy_(init_poses.reshape(self.n_prob, 12))
+    def _launch(self, params: Params) -> None:
         ip = params.icp()
         ss = self.sw.struct()
         _abi.check("upslam_icp_batched",
                    _abi.lib().upslam_icp_batched(_p(self.d_table), self._host, self.n_kf, ctypes.byref(ss), self.n_hyp,
                                                  _p(self.poses), ctypes.byref(ip), _p(self.stats), _p(self.ws),
                                                  self.ws_bytes, ctypes.byref(self.tiles), _stream()))
+
+    def run(self, init_poses: torch.Tensor, params: Params = Params()) -> None:
+        """Register every problem from ``init_poses`` ([n_prob, 12] FP64) in one launch (eager)."""
+        self.poses.copy_(init_poses.reshape(self.n_prob, 12))
+        self._launch(params)
+
+    def capture(self, params: Params = Params()) -> None:
+        """Record one whole batched registration as a CUDA graph: the copy of ``self.init`` (FP64
+        [n_prob, 12], write the initial poses there) into ``poses`` and the persistent launch.
+        ``replay()`` then runs it with no host work.  The tiles and params are fixed at capture."""
+        self.init = torch.zeros_like(self.poses)
+        s = torch.cuda.Stream(device=self.poses.device)
+        s.wait_stream(torch.cuda.current_stream())
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            self.poses.copy_(self.init)
+            self._launch(params)
+        torch.cuda.current_stream().wait_stream(s)
+        self.graph = g
+
+    def replay(self) -> None:
+        """Run the captured registration on the current stream (``capture`` first)."""
+        self.graph.replay()
 
     def read_stats(self) -> list:
         raw = self.stats.cpu().numpy()

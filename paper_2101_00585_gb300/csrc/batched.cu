@@ -49,6 +49,7 @@ struct BatchArgs {
     const void *snrm;
     int sprec;
     float d_max2, cos_min;
+    float d_max2_fine;        // the gate from step ip.coarse_iters on (when ip.coarse_iters > 0)
     int l1;                   // 1: absolute error by IRLS, weights 1 / max(|r|, loss_delta)
     float loss_delta;
     double *poses;            // [n_prob][12] in/out
@@ -156,6 +157,8 @@ __global__ void __launch_bounds__(512, 1) icp_batched_kernel(BatchArgs a) {
 
     int it = 0;
     for (; it < a.ip.max_iters; ++it) {
+        // this step's Omega distance gate (coarse-to-fine when coarse_iters > 0)
+        const float gate2 = (a.ip.coarse_iters > 0 && it >= a.ip.coarse_iters) ? a.d_max2_fine : a.d_max2;
         for (int i = threadIdx.x; i < a.n_prob * kRecWords; i += T) acc[i] = 0.0f;
         __syncthreads();
         // ---- 1. accumulate every active hypothesis of every keyframe over this CTA's samples
@@ -192,7 +195,7 @@ __global__ void __launch_bounds__(512, 1) icp_batched_kernel(BatchArgs a) {
                     const float pz = fmaf(r[8], P.x, fmaf(r[9], P.y, fmaf(r[10], P.z, r[11])));
                     const float3 Rm = rotate(Tp, m.x, m.y, m.z);
                     const float ex = px - s.x, ey = py - s.y, ez = pz - s.z;
-                    ok = ok && (ex * ex + ey * ey + ez * ez <= a.d_max2) &&
+                    ok = ok && (ex * ex + ey * ey + ez * ez <= gate2) &&
                          (Rm.x * n.x + Rm.y * n.y + Rm.z * n.z >= a.cos_min);
                     const float r0 = ex * n.x + ey * n.y + ez * n.z;
                     // square root of the IRLS weight (1 for the squared error); 0 for an outlier
@@ -401,9 +404,16 @@ extern "C" upslam_status upslam_icp_batched(const upslam_keyframe *d_kfs, const 
     cudaFuncAttributes fa;
     if (cudaFuncGetAttributes(&fa, icp_batched_kernel) != cudaSuccess) return UPSLAM_ERR_CUDA;
     if ((int)(dyn + fa.sharedSizeBytes) > optin) return UPSLAM_ERR_CAPACITY;
-    if (cudaFuncSetAttribute(icp_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             optin - (int)fa.sharedSizeBytes) != cudaSuccess)
-        return UPSLAM_ERR_UNSUPPORTED;
+    // raise the dynamic shared-memory limit once per device, so that a later call made while a
+    // stream is being captured into a CUDA graph issues no attribute change
+    static std::atomic<int> smem_raised[64];
+    if (dev < 0 || dev >= 64) return UPSLAM_ERR_UNSUPPORTED;
+    if (!smem_raised[dev].load(std::memory_order_acquire)) {
+        if (cudaFuncSetAttribute(icp_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 optin - (int)fa.sharedSizeBytes) != cudaSuccess)
+            return UPSLAM_ERR_UNSUPPORTED;
+        smem_raised[dev].store(1, std::memory_order_release);
+    }
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, icp_batched_kernel, threads, dyn) != cudaSuccess ||
         per_sm < 1)
@@ -422,6 +432,7 @@ extern "C" upslam_status upslam_icp_batched(const upslam_keyframe *d_kfs, const 
     a.snrm = sw->d_nrm;
     a.sprec = sw->nrm_precision;
     a.d_max2 = ip->d_max * ip->d_max;
+    a.d_max2_fine = ip->d_max_fine * ip->d_max_fine;
     a.cos_min = ip->cos_theta_max;
     a.l1 = ip->loss == UPSLAM_LOSS_L1 ? 1 : 0;
     a.loss_delta = ip->loss_delta;

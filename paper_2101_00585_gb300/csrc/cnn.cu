@@ -998,13 +998,18 @@ static TcOperand op_dense(const __nv_bfloat16 *x, long long ld) {
 // ----------------------------------------------------------------------------- tensor maps
 
 static PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    // looked up once per process (a driver entry point is the same for every device); atomic since
+    // any host thread may call, and every writer stores the same pointer
+    static std::atomic<PFN_cuTensorMapEncodeTiled_v12000> cached{nullptr};
+    PFN_cuTensorMapEncodeTiled_v12000 fn = cached.load(std::memory_order_acquire);
     if (!fn) {
         void *p = nullptr;
         cudaDriverEntryPointQueryResult q;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
+            q == cudaDriverEntryPointSuccess) {
             fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+            cached.store(fn, std::memory_order_release);
+        }
     }
     return fn;
 }
@@ -1055,15 +1060,17 @@ static bool tmap_matrix(CUtensorMap *m, const void *p, long long rows, long long
 
 // The ones box's device address, per device (host code must not take the symbol itself as an address).
 static const void *ones_box_address() {
-    static const void *addr[64] = {nullptr};
+    static std::atomic<const void *> addr[64];  // any host thread may call; writers store the same address
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
-    if (!addr[dev]) {
+    const void *a = addr[dev].load(std::memory_order_acquire);
+    if (!a) {
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, kOnesBox) != cudaSuccess) return nullptr;
-        addr[dev] = p;
+        a = p;
+        addr[dev].store(a, std::memory_order_release);
     }
-    return addr[dev];
+    return a;
 }
 
 // C(m, n) = sum_k A(m, k) B(n, k) on the tensor cores, K cut into `splits` slices (rounded to 64).
@@ -1071,10 +1078,16 @@ static const void *ones_box_address() {
 template <int EPI, int BN, int LA, int LB>
 static bool gemm(TcGemm g, int *err, cudaStream_t s, int splits = 1) {
     constexpr int smem = tc_smem_bytes<BN>();
-    static bool attr = false;  // per process; every GB300 of a box takes the same value
-    if (!attr) {
-        cudaFuncSetAttribute(gemm_tc_kernel<EPI, BN, LA, LB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        attr = true;
+    // the dynamic shared-memory limit is a per-device attribute: raised once on each device (atomic
+    // flags, since any host thread may call)
+    static std::atomic<bool> attr[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
+    if (!attr[dev].load(std::memory_order_acquire)) {
+        if (cudaFuncSetAttribute(gemm_tc_kernel<EPI, BN, LA, LB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 smem) != cudaSuccess)
+            return false;
+        attr[dev].store(true, std::memory_order_release);
     }
     g.a.rows = g.M;
     g.b.rows = g.N;

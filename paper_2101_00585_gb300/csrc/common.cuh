@@ -11,6 +11,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "../../include/upslam.h"
 
 namespace upslam {
@@ -870,20 +872,22 @@ static inline bool upslam_aligned(const void *p, size_t a) { return ((uintptr_t)
 
 static inline bool upslam_icp_params_ok(const upslam_icp_params *ip) {
     return ip && ip->d_max > 0.0f && ip->max_iters >= 0 && ip->min_inliers >= 0 &&
-           (ip->loss == UPSLAM_LOSS_L2 || (ip->loss == UPSLAM_LOSS_L1 && ip->loss_delta > 0.0f));
+           (ip->loss == UPSLAM_LOSS_L2 || (ip->loss == UPSLAM_LOSS_L1 && ip->loss_delta > 0.0f)) &&
+           ip->coarse_iters >= 0 && (ip->coarse_iters == 0 || ip->d_max_fine > 0.0f);
 }
 
-// Multiprocessor count of the current device, cached per device ordinal.
+// Multiprocessor count of the current device, cached per device ordinal.  Any host thread may call
+// the library, so the cache is atomic (every writer stores the same value).
 static inline int upslam_sm_count() {
-    static int cache[64] = {0};
+    static std::atomic<int> cache[64];
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
-    if (cache[dev] == 0) {
-        int sms = 0;
+    int sms = cache[dev].load(std::memory_order_relaxed);
+    if (sms == 0) {
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 152;
-        cache[dev] = sms;
+        cache[dev].store(sms, std::memory_order_relaxed);
     }
-    return cache[dev];
+    return sms;
 }
 
 // Grid for a grid-stride loop over `work` items: enough CTAs to fill every SM

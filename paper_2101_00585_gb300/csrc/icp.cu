@@ -39,6 +39,9 @@ constexpr size_t kCtrlBytes = 4096;  // IcpCtrl, then the persistent form's exac
 constexpr size_t kAccOffset = 256;   // three buffers of kAccWords 64-bit integers
 constexpr int kAccWords = 96;        // 28 sums x 3 chunks, inliers, valid (86 used)
 constexpr long long kWaitCycles = 4000000000ll;  // about 2 s at 2 GHz
+// the exact accumulators sit after IcpCtrl inside the control block that every call clears
+static_assert(kAccOffset + 3 * kAccWords * sizeof(unsigned long long) <= kCtrlBytes,
+              "three accumulator buffers fit the control block");
 
 struct IcpArgs {
     upslam_pano kp;
@@ -54,6 +57,8 @@ struct IcpArgs {
     float cos_min;
     int l1;            // 1: absolute error by IRLS (weights 1 / max(|r|, loss_delta)); 0: squared error
     float loss_delta;
+    float d_max2_fine;  // the gate of steps coarse_iters, coarse_iters + 1, ... (coarse_iters > 0)
+    int coarse_iters;
 };
 
 // Square root of the IRLS weight of residual r: each correspondence enters the
@@ -96,6 +101,7 @@ struct IcpCtrl {
     int valid;                         // unused by the current kernels (kept zero)
     unsigned long long arrive64;       // persistent form: CTA arrivals, monotonic across launches
 };
+static_assert(sizeof(IcpCtrl) <= kAccOffset, "the control words end before the exact accumulators");
 
 template <int L1>
 __device__ __forceinline__ void accumulate_pixel(const IcpArgs &a, const PoseF &T, int k, float acc[28], int &inl) {
@@ -646,23 +652,26 @@ __global__ void __launch_bounds__(kTileThreads, 1)
 #pragma unroll
         for (int i = 0; i < 28; ++i) acc[i] = 0.0f;
         int inl = 0;
+        // this step's Omega distance gate (coarse-to-fine when coarse_iters > 0)
+        IcpArgs as = a;
+        if (a.coarse_iters > 0 && it >= a.coarse_iters) as.d_max2 = a.d_max2_fine;
         // Software-pipelined: the gathers of a thread's next entry are issued
         // before the current one is reduced, so each L2 round trip overlaps
         // the previous entry's arithmetic.  The entries are still summed in
         // the same order.
         if (threadIdx.x < staged) {
-            SweepHit h = gather_entry(a, T, make_float3(sx[threadIdx.x], sy[threadIdx.x], sz[threadIdx.x]));
+            SweepHit h = gather_entry(as, T, make_float3(sx[threadIdx.x], sy[threadIdx.x], sz[threadIdx.x]));
             for (int e = threadIdx.x; e < staged; e += kTileThreads) {
                 const int e1 = min(e + kTileThreads, staged - 1);  // the last prefetch repeats an entry, unused
-                const SweepHit h1 = gather_entry(a, T, make_float3(sx[e1], sy[e1], sz[e1]));
-                accumulate_entry<L1>(a, T, make_float3(sx[e], sy[e], sz[e]), make_float3(snx[e], sny[e], snz[e]), h,
+                const SweepHit h1 = gather_entry(as, T, make_float3(sx[e1], sy[e1], sz[e1]));
+                accumulate_entry<L1>(as, T, make_float3(sx[e], sy[e], sz[e]), make_float3(snx[e], sny[e], snz[e]), h,
                                      acc, inl);
                 h = h1;
             }
         }
         for (int q = spill_q; q < nchunks; q += gridDim.x) {
             const int k = q * kTileThreads + threadIdx.x;
-            if (k < npx) accumulate_pixel<L1>(a, T, k, acc, inl);
+            if (k < npx) accumulate_pixel<L1>(as, T, k, acc, inl);
         }
         const int valid = it == 0 ? count_valid(a) : 0;
         tile_fx(acc, inl, valid, fxs);
@@ -833,6 +842,8 @@ static IcpArgs make_args(const upslam_keyframe *kf, const upslam_sweep *sw, cons
     a.cos_min = ip->cos_theta_max;
     a.l1 = ip->loss == UPSLAM_LOSS_L1 ? 1 : 0;
     a.loss_delta = ip->loss_delta;
+    a.d_max2_fine = ip->d_max_fine * ip->d_max_fine;
+    a.coarse_iters = ip->coarse_iters;
     return a;
 }
 
@@ -862,20 +873,28 @@ static upslam_status launch_tile(const IcpArgs &a, double *pose, const upslam_ic
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (!coop) return UPSLAM_ERR_UNSUPPORTED;
-    static bool attr_set[2][64] = {{false}};
+    // per device and kernel variant: the kernel's static shared memory, recorded when its dynamic
+    // limit is raised (once, so later calls under stream capture change no attribute); any host
+    // thread may call, so the flags are atomic (the release store publishes static_smem)
+    static std::atomic<bool> attr_set[2][64];
     static size_t static_smem[2][64] = {{0}};
     if (dev < 0 || dev >= 64) return UPSLAM_ERR_UNSUPPORTED;
     const int var = a.l1 ? 1 : 0;
     const void *fn = var ? (const void *)icp_tile_kernel<1> : (const void *)icp_tile_kernel<0>;
     const size_t reserve = 1024;
-    if (!attr_set[var][dev]) {
-        cudaFuncAttributes fa;
-        if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) return UPSLAM_ERR_CUDA;
-        static_smem[var][dev] = fa.sharedSizeBytes;
-        const int dyn_max = optin - (int)fa.sharedSizeBytes - (int)reserve;
-        if (dyn_max <= 0 || cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max) != cudaSuccess)
-            return UPSLAM_ERR_UNSUPPORTED;
-        attr_set[var][dev] = true;
+    if (!attr_set[var][dev].load(std::memory_order_acquire)) {
+        static std::mutex mu;
+        std::lock_guard<std::mutex> lock(mu);
+        if (!attr_set[var][dev].load(std::memory_order_relaxed)) {
+            cudaFuncAttributes fa;
+            if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) return UPSLAM_ERR_CUDA;
+            const int dyn_max = optin - (int)fa.sharedSizeBytes - (int)reserve;
+            if (dyn_max <= 0 ||
+                cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max) != cudaSuccess)
+                return UPSLAM_ERR_UNSUPPORTED;
+            static_smem[var][dev] = fa.sharedSizeBytes;
+            attr_set[var][dev].store(true, std::memory_order_release);
+        }
     }
     const int grid = upslam_sm_count();
     const int64_t npx = (int64_t)a.kp.rows * a.kp.cols;
@@ -1060,8 +1079,15 @@ extern "C" upslam_status upslam_track_scan(const upslam_keyframe *kf, const floa
 
 namespace upslam {
 
-constexpr int kNoAllocMaxCtas = 2048;
-constexpr size_t kNoAllocBytes = kCtrlBytes + (size_t)kNoAllocMaxCtas * kSlots * sizeof(float);  // 512.25 KiB
+// A launch needs the control block plus two 64-float records per CTA (one CTA per SM), so the
+// array's record count fixes the largest device it serves: 2048 records = 1024 CTAs, and
+// 4096 + 2048 * 64 * 4 = 528384 bytes (516 KiB).
+constexpr int kNoAllocMaxRecords = 2048;
+constexpr int kNoAllocMaxCtas = kNoAllocMaxRecords / 2;
+constexpr size_t kNoAllocBytes = kCtrlBytes + (size_t)kNoAllocMaxRecords * kSlots * sizeof(float);
+static_assert(kNoAllocBytes == 528384, "the documented capacity of the allocation-free scratch");
+static_assert(kCtrlBytes + 2 * (size_t)kNoAllocMaxCtas * kSlots * sizeof(float) <= kNoAllocBytes,
+              "the largest accepted grid fits the array");
 
 static __device__ __align__(256) unsigned char g_icp_noalloc_ws[kNoAllocBytes];
 
@@ -1098,8 +1124,7 @@ extern "C" upslam_status upslam_icp_noalloc(const upslam_keyframe *kf, const ups
     if (!upslam_icp_params_ok(ip)) return UPSLAM_ERR_INVALID_ARG;
     if (ip->max_iters == 0) return UPSLAM_OK;
     // the scratch a launch on this device needs (two records per SM) must fit the fixed array
-    if (kCtrlBytes + 2 * (size_t)upslam_sm_count() * kSlots * sizeof(float) > kNoAllocBytes)
-        return UPSLAM_ERR_CAPACITY;
+    if (upslam_sm_count() > kNoAllocMaxCtas) return UPSLAM_ERR_CAPACITY;
     void *ws = nullptr;
     const upslam_status st = noalloc_scratch(&ws);
     if (st != UPSLAM_OK) return st;

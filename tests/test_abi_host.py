@@ -74,8 +74,11 @@ def test_invalid_arguments_are_rejected_on_the_host():
     assert L.upslam_fuse(ctypes.byref(ks), ctypes.byref(ss), fake, ctypes.byref(fp), None, fake,
                          None) == _abi.ERR_INVALID_ARG
     # unknown loss, or the absolute error without a positive delta
+    # ... or a coarse-to-fine gate with a negative step count or no fine gate
     for bad_ip in (_abi.IcpParams(0.5, 0.86, 10, 6, 1e-6, 1e-6, 1e-12, 2, 0.01),
-                   _abi.IcpParams(0.5, 0.86, 10, 6, 1e-6, 1e-6, 1e-12, 1, 0.0)):
+                   _abi.IcpParams(0.5, 0.86, 10, 6, 1e-6, 1e-6, 1e-12, 1, 0.0),
+                   _abi.IcpParams(0.5, 0.86, 10, 6, 1e-6, 1e-6, 1e-12, 0, 0.01, -1, 0.5),
+                   _abi.IcpParams(0.5, 0.86, 10, 6, 1e-6, 1e-6, 1e-12, 0, 0.01, 5, 0.0)):
         assert L.upslam_icp(ctypes.byref(ks), ctypes.byref(ss), fake, ctypes.byref(bad_ip), fake, fake, ws,
                             None) == _abi.ERR_INVALID_ARG
     assert L.upslam_predict_pose(None, None, fake, None) == _abi.ERR_INVALID_ARG
@@ -94,11 +97,29 @@ def test_invalid_arguments_are_rejected_on_the_host():
                                    ctypes.byref(_abi.AtrousParams(2, float("nan"), 0.02)), None) == _abi.ERR_INVALID_ARG
 
 
-def test_struct_layouts_match_header():
-    """ctypes mirrors of the header structs have the C sizes the library expects."""
-    assert ctypes.sizeof(_abi.Pano) == 28
-    assert ctypes.sizeof(_abi.IcpParams) == 48
-    assert ctypes.sizeof(_abi.IcpStats) == 21 * 8 + 6 * 8 + 8 + 8 + 8 + 4 + 4 + 6 * 8 + 4 + 4
+def test_struct_layouts_match_header(tmp_path):
+    """ctypes mirrors of the header structs have the sizes and field offsets a C compiler gives them."""
+    import subprocess
+    mirrors = {"upslam_pano": _abi.Pano, "upslam_normal_params": _abi.NormalParams,
+               "upslam_icp_params": _abi.IcpParams, "upslam_fuse_params": _abi.FuseParams,
+               "upslam_icp_stats": _abi.IcpStats, "upslam_sweep": _abi.Sweep, "upslam_keyframe": _abi.Keyframe,
+               "upslam_atrous_params": _abi.AtrousParams, "upslam_batch_tiles": _abi.BatchTiles,
+               "upslam_sweep_buffers": _abi.SweepBuffers}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "upslam.h"', "int main(void) {"]
+    for cname, cls in mirrors.items():
+        lines.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
+        for f, _ in cls._fields_:
+            lines.append(f'printf("{cname}.{f} %zu\\n", offsetof({cname}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = dict(ln.split() for ln in subprocess.check_output([str(exe)], text=True).splitlines())
+    for cname, cls in mirrors.items():
+        assert int(got[cname]) == ctypes.sizeof(cls), cname
+        for f, _ in cls._fields_:
+            assert int(got[f"{cname}.{f}"]) == getattr(cls, f).offset, (cname, f)
 
 
 def test_product_path_has_no_oracle_or_cpu_fallback():

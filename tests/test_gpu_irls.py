@@ -111,7 +111,7 @@ def test_tracker_l1_sequence_matches_oracle():
         trk.track(dev(scans[k]))
         T_ref, _, _, acc_ref = oracle.process_scan(kf_ref, scans[k], seq.sweep, T_ref, prm)
         dt, dr = rot_err(pose_host(trk.state.pose), T_ref)
-        assert dt < 1e-3 and dr < 1e-4, (k, dt, dr)
+        assert dt < 1e-4 and dr < 1e-5, (k, dt, dr)
         assert trk.state.read_stats()["accepted"] == int(acc_ref)
     # sanity against the truth: on Gaussian noise with no outliers the absolute error is the less
     # efficient estimator (delta 1 cm under sigma 2 cm), so its drift bound is wider than L2's

@@ -64,11 +64,23 @@ def angle_between(a, b):
 # ----------------------------------------------------------------------------- a1
 
 
-@pytest.mark.parametrize("pano", ["sweep16", "sweep64", "kf256", "kf512", "tiny"])
+# every panorama geometry the five workloads use: sweeps 16x512, 64x1024, 128x2048; keyframes 256x512,
+# 256x1024, 512x2048, 1024x4096; the 64x256 network-input keyframe; and a ragged tiny one
+_PANOS = {"sweep16": lambda: configs.LIDAR_16.pano(), "sweep64": lambda: configs.LIDAR_64.pano(),
+          "sweep128": lambda: configs.LIDAR_128.pano(), "kf256x512": lambda: synth.keyframe_pano(256, 512),
+          "room_kf256x512": lambda: configs.room_case().kf,
+          "kf256x1024": lambda: synth.keyframe_pano(256, 1024, 0.3, 150.0),
+          "kf512x2048": lambda: synth.keyframe_pano(512, 2048, 0.3, 150.0),
+          "kf1024x4096": lambda: synth.keyframe_pano(1024, 4096, 0.3, 150.0),
+          "kf64x256": lambda: synth.keyframe_pano(64, 256, 0.3, 150.0),
+          "kf128x512": lambda: synth.keyframe_pano(128, 512, 0.3, 30.0), "tiny": lambda: tiny_pano(3, 5)}
+
+
+@pytest.mark.parametrize("pano", sorted(_PANOS))
 def test_direction_table_bit_exact(pano):
-    pp = {"sweep16": configs.LIDAR_16.pano(), "sweep64": configs.LIDAR_64.pano(),
-          "kf256": synth.keyframe_pano(256, 512), "kf512": synth.keyframe_pano(512, 2048),
-          "tiny": tiny_pano(3, 5)}[pano]
+    """FP64 sincos on the device rounded to FP32 against the oracle's libm cos/sin rounded to FP32: every
+    binning decision that uses a pixel's direction rests on these bits."""
+    pp = _PANOS[pano]()
     got = host(up.pano_dirs(pp))
     rt, ct = oracle.dir_table(pp)
     assert np.array_equal(got.view(np.uint32), np.concatenate([rt, ct]).view(np.uint32))
@@ -370,30 +382,6 @@ def test_fuse_gated_by_registration_quality():
 
 
 # ----------------------------------------------------------------------------- whole path
-
-
-def test_tracker_sequence_matches_oracle():
-    """Workload 2, first 12 sweeps: the device-resident Tracker vs the oracle's chained path."""
-    n = 12
-    seq = configs.tunnel_sequence(n_scans=n)
-    scans = [seq.scan(k) for k in range(n)]
-    prm = oracle.Params(accept_quality=0.1)
-    trk = up.Tracker(seq.sweep, seq.kf, up.Params(accept_quality=0.1), constant_velocity=False)
-    trk.new_keyframe(dev(scans[0]))
-    kf_ref = oracle.Keyframe(seq.kf)
-    sp, sn, _, _ = oracle.sweep_frame(scans[0], seq.sweep, prm)
-    oracle.fuse(kf_ref, sp, sn, seq.sweep, IDENTITY, prm)
-    T_ref = IDENTITY.copy()
-    for k in range(1, n):
-        trk.track(dev(scans[k]))
-        T_ref, st_ref, it_ref, acc_ref = oracle.process_scan(kf_ref, scans[k], seq.sweep, T_ref, prm)
-        st = trk.state.read_stats()
-        T = pose_host(trk.state.pose)
-        dt, dr = rot_err(T, T_ref)
-        assert dt < 1e-3 and dr < 1e-4, (k, dt, dr)
-        assert st["accepted"] == int(acc_ref)
-    et, er = rot_err(pose_host(trk.state.pose), synth.relative(seq.poses[0], seq.poses[n - 1]))
-    assert et < 0.03 and er < math.radians(0.3)
 
 
 def test_register_equals_prior_icp_motion_chain():

@@ -77,6 +77,19 @@ MUTANTS = [
     ("fusion_distance_gate_dropped",
      "            if (!(sqrt(e0 * e0 + e1 * e1 + e2 * e2) <= (double)fp->d_max)) continue;",
      "            (void)e0; (void)e1; (void)e2;"),
+    # motion prior (Sec. IV-F footnote)
+    ("prior_product_order", "        pose_mul34(T_prev, M, t);", "        pose_mul34(M, T_prev, t);"),
+    ("prior_not_orthonormalised", "        pose_mul34(T_prev, M, t);\n        orc_orthonormalise_rows(t);",
+     "        pose_mul34(T_prev, M, t);"),
+    ("prior_translation_dropped", "            if (j == 3) s += A[4 * i + 3];", "            (void)0;"),
+    ("motion_inverse_translation_sign",
+     "        inv[4 * i + 3] = -(T_prev[i] * T_prev[3] + T_prev[4 + i] * T_prev[7] + T_prev[8 + i] * T_prev[11]);",
+     "        inv[4 * i + 3] = (T_prev[i] * T_prev[3] + T_prev[4 + i] * T_prev[7] + T_prev[8 + i] * T_prev[11]);"),
+    ("motion_inverse_not_transposed", "        for (int j = 0; j < 3; ++j) inv[4 * i + j] = T_prev[4 * j + i];",
+     "        for (int j = 0; j < 3; ++j) inv[4 * i + j] = T_prev[4 * i + j];"),
+    ("gram_schmidt_projection_dropped", "    for (int i = 0; i < 3; ++i) r1[i] -= d * r0[i];", "    (void)d;"),
+    ("gram_schmidt_third_row_reversed", "    r2[0] = r0[1] * r1[2] - r0[2] * r1[1];\n    r2[1] = r0[2] * r1[0] - r0[0] * r1[2];\n    r2[2] = r0[0] * r1[1] - r0[1] * r1[0];",
+     "    r2[0] = r0[2] * r1[1] - r0[1] * r1[2];\n    r2[1] = r0[0] * r1[2] - r0[2] * r1[0];\n    r2[2] = r0[1] * r1[0] - r0[0] * r1[1];"),
     ("hole_fill_farthest",
      "        if (!was_empty[k]) continue;\n        uint32_t rb;\n        memcpy(&rb, &r, 4);\n"
      "        uint64_t key = ((uint64_t)rb << 32) | (uint32_t)j;\n        if (key < best[k]) best[k] = key;",
