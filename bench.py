@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["tunnel", "campus", "forest-batch", "learned"], default="tunnel",
+    ap.add_argument("--workload", choices=["tunnel", "room", "campus", "forest-batch", "learned"], default="tunnel",
                     help="tunnel: the headline line; campus: the FP16 precision form; forest-batch: the batched "
                          "form; learned: train the pose proposal and evaluate learned vs plain initialisation")
     ap.add_argument("--train-pairs", type=int, default=200000)
@@ -65,6 +65,10 @@ def parse():
     ap.add_argument("--atrous-levels", type=int, default=3,
                     help="also time the a-trous normal smoothing with this many levels (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--forms", choices=["all", "none"], default="all",
+                    help="also run the other workloads (room latency, campus precision form, forest batched form, "
+                         "learned proposal) after the headline and report them under 'forms'")
+    ap.add_argument("--form-steps", type=int, default=40, help="timed sweeps of the campus form")
     ap.add_argument("--quiet", action="store_true")
     return ap.parse_args()
 
@@ -465,7 +469,8 @@ def run_ours(args, ws, rank, local):
                                                                         hbm, hbm_src) if n_scans > kf_every else
                                                         {"skipped": "the run opened no second keyframe"}),
                                 "fuse_kernels": run_fuse(pool[0], seq, d_scans[k_fuse], hist_pose[k_fuse].clone(),
-                                                         device, up, hbm, hbm_src)}
+                                                         device, up, hbm, hbm_src),
+                                "keyframe_switch": run_switch(trk, seq, device, up, hbm, hbm_src)}
     if dist:
         dist.barrier()
     return out
@@ -538,6 +543,51 @@ def run_consistency(pool, T_ab, device, up, hbm, hbm_src):
     return {"pixels": px, "launches": 2, "ms_avg": round(ms, 5), "bytes": nbytes_alg, "gbs": round(gbs, 1),
             "bound": "hbm", "peak": hbm, "frac": round(gbs / hbm, 4), "peak_source": hbm_src,
             "l2": "flushed before each call"}
+
+
+def run_switch(trk, seq, device, up, hbm, hbm_src, reps=20):
+    """A keyframe switch (Sec. III-C, a new keyframe every 5 m) timed alone through the public API:
+    ``Tracker.new_keyframe(buffer=..., consistency=True)`` on the tracker's last sweep, i.e. the
+    sweep's hole fill into an empty 512 x 2048 keyframe (two launches) and the mutual consistency
+    check between the keyframe being left and the new one (workspace clear and two launches).  The
+    keyframe being left is restored and the new one cleared before each call, and L2 is flushed,
+    all outside the events."""
+    import torch
+    old = trk.kf
+    d0, n0 = old.depth.clone(), old.nw.clone()
+    prev0 = trk.prev.clone()
+    new = up.KeyframeBuffer(seq.kf, device)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=device)
+    cr = Cudart()
+    cr.external = False
+    st = torch.cuda.current_stream().cuda_stream
+    evs = [(cr.event(), cr.event()) for _ in range(reps)]
+    removed = []
+    for i in range(reps + 3):
+        trk.kf = old
+        old.set(d0, n0)
+        new.clear()
+        flush.zero_()
+        if i >= 3:
+            cr.record(evs[i - 3][0], st)
+        trk.new_keyframe(buffer=new, consistency=True)
+        if i >= 3:
+            cr.record(evs[i - 3][1], st)
+            removed.append(trk.last_removed)
+    torch.cuda.synchronize()
+    trk.kf = old
+    old.set(d0, n0)
+    trk.prev.copy_(prev0)
+    ms = statistics.mean(cr.elapsed(a, b) for a, b in evs)
+    px = int(old.depth.numel())
+    # hole fill: sweep read (32 B/px) + every new keyframe pixel written once (20 B); consistency: both
+    # keyframes' depth read (4 B/px) and flags written and read (2 B/px)
+    alg = seq.sweep.pixels * 32 + px * 20 + 2 * px * 6
+    gbs = alg / (ms * 1e-3) / 1e9
+    rem = removed[-1].cpu().tolist() if removed else None
+    return {"ms_avg": round(ms, 5), "launches": 5, "bytes": alg, "gbs": round(gbs, 1), "bound": "hbm", "peak": hbm,
+            "frac": round(gbs / hbm, 4), "peak_source": hbm_src, "samples_removed": rem,
+            "l2": "flushed before each call", "note": "one switch per 50 sweeps in the headline sequence"}
 
 
 def run_fuse(kf, seq, scan, T, device, up, hbm, hbm_src, reps=20):
@@ -760,7 +810,7 @@ def run_campus(args, local):
     from synth import configs
     torch.cuda.set_device(local)
     device = torch.device("cuda", local)
-    W, K = args.warmup, min(args.steps, 200)
+    W, K = args.warmup, min(args.steps, args.form_steps)
     seq = configs.campus_sequence(n_scans=1 + W + K)
     scans = np.stack([seq.scan(k) for k in range(1 + W + K)])
     d_scans = torch.from_numpy(scans).to(device)
@@ -807,7 +857,14 @@ def run_campus(args, local):
 
 def run_forest_batch(args, local):
     """Batched form: one 64x1024 forest sweep vs 64 keyframes (22 x 256x1024, 21 x 512x2048,
-    21 x 1024x4096) x 8 hypotheses up to 2 m / 20 deg = 512 problems per launch."""
+    21 x 1024x4096) x 8 hypotheses up to 2 m / 20 deg = 512 problems in one persistent launch,
+    captured once as a CUDA graph and replayed.  The Omega gate is coarse-to-fine: 1.0 m for five
+    Gauss-Newton steps, then 0.5 m.
+
+    Algorithmic bytes per launch: every keyframe pixel read once by the staging prologue (depth 4 B +
+    normal and count 16 B), then per problem and step the sweep pixel each of the keyframe's samples
+    bins into (point 16 B + normal 16 B).  The same bytes by the survey's per-iteration estimate
+    (0.67 GB per step over all 64 keyframes) are reported beside it."""
     import torch
     import paper_2101_00585_gb300 as up
     from paper_2101_00585_gb300 import autotune
@@ -816,7 +873,7 @@ def run_forest_batch(args, local):
     torch.cuda.set_device(local)
     device = torch.device("cuda", local)
     case = configs.forest_batch()
-    p = up.Params(max_iters=15, d_max=1.0)
+    p = up.Params(max_iters=15, d_max=1.0, coarse_iters=5, d_max_fine=0.5)
     sw = up.SweepFrame(case.sweep, device)
     sw.load(torch.from_numpy(case.scan).to(device), p)
     bufs = []
@@ -831,15 +888,20 @@ def run_forest_batch(args, local):
     batch = up.Batch(sw, bufs, case.n_hyp)
     init = torch.from_numpy(np.stack([np.asarray(h).reshape(12) for hyps in case.T_init for h in hyps])).to(device)
     tuned = autotune.tune(batch, init, p, reps=2)
+    batch.run(init, p)  # first launch outside the capture
+    batch.capture(p)
+    batch.init.copy_(init)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=device)
     for _ in range(max(1, args.warmup)):
-        batch.run(init, p)
+        batch.replay()
     torch.cuda.synchronize()
     K = max(1, min(args.steps, 50))
     ms = []
     for _ in range(K):
+        flush.zero_()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
-        batch.run(init, p)
+        batch.replay()
         b.record()
         b.synchronize()
         ms.append(a.elapsed_time(b))
@@ -851,14 +913,98 @@ def run_forest_batch(args, local):
         dt, dr = synth.pose_error(poses[q], case.T_true[k])
         ok += dt < 0.02 and dr < math.radians(0.1)
     avg = statistics.mean(ms)
+    samples = [int((b.nw[..., 3] > 0).sum()) for b in bufs]
+    kf_bytes = sum(int(b.depth.numel()) for b in bufs) * 20
+    steps_by_problem = [r["iters"] for r in recs]
+    gather_bytes = sum(steps_by_problem[q] * samples[q // case.n_hyp] * 32 for q in range(batch.n_prob))
+    alg = kf_bytes + gather_bytes
+    survey_bytes = 0.67e9 * float(np.mean(steps_by_problem))
+    hbm, src = peaks()
+    gbs = alg / (avg * 1e-3) / 1e9
     return {"metric": "batched ICP problems/s (64 keyframes x 8 hypotheses, one launch)",
             "value": round(batch.n_prob / (avg * 1e-3), 1), "unit": "problems/s", "n_gpus": 1, "steps": K,
             "ms_per_launch": round(avg, 3), "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "graph": True, "gpu_launches_per_replay": 2,
             "config": {"workload": "forest: 64 keyframes (22x256x1024, 21x512x2048, 21x1024x4096) x 8 hypotheses "
-                                   "up to 2 m / 20 deg, keyframes started from a sweep each", "tiles": tuned["tiles"],
-                       "autotune_ms": tuned["ms"]},
-            "iters_avg": float(np.mean([r["iters"] for r in recs])),
+                                   "up to 2 m / 20 deg, keyframes started from a sweep each",
+                       "gate": "d_max 1.0 m for 5 steps, then 0.5 m", "tiles": tuned["tiles"],
+                       "autotune_ms": tuned["ms"], "l2": "flushed between launches"},
+            "roofline": {"kernel": "icp_batched_kernel", "bound": "hbm", "achieved": round(gbs, 1), "peak": hbm,
+                         "unit": "GB/s", "frac": round(gbs / hbm, 4), "bytes_per_launch": alg,
+                         "peak_source": src,
+                         "survey_estimate": {"bytes_per_launch": round(survey_bytes),
+                                             "frac": round(survey_bytes / (avg * 1e-3) / 1e9 / hbm, 4)}},
+            "samples_per_keyframe_mean": float(np.mean(samples)),
+            "iters_avg": float(np.mean(steps_by_problem)),
             "within_2cm_0.1deg": int(ok), "problems": batch.n_prob}
+
+
+def run_room(args, local):
+    """Workload 1, a latency case: a 16 x 512 sweep of the box room (8192 points) registered against a
+    256 x 512 keyframe rendered from a second pose 5 cm / 2 deg away, 10 Gauss-Newton steps, then fused.
+    Reports microseconds per whole sweep (one upslam_track_scan launch: projection, normals, ICP,
+    keyframe update; the keyframe is restored before each call) and per ICP step (upslam_icp with ten
+    forced steps, divided by ten).  Not a roofline case: the work is too small to fill the GPU."""
+    import torch
+    import paper_2101_00585_gb300 as up
+    import synth
+    from synth import configs
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    c = configs.room_case(noise=True)
+    p = up.Params(max_iters=10, accept_quality=0.1)
+    d, _, _ = synth.render_keyframe(c.scene, c.kf, c.P_w_kf)
+    depth = torch.from_numpy(d.astype(np.float32)).to(device)
+    trk = up.Tracker(c.sweep, c.kf, p, device=device, constant_velocity=False)
+    pix = up.unproject(depth, c.kf, trk.kf.dirs)
+    nrm = up.normals(pix, depth, c.kf, p)
+    nrm[..., 3] = (depth > 0).float()
+    trk.kf.set(depth, nrm)
+    d0, n0 = trk.kf.depth.clone(), trk.kf.nw.clone()
+    scan = torch.from_numpy(c.scan).to(device)
+    K = max(10, min(args.steps, 200))
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=device)
+    cr = Cudart()
+    cr.external = False
+    st = torch.cuda.current_stream().cuda_stream
+    evs = [(cr.event(), cr.event()) for _ in range(K)]
+    iters = []
+    for i in range(K + 3):
+        trk.kf.set(d0, n0)
+        trk.prev.copy_(trk.identity)
+        flush.zero_()
+        if i >= 3:
+            cr.record(evs[i - 3][0], st)
+        trk.track(scan)
+        if i >= 3:
+            cr.record(evs[i - 3][1], st)
+            iters.append(trk.state.read_stats()["iters"])
+    torch.cuda.synchronize()
+    scan_us = 1e3 * statistics.median(cr.elapsed(a, b) for a, b in evs)
+    err = synth.pose_error(trk.state.pose.cpu().numpy().reshape(3, 4), c.T_true)
+    # ICP steps alone: the same sweep, ten forced steps per launch
+    trk.kf.set(d0, n0)
+    trk.sw.load(scan, p)
+    state = up.IcpState(trk.kf, device)
+    p10 = up.Params(max_iters=10, eps_rot=0.0, eps_trans=0.0)
+    evs2 = [(cr.event(), cr.event()) for _ in range(K)]
+    for i in range(K + 3):
+        state.pose.copy_(trk.identity)
+        flush.zero_()
+        if i >= 3:
+            cr.record(evs2[i - 3][0], st)
+        up.icp(trk.kf, trk.sw, state, p10)
+        if i >= 3:
+            cr.record(evs2[i - 3][1], st)
+    torch.cuda.synchronize()
+    icp_us = 1e3 * statistics.median(cr.elapsed(a, b) for a, b in evs2)
+    return {"metric": "latency of one 16x512 room sweep vs a 256x512 keyframe", "unit": "us",
+            "higher_is_better": False, "us_per_scan": round(scan_us, 2), "us_per_icp_step": round(icp_us / 10, 3),
+            "icp_launch_us_10_steps": round(icp_us, 2), "icp_iters_avg": float(np.mean(iters)), "reps": K,
+            "pose_error_m": float(err[0]), "pose_error_deg": float(math.degrees(err[1])),
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "room 16x512 sweep (8192 points) vs 256x512 keyframe, 5 cm / 2 deg, <=10 steps",
+                       "l2": "flushed before each call", "stat": "median of reps"}}
 
 
 def run_learned(args, local):
@@ -890,7 +1036,13 @@ def run_learned(args, local):
             "plain_fraction": res["plain_success"] / res["pairs"], "learned_only_fraction":
                 res["learned_success"] / res["pairs"], "fallbacks": res["fallbacks"], "pairs": res["pairs"],
             "plain_pairs_per_s": round(res["plain_pairs_per_s"], 1),
-            "gated_pairs_per_s": round(res["gated_pairs_per_s"], 1), "cnn_ms_per_pair": res["cnn_ms_per_pair"],
+            "gated_pairs_per_s": round(res["gated_pairs_per_s"], 1),
+            "pairs_per_s_basis": "device time of the ICP launches (+ the network forward for the gated path)",
+            "plain_pairs_per_s_wall": round(res["plain_pairs_per_s_wall"], 1),
+            "gated_pairs_per_s_wall": round(res["gated_pairs_per_s_wall"], 1),
+            "icp_steps_per_pair_plain": round(res["icp_steps_per_pair_plain"], 2),
+            "icp_steps_per_pair_gated": round(res["icp_steps_per_pair_gated"], 2),
+            "cnn_ms_per_pair": res["cnn_ms_per_pair"],
             "train": {"pairs": args.train_pairs, "epochs": args.epochs, "batch": net.batch, "loss": hist,
                       "seconds": round(t_train, 2), "ms_per_step": round(t_train * 1e3 / max(1, steps), 3),
                       "pairs_per_s": round(pairs_trained / t_train, 1),
@@ -906,7 +1058,8 @@ def main():
     args = parse()
     ws, rank, local = dist_env()
     if args.impl == "ours" and args.workload != "tunnel":
-        runner = {"campus": run_campus, "forest-batch": run_forest_batch, "learned": run_learned}[args.workload]
+        runner = {"room": run_room, "campus": run_campus, "forest-batch": run_forest_batch,
+                  "learned": run_learned}[args.workload]
         out = runner(args, local)
         print(json.dumps(out), flush=True)
         return
@@ -922,8 +1075,25 @@ def main():
         out["cpu_baseline"] = {"value": round(rate, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
                                "sample": f"{n} consecutive tunnel sweeps (whole path each) after 1 warm-up, "
                                          f"{dt:.1f} s on one host thread"}
+    if rank == 0 and args.forms == "all":
+        out["forms"] = run_forms(args, local)
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+def run_forms(args, local) -> dict:
+    """The other workloads, each timed on its own after the headline (rank 0 only)."""
+    forms = {}
+    for name, fn in (("room", run_room), ("campus", run_campus), ("forest_batch", run_forest_batch),
+                     ("learned", run_learned)):
+        t0 = time.perf_counter()
+        try:
+            forms[name] = fn(args, local)
+        except Exception as e:  # one form failing must not lose the headline line
+            forms[name] = {"error": f"{type(e).__name__}: {e}"}
+        forms[name]["wall_s"] = round(time.perf_counter() - t0, 1)
+        log(f"[bench] form {name}: {forms[name].get('value', forms[name].get('us_per_scan'))}")
+    return forms
 
 
 if __name__ == "__main__":

@@ -259,6 +259,21 @@ upslam_status upslam_icp(const upslam_keyframe *kf, const upslam_sweep *sw, doub
                          void *stream);
 
 /*
+ * Test support for the bounded grid-barrier waits of the persistent launch
+ * (the paper has no counterpart).  Runs upslam_icp with every barrier wait
+ * limited to wait_cycles SM clock cycles (1000 .. 4e9) and with CTA 0 not
+ * arriving at the first Gauss-Newton barrier, so that barrier cannot complete:
+ * every CTA's wait gives up, the launch ends, and stats.status becomes
+ * UPSLAM_ERR_TIMEOUT; the pose is left unchanged.  This is how the tests show
+ * that a wait that never completes ends in a status instead of a hang, and that
+ * the device stays usable afterwards.  Zero the workspace again before its next
+ * use (its barrier counter is left mid-count).
+ */
+upslam_status upslam_icp_wait_probe(const upslam_keyframe *kf, const upslam_sweep *sw, double *d_pose12,
+                                    const upslam_icp_params *ip, upslam_icp_stats *d_stats, void *d_ws,
+                                    size_t ws_bytes, long long wait_cycles, void *stream);
+
+/*
  * Registration of one sweep in one launch: the motion prior (Sec. IV-F
  * footnote), then upslam_icp, then the motion update.
  * prior = 0: start from d_pose12 as given (d_prev, d_motion unused);
@@ -480,6 +495,19 @@ size_t upslam_cnn_workspace_bytes(int32_t batch);
 size_t upslam_cnn_error_offset(int32_t batch);
 upslam_status upslam_cnn_forward(const float *d_params, const void *d_x, int32_t batch, float *d_out, void *d_ws,
                                  size_t ws_bytes, void *stream);
+/*
+ * Test support for the bounded tensor-core waits (the paper has no
+ * counterpart): upslam_cnn_forward with every mbarrier wait of the first
+ * layer's GEMM limited to timeout_ns nanoseconds (1000 .. 2e9) and its MMA
+ * thread not signalling its first accumulator as full, so the epilogue's wait
+ * cannot end: the CTAs give up, drain the copies and MMAs they issued, free
+ * their tensor memory and stop, and the error word at
+ * upslam_cnn_error_offset(batch) becomes nonzero.  The outputs of the call are
+ * incomplete; the device stays usable.
+ */
+upslam_status upslam_cnn_forward_wait_probe(const float *d_params, const void *d_x, int32_t batch, float *d_out,
+                                            void *d_ws, size_t ws_bytes, unsigned long long timeout_ns,
+                                            void *stream);
 /* Pose network (not in the paper), backward: loss sum_b sum_i w_i (out - target)^2 / batch into *d_loss and
  * every parameter's gradient into d_grads
  * (overwritten), for the activations of the preceding upslam_cnn_forward on the same workspace. */

@@ -95,6 +95,8 @@ SIGNATURES = {
                                        ctypes.c_size_t, _vp]),
     "upslam_icp_noalloc_capacity_bytes": (ctypes.c_size_t, []),
     "upslam_icp_noalloc": (ctypes.c_int, [_P(Keyframe), _P(Sweep), _vp, _P(IcpParams), _vp, _vp]),
+    "upslam_icp_wait_probe": (ctypes.c_int, [_P(Keyframe), _P(Sweep), _vp, _P(IcpParams), _vp, _vp, ctypes.c_size_t,
+                                             ctypes.c_longlong, _vp]),
     "upslam_predict_pose": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "upslam_update_motion": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "upslam_icp_batched_workspace_bytes": (ctypes.c_size_t, [_P(Keyframe), ctypes.c_int32, ctypes.c_int32,
@@ -111,6 +113,8 @@ SIGNATURES = {
     "upslam_cnn_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int32]),
     "upslam_cnn_error_offset": (ctypes.c_size_t, [ctypes.c_int32]),
     "upslam_cnn_forward": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, _vp, _vp, ctypes.c_size_t, _vp]),
+    "upslam_cnn_forward_wait_probe": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, _vp, _vp, ctypes.c_size_t,
+                                                     ctypes.c_ulonglong, _vp]),
     "upslam_cnn_backward": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_size_t,
                                            _vp]),
     "upslam_cnn_adam": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_int32, ctypes.c_float, _vp]),

@@ -12,15 +12,16 @@
 // arrays), so later steps touch samples only.
 //
 // Each step:
-//  1. for each keyframe, each staged sample is evaluated under every active
-//     hypothesis of that keyframe (the sample is loaded once for all of them);
-//     a warp reduce-scatter (31 shuffles for 32 sums) turns 32 lanes'
-//     contributions into one sum per lane, added to per-problem accumulators
-//     in shared memory;
+//  1. every active problem (keyframe kf, hypothesis h) is one work item: one warp
+//     evaluates all of this CTA's staged samples of kf under h, keeps the sums
+//     in registers, reduces them once across the warp and stores them to the
+//     problem's accumulator in shared memory (no two warps add into one
+//     accumulator, so the result does not depend on timing);
 //  2. every CTA writes one record (29 sums) per problem; grid barrier;
-//  3. problem p is owned by CTA p mod grid: its warps sum the records of p
-//     (compensated FP32), one warp solves in FP64 (L D L^T, SE(3) exp) and
-//     writes the pose, the record and the active flag; grid barrier;
+//  3. problem p is owned by CTA p mod grid: its warps sum the records of p in
+//     a fixed order (compensated FP32), and the CTA's warps then solve up to
+//     one owned problem each, side by side, in FP64 (L D L^T, SE(3) exp) and
+//     write the pose, the record and the active flag; grid barrier;
 //  4. every CTA reloads the poses and flags of the active problems.
 // The launch ends when no problem is active or after max_iters steps.
 // Grid barriers are a monotonic 64-bit arrival counter with a clock64 budget.
@@ -73,6 +74,66 @@ __device__ __forceinline__ bool grid_wait(BatchCtrl *ctrl, unsigned long long ta
     return true;
 }
 
+// A staged keyframe sample's correspondence: the sweep pixel it bins into under the hypothesis,
+// that pixel's point and normal (gathered from L2), and whether it binned at all.
+struct BatchHit {
+    float4 P, m;
+    bool binned;
+};
+
+__device__ __forceinline__ BatchHit batch_gather(const BatchArgs &a, const float *ent, const PoseF &Tp, int q,
+                                                 float3 &s, float3 &n) {
+    s = make_float3(ent[q], ent[a.cta_cap + q], ent[2 * a.cta_cap + q]);
+    n = make_float3(ent[3 * a.cta_cap + q], ent[4 * a.cta_cap + q], ent[5 * a.cta_cap + q]);
+    const float3 qq = xform_inv(Tp, s.x, s.y, s.z);
+    int jv = 0, ju = 0;
+    float rr;
+    BatchHit h;
+    h.binned = bin_point(qq.x, qq.y, qq.z, a.sp, jv, ju, rr);
+    const int j = h.binned ? jv * a.sp.cols + ju : 0;
+    h.P = __ldg(a.spix + j);
+    h.m = load_nw(a.snrm, j, a.sprec);
+    return h;
+}
+
+// One correspondence of Eq. 1 under the problem's pose, branch-free (a rejected pair adds zeros):
+// Omega with the step's squared distance gate, r = (T s2 - s1) . n, J = [p x n, n], IRLS weight.
+__device__ __forceinline__ void batch_accumulate(const BatchArgs &a, const PoseF &Tp, float gate2, float3 s, float3 n,
+                                                 const BatchHit &h, float acc[28], int &inl) {
+    const float4 P = h.P, m = h.m;
+    bool ok = h.binned && P.w != 0.0f && m.w != 0.0f;
+    const float *r = Tp.r;
+    const float px = fmaf(r[0], P.x, fmaf(r[1], P.y, fmaf(r[2], P.z, r[3])));
+    const float py = fmaf(r[4], P.x, fmaf(r[5], P.y, fmaf(r[6], P.z, r[7])));
+    const float pz = fmaf(r[8], P.x, fmaf(r[9], P.y, fmaf(r[10], P.z, r[11])));
+    const float3 Rm = rotate(Tp, m.x, m.y, m.z);
+    const float ex = px - s.x, ey = py - s.y, ez = pz - s.z;
+    ok = ok && (ex * ex + ey * ey + ez * ez <= gate2) && (Rm.x * n.x + Rm.y * n.y + Rm.z * n.z >= a.cos_min);
+    const float r0 = ex * n.x + ey * n.y + ez * n.z;
+    // square root of the IRLS weight (1 for the squared error); 0 for an outlier
+    const float w = ok ? (a.l1 ? rsqrtf(fmaxf(fabsf(r0), a.loss_delta)) : 1.0f) : 0.0f;
+    const float res = r0 * w;
+    float J[6];
+    J[0] = (py * n.z - pz * n.y) * w;
+    J[1] = (pz * n.x - px * n.z) * w;
+    J[2] = (px * n.y - py * n.x) * w;
+    J[3] = n.x * w;
+    J[4] = n.y * w;
+    J[5] = n.z * w;
+    int c = 0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int k2 = i; k2 < 6; ++k2) {
+            acc[c] = fmaf(J[i], J[k2], acc[c]);
+            ++c;
+        }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) acc[21 + i] = fmaf(J[i], res, acc[21 + i]);
+    acc[27] = fmaf(res, res, acc[27]);
+    inl += ok ? 1 : 0;
+}
+
 __global__ void __launch_bounds__(512, 1) icp_batched_kernel(BatchArgs a) {
     extern __shared__ float smem[];
     float *acc = smem;                                 // [n_prob][kRecWords]
@@ -81,9 +142,11 @@ __global__ void __launch_bounds__(512, 1) icp_batched_kernel(BatchArgs a) {
     __shared__ int kf_off[kBatchMaxKf], kf_cnt[kBatchMaxKf];
     __shared__ int wcnt[32];
     __shared__ int base_s, flag_s, any_active;
-    __shared__ double tot[32];
-    __shared__ double Tsh[16][12];
+    __shared__ double totq[16][32];   // step sums of the problems being solved, one per warp
+    __shared__ double Tsh[16][12];    // their poses
+    __shared__ int pown[16];
     __shared__ float shs[16][32], shc[16][32];
+    __shared__ float wpart[16][32];   // per-warp totals when warps share a problem
     const int T = blockDim.x, nw = T / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned long long G = gridDim.x;
@@ -161,69 +224,61 @@ __global__ void __launch_bounds__(512, 1) icp_batched_kernel(BatchArgs a) {
         const float gate2 = (a.ip.coarse_iters > 0 && it >= a.ip.coarse_iters) ? a.d_max2_fine : a.d_max2;
         for (int i = threadIdx.x; i < a.n_prob * kRecWords; i += T) acc[i] = 0.0f;
         __syncthreads();
-        // ---- 1. accumulate every active hypothesis of every keyframe over this CTA's samples
-        for (int kf = 0; kf < a.n_kf; ++kf) {
+        // ---- 1. accumulate.  A work item is one problem p = (keyframe kf, hypothesis h) over every
+        // sample this CTA staged for kf.  One warp takes an item (items dealt round-robin to the
+        // warps), keeps the 28 sums and the inlier count per lane in registers, reduces them once
+        // (reduce-scatter) and stores the totals to p's accumulator.  No two warps add into one
+        // accumulator, so the sums do not depend on timing.  With fewer problems than warps, `split`
+        // warps share a problem (each takes every split-th group of 32 samples) and their totals are
+        // added in warp order.  Each lane bins and gathers its next sample before it reduces the
+        // current one, so the L2 round trips overlap the arithmetic.
+        const int split = a.n_prob < nw ? nw / a.n_prob : 1;
+        for (int item = warp; item < a.n_prob * split; item += nw) {
+            const int p = item / split, part = item - p * split;
+            if (!act[p]) continue;
+            const int kf = p / a.n_hyp;
             const int cnt = kf_cnt[kf], off = kf_off[kf];
-            const upslam_keyframe K = a.kfs[kf];
-            (void)K;
-            for (int e0 = warp * 32; e0 < cnt; e0 += T) {
-                const int e = e0 + lane;
-                const bool have = e < cnt;
-                float3 s = make_float3(0.f, 0.f, 0.f), n = make_float3(0.f, 0.f, 0.f);
-                if (have) {
-                    const int q = off + e;
-                    s = make_float3(ent[q], ent[a.cta_cap + q], ent[2 * a.cta_cap + q]);
-                    n = make_float3(ent[3 * a.cta_cap + q], ent[4 * a.cta_cap + q], ent[5 * a.cta_cap + q]);
+            PoseF Tp;
+#pragma unroll
+            for (int i = 0; i < 12; ++i) Tp.r[i] = pose_f[p * 12 + i];
+            float accr[28];
+#pragma unroll
+            for (int i = 0; i < 28; ++i) accr[i] = 0.0f;
+            int inl = 0;
+            const int stride = 32 * split;
+            int e = part * 32 + lane;
+            if (e < cnt) {
+                float3 sc, nc;
+                BatchHit hc = batch_gather(a, ent, Tp, off + e, sc, nc);
+                for (; e < cnt; e += stride) {
+                    float3 sn = sc, nn = nc;
+                    BatchHit hn = hc;
+                    if (e + stride < cnt) hn = batch_gather(a, ent, Tp, off + e + stride, sn, nn);
+                    batch_accumulate(a, Tp, gate2, sc, nc, hc, accr, inl);
+                    sc = sn;
+                    nc = nn;
+                    hc = hn;
                 }
-                for (int h = 0; h < a.n_hyp; ++h) {
-                    const int p = kf * a.n_hyp + h;
-                    if (!act[p]) continue;
-                    PoseF Tp;
+            }
+            float v[32];
 #pragma unroll
-                    for (int i = 0; i < 12; ++i) Tp.r[i] = pose_f[p * 12 + i];
-                    const float3 q = xform_inv(Tp, s.x, s.y, s.z);
-                    int jv = 0, ju = 0;
-                    float rr;
-                    bool ok = have && bin_point(q.x, q.y, q.z, a.sp, jv, ju, rr);
-                    const int j = ok ? jv * a.sp.cols + ju : 0;
-                    const float4 P = __ldg(a.spix + j);
-                    const float4 m = load_nw(a.snrm, j, a.sprec);
-                    ok = ok && P.w != 0.0f && m.w != 0.0f;
-                    const float *r = Tp.r;
-                    const float px = fmaf(r[0], P.x, fmaf(r[1], P.y, fmaf(r[2], P.z, r[3])));
-                    const float py = fmaf(r[4], P.x, fmaf(r[5], P.y, fmaf(r[6], P.z, r[7])));
-                    const float pz = fmaf(r[8], P.x, fmaf(r[9], P.y, fmaf(r[10], P.z, r[11])));
-                    const float3 Rm = rotate(Tp, m.x, m.y, m.z);
-                    const float ex = px - s.x, ey = py - s.y, ez = pz - s.z;
-                    ok = ok && (ex * ex + ey * ey + ez * ez <= gate2) &&
-                         (Rm.x * n.x + Rm.y * n.y + Rm.z * n.z >= a.cos_min);
-                    const float r0 = ex * n.x + ey * n.y + ez * n.z;
-                    // square root of the IRLS weight (1 for the squared error); 0 for an outlier
-                    const float w = ok ? (a.l1 ? rsqrtf(fmaxf(fabsf(r0), a.loss_delta)) : 1.0f) : 0.0f;
-                    const float res = r0 * w;
-                    float J[6];
-                    J[0] = (py * n.z - pz * n.y) * w;
-                    J[1] = (pz * n.x - px * n.z) * w;
-                    J[2] = (px * n.y - py * n.x) * w;
-                    J[3] = n.x * w;
-                    J[4] = n.y * w;
-                    J[5] = n.z * w;
-                    float v[32];
-                    int c = 0;
-#pragma unroll
-                    for (int i = 0; i < 6; ++i)
-#pragma unroll
-                        for (int k2 = i; k2 < 6; ++k2) v[c++] = J[i] * J[k2];
-#pragma unroll
-                    for (int i = 0; i < 6; ++i) v[21 + i] = J[i] * res;
-                    v[27] = res * res;
-                    v[28] = w;
-                    v[29] = 0.0f;
-                    v[30] = 0.0f;
-                    v[31] = 0.0f;
-                    const float sum = warp_reduce_scatter(v);
-                    if (lane < 29) atomicAdd(&acc[p * kRecWords + lane], sum);
-                }
+            for (int i = 0; i < 28; ++i) v[i] = accr[i];
+            v[28] = (float)inl;
+            v[29] = v[30] = v[31] = 0.0f;
+            const float sum = warp_reduce_scatter(v);
+            if (lane < 29) {
+                if (split == 1) acc[p * kRecWords + lane] = sum;
+                else wpart[item][lane] = sum;  // items < nw here
+            }
+        }
+        __syncthreads();
+        if (split > 1) {
+            for (int i = threadIdx.x; i < a.n_prob * 29; i += T) {
+                const int p = i / 29, l = i - p * 29;
+                if (!act[p]) continue;
+                float t = 0.0f;
+                for (int q = 0; q < split; ++q) t += wpart[p * split + q][l];
+                acc[p * kRecWords + l] = t;
             }
         }
         __syncthreads();
@@ -241,51 +296,63 @@ __global__ void __launch_bounds__(512, 1) icp_batched_kernel(BatchArgs a) {
         }
         __syncthreads();
         if (flag_s) break;
-        // ---- 3. the problems this CTA owns: sum records, solve, publish
-        for (int p = blockIdx.x; p < a.n_prob; p += gridDim.x) {
-            if (!act[p]) continue;
-            float s = 0.0f, c = 0.0f;
-            for (int b = warp; b < (int)gridDim.x; b += nw) {
-                const float x = __ldcg(a.records + ((size_t)p * gridDim.x + b) * kRecWords + lane);
-                kadd(s, c, x);
-            }
-            shs[warp][lane] = s;
-            shc[warp][lane] = c;
-            __syncthreads();
-            if (threadIdx.x < 29) {
-                float t = 0.0f, cc = 0.0f;
-                for (int w = 0; w < nw; ++w) {
-                    kadd(t, cc, shs[w][threadIdx.x]);
-                    cc += shc[w][threadIdx.x];
+        // ---- 3. the problems this CTA owns (p = blockIdx.x + j * grid), up to one per warp at a
+        // time: all warps sum each problem's records over the CTAs in a fixed order (compensated
+        // FP32), then the warps solve their problems side by side in FP64 and publish them.
+        for (int p0 = blockIdx.x; p0 < a.n_prob; p0 += (int)gridDim.x * nw) {
+            int n_own = 0;
+            for (int j = 0; j < nw; ++j) {
+                const int p = p0 + j * (int)gridDim.x;
+                if (p >= a.n_prob) break;
+                if (!act[p]) continue;
+                float s = 0.0f, c = 0.0f;
+                for (int b = warp; b < (int)gridDim.x; b += nw) {
+                    const float x = __ldcg(a.records + ((size_t)p * gridDim.x + b) * kRecWords + lane);
+                    kadd(s, c, x);
                 }
-                tot[threadIdx.x] = (double)t + (double)cc;
+                shs[warp][lane] = s;
+                shc[warp][lane] = c;
+                __syncthreads();
+                if (threadIdx.x < 29) {
+                    float t = 0.0f, cc = 0.0f;
+                    for (int w = 0; w < nw; ++w) {
+                        kadd(t, cc, shs[w][threadIdx.x]);
+                        cc += shc[w][threadIdx.x];
+                    }
+                    totq[n_own][threadIdx.x] = (double)t + (double)cc;
+                }
+                if (threadIdx.x < 12) Tsh[n_own][threadIdx.x] = __ldcg(a.poses + (size_t)p * 12 + threadIdx.x);
+                if (threadIdx.x == 0) pown[n_own] = p;
+                __syncthreads();
+                ++n_own;
             }
-            if (threadIdx.x < 12) Tsh[0][threadIdx.x] = __ldcg(a.poses + (size_t)p * 12 + threadIdx.x);
-            __syncthreads();
-            if (warp == 0) {
-                const long long inliers = (long long)(tot[28] + 0.5);
+            if (warp < n_own) {
+                const int p = pown[warp];
+                const double *tq = totq[warp];
+                double *Tw = Tsh[warp];
+                const long long inliers = (long long)(tq[28] + 0.5);
                 double xi[6] = {0, 0, 0, 0, 0, 0};
                 int status = UPSLAM_OK, conv = 0;
                 if (inliers < a.ip.min_inliers) {
                     status = UPSLAM_ERR_DEGENERATE;
-                } else if (!warp_solve6(tot, a.ip.pivot_eps, xi)) {
+                } else if (!warp_solve6(tq, a.ip.pivot_eps, xi)) {
                     status = UPSLAM_ERR_DEGENERATE;
 #pragma unroll
                     for (int i = 0; i < 6; ++i) xi[i] = 0.0;
                 } else {
-                    warp_se3_update(xi, Tsh[0]);
+                    warp_se3_update(xi, Tw);
                     conv = warp_converged(xi, a.ip.eps_rot * a.ip.eps_rot, a.ip.eps_trans * a.ip.eps_trans) ? 1 : 0;
                 }
                 upslam_icp_stats *st = a.stats + p;
                 if (lane < 12) {
-                    a.poses[(size_t)p * 12 + lane] = Tsh[0][lane];
-                    a.poses_f[(size_t)p * 12 + lane] = (float)Tsh[0][lane];
+                    a.poses[(size_t)p * 12 + lane] = Tw[lane];
+                    a.poses_f[(size_t)p * 12 + lane] = (float)Tw[lane];
                 }
-                if (lane < 21) st->A[lane] = tot[lane];
-                else if (lane < 27) st->b[lane - 21] = tot[lane];
+                if (lane < 21) st->A[lane] = tq[lane];
+                else if (lane < 27) st->b[lane - 21] = tq[lane];
                 if (lane < 6) st->xi[lane] = xi[lane];
                 if (lane == 0) {
-                    st->sse = tot[27];
+                    st->sse = tq[27];
                     st->inliers = inliers;
                     st->valid = *((volatile int *)&a.ctrl->valid);
                     st->status = status;

@@ -114,6 +114,8 @@ struct TcGemm {
     const float *bias;
     const __nv_bfloat16 *mask;  // EPI_DGRAD_MASK_BF16: the layer input, whose ReLU masks dX
     float *db;                  // EPI_F32_RED_T with a ones row: the bias gradient it feeds
+    unsigned long long timeout_ns;  // limit of every mbarrier wait (global-timer nanoseconds)
+    int withhold;  // test support: the MMA thread does not signal its first accumulator as full
 };
 
 constexpr int kTcBM = 128, kTcBK = 64;
@@ -399,7 +401,8 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
-__device__ __forceinline__ bool tc_wait(unsigned mbar, unsigned parity, volatile int *abort, int *err) {
+__device__ __forceinline__ bool tc_wait(unsigned mbar, unsigned parity, volatile int *abort, int *err,
+                                        unsigned long long timeout_ns) {
     unsigned long long t0 = 0;
     for (unsigned it = 0;; ++it) {
         unsigned done;
@@ -414,7 +417,7 @@ __device__ __forceinline__ bool tc_wait(unsigned mbar, unsigned parity, volatile
             const unsigned long long t = global_ns();
             if (t0 == 0) {
                 t0 = t;
-            } else if (t - t0 > kTcTimeoutNs) {
+            } else if (t - t0 > timeout_ns) {
                 *abort = 1;
                 atomicExch(err, 1);
                 return false;
@@ -568,7 +571,7 @@ __global__ void __launch_bounds__(tc_threads<LA>(), 2)
                 const TcUnit t = tc_unit<EPI, BN>(g, u);
                 for (int k = 0; k < t.nkt; ++k, ++it) {
                     const int st = it % S;
-                    if (it >= S && !tc_wait(smem_u32(&sy.empty[st]), (unsigned)(((it / S) - 1) & 1), abort, err)) {
+                    if (it >= S && !tc_wait(smem_u32(&sy.empty[st]), (unsigned)(((it / S) - 1) & 1), abort, err, g.timeout_ns)) {
                         ok = false;
                         break;
                     }
@@ -629,7 +632,7 @@ __global__ void __launch_bounds__(tc_threads<LA>(), 2)
             for (int u = blockIdx.x; ok && u < g.units; u += gridDim.x, ++uc) {
                 const TcUnit t = tc_unit<EPI, BN>(g, u);
                 const int b = uc & 1;
-                if (uc >= 2 && !tc_wait(smem_u32(&sy.acce[b]), (unsigned)(((uc >> 1) - 1) & 1), abort, err)) {
+                if (uc >= 2 && !tc_wait(smem_u32(&sy.acce[b]), (unsigned)(((uc >> 1) - 1) & 1), abort, err, g.timeout_ns)) {
                     ok = false;
                     break;
                 }
@@ -637,7 +640,7 @@ __global__ void __launch_bounds__(tc_threads<LA>(), 2)
                 const unsigned acc = tmem + (unsigned)(b * BN);
                 for (int k = 0; k < t.nkt; ++k, ++it) {
                     const int st = it % S;
-                    if (!tc_wait(smem_u32(&sy.full[st]), (unsigned)((it / S) & 1), abort, err)) {
+                    if (!tc_wait(smem_u32(&sy.full[st]), (unsigned)((it / S) & 1), abort, err, g.timeout_ns)) {
                         ok = false;
                         break;
                     }
@@ -675,10 +678,11 @@ __global__ void __launch_bounds__(tc_threads<LA>(), 2)
                     last_par = (unsigned)((it / S) & 1);
                 }
                 if (!ok) break;
-                tc_commit(smem_u32(&sy.accf[b]));
+                if (!(g.withhold && uc == 0)) tc_commit(smem_u32(&sy.accf[b]));
             }
-            // after an abort, let the MMAs already issued finish before the accumulators are freed
-            if (!ok && last_bar) {
+            // after an abort (or with a withheld signal, which nothing else waits out), let the MMAs already
+            // issued finish before the accumulators are freed
+            if ((!ok || g.withhold) && last_bar) {
                 for (unsigned w = 0; w < kTcWaitIters; ++w) {
                     unsigned done;
                     asm volatile(
@@ -704,7 +708,7 @@ __global__ void __launch_bounds__(tc_threads<LA>(), 2)
         for (int u = blockIdx.x; u < g.units; u += gridDim.x, ++uc) {
             const TcUnit t = tc_unit<EPI, BN>(g, u);
             const int b = uc & 1;
-            if (!tc_wait(smem_u32(&sy.accf[b]), (unsigned)((uc >> 1) & 1), abort, err)) break;
+            if (!tc_wait(smem_u32(&sy.accf[b]), (unsigned)((uc >> 1) & 1), abort, err, g.timeout_ns)) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             tc_epilogue<EPI, BN>(g, t, tmem + (unsigned)(b * BN), warp, lane, sbias);
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -1089,6 +1093,7 @@ static bool gemm(TcGemm g, int *err, cudaStream_t s, int splits = 1) {
             return false;
         attr[dev].store(true, std::memory_order_release);
     }
+    if (g.timeout_ns == 0) g.timeout_ns = kTcTimeoutNs;
     g.a.rows = g.M;
     g.b.rows = g.N;
     g.k_split = ((g.K + splits - 1) / splits + kTcBK - 1) / kTcBK * kTcBK;
@@ -1145,8 +1150,9 @@ extern "C" size_t upslam_cnn_error_offset(int32_t batch) {
     return cnn_ws_layout(batch, nullptr, nullptr) - 256;  // the last block of the layout
 }
 
-extern "C" upslam_status upslam_cnn_forward(const float *d_params, const void *d_x, int32_t batch, float *d_out,
-                                            void *d_ws, size_t ws_bytes, void *stream) {
+// The forward pass; timeout_ns / withhold (test support) go to the first layer's GEMM.
+static upslam_status cnn_forward(const float *d_params, const void *d_x, int32_t batch, float *d_out, void *d_ws,
+                                 size_t ws_bytes, void *stream, unsigned long long timeout_ns, int withhold) {
     if (!d_params || !d_x || !d_out || !d_ws || batch <= 0 || !upslam_aligned(d_ws, 256) ||
         ws_bytes < upslam_cnn_workspace_bytes(batch) || !upslam_aligned(d_x, 16))
         return UPSLAM_ERR_INVALID_ARG;
@@ -1177,6 +1183,10 @@ extern "C" upslam_status upslam_cnn_forward(const float *d_params, const void *d
         g.C = w.act[l];
         g.ldc = N;
         g.bias = d_params + L.off_b[l];
+        if (l == 0) {
+            g.timeout_ns = timeout_ns;
+            g.withhold = withhold;
+        }
         // the staged-bias epilogue needs one column tile: BN = N
         // layers with C >= 32 load through TMA (128- or 64-byte swizzle); the 8-channel input is gathered
         const bool ok = C >= 64   ? gemm<EPI_BIAS_RELU_BF16, 128, LD_IM2COL_KT, LD_DENSE_KT>(g, w.err, s)
@@ -1191,6 +1201,18 @@ extern "C" upslam_status upslam_cnn_forward(const float *d_params, const void *d
                                            d_out);
     UPSLAM_CHECK_LAUNCH();
     return UPSLAM_OK;
+}
+
+extern "C" upslam_status upslam_cnn_forward(const float *d_params, const void *d_x, int32_t batch, float *d_out,
+                                            void *d_ws, size_t ws_bytes, void *stream) {
+    return cnn_forward(d_params, d_x, batch, d_out, d_ws, ws_bytes, stream, 0, 0);
+}
+
+extern "C" upslam_status upslam_cnn_forward_wait_probe(const float *d_params, const void *d_x, int32_t batch,
+                                                       float *d_out, void *d_ws, size_t ws_bytes,
+                                                       unsigned long long timeout_ns, void *stream) {
+    if (timeout_ns < 1000 || timeout_ns > kTcTimeoutNs) return UPSLAM_ERR_INVALID_ARG;
+    return cnn_forward(d_params, d_x, batch, d_out, d_ws, ws_bytes, stream, timeout_ns, 1);
 }
 
 extern "C" upslam_status upslam_cnn_backward(const float *d_params, const void *d_x, int32_t batch,

@@ -59,6 +59,8 @@ struct IcpArgs {
     float loss_delta;
     float d_max2_fine;  // the gate of steps coarse_iters, coarse_iters + 1, ... (coarse_iters > 0)
     int coarse_iters;
+    long long wait_cycles;  // budget of every grid-barrier wait (clock64 cycles)
+    int withhold;           // test support: CTA 0 does not arrive at the first Gauss-Newton barrier
 };
 
 // Square root of the IRLS weight of residual r: each correspondence enters the
@@ -403,26 +405,27 @@ __device__ __forceinline__ void tile_fx(float acc[28], int inl, int valid, unsig
 // wrote before the barrier; the polls are relaxed loads, and one acquire fence
 // after the last makes every other CTA's writes visible (the caller's next
 // __syncthreads extends both to the whole CTA).  False when the count has not
-// reached target after kWaitCycles (the caller reports UPSLAM_ERR_TIMEOUT).
+// reached target after `budget` cycles (the caller reports UPSLAM_ERR_TIMEOUT).
 __device__ __forceinline__ void grid_arrive(unsigned long long *ctr) {
     asm volatile("red.release.gpu.global.add.u64 [%0], 1;" ::"l"(ctr) : "memory");
 }
 
-__device__ __forceinline__ bool grid_wait(unsigned long long *ctr, unsigned long long target) {
+__device__ __forceinline__ bool grid_wait(unsigned long long *ctr, unsigned long long target, long long budget) {
     const long long t0 = clock64();
     unsigned long long v;
     for (;;) {
         asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(ctr) : "memory");
         if (v >= target) break;
-        if (clock64() - t0 > kWaitCycles) return false;
+        if (clock64() - t0 > budget) return false;
     }
     asm volatile("fence.acq_rel.gpu;" ::: "memory");
     return true;
 }
 
-__device__ __forceinline__ bool grid_arrive_wait(unsigned long long *ctr, unsigned long long target) {
+__device__ __forceinline__ bool grid_arrive_wait(unsigned long long *ctr, unsigned long long target,
+                                                 long long budget) {
     grid_arrive(ctr);
-    return grid_wait(ctr, target);
+    return grid_wait(ctr, target, budget);
 }
 
 // Split-phase grid barrier: the CTA arrives (after everything it wrote), does other work,
@@ -433,27 +436,11 @@ __device__ __forceinline__ void cta_grid_arrive(IcpCtrl *ctrl) {
 }
 
 __device__ __forceinline__ bool cta_grid_await(IcpCtrl *ctrl, unsigned long long target, upslam_icp_stats *st,
-                                               int *flag_s) {
+                                               int *flag_s, long long budget) {
     __syncthreads();
     if (threadIdx.x == 0) {
         *flag_s = 0;
-        if (!grid_wait(&ctrl->arrive64, target)) {
-            *flag_s = 3;
-            st->status = UPSLAM_ERR_TIMEOUT;
-        }
-    }
-    __syncthreads();
-    return *flag_s != 3;
-}
-
-// A grid barrier for the whole CTA: thread 0 arrives and waits, the CTA follows.
-// False after a timeout (reported in the record).
-__device__ __forceinline__ bool cta_grid_sync(IcpCtrl *ctrl, unsigned long long target, upslam_icp_stats *st,
-                                              int *flag_s) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        *flag_s = 0;
-        if (!grid_arrive_wait(&ctrl->arrive64, target)) {
+        if (!grid_wait(&ctrl->arrive64, target, budget)) {
             *flag_s = 3;
             st->status = UPSLAM_ERR_TIMEOUT;
         }
@@ -620,7 +607,7 @@ __global__ void __launch_bounds__(kTileThreads, 1)
             project_point(fr.pts, i, a.sp, fr.zbuf);
         cta_grid_arrive(ctrl);
         stage_groups(0, my_groups / 2);
-        if (!cta_grid_await(ctrl, base + G * ++nbar, st, &flag)) return;
+        if (!cta_grid_await(ctrl, base + G * ++nbar, st, &flag, a.wait_cycles)) return;
         clear_prev(nbar);
         const PixZbuf zb{fr.pts, fr.zbuf};
         for (int k = blockIdx.x * kTileThreads + threadIdx.x; k < ns; k += stride) {
@@ -629,7 +616,7 @@ __global__ void __launch_bounds__(kTileThreads, 1)
         }
         cta_grid_arrive(ctrl);
         stage_groups(my_groups / 2, my_groups);
-        if (!cta_grid_await(ctrl, base + G * ++nbar, st, &flag)) return;
+        if (!cta_grid_await(ctrl, base + G * ++nbar, st, &flag, a.wait_cycles)) return;
         clear_prev(nbar);
         for (int k = blockIdx.x * kTileThreads + threadIdx.x; k < ns; k += stride) fr.zbuf[k] = kEmptyKey;
     } else {
@@ -685,7 +672,9 @@ __global__ void __launch_bounds__(kTileThreads, 1)
         __syncthreads();
         if (threadIdx.x == 0) {
             flag = 0;
-            if (!grid_arrive_wait(&ctrl->arrive64, base + G * jb)) {
+            // (test support: with `withhold`, CTA 0 skips its first arrival, so no CTA's wait can end)
+            if (!(a.withhold && it == 0 && blockIdx.x == 0)) grid_arrive(&ctrl->arrive64);
+            if (!grid_wait(&ctrl->arrive64, base + G * jb, a.wait_cycles)) {
                 flag = 3;
                 st->status = UPSLAM_ERR_TIMEOUT;
             }
@@ -776,7 +765,7 @@ __global__ void __launch_bounds__(kTileThreads, 1)
         __syncthreads();
         if (threadIdx.x == 0) {
             flag = 0;
-            if (!grid_arrive_wait(&ctrl->arrive64, base + G * (nbar + (unsigned long long)(it + 1)))) {
+            if (!grid_arrive_wait(&ctrl->arrive64, base + G * (nbar + (unsigned long long)(it + 1)), a.wait_cycles)) {
                 flag = 3;
                 st->status = UPSLAM_ERR_TIMEOUT;
             }
@@ -844,6 +833,8 @@ static IcpArgs make_args(const upslam_keyframe *kf, const upslam_sweep *sw, cons
     a.loss_delta = ip->loss_delta;
     a.d_max2_fine = ip->d_max_fine * ip->d_max_fine;
     a.coarse_iters = ip->coarse_iters;
+    a.wait_cycles = kWaitCycles;
+    a.withhold = 0;
     return a;
 }
 
@@ -983,6 +974,18 @@ extern "C" upslam_status upslam_icp(const upslam_keyframe *kf, const upslam_swee
     if (chk != UPSLAM_OK) return chk;
     if (ip->max_iters == 0) return UPSLAM_OK;
     return launch_tile(make_args(kf, sw, ip), d_pose12, ip, d_stats, d_ws, ws_bytes, (cudaStream_t)stream);
+}
+
+extern "C" upslam_status upslam_icp_wait_probe(const upslam_keyframe *kf, const upslam_sweep *sw, double *d_pose12,
+                                               const upslam_icp_params *ip, upslam_icp_stats *d_stats, void *d_ws,
+                                               size_t ws_bytes, long long wait_cycles, void *stream) {
+    const upslam_status chk = icp_common_checks(kf, sw, d_pose12, ip, d_stats, d_ws, ws_bytes);
+    if (chk != UPSLAM_OK) return chk;
+    if (ip->max_iters < 1 || wait_cycles < 1000 || wait_cycles > kWaitCycles) return UPSLAM_ERR_INVALID_ARG;
+    IcpArgs a = make_args(kf, sw, ip);
+    a.wait_cycles = wait_cycles;
+    a.withhold = 1;
+    return launch_tile(a, d_pose12, ip, d_stats, d_ws, ws_bytes, (cudaStream_t)stream);
 }
 
 extern "C" upslam_status upslam_register(const upslam_keyframe *kf, const upslam_sweep *sw, double *d_prev,

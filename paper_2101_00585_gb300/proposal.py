@@ -339,41 +339,56 @@ def evaluate(net: PoseNet, x: torch.Tensor, motions: list, scans, params: Params
     builder = PairBuilder(sw_pano, synth.keyframe_pano(512, 2048, 0.3, 150.0), params, device)
     state = IcpState(builder.kf, device)
     preds = torch.zeros((n, 6), dtype=torch.float32, device=device)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    ev0.record()
     for b0 in range(0, n, net.batch):
         xb = x[b0:b0 + net.batch].contiguous()
         preds[b0:b0 + xb.shape[0]] = net.forward(xb)
     init_learned = poses_from_twists(preds)
+    ev1.record()
     torch.cuda.synchronize()
     t_cnn = time.perf_counter() - t0
+    g_cnn = ev0.elapsed_time(ev1) * 1e-3
     ok_plain = ok_learned = ok_gated = fallbacks = 0
     t_plain = t_learned = 0.0
+    g_plain = g_learned = 0.0  # device time of the ICP launches (CUDA events), seconds
     I = identity_pose(device)
 
     def run(T0):
+        """ICP from T0 -> (T, stats, rms, quality, device seconds of the launch)."""
         state.pose.copy_(T0)
+        ev0.record()
         icp(builder.kf, builder.sw, state, params)
+        ev1.record()
         st = state.read_stats()
         T = state.pose.cpu().numpy().reshape(3, 4)
         rms = math.sqrt(st["sse"] / max(1, st["inliers"]))
         q = st["inliers"] / max(1, st["valid"])
-        return T, st, rms, q
+        return T, st, rms, q, ev0.elapsed_time(ev1) * 1e-3
 
+    iters_plain = iters_learned = 0
     for i in range(n):
         builder.load(kf_scans[i], sw_scans[i])
         truth = motions[i]
         torch.cuda.synchronize()
         a = time.perf_counter()
-        Tp, stp, rmsp, qp = run(I)
+        Tp, stp, rmsp, qp, gp = run(I)
         torch.cuda.synchronize()
         t_plain += time.perf_counter() - a
+        g_plain += gp
+        iters_plain += stp["iters"]
         a = time.perf_counter()
-        Tl, stl, rmsl, ql = run(init_learned[i])
+        Tl, stl, rmsl, ql, gl = run(init_learned[i])
+        g_learned += gl
+        iters_learned += stl["iters"]
         use = Tl
         if not (stl["status"] == 0 and ql >= gate_quality and rmsl <= gate_rms):
             fallbacks += 1
-            Tf, stf, rmsf, qf = run(I)
+            Tf, stf, rmsf, qf, gf = run(I)
+            g_learned += gf
+            iters_learned += stf["iters"]
             if stf["status"] == 0 and (stl["status"] != 0 or rmsf < rmsl):
                 use = Tf
         torch.cuda.synchronize()
@@ -387,9 +402,13 @@ def evaluate(net: PoseNet, x: torch.Tensor, motions: list, scans, params: Params
                 ok_learned += good
             else:
                 ok_gated += good
+    # pairs/s by device time (the ICP launches, and for the gated path also the network's forward over
+    # every pair), and by host wall time around the same calls (which adds one stats read per launch)
     return {"pairs": n, "plain_success": ok_plain, "learned_success": ok_learned, "gated_success": ok_gated,
-            "fallbacks": fallbacks, "plain_pairs_per_s": n / t_plain, "gated_pairs_per_s": n / (t_learned + t_cnn),
-            "cnn_ms_per_pair": 1e3 * t_cnn / n}
+            "fallbacks": fallbacks, "plain_pairs_per_s": n / g_plain, "gated_pairs_per_s": n / (g_learned + g_cnn),
+            "plain_pairs_per_s_wall": n / t_plain, "gated_pairs_per_s_wall": n / (t_learned + t_cnn),
+            "icp_steps_per_pair_plain": iters_plain / n, "icp_steps_per_pair_gated": iters_learned / n,
+            "cnn_ms_per_pair": 1e3 * g_cnn / n}
 
 
 def _lidar():
