@@ -492,6 +492,18 @@ upslam_status upslam_keyframe_consistency(const upslam_keyframe *kf_a, const ups
  */
 size_t upslam_cnn_param_count(void);
 size_t upslam_cnn_workspace_bytes(int32_t batch);
+/*
+ * Where the pose network (not in the paper) keeps its tensors inside a workspace for `batch` pairs, so a
+ * caller can inspect them after upslam_cnn_forward / upslam_cnn_backward (e.g. to check one layer at a
+ * time).  Writes 16 byte offsets and returns upslam_cnn_workspace_bytes(batch) (0 for batch <= 0 or a
+ * null array):
+ *   [l]      BF16 conv weights of layer l, [C_out][3 * 3 * C_in] ((ky * 3 + kx) * C_in + ci), l = 0..3;
+ *   [4 + l]  BF16 output of layer l after its ReLU, NHWC [batch][64 >> (l+1)][256 >> (l+1)][C_out];
+ *   [8 + l]  BF16 gradient of the loss at layer l's pre-activation (ReLU mask applied), same shape;
+ *   [12]     FP32 pooled features [batch][128]; [13] their gradient; [14] FP32 outputs [batch][6];
+ *   [15]     the int32 error word (upslam_cnn_error_offset).
+ */
+size_t upslam_cnn_workspace_layout(int32_t batch, size_t *offsets16);
 size_t upslam_cnn_error_offset(int32_t batch);
 upslam_status upslam_cnn_forward(const float *d_params, const void *d_x, int32_t batch, float *d_out, void *d_ws,
                                  size_t ws_bytes, void *stream);

@@ -112,6 +112,7 @@ SIGNATURES = {
     "upslam_cnn_param_count": (ctypes.c_size_t, []),
     "upslam_cnn_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int32]),
     "upslam_cnn_error_offset": (ctypes.c_size_t, [ctypes.c_int32]),
+    "upslam_cnn_workspace_layout": (ctypes.c_size_t, [ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)]),
     "upslam_cnn_forward": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, _vp, _vp, ctypes.c_size_t, _vp]),
     "upslam_cnn_forward_wait_probe": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, _vp, _vp, ctypes.c_size_t,
                                                      ctypes.c_ulonglong, _vp]),

@@ -1145,6 +1145,24 @@ extern "C" size_t upslam_cnn_workspace_bytes(int32_t batch) {
     return cnn_ws_layout(batch, nullptr, nullptr);
 }
 
+extern "C" size_t upslam_cnn_workspace_layout(int32_t batch, size_t *offsets16) {
+    if (batch <= 0 || !offsets16) return 0;
+    CnnWs w;
+    char *const base = reinterpret_cast<char *>(256);  // any non-null base: offsets are relative to it
+    const size_t total = cnn_ws_layout(batch, &w, base);
+    auto off = [&](const void *p) { return (size_t)(reinterpret_cast<const char *>(p) - base); };
+    for (int l = 0; l < 4; ++l) {
+        offsets16[l] = off(w.wb[l]);
+        offsets16[4 + l] = off(w.act[l]);
+        offsets16[8 + l] = off(w.dy[l]);
+    }
+    offsets16[12] = off(w.g);
+    offsets16[13] = off(w.dg);
+    offsets16[14] = off(w.out);
+    offsets16[15] = off(w.err);
+    return total;
+}
+
 extern "C" size_t upslam_cnn_error_offset(int32_t batch) {
     if (batch <= 0) return 0;
     return cnn_ws_layout(batch, nullptr, nullptr) - 256;  // the last block of the layout

@@ -129,6 +129,30 @@ class PoseNet:
         _abi.check("upslam_cnn_adam", _abi.lib().upslam_cnn_adam(_p(self.params), _p(self.grads), _p(self.m),
                                                                  _p(self.v), self.step, float(lr), _stream()))
 
+    def workspace_tensors(self, B: int) -> dict:
+        """Views of the tensors the last forward / backward left in the workspace for batch B: BF16 conv
+        weights ``wb`` [4], layer outputs ``act`` [4] and pre-activation gradients ``dy`` [4] (NHWC), FP32
+        pooled features ``g`` and their gradient ``dg``."""
+        L = _abi.lib()
+        offs = (ctypes.c_size_t * 16)()
+        if L.upslam_cnn_workspace_layout(B, offs) == 0:
+            raise ValueError("batch must be positive")
+
+        def view(i, shape, dtype):
+            n = int(np.prod(shape)) * torch.tensor([], dtype=dtype).element_size()
+            return self.ws[offs[i]:offs[i] + n].view(dtype).view(shape)
+
+        out = {"wb": [], "act": [], "dy": []}
+        for l in range(4):
+            ci, co = CHANNELS[l], CHANNELS[l + 1]
+            shape = (B, IN_H >> (l + 1), IN_W >> (l + 1), co)
+            out["wb"].append(view(l, (co, 9 * ci), torch.bfloat16))
+            out["act"].append(view(4 + l, shape, torch.bfloat16))
+            out["dy"].append(view(8 + l, shape, torch.bfloat16))
+        out["g"] = view(12, (B, 128), torch.float32)
+        out["dg"] = view(13, (B, 128), torch.float32)
+        return out
+
     def check(self) -> None:
         """Raise if a tensor-core wait of any call so far gave up (its outputs were left incomplete)."""
         L = _abi.lib()

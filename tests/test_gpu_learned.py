@@ -4,8 +4,11 @@ encoding, and what the trained network gains over plain initialisation.
 The GPU rounds inputs, conv weights and every activation to BF16 and accumulates in FP32.  The oracle runs in
 FP64 on the same BF16-rounded inputs and weights.  Tolerances come from BF16's 2^-9 relative step, compounded
 over four layers:
-* outputs: relative 3e-2;
-* gradients: cosine >= 0.99 and relative norm error <= 0.1 per tensor.
+* end to end (every layer's rounding compounded): outputs relative 3e-2, gradients cosine >= 0.999 and
+  relative norm error <= 5e-2 per tensor (the weight-gradient sums cancel, which lifts the 2^-9 rounding of
+  the BF16 activations and gradients they multiply to a few percent of the sum);
+* layer by layer, on the BF16 tensors the GPU held: 4e-3 for what the GPU stores in BF16, 1e-4 for the FP32
+  weight and bias gradients (``LAYER_TOL``).
 
 Adam and the SE(3) exponential run in FP32 / FP64 and match to 1e-5 / 1e-12.
 """
@@ -61,14 +64,116 @@ def test_forward_backward_match_oracle(B):
     loss = net.backward(x_dev, torch.from_numpy(target).cuda())
     assert abs(float(loss) - L_ref) <= 3e-2 * abs(L_ref)
     g = ocnn.unflatten(net.grads.cpu().numpy().astype(np.float64))
+    worst = {}
     for k in g_ref:
         a, b = g[k].ravel(), g_ref[k].ravel()
         if np.linalg.norm(b) < 1e-12:
             continue
         cos = float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b)))
-        assert cos >= 0.99, (k, cos)
-        assert np.linalg.norm(a - b) <= 0.1 * np.linalg.norm(b), k
+        worst[k] = (cos, float(np.linalg.norm(a - b) / np.linalg.norm(b)))
+        assert cos >= 0.999, (k, cos)
+        assert np.linalg.norm(a - b) <= 5e-2 * np.linalg.norm(b), (k, worst[k])
     net.check()  # no tensor-core wait gave up
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-30))
+
+
+def _f64(t):
+    return t.float().cpu().numpy().astype(np.float64)
+
+
+def _layer_errors(net, x_dev, B, target, onet=ocnn):
+    """Each layer of the GPU's forward and backward against the oracle's arithmetic for that layer alone,
+    fed the GPU's own BF16 tensors (its input, its weights, the gradient arriving from above), so the
+    BF16 rounding of earlier layers does not enter.  -> {check name: relative Frobenius error}."""
+    ws = net.workspace_tensors(B)
+    wb = [_f64(w) for w in ws["wb"]]
+    act = [_f64(a) for a in ws["act"]]
+    dy = [_f64(d) for d in ws["dy"]]
+    ins = [_f64(x_dev)] + act[:3]
+    p = ocnn.unflatten(net.params.cpu().numpy().astype(np.float64))
+    g = ocnn.unflatten(net.grads.cpu().numpy().astype(np.float64))
+    err = {}
+    for l in range(4):
+        co = ocnn.CHANNELS[l + 1]
+        cols = onet.im2col(ins[l])
+        pre = cols @ wb[l].T + p[f"b{l}"]
+        err[f"act{l}"] = _rel(act[l].reshape(-1, co), np.maximum(pre, 0.0))
+        dyl = dy[l].reshape(-1, co)
+        err[f"w{l}"] = _rel(g[f"w{l}"].reshape(co, -1), dyl.T @ cols)
+        err[f"b{l}"] = _rel(g[f"b{l}"], dyl.sum(axis=0))
+        if l > 0:
+            dx = onet.col2im(dyl @ wb[l], ins[l].shape) * (act[l - 1] > 0)
+            err[f"dx{l}"] = _rel(dy[l - 1], dx)
+    # the head: pooled features, the output, and the gradient it sends into the last feature map
+    gpool = act[3].mean(axis=(1, 2))
+    out = gpool @ p["wf"].T + p["bf"]
+    err["pool"] = _rel(_f64(ws["g"]), gpool)
+    err["out"] = _rel(net.out[:B].cpu().numpy().astype(np.float64), out)
+    _, dout = ocnn.loss(out, target, np.array(proposal.LOSS_W))
+    H, W = act[3].shape[1:3]
+    da = np.broadcast_to((dout @ p["wf"])[:, None, None, :] / (H * W), act[3].shape) * (act[3] > 0)
+    err["dy3"] = _rel(dy[3], da)
+    err["wf"] = _rel(g["wf"], dout.T @ gpool)
+    err["bf"] = _rel(g["bf"], dout.sum(axis=0))
+    return err
+
+
+# Tolerances per check, from the arithmetic: values the GPU stores in BF16 (layer outputs, the gradients
+# passed down) carry its 2^-9 relative rounding, plus FP32 accumulation; weight and bias gradients are FP32
+# sums of exact BF16 x BF16 products (2^-24 per addition over reductions of up to 1.6e5 terms, in slices)
+LAYER_TOL = {"act": 4e-3, "dx": 4e-3, "dy": 4e-3, "w": 1e-4, "b": 1e-4, "pool": 1e-5, "out": 1e-5, "wf": 1e-5,
+             "bf": 1e-5}
+
+
+def _tol(name):
+    return LAYER_TOL[name.rstrip("0123456789")]
+
+
+def _run_layers(B, seed):
+    rng = np.random.default_rng(seed)
+    x = rng.uniform(-1, 1, size=(B, 64, 256, 8)) * (rng.random((B, 64, 256, 1)) < 0.7)
+    net = proposal.PoseNet(B, params=torch.from_numpy(ocnn.flatten(_flat_params(seed + 1))))
+    x_dev = torch.from_numpy(x.astype(np.float32)).to(torch.bfloat16).cuda().contiguous()
+    net.forward(x_dev)
+    target = rng.standard_normal((B, 6)) * 0.3
+    net.backward(x_dev, torch.from_numpy(target).cuda())
+    torch.cuda.synchronize()
+    net.check()
+    return net, x_dev, target
+
+
+@pytest.mark.parametrize("B", [3, 24])
+def test_every_layer_matches_oracle_on_the_gpus_own_tensors(B):
+    """Layer by layer: forward outputs, weight and bias gradients, and the gradient passed to the layer below
+    (the data-gradient GEMM with its tap parity classes and ReLU mask), each against the oracle's FP64
+    arithmetic of that one layer on the BF16 tensors the GPU held."""
+    net, x_dev, target = _run_layers(B, 40 + B)
+    err = _layer_errors(net, x_dev, B, target)
+    bad = {k: v for k, v in err.items() if not v <= _tol(k)}
+    assert not bad, (bad, err)
+
+
+def test_layer_check_catches_a_dropped_tap_in_the_data_gradient(monkeypatch):
+    """The per-layer check has the power to see a one-tap mistake: with one of the nine taps dropped from
+    the oracle's col2im (the adjoint the data gradient is checked against), the dx checks fail."""
+    B = 3
+    net, x_dev, target = _run_layers(B, 43)
+
+    class Dropped:
+        im2col = staticmethod(ocnn.im2col)
+
+        @staticmethod
+        def col2im(dcols, shape):
+            Bn, H, W, C = shape
+            d = dcols.reshape(Bn, H // 2, W // 2, 3, 3, C).copy()
+            d[:, :, :, 2, 1, :] = 0.0  # the tap (ky, kx) = (2, 1) forgotten
+            return ocnn.col2im(d.reshape(dcols.shape), shape)
+
+    err = _layer_errors(net, x_dev, B, target, onet=Dropped)
+    assert all(err[f"dx{l}"] > 10 * _tol("dx") for l in (1, 2, 3)), err
 
 
 def test_adam_matches_oracle():

@@ -470,10 +470,9 @@ def test_track_scan_one_launch_equals_separate_launches():
 
 
 def test_persistent_steps_keep_the_exact_association():
-    """After the first step the persistent kernel reuses each sample's previous sweep pixel where a
-    certified test proves the exact FP32 rule gives it again.  Step k's record must equal the oracle's
-    normal equations at the pose the kernel reached after k - 1 steps (inliers within the gate's
-    near-ties, J^T J 1e-5), for the tunnel workload at full size."""
+    """Every step of the persistent launch associates afresh at the current pose: step k's record must
+    equal the oracle's normal equations at the pose the kernel reached after k - 1 steps (inliers within
+    the gate's near-ties, J^T J 1e-5), for the tunnel workload at full size."""
     seq = configs.tunnel_sequence(n_scans=3)
     prm = oracle.Params(accept_quality=0.1)
     kf_ref = oracle.Keyframe(seq.kf)
