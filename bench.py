@@ -476,20 +476,33 @@ def run_ours(args, ws, rank, local):
     return out
 
 
-def _time_calls(fn, reps, flush, warm=3):
-    """Mean ms of fn() over reps calls, CUDA events on the current stream, L2 flushed before each call."""
+def _time_graph(fn, reps, pre=None, warm=2):
+    """Mean ms of fn() from CUDA events that are nodes of one captured graph: reps x [pre(), event, fn(),
+    event], replayed once.  Each call is then timed as it runs inside a stream of work, without the few
+    microseconds an idle stream adds before its first launch; pre() (restore the inputs, flush L2) runs
+    outside the events.  fn and pre must launch on torch's current stream (the capturing one)."""
     import torch
-    cr = Cudart()
-    cr.external = False
-    st = torch.cuda.current_stream().cuda_stream
-    evs = [(cr.event(), cr.event()) for _ in range(reps)]
-    for i in range(reps + warm):
-        flush.zero_()
-        if i >= warm:
-            cr.record(evs[i - warm][0], st)
+    for _ in range(warm):
+        if pre:
+            pre()
         fn()
-        if i >= warm:
-            cr.record(evs[i - warm][1], st)
+    torch.cuda.synchronize()
+    cr = Cudart()
+    cr.external = True
+    evs = [(cr.event(), cr.event()) for _ in range(reps)]
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            st = torch.cuda.current_stream().cuda_stream
+            for a, b in evs:
+                if pre:
+                    pre()
+                cr.record(a, st)
+                fn()
+                cr.record(b, st)
+        g.replay()
     torch.cuda.synchronize()
     return statistics.mean(cr.elapsed(a, b) for a, b in evs)
 
@@ -508,12 +521,13 @@ def run_grid(trk, device, up, hbm, hbm_src):
     poses = up.grid_candidates(trk.state.pose.clone(), xi)
     p = up.Params(d_max=0.1)
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=device)
-    ms = _time_calls(lambda: up.grid_score(trk.kf, trk.sw, poses, p, 4), 20, flush)
+    ms = _time_graph(lambda: up.grid_score(trk.kf, trk.sw, poses, p, 4), 20, flush.zero_)
     samples = int((trk.kf.depth[::4, ::4] > 0).sum().item())
     pairs = samples * poses.shape[0]
     return {"candidates": int(poses.shape[0]), "stride": 4, "sampled_keyframe_samples": samples,
             "launches": 2, "ms_avg": round(ms, 5), "pairs_per_s": round(pairs / (ms * 1e-3), 1),
-            "bound": "alu (FP32 binning rule per pair) + L2 gathers", "l2": "flushed before each call"}
+            "bound": "alu (FP32 binning rule per pair) + L2 gathers", "l2": "flushed before each call",
+            "timing": "CUDA-event nodes of one captured graph"}
 
 
 def run_consistency(pool, T_ab, device, up, hbm, hbm_src):
@@ -530,19 +544,23 @@ def run_consistency(pool, T_ab, device, up, hbm, hbm_src):
     ws = torch.zeros(nbytes, dtype=torch.uint8, device=device)
     removed = torch.zeros(2, dtype=torch.int64, device=device)
     T = T_ab
-    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     # repeated calls only remove what the first one did not: the timing is of the flag pass and a no-op apply
     args = (ctypes.byref(ka), ctypes.byref(kb), ctypes.c_void_p(T.data_ptr()), ctypes.c_float(0.05),
             ctypes.c_float(0.2), ctypes.c_void_p(ws.data_ptr()), ctypes.c_size_t(nbytes),
-            ctypes.c_void_p(removed.data_ptr()), st)
+            ctypes.c_void_p(removed.data_ptr()))
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=device)
-    ms = _time_calls(lambda: L.upslam_keyframe_consistency(*args), 20, flush)
+
+    def fn():
+        rc = L.upslam_keyframe_consistency(*args, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        assert rc == 0, rc
+
+    ms = _time_graph(fn, 20, flush.zero_)
     px = int(a.depth.numel() + b.depth.numel())
     nbytes_alg = px * 6
     gbs = nbytes_alg / (ms * 1e-3) / 1e9
     return {"pixels": px, "launches": 2, "ms_avg": round(ms, 5), "bytes": nbytes_alg, "gbs": round(gbs, 1),
             "bound": "hbm", "peak": hbm, "frac": round(gbs / hbm, 4), "peak_source": hbm_src,
-            "l2": "flushed before each call"}
+            "timing": "CUDA-event nodes of one captured graph", "l2": "flushed before each call"}
 
 
 def run_switch(trk, seq, device, up, hbm, hbm_src, reps=20):
@@ -558,27 +576,23 @@ def run_switch(trk, seq, device, up, hbm, hbm_src, reps=20):
     prev0 = trk.prev.clone()
     new = up.KeyframeBuffer(seq.kf, device)
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=device)
-    cr = Cudart()
-    cr.external = False
-    st = torch.cuda.current_stream().cuda_stream
-    evs = [(cr.event(), cr.event()) for _ in range(reps)]
-    removed = []
-    for i in range(reps + 3):
+
+    def pre():
         trk.kf = old
         old.set(d0, n0)
         new.clear()
         flush.zero_()
-        if i >= 3:
-            cr.record(evs[i - 3][0], st)
+
+    removed = []
+
+    def fn():
         trk.new_keyframe(buffer=new, consistency=True)
-        if i >= 3:
-            cr.record(evs[i - 3][1], st)
-            removed.append(trk.last_removed)
-    torch.cuda.synchronize()
+        removed.append(trk.last_removed)
+
+    ms = _time_graph(fn, reps, pre)
     trk.kf = old
     old.set(d0, n0)
     trk.prev.copy_(prev0)
-    ms = statistics.mean(cr.elapsed(a, b) for a, b in evs)
     px = int(old.depth.numel())
     # hole fill: sweep read (32 B/px) + every new keyframe pixel written once (20 B); consistency: both
     # keyframes' depth read (4 B/px) and flags written and read (2 B/px)
@@ -587,7 +601,8 @@ def run_switch(trk, seq, device, up, hbm, hbm_src, reps=20):
     rem = removed[-1].cpu().tolist() if removed else None
     return {"ms_avg": round(ms, 5), "launches": 5, "bytes": alg, "gbs": round(gbs, 1), "bound": "hbm", "peak": hbm,
             "frac": round(gbs / hbm, 4), "peak_source": hbm_src, "samples_removed": rem,
-            "l2": "flushed before each call", "note": "one switch per 50 sweeps in the headline sequence"}
+            "timing": "CUDA-event nodes of one captured graph", "l2": "flushed before each call",
+            "note": "one switch per 50 sweeps in the headline sequence"}
 
 
 def run_fuse(kf, seq, scan, T, device, up, hbm, hbm_src, reps=20):
@@ -607,30 +622,27 @@ def run_fuse(kf, seq, scan, T, device, up, hbm, hbm_src, reps=20):
     changed = int(((kf.depth != d0) | (kf.nw != n0).any(-1)).sum())
     samples = int((n0[..., 3] > 0).sum())
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=device)
-    cr = Cudart()
-    cr.external = False
-    st = torch.cuda.current_stream().cuda_stream
-    evs = [(cr.event(), cr.event()) for _ in range(reps)]
-    for i in range(reps + 3):
+
+    def pre():
         kf.depth.copy_(d0)
         kf.nw.copy_(n0)
         flush.zero_()
-        if i >= 3:
-            cr.record(evs[i - 3][0], st)
-        up.fuse(kf, sw, T, p)
-        if i >= 3:
-            cr.record(evs[i - 3][1], st)
-    torch.cuda.synchronize()
-    ms = statistics.mean(cr.elapsed(a, b) for a, b in evs)
+
+    ms = _time_graph(lambda: up.fuse(kf, sw, T, p), reps, pre)
     kf.depth.copy_(d0)
     kf.nw.copy_(n0)
     kf_px, sw_px = kf.depth.numel(), seq.sweep.pixels
-    nbytes = kf_px * 20 + changed * 20 + sw_px * 64
+    # the survey's algorithmic bytes: every keyframe pixel read and written once (20 B each way) and the
+    # hole fill's read of the sweep (24 B per sweep pixel)
+    nbytes = kf_px * 40 + sw_px * 24
+    touched = kf_px * 20 + changed * 20 + sw_px * 64
     gbs = nbytes / (ms * 1e-3) / 1e9
     return {"keyframe": f"{int(seq.kf.rows)}x{int(seq.kf.cols)} f32", "samples_before": samples,
             "pixels_written": changed, "launches": 2, "ms_avg": round(ms, 5), "bytes": nbytes,
             "gbs": round(gbs, 1), "bound": "hbm", "peak": hbm, "frac": round(gbs / hbm, 4),
-            "peak_source": hbm_src, "l2": "flushed before each call (keyframe restored first)"}
+            "peak_source": hbm_src, "bytes_touched": touched,
+            "timing": "CUDA-event nodes of one captured graph (restore + flush between calls, outside the events)",
+            "l2": "flushed before each call (keyframe restored first)"}
 
 
 def run_atrous(args, seq, d_scans, device, up, hbm, hbm_src):
@@ -651,31 +663,30 @@ def run_atrous(args, seq, d_scans, device, up, hbm, hbm_src):
     ap = p.atrous()
     L = up.lib()
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=device)
-    cr = Cudart()
-    cr.external = False  # eager launches: plain event records
     reps = min(50, d_scans.shape[0])
-    evs = [(cr.event(), cr.event()) for _ in range(reps)]
-    st = torch.cuda.current_stream().cuda_stream
-    for i in range(reps + 3):
-        sw.load(d_scans[i % d_scans.shape[0]], up.Params(accept_quality=0.1))
+    rep = [0]
+
+    def pre():
+        sw.load(d_scans[rep[0] % d_scans.shape[0]], up.Params(accept_quality=0.1))
+        rep[0] += 1
         raw.copy_(sw.nrm)
         flush.zero_()
-        if i >= 3:
-            cr.record(evs[i - 3][0], st)
+
+    def fn():
+        st = torch.cuda.current_stream().cuda_stream
         rc = L.upslam_atrous_normals(ctypes.byref(ps), ctypes.c_void_p(sw.pix.data_ptr()),
                                      ctypes.c_void_p(raw.data_ptr()), ctypes.c_void_p(out.data_ptr()),
                                      ctypes.c_void_p(tmp.data_ptr()), up.F32, ctypes.byref(ap), ctypes.c_void_p(st))
         assert rc == 0, rc
-        if i >= 3:
-            cr.record(evs[i - 3][1], st)
-    torch.cuda.synchronize()
-    ms = statistics.mean(cr.elapsed(a, b) for a, b in evs)
+
+    ms = _time_graph(fn, reps, pre)
     px = seq.sweep.pixels
     bytes_level = px * 48
     gbs = bytes_level * levels / (ms * 1e-3) / 1e9
     return {"levels": levels, "launches": levels, "ms_avg": round(ms, 5), "us_per_level": round(ms * 1e3 / levels, 3),
             "bytes_per_level": bytes_level, "gbs": round(gbs, 1), "bound": "hbm", "peak": hbm,
             "frac": round(gbs / hbm, 4), "peak_source": hbm_src, "reps": reps,
+            "timing": "CUDA-event nodes of one captured graph",
             "l2": "flushed before each repetition (outside the events)"}
 
 
