@@ -13,7 +13,8 @@
 // Launches:
 //  1. fuse_main_kernel: CTAs [0, gk) average keyframe pixels in place; CTAs
 //     [gk, gk + gs) run the hole-fill atomics.  The two touch disjoint pixels
-//     (averaging only writes pixels with w > 0, hole fill only targets w == 0).
+//     (a pixel holds a sample exactly when its depth and count are positive;
+//     averaging only writes such pixels, hole fill only targets depth 0).
 //  2. fuse_fill_kernel: each sweep pixel re-derives its key; the one whose key
 //     won writes the pixel and resets the z-buffer word to all-ones.
 // Both launches read the registration record first and do nothing unless the
@@ -21,10 +22,13 @@
 // per-pixel functions (common.cuh) serve the fused register + update launch.
 //
 // Roofline: the keyframe is streamed once in and once out: 4 + 16 B (FP32) or
-// 4 + 8 B (FP16) each way per pixel, plus sweep gathers from L2.
+// 4 + 8 B (FP16) each way per pixel, plus sweep gathers from L2.  Empty pixels
+// are read only as far as their depth.
 #include "common.cuh"
 
 namespace upslam {
+
+constexpr int kFuseB = 2;  // keyframe pixels per averaging thread and iteration
 
 // Registration accepted?  Decided by one thread per CTA (in FP32, off the FP64 pipe) and broadcast.
 __device__ __forceinline__ bool accepted(const upslam_icp_stats *st, float accept) {
@@ -45,19 +49,25 @@ __global__ void __launch_bounds__(256) fuse_main_kernel(FuseView f, const double
     if (!accepted(st, f.accept)) return;
     const PoseF T = cta_pose_f32(pose);
     if ((int)blockIdx.x < gk) {
-        // averaging: each thread takes 4 pixels a CTA-width apart, issuing their keyframe loads together
-        constexpr int kB = 4;
+        // averaging: each thread takes kB pixels a CTA-width apart, issuing their depth loads together,
+        // then the normal and count of the pixels that hold a sample (an empty pixel has depth 0 and
+        // count 0, so half a fresh keyframe is never read past its depth)
         const int npx = f.kp.rows * f.kp.cols;
         const int W = f.kp.cols;
-        const int stride = gk * blockDim.x * kB;
-        for (int base = blockIdx.x * blockDim.x * kB + threadIdx.x; base < npx; base += stride) {
+        const int stride = gk * blockDim.x * kFuseB;
+        for (int base = blockIdx.x * blockDim.x * kFuseB + threadIdx.x; base < npx; base += stride) {
+            constexpr int kB = kFuseB;
             float4 n[kB];
             float d[kB];
 #pragma unroll
             for (int b = 0; b < kB; ++b) {
                 const int k = base + b * blockDim.x;
-                n[b] = k < npx ? load_nw(f.knw, k, f.kprec) : make_float4(0.f, 0.f, 0.f, 0.f);
                 d[b] = k < npx ? __ldg(f.kdepth + k) : 0.0f;
+            }
+#pragma unroll
+            for (int b = 0; b < kB; ++b) {
+                const int k = base + b * blockDim.x;
+                n[b] = d[b] > 0.0f ? load_nw(f.knw, k, f.kprec) : make_float4(0.f, 0.f, 0.f, 0.f);
             }
 #pragma unroll
             for (int b = 0; b < kB; ++b) {
@@ -77,7 +87,7 @@ __global__ void __launch_bounds__(256) fuse_main_kernel(FuseView f, const double
             float r;
             float4 m;
             if (!holefill_key(f, T, j, k, key, r, m)) continue;
-            if (load_nw(f.knw, k, f.kprec).w != 0.0f) continue;
+            if (__ldg(f.kdepth + k) > 0.0f) continue;  // a pixel holding a sample is averaged, not filled
             atomicMin(f.zbuf + k, key);
         }
     }
@@ -141,7 +151,7 @@ extern "C" upslam_status upslam_fuse(const upslam_keyframe *kf, const upslam_swe
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t npx = (int64_t)kf->pano.rows * kf->pano.cols;
     const int64_t ns = (int64_t)sw->pano.rows * sw->pano.cols;
-    const int gk = upslam_grid((npx + 3) / 4, 256, 8);
+    const int gk = upslam_grid((npx + kFuseB - 1) / kFuseB, 256, 8);
     const int gs = upslam_grid(ns, 256, 2);
     fuse_main_kernel<<<gk + gs, 256, 0, s>>>(f, d_pose12, d_stats, gk);
     UPSLAM_CHECK_LAUNCH();

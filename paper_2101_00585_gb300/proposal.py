@@ -348,12 +348,15 @@ def train(net: PoseNet, x: torch.Tensor, xi: torch.Tensor, epochs: int = 3, lr: 
 
 
 def evaluate(net: PoseNet, x: torch.Tensor, motions: list, scans, params: Params = Params(),
-             gate_rms: float = 0.05, gate_quality: float = 0.2, tol_m: float = 0.02, tol_deg: float = 0.1) -> dict:
+             gate_rms: float = 0.05, gate_quality: float = 0.2, tol_m: float = 0.02, tol_deg: float = 0.1,
+             learned_max_iters: int | None = None) -> dict:
     """Plain init + ICP against learned init + ICP (gated, with plain fallback) on held-out pairs.
 
     Success: final pose within tol_m and tol_deg of the true motion.  The gate accepts the learned start's result
     when ICP reports status OK, inliers / valid >= gate_quality and RMS residual <= gate_rms; otherwise ICP also
-    runs from the plain start and the result with the smaller RMS residual is kept.
+    runs from the plain start and the result with the smaller RMS residual is kept.  ``learned_max_iters`` caps
+    the Gauss-Newton steps from the learned start (it starts close, so fewer are needed); the plain start and the
+    fallback keep ``params.max_iters``.
     """
     import synth
     device = x.device
@@ -380,11 +383,14 @@ def evaluate(net: PoseNet, x: torch.Tensor, motions: list, scans, params: Params
     g_plain = g_learned = 0.0  # device time of the ICP launches (CUDA events), seconds
     I = identity_pose(device)
 
-    def run(T0):
+    import dataclasses
+    p_learned = params if learned_max_iters is None else dataclasses.replace(params, max_iters=int(learned_max_iters))
+
+    def run(T0, prm=params):
         """ICP from T0 -> (T, stats, rms, quality, device seconds of the launch)."""
         state.pose.copy_(T0)
         ev0.record()
-        icp(builder.kf, builder.sw, state, params)
+        icp(builder.kf, builder.sw, state, prm)
         ev1.record()
         st = state.read_stats()
         T = state.pose.cpu().numpy().reshape(3, 4)
@@ -404,7 +410,7 @@ def evaluate(net: PoseNet, x: torch.Tensor, motions: list, scans, params: Params
         g_plain += gp
         iters_plain += stp["iters"]
         a = time.perf_counter()
-        Tl, stl, rmsl, ql, gl = run(init_learned[i])
+        Tl, stl, rmsl, ql, gl = run(init_learned[i], p_learned)
         g_learned += gl
         iters_learned += stl["iters"]
         use = Tl
