@@ -163,7 +163,12 @@ __global__ void __launch_bounds__(512, 1) icp_batched_kernel(BatchArgs a) {
         const int nch = (npx + a.chunk - 1) / a.chunk;
         if (threadIdx.x == 0) kf_off[kf] = base_s;
         __syncthreads();
-        for (int c = blockIdx.x; c < nch; c += gridDim.x) {
+        // chunk c goes to CTA (c + rot) mod grid, the rotation stepping by a number prime to the grid from
+        // one keyframe to the next: the rows holding samples are a band, so without it the same CTAs would
+        // take one chunk more of every keyframe of a size
+        const int rot = (int)(((long long)kf * 61) % gridDim.x);
+        const int c0 = ((int)blockIdx.x - rot + (int)gridDim.x) % (int)gridDim.x;
+        for (int c = c0; c < nch; c += gridDim.x) {
             for (int b0 = c * a.chunk; b0 < min(npx, (c + 1) * a.chunk); b0 += T) {
                 const int k = b0 + threadIdx.x;
                 bool ok = false;
