@@ -72,6 +72,9 @@ def parse():
                     help="also run the other workloads (room latency, campus precision form, forest batched form, "
                          "learned proposal) after the headline and report them under 'forms'")
     ap.add_argument("--form-steps", type=int, default=40, help="timed sweeps of the campus form")
+    ap.add_argument("--batch-keyframes", type=int, default=64,
+                    help="forest batched form: keyframes in the batch (the workload has 64; fewer for profiling)")
+    ap.add_argument("--no-autotune", action="store_true", help="forest batched form: default tiles (512 x 512)")
     ap.add_argument("--quiet", action="store_true")
     return ap.parse_args()
 
@@ -895,7 +898,9 @@ def run_forest_batch(args, local):
     from synth import configs
     torch.cuda.set_device(local)
     device = torch.device("cuda", local)
-    case = configs.forest_batch()
+    n_kf = args.batch_keyframes
+    case = configs.forest_batch() if n_kf == 64 else configs.forest_batch(
+        n_kf=n_kf, kf_sizes=tuple(((256, 1024), (512, 2048), (1024, 4096))[i % 3] for i in range(n_kf)))
     p = up.Params(max_iters=15, d_max=1.0, coarse_iters=5, d_max_fine=0.5)
     sw = up.SweepFrame(case.sweep, device)
     sw.load(torch.from_numpy(case.scan).to(device), p)
@@ -910,7 +915,7 @@ def run_forest_batch(args, local):
         bufs.append(b)
     batch = up.Batch(sw, bufs, case.n_hyp)
     init = torch.from_numpy(np.stack([np.asarray(h).reshape(12) for hyps in case.T_init for h in hyps])).to(device)
-    tuned = autotune.tune(batch, init, p, reps=2)
+    tuned = ({"tiles": [512, 512], "ms": {}} if args.no_autotune else autotune.tune(batch, init, p, reps=2))
     batch.run(init, p)  # first launch outside the capture
     batch.capture(p)
     batch.init.copy_(init)
@@ -948,8 +953,10 @@ def run_forest_batch(args, local):
             "value": round(batch.n_prob / (avg * 1e-3), 1), "unit": "problems/s", "n_gpus": 1, "steps": K,
             "ms_per_launch": round(avg, 3), "higher_is_better": True, "dtype": "f32", "data": "synthetic",
             "graph": True, "gpu_launches_per_replay": 2,
-            "config": {"workload": "forest: 64 keyframes (22x256x1024, 21x512x2048, 21x1024x4096) x 8 hypotheses "
-                                   "up to 2 m / 20 deg, keyframes started from a sweep each",
+            "config": {"workload": (f"forest: 64 keyframes (22x256x1024, 21x512x2048, 21x1024x4096) x 8 hypotheses "
+                                    f"up to 2 m / 20 deg, keyframes started from a sweep each" if n_kf == 64 else
+                                    f"forest: {n_kf} keyframes (256x1024, 512x2048, 1024x4096 in turn) x 8 "
+                                    f"hypotheses up to 2 m / 20 deg"),
                        "gate": "d_max 1.0 m for 5 steps, then 0.5 m", "tiles": tuned["tiles"],
                        "autotune_ms": tuned["ms"], "l2": "flushed between launches"},
             "roofline": {"kernel": "icp_batched_kernel", "bound": "hbm", "achieved": round(gbs, 1), "peak": hbm,
@@ -1021,10 +1028,26 @@ def run_room(args, local):
             cr.record(evs2[i - 3][1], st)
     torch.cuda.synchronize()
     icp_us = 1e3 * statistics.median(cr.elapsed(a, b) for a, b in evs2)
+    cpu = None
+    if not args.no_cpu_baseline:
+        # the FP64 oracle on the same registration: sweep frame, 10 Gauss-Newton steps, keyframe update
+        import oracle
+        prm = oracle.Params(max_iters=10, accept_quality=0.1)
+        kd = d.astype(np.float32)
+        kn, kv = oracle.normals(oracle.keyframe_points(kd, c.kf).astype(np.float32), kd, c.kf, prm)
+        kn4 = oracle.normals4(kn, kv)
+        reps, t0 = 3, time.perf_counter()
+        for _ in range(reps):
+            kf_ref = oracle.Keyframe(c.kf, kd.astype(np.float64), kn4[..., :3].astype(np.float64),
+                                     (kd > 0).astype(np.float64))
+            oracle.process_scan(kf_ref, c.scan, c.sweep, np.hstack([np.eye(3), np.zeros((3, 1))]), prm)
+        dt = (time.perf_counter() - t0) / reps
+        cpu = {"value": round(dt * 1e6, 1), "unit": "us per sweep", "cores": 1, "kind": "oracle",
+               "sample": f"the same room registration, {reps} repetitions on one host thread"}
     return {"metric": "latency of one 16x512 room sweep vs a 256x512 keyframe", "unit": "us",
             "higher_is_better": False, "us_per_scan": round(scan_us, 2), "us_per_icp_step": round(icp_us / 10, 3),
             "icp_launch_us_10_steps": round(icp_us, 2), "icp_iters_avg": float(np.mean(iters)), "reps": K,
-            "pose_error_m": float(err[0]), "pose_error_deg": float(math.degrees(err[1])),
+            "pose_error_m": float(err[0]), "pose_error_deg": float(math.degrees(err[1])), "cpu_baseline": cpu,
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": "room 16x512 sweep (8192 points) vs 256x512 keyframe, 5 cm / 2 deg, <=10 steps",
                        "l2": "flushed before each call", "stat": "median of reps"}}
