@@ -57,8 +57,8 @@ struct BatchArgs {
     upslam_icp_stats *stats;  // [n_prob]
     int *active;              // [n_prob] workspace flags
     float *poses_f;           // [n_prob][12] FP32 copies written by each problem's owner
-    float *entries;           // per-CTA entry regions
-    long long cta_cap;        // entries per CTA region
+    float *entries;           // per keyframe, its samples as [6][rows*cols] floats (structure of arrays)
+    int *counts;              // [n_kf][grid] samples each CTA found in its chunks of each keyframe
     float *records;           // [n_prob][grid][kRecWords]
     BatchCtrl *ctrl;
     upslam_icp_params ip;
@@ -81,10 +81,10 @@ struct BatchHit {
     bool binned;
 };
 
-__device__ __forceinline__ BatchHit batch_gather(const BatchArgs &a, const float *ent, const PoseF &Tp, int q,
+__device__ __forceinline__ BatchHit batch_gather(const BatchArgs &a, const float *ent, int cap, const PoseF &Tp, int q,
                                                  float3 &s, float3 &n) {
-    s = make_float3(ent[q], ent[a.cta_cap + q], ent[2 * a.cta_cap + q]);
-    n = make_float3(ent[3 * a.cta_cap + q], ent[4 * a.cta_cap + q], ent[5 * a.cta_cap + q]);
+    s = make_float3(ent[q], ent[cap + q], ent[2 * cap + q]);
+    n = make_float3(ent[3 * cap + q], ent[4 * cap + q], ent[5 * cap + q]);
     const float3 qq = xform_inv(Tp, s.x, s.y, s.z);
     int jv = 0, ju = 0;
     float rr;
@@ -134,13 +134,28 @@ __device__ __forceinline__ void batch_accumulate(const BatchArgs &a, const PoseF
     inl += ok ? 1 : 0;
 }
 
+constexpr int kPx = 8;  // keyframe pixels per thread in flight in the prologue
+
+// Keyframe pixel k as a sample: it holds one when its depth is positive and its normal unit (the test of the
+// single-problem launch); the normal is read only where the depth holds a sample.
+__device__ __forceinline__ bool kf_sample(const upslam_keyframe &K, int k, float d, float4 &n4) {
+    n4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (!(d > 0.0f)) return false;
+    n4 = load_nw(K.d_nw, k, K.precision);
+    return __fadd_rn(__fadd_rn(__fmul_rn(n4.x, n4.x), __fmul_rn(n4.y, n4.y)), __fmul_rn(n4.z, n4.z)) > 0.25f;
+}
+
 __global__ void __launch_bounds__(512, 1) icp_batched_kernel(BatchArgs a) {
     extern __shared__ float smem[];
     float *acc = smem;                                 // [n_prob][kRecWords]
     float *pose_f = acc + a.n_prob * kRecWords;        // [n_prob][12]
     int *act = reinterpret_cast<int *>(pose_f + a.n_prob * 12);  // [n_prob]
-    __shared__ int kf_off[kBatchMaxKf], kf_cnt[kBatchMaxKf];
+    __shared__ long long kf_base[kBatchMaxKf];              // float offset of a keyframe's sample arrays
+    __shared__ int kf_cap[kBatchMaxKf];                      // its pixels: the length of each array
+    __shared__ int kf_lo[kBatchMaxKf], kf_hi[kBatchMaxKf];   // this CTA's slice of its samples
+    __shared__ int kf_wb[kBatchMaxKf];                       // where this CTA's own samples go
     __shared__ int wcnt[32];
+    __shared__ int pcnt[2][kPx][16];
     __shared__ int base_s, flag_s, any_active;
     __shared__ double totq[16][32];   // step sums of the problems being solved, one per warp
     __shared__ double Tsh[16][12];    // their poses
@@ -151,63 +166,126 @@ __global__ void __launch_bounds__(512, 1) icp_batched_kernel(BatchArgs a) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned long long G = gridDim.x;
     unsigned long long base = 0;
-    if (threadIdx.x == 0) base = (*((volatile unsigned long long *)&a.ctrl->arrive) / G) * G;
-    float *ent = a.entries + (size_t)blockIdx.x * 6 * a.cta_cap;  // SoA: [6][cta_cap]
-
-    // ---- prologue: compact this CTA's keyframe chunks
-    if (threadIdx.x == 0) base_s = 0;
+    if (threadIdx.x == 0) {
+        base = (*((volatile unsigned long long *)&a.ctrl->arrive) / G) * G;
+        flag_s = 0;
+    }
+    // ---- prologue, once per launch: the keyframe samples.  Keyframe chunks are dealt to CTAs round-robin,
+    // the deal rotated from one keyframe to the next (the samples sit in a band of rows: without the
+    // rotation the same CTAs would take one chunk more of every keyframe of a size).
+    //  (1) every CTA counts the samples in its chunks of each keyframe;
+    //  (2) after a grid barrier, it writes them to the keyframe's sample arrays behind those of the CTAs
+    //      before it, in pixel order, so the arrays are the same on every launch;
+    //  (3) after a second barrier, each CTA takes an equal slice of every keyframe's samples for the steps.
+    // A thread keeps kPx pixels in flight, and reads a normal only where the depth holds a sample.
+    if (threadIdx.x == 0) {
+        long long o = 0;
+        for (int kf = 0; kf < a.n_kf; ++kf) {
+            const int npx = a.kfs[kf].pano.rows * a.kfs[kf].pano.cols;
+            kf_base[kf] = o;
+            kf_cap[kf] = npx;
+            o += 6ll * npx;
+        }
+    }
     __syncthreads();
-    for (int kf = 0; kf < a.n_kf; ++kf) {
-        const upslam_keyframe K = a.kfs[kf];
-        const int npx = K.pano.rows * K.pano.cols, W = K.pano.cols;
-        const int nch = (npx + a.chunk - 1) / a.chunk;
-        if (threadIdx.x == 0) kf_off[kf] = base_s;
-        __syncthreads();
-        // chunk c goes to CTA (c + rot) mod grid, the rotation stepping by a number prime to the grid from
-        // one keyframe to the next: the rows holding samples are a band, so without it the same CTAs would
-        // take one chunk more of every keyframe of a size
-        const int rot = (int)(((long long)kf * 61) % gridDim.x);
-        const int c0 = ((int)blockIdx.x - rot + (int)gridDim.x) % (int)gridDim.x;
-        for (int c = c0; c < nch; c += gridDim.x) {
-            for (int b0 = c * a.chunk; b0 < min(npx, (c + 1) * a.chunk); b0 += T) {
-                const int k = b0 + threadIdx.x;
-                bool ok = false;
-                float3 s = make_float3(0.f, 0.f, 0.f);
-                float4 n4 = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (k < npx && k < (c + 1) * a.chunk) {
-                    const float d = __ldg(K.d_depth + k);
-                    n4 = load_nw(K.d_nw, k, K.precision);
-                    if (d > 0.0f && __fadd_rn(__fadd_rn(__fmul_rn(n4.x, n4.x), __fmul_rn(n4.y, n4.y)),
-                                              __fmul_rn(n4.z, n4.z)) > 0.25f) {
-                        ok = true;
-                        const int v = k / W;
-                        s = pixel_point(K.d_dirs, K.pano.rows, v, k - v * W, d);
+    for (int pass = 0; pass < 2 && !flag_s; ++pass) {
+        for (int kf = 0; kf < a.n_kf; ++kf) {
+            const upslam_keyframe K = a.kfs[kf];
+            const int npx = kf_cap[kf], W = K.pano.cols;
+            const int nch = (npx + a.chunk - 1) / a.chunk;
+            const int rot = (int)(((long long)kf * 61) % gridDim.x);
+            const int c0 = ((int)blockIdx.x - rot + (int)gridDim.x) % (int)gridDim.x;
+            float *E = a.entries + kf_base[kf];
+            int mine = 0, run = pass == 1 ? kf_wb[kf] : 0, par = 0;
+            for (int c = c0; c < nch; c += gridDim.x) {
+                const int cend = min(npx, (c + 1) * a.chunk);
+                for (int b0 = c * a.chunk; b0 < cend; b0 += T * kPx, par ^= 1) {
+                    float d[kPx];
+                    float4 n4[kPx];
+                    bool ok[kPx];
+#pragma unroll
+                    for (int i = 0; i < kPx; ++i) {
+                        const int k = b0 + i * T + threadIdx.x;
+                        d[i] = k < cend ? __ldg(K.d_depth + k) : 0.0f;
                     }
+#pragma unroll
+                    for (int i = 0; i < kPx; ++i) ok[i] = kf_sample(K, b0 + i * T + threadIdx.x, d[i], n4[i]);
+                    if (pass == 0) {
+#pragma unroll
+                        for (int i = 0; i < kPx; ++i) mine += ok[i] ? 1 : 0;
+                        continue;
+                    }
+                    // positions in pixel order: ballots per pixel slot, counts per warp, double-buffered
+                    unsigned bal[kPx];
+#pragma unroll
+                    for (int i = 0; i < kPx; ++i) {
+                        bal[i] = __ballot_sync(0xffffffffu, ok[i]);
+                        if (lane == 0) pcnt[par][i][warp] = __popc(bal[i]);
+                    }
+                    __syncthreads();
+                    int o = run;
+#pragma unroll
+                    for (int i = 0; i < kPx; ++i) {
+                        int before = 0, tot = 0;
+                        for (int w = 0; w < nw; ++w) {
+                            const int cw = pcnt[par][i][w];
+                            before += w < warp ? cw : 0;
+                            tot += cw;
+                        }
+                        if (ok[i]) {
+                            const int slot = o + before + __popc(bal[i] & ((1u << lane) - 1u));
+                            const int k = b0 + i * T + threadIdx.x;
+                            const int v = k / W;
+                            const float3 sp = pixel_point(K.d_dirs, K.pano.rows, v, k - v * W, d[i]);
+                            E[slot] = sp.x;
+                            E[npx + slot] = sp.y;
+                            E[2 * npx + slot] = sp.z;
+                            E[3 * npx + slot] = n4[i].x;
+                            E[4 * npx + slot] = n4[i].y;
+                            E[5 * npx + slot] = n4[i].z;
+                        }
+                        o += tot;
+                    }
+                    run = o;
                 }
-                const unsigned bal = __ballot_sync(0xffffffffu, ok);
-                if (lane == 0) wcnt[warp] = __popc(bal);
+            }
+            if (pass == 0) {
+                mine = __reduce_add_sync(0xffffffffu, mine);
+                if (lane == 0) wcnt[warp] = mine;
                 __syncthreads();
-                int off = base_s, total = base_s;
-                for (int w = 0; w < nw; ++w) {
-                    off += w < warp ? wcnt[w] : 0;
-                    total += wcnt[w];
+                if (threadIdx.x == 0) {
+                    int t = 0;
+                    for (int w = 0; w < nw; ++w) t += wcnt[w];
+                    a.counts[(size_t)kf * gridDim.x + blockIdx.x] = t;
                 }
-                const int slot = off + __popc(bal & ((1u << lane) - 1u));
-                if (ok && slot < a.cta_cap) {
-                    ent[slot] = s.x;
-                    ent[a.cta_cap + slot] = s.y;
-                    ent[2 * a.cta_cap + slot] = s.z;
-                    ent[3 * a.cta_cap + slot] = n4.x;
-                    ent[4 * a.cta_cap + slot] = n4.y;
-                    ent[5 * a.cta_cap + slot] = n4.z;
-                }
-                __syncthreads();
-                if (threadIdx.x == 0) base_s = total < a.cta_cap ? total : (int)a.cta_cap;
                 __syncthreads();
             }
         }
-        if (threadIdx.x == 0) kf_cnt[kf] = base_s - kf_off[kf];
+        // grid barrier: the counts (after pass 0), the sample arrays (after pass 1)
         __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(&a.ctrl->arrive, 1ull);
+            flag_s = grid_wait(a.ctrl, base + G * (unsigned long long)(pass + 1)) ? 0 : 1;
+            __threadfence();
+        }
+        __syncthreads();
+        if (pass == 0 && !flag_s) {
+            // where this CTA's samples go, and its slice of each keyframe's samples
+            for (int kf = threadIdx.x; kf < a.n_kf; kf += T) {
+                const int *ck = a.counts + (size_t)kf * gridDim.x;
+                int before = 0, tot = 0;
+                for (int c = 0; c < (int)gridDim.x; ++c) {
+                    const int v = __ldcg(ck + c);
+                    before += c < (int)blockIdx.x ? v : 0;
+                    tot += v;
+                }
+                kf_wb[kf] = before;
+                kf_lo[kf] = (int)((long long)tot * blockIdx.x / gridDim.x);
+                kf_hi[kf] = (int)((long long)tot * (blockIdx.x + 1) / gridDim.x);
+            }
+            __syncthreads();
+        }
     }
     // sweep pixels holding a point (for the registration quality)
     {
@@ -224,7 +302,7 @@ __global__ void __launch_bounds__(512, 1) icp_batched_kernel(BatchArgs a) {
     __syncthreads();
 
     int it = 0;
-    for (; it < a.ip.max_iters; ++it) {
+    for (; it < a.ip.max_iters && !flag_s; ++it) {
         // this step's Omega distance gate (coarse-to-fine when coarse_iters > 0)
         const float gate2 = (a.ip.coarse_iters > 0 && it >= a.ip.coarse_iters) ? a.d_max2_fine : a.d_max2;
         for (int i = threadIdx.x; i < a.n_prob * kRecWords; i += T) acc[i] = 0.0f;
@@ -242,7 +320,8 @@ __global__ void __launch_bounds__(512, 1) icp_batched_kernel(BatchArgs a) {
             const int p = item / split, part = item - p * split;
             if (!act[p]) continue;
             const int kf = p / a.n_hyp;
-            const int cnt = kf_cnt[kf], off = kf_off[kf];
+            const int lo = kf_lo[kf], hi = kf_hi[kf], capk = kf_cap[kf];
+            const float *E = a.entries + kf_base[kf];
             PoseF Tp;
 #pragma unroll
             for (int i = 0; i < 12; ++i) Tp.r[i] = pose_f[p * 12 + i];
@@ -251,14 +330,14 @@ __global__ void __launch_bounds__(512, 1) icp_batched_kernel(BatchArgs a) {
             for (int i = 0; i < 28; ++i) accr[i] = 0.0f;
             int inl = 0;
             const int stride = 32 * split;
-            int e = part * 32 + lane;
-            if (e < cnt) {
+            int e = lo + part * 32 + lane;
+            if (e < hi) {
                 float3 sc, nc;
-                BatchHit hc = batch_gather(a, ent, Tp, off + e, sc, nc);
-                for (; e < cnt; e += stride) {
+                BatchHit hc = batch_gather(a, E, capk, Tp, e, sc, nc);
+                for (; e < hi; e += stride) {
                     float3 sn = sc, nn = nc;
                     BatchHit hn = hc;
-                    if (e + stride < cnt) hn = batch_gather(a, ent, Tp, off + e + stride, sn, nn);
+                    if (e + stride < hi) hn = batch_gather(a, E, capk, Tp, e + stride, sn, nn);
                     batch_accumulate(a, Tp, gate2, sc, nc, hc, accr, inl);
                     sc = sn;
                     nc = nn;
@@ -296,7 +375,7 @@ __global__ void __launch_bounds__(512, 1) icp_batched_kernel(BatchArgs a) {
         if (threadIdx.x == 0) {
             __threadfence();
             atomicAdd(&a.ctrl->arrive, 1ull);
-            flag_s = grid_wait(a.ctrl, base + G * (2ull * it + 1ull)) ? 0 : 1;
+            flag_s = grid_wait(a.ctrl, base + G * (2ull * it + 3ull)) ? 0 : 1;
             __threadfence();
         }
         __syncthreads();
@@ -373,7 +452,7 @@ __global__ void __launch_bounds__(512, 1) icp_batched_kernel(BatchArgs a) {
         if (threadIdx.x == 0) {
             __threadfence();
             atomicAdd(&a.ctrl->arrive, 1ull);
-            flag_s = grid_wait(a.ctrl, base + G * (2ull * it + 2ull)) ? 0 : 1;
+            flag_s = grid_wait(a.ctrl, base + G * (2ull * it + 4ull)) ? 0 : 1;
             __threadfence();
             any_active = 0;
         }
@@ -402,32 +481,26 @@ __global__ void __launch_bounds__(512, 1) icp_batched_kernel(BatchArgs a) {
 
 using namespace upslam;
 
-static size_t batch_region_entries(const upslam_keyframe *kfs, int32_t n_kf, int grid, int chunk) {
-    // per CTA: ceil(chunks / grid) chunks of every keyframe, each up to `chunk` samples
-    size_t cap = 0;
-    for (int i = 0; i < n_kf; ++i) {
-        const int64_t npx = (int64_t)kfs[i].pano.rows * kfs[i].pano.cols;
-        const int64_t nch = (npx + chunk - 1) / chunk;
-        cap += (size_t)((nch + grid - 1) / grid) * chunk;
-    }
-    return cap;
-}
-
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-static size_t batch_ws_layout(const upslam_keyframe *kfs, int32_t n_kf, int32_t n_prob, int grid, int chunk,
-                              size_t *off_active, size_t *off_records, size_t *off_entries, size_t *cap,
-                              size_t *off_posef = nullptr) {
-    *cap = batch_region_entries(kfs, n_kf, grid, chunk);
+// Workspace: control block, active flags, FP32 poses, per-CTA records, the per-(keyframe, CTA) sample counts,
+// then every keyframe's sample arrays (6 floats per pixel: the worst case of a keyframe full of samples).
+static size_t batch_ws_layout(const upslam_keyframe *kfs, int32_t n_kf, int32_t n_prob, int grid,
+                              size_t *off_active, size_t *off_records, size_t *off_counts, size_t *off_entries,
+                              size_t *off_posef) {
     size_t o = 256;  // control block
     *off_active = o;
     o = align256(o + (size_t)n_prob * sizeof(int));
-    if (off_posef) *off_posef = o;
+    *off_posef = o;
     o = align256(o + (size_t)n_prob * 12 * sizeof(float));
     *off_records = o;
     o = align256(o + (size_t)n_prob * grid * kRecWords * sizeof(float));
+    *off_counts = o;
+    o = align256(o + (size_t)n_kf * grid * sizeof(int));
     *off_entries = o;
-    o = align256(o + (size_t)grid * 6 * (*cap) * sizeof(float));
+    size_t px = 0;
+    for (int i = 0; i < n_kf; ++i) px += (size_t)kfs[i].pano.rows * kfs[i].pano.cols;
+    o = align256(o + 6 * px * sizeof(float));
     return o;
 }
 
@@ -437,8 +510,9 @@ static int batch_threads(const upslam_batch_tiles *tiles) { return tiles ? tiles
 extern "C" size_t upslam_icp_batched_workspace_bytes(const upslam_keyframe *kfs, int32_t n_kf, int32_t n_hyp,
                                                      const upslam_batch_tiles *tiles) {
     if (!kfs || n_kf <= 0 || n_hyp <= 0) return 0;
-    size_t a, r, e, cap;
-    return batch_ws_layout(kfs, n_kf, n_kf * n_hyp, upslam_sm_count(), batch_chunk(tiles), &a, &r, &e, &cap);
+    (void)tiles;
+    size_t a, r, c, e, f;
+    return batch_ws_layout(kfs, n_kf, n_kf * n_hyp, upslam_sm_count(), &a, &r, &c, &e, &f);
 }
 
 extern "C" upslam_status upslam_icp_batched(const upslam_keyframe *d_kfs, const upslam_keyframe *kfs, int32_t n_kf,
@@ -468,9 +542,9 @@ extern "C" upslam_status upslam_icp_batched(const upslam_keyframe *d_kfs, const 
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (!coop) return UPSLAM_ERR_UNSUPPORTED;
     const int grid = upslam_sm_count();
-    size_t off_active, off_records, off_entries, cap, off_posef;
-    const size_t need =
-        batch_ws_layout(kfs, n_kf, n_prob, grid, chunk, &off_active, &off_records, &off_entries, &cap, &off_posef);
+    size_t off_active, off_records, off_counts, off_entries, off_posef;
+    const size_t need = batch_ws_layout(kfs, n_kf, n_prob, grid, &off_active, &off_records, &off_counts, &off_entries,
+                                        &off_posef);
     if (ws_bytes < need) return UPSLAM_ERR_INVALID_ARG;
     const size_t dyn = (size_t)n_prob * (kRecWords + 12) * sizeof(float) + (size_t)n_prob * sizeof(int);
     cudaFuncAttributes fa;
@@ -513,7 +587,7 @@ extern "C" upslam_status upslam_icp_batched(const upslam_keyframe *d_kfs, const 
     a.active = reinterpret_cast<int *>(ws + off_active);
     a.poses_f = reinterpret_cast<float *>(ws + off_posef);
     a.entries = reinterpret_cast<float *>(ws + off_entries);
-    a.cta_cap = (long long)cap;
+    a.counts = reinterpret_cast<int *>(ws + off_counts);
     a.records = reinterpret_cast<float *>(ws + off_records);
     a.ctrl = reinterpret_cast<BatchCtrl *>(ws);
     a.ip = *ip;
