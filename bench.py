@@ -615,17 +615,16 @@ def run_switch(trk, seq, device, up, hbm, hbm_src, reps=20):
     alg = seq.sweep.pixels * 32 + px * 20 + 2 * px * 6
     gbs = alg / (ms * 1e-3) / 1e9
     rem = removed[-1].cpu().tolist() if removed else None
-    return {"ms_avg": round(ms, 5), "launches": 3, "bytes": alg, "gbs": round(gbs, 1), "bound": "hbm", "peak": hbm,
+    return {"ms_avg": round(ms, 5), "launches": 4, "bytes": alg, "gbs": round(gbs, 1), "bound": "hbm", "peak": hbm,
             "frac": round(gbs / hbm, 4), "peak_source": hbm_src, "samples_removed": rem,
             "timing": DIFF_TIMING, "l2": "flushed before each call",
             "note": "one switch per 50 sweeps in the headline sequence"}
 
 
 def run_fuse(kf, seq, scan, T, device, up, hbm, hbm_src, reps=20):
-    """Keyframe update (Sec. III-C) timed alone through the C ABI (`upslam_fuse_persistent`: the averaging
-    and hole-fill atomics, a grid barrier and the hole-fill writes in one launch; the two-launch
-    `upslam_fuse` beside it): one sweep fused into a 512 x 2048 FP32 keyframe of the run at its registered
-    pose T.  Before every call the keyframe is put back to its saved state and
+    """Keyframe update (Sec. III-C) timed alone through the C ABI (`upslam_fuse`: the averaging + hole-fill
+    atomics launch, then the hole-fill write launch): one sweep fused into a 512 x 2048 FP32 keyframe of
+    the run at its registered pose T.  Before every call the keyframe is put back to its saved state and
     L2 is flushed, both outside the events, so each call does the same work from DRAM.
     Algorithmic bytes per call: every keyframe pixel read once (depth 4 B + normal and count 16 B), every
     pixel the call changes written once (20 B), each sweep pixel's point and normal read by both launches
@@ -646,7 +645,6 @@ def run_fuse(kf, seq, scan, T, device, up, hbm, hbm_src, reps=20):
         flush.zero_()
 
     ms = _time_graph_diff(lambda: up.fuse(kf, sw, T, p), reps, pre)
-    ms2 = _time_graph_diff(lambda: up.fuse(kf, sw, T, p, one_launch=False), reps, pre)
     kf.depth.copy_(d0)
     kf.nw.copy_(n0)
     kf_px, sw_px = kf.depth.numel(), seq.sweep.pixels
@@ -656,8 +654,7 @@ def run_fuse(kf, seq, scan, T, device, up, hbm, hbm_src, reps=20):
     touched = kf_px * 20 + changed * 20 + sw_px * 64
     gbs = nbytes / (ms * 1e-3) / 1e9
     return {"keyframe": f"{int(seq.kf.rows)}x{int(seq.kf.cols)} f32", "samples_before": samples,
-            "pixels_written": changed, "launches": 1, "ms_avg": round(ms, 5), "bytes": nbytes,
-            "two_launch_form": {"ms_avg": round(ms2, 5), "frac": round(nbytes / (ms2 * 1e-3) / 1e9 / hbm, 4)},
+            "pixels_written": changed, "launches": 2, "ms_avg": round(ms, 5), "bytes": nbytes,
             "gbs": round(gbs, 1), "bound": "hbm", "peak": hbm, "frac": round(gbs / hbm, 4),
             "peak_source": hbm_src, "bytes_touched": touched,
             "timing": DIFF_TIMING,

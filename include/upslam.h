@@ -318,22 +318,6 @@ upslam_status upslam_fuse(const upslam_keyframe *kf, const upslam_sweep *sw, con
                           void *stream);
 
 /*
- * The keyframe update of upslam_fuse (Sec. III-C) in ONE cooperative launch:
- * the averaging and the hole-fill atomics, a grid barrier, then the hole-fill
- * writes, with the same results as upslam_fuse.  The barrier's arrival counter
- * lives in d_ws: upslam_fuse_workspace_bytes() bytes (8-byte aligned) that must
- * be zeroed once before the first call and are kept between calls; calls that
- * share a workspace must not overlap.  A barrier wait that gives up (about 2 s)
- * sets stats.status = UPSLAM_ERR_TIMEOUT (when d_stats is given) and leaves the
- * hole fill unwritten; zero the workspace again after that.  Returns
- * UPSLAM_ERR_UNSUPPORTED on a device without cooperative launches.
- */
-size_t upslam_fuse_workspace_bytes(void);
-upslam_status upslam_fuse_persistent(const upslam_keyframe *kf, const upslam_sweep *sw, const double *d_pose12,
-                                     const upslam_fuse_params *fp, upslam_icp_stats *d_stats, uint64_t *d_zbuf_kf,
-                                     void *d_ws, size_t ws_bytes, void *stream);
-
-/*
  * Allocation-free ICP.  The paper has no counterpart: this exists for callers
  * that cannot allocate device memory once they are running, such as a robot's
  * real-time control loop (a cudaMalloc can block on a driver lock and miss the

@@ -86,9 +86,6 @@ SIGNATURES = {
     "upslam_icp_step": (ctypes.c_int, [_P(Keyframe), _P(Sweep), _vp, _P(IcpParams), _vp, _vp, ctypes.c_size_t, _vp]),
     "upslam_icp": (ctypes.c_int, [_P(Keyframe), _P(Sweep), _vp, _P(IcpParams), _vp, _vp, ctypes.c_size_t, _vp]),
     "upslam_fuse": (ctypes.c_int, [_P(Keyframe), _P(Sweep), _vp, _P(FuseParams), _vp, _vp, _vp]),
-    "upslam_fuse_workspace_bytes": (ctypes.c_size_t, []),
-    "upslam_fuse_persistent": (ctypes.c_int, [_P(Keyframe), _P(Sweep), _vp, _P(FuseParams), _vp, _vp, _vp,
-                                              ctypes.c_size_t, _vp]),
     "upslam_track": (ctypes.c_int, [_P(Keyframe), _P(Sweep), _vp, _vp, _vp, ctypes.c_int32, _P(IcpParams),
                                     _P(FuseParams), _vp, _vp, ctypes.c_size_t, _vp, _vp]),
     "upslam_track_scan": (ctypes.c_int, [_P(Keyframe), _vp, ctypes.c_int32, _P(SweepBuffers), _P(NormalParams), _vp,

@@ -217,8 +217,6 @@ class KeyframeBuffer:
         self.nw = torch.zeros((H, W, 4), dtype=torch.float32 if precision == F32 else torch.float16, device=device)
         self.dirs = pano_dirs(pp, device)
         self.zbuf = empty_zbuf(H * W, device)
-        # the one-launch keyframe update's grid-barrier counter (zeroed once, kept between calls)
-        self.fuse_ws = torch.zeros(int(_abi.lib().upslam_fuse_workspace_bytes()), dtype=torch.uint8, device=device)
         self._ps = pano_struct(pp)
 
     def struct(self) -> _abi.Keyframe:
@@ -268,18 +266,10 @@ def icp(kf: KeyframeBuffer, sw: SweepFrame, state: IcpState, params: Params = Pa
 
 
 def fuse(kf: KeyframeBuffer, sw: SweepFrame, pose: torch.Tensor, params: Params = Params(),
-         stats: torch.Tensor | None = None, one_launch: bool = True) -> None:
-    """Sec. III-C keyframe update with the sweep at ``pose``: one cooperative launch
-    (``upslam_fuse_persistent``), or the two-launch ``upslam_fuse``; the results are the same."""
+         stats: torch.Tensor | None = None) -> None:
     ks, ss, fp = kf.struct(), sw.struct(), params.fuse()
-    L = _abi.lib()
-    if one_launch:
-        _abi.check("upslam_fuse_persistent",
-                   L.upslam_fuse_persistent(ctypes.byref(ks), ctypes.byref(ss), _p(pose), ctypes.byref(fp), _p(stats),
-                                            _p(kf.zbuf), _p(kf.fuse_ws), kf.fuse_ws.numel(), _stream()))
-        return
-    _abi.check("upslam_fuse", L.upslam_fuse(ctypes.byref(ks), ctypes.byref(ss), _p(pose), ctypes.byref(fp),
-                                            _p(stats), _p(kf.zbuf), _stream()))
+    _abi.check("upslam_fuse", _abi.lib().upslam_fuse(ctypes.byref(ks), ctypes.byref(ss), _p(pose), ctypes.byref(fp),
+                                                     _p(stats), _p(kf.zbuf), _stream()))
 
 
 # ----------------------------------------------------------------------------- the per-sweep path
@@ -401,8 +391,8 @@ class Tracker:
         if self.front_fused:
             return 1
         return (4 if self.fused else 6) + int(self.params.atrous_levels)
-    # kernels launched by new_keyframe() (after loading): the one-launch keyframe update
-    LAUNCHES_PER_NEW_KEYFRAME = 1
+    # kernels launched by new_keyframe() (after loading): fuse (2)
+    LAUNCHES_PER_NEW_KEYFRAME = 2
 
 
 # ----------------------------------------------------------------------------- loop-closure grid search

@@ -196,20 +196,29 @@ __global__ void __launch_bounds__(512, 1) icp_batched_kernel(BatchArgs a) {
             const int rot = (int)(((long long)kf * 61) % gridDim.x);
             const int c0 = ((int)blockIdx.x - rot + (int)gridDim.x) % (int)gridDim.x;
             float *E = a.entries + kf_base[kf];
+            // this CTA's pixels as blocks of T: chunk c0 + m * grid holds blocks m * bpc .. m * bpc + bpc - 1,
+            // taken kPx blocks at a time in that order
+            const int bpc = a.chunk / T;
+            const int nmine = c0 < nch ? ((nch - 1 - c0) / (int)gridDim.x + 1) * bpc : 0;
             int mine = 0, run = pass == 1 ? kf_wb[kf] : 0, par = 0;
-            for (int c = c0; c < nch; c += gridDim.x) {
-                const int cend = min(npx, (c + 1) * a.chunk);
-                for (int b0 = c * a.chunk; b0 < cend; b0 += T * kPx, par ^= 1) {
+            for (int b0 = 0; b0 < nmine; b0 += kPx, par ^= 1) {
+                {
                     float d[kPx];
                     float4 n4[kPx];
                     bool ok[kPx];
+                    int kk[kPx];
 #pragma unroll
                     for (int i = 0; i < kPx; ++i) {
-                        const int k = b0 + i * T + threadIdx.x;
-                        d[i] = k < cend ? __ldg(K.d_depth + k) : 0.0f;
+                        const int b = b0 + i;
+                        kk[i] = -1;
+                        if (b < nmine) {
+                            const int k = (c0 + (b / bpc) * (int)gridDim.x) * a.chunk + (b % bpc) * T + threadIdx.x;
+                            kk[i] = k < npx ? k : -1;
+                        }
+                        d[i] = kk[i] >= 0 ? __ldg(K.d_depth + kk[i]) : 0.0f;
                     }
 #pragma unroll
-                    for (int i = 0; i < kPx; ++i) ok[i] = kf_sample(K, b0 + i * T + threadIdx.x, d[i], n4[i]);
+                    for (int i = 0; i < kPx; ++i) ok[i] = kf_sample(K, kk[i], d[i], n4[i]);
                     if (pass == 0) {
 #pragma unroll
                         for (int i = 0; i < kPx; ++i) mine += ok[i] ? 1 : 0;
@@ -234,7 +243,7 @@ __global__ void __launch_bounds__(512, 1) icp_batched_kernel(BatchArgs a) {
                         }
                         if (ok[i]) {
                             const int slot = o + before + __popc(bal[i] & ((1u << lane) - 1u));
-                            const int k = b0 + i * T + threadIdx.x;
+                            const int k = kk[i];
                             const int v = k / W;
                             const float3 sp = pixel_point(K.d_dirs, K.pano.rows, v, k - v * W, d[i]);
                             E[slot] = sp.x;

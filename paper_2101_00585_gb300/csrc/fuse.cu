@@ -109,93 +109,6 @@ __global__ void __launch_bounds__(256) fuse_fill_kernel(FuseView f, const double
     if (st && blockIdx.x == 0 && threadIdx.x == 0) st->accepted = 1;
 }
 
-// Bounded grid-barrier wait of the one-launch form (clock64 cycles, about 2 s at 2 GHz).
-constexpr long long kFuseWaitCycles = 4000000000ll;
-
-// The whole keyframe update in one cooperative launch: the averaging and the hole-fill atomics (every CTA
-// takes its share of both), a grid barrier on a monotonic arrival counter in the caller's workspace, then
-// the hole-fill writes.  Every CTA reads the same record, so all return together when the sweep was not
-// accepted, and none arrives.
-__global__ void __launch_bounds__(256) fuse_persistent_kernel(FuseView f, const double *pose, upslam_icp_stats *st,
-                                                              unsigned long long *ctr) {
-    if (!accepted(st, f.accept)) return;
-    const PoseF T = cta_pose_f32(pose);
-    __shared__ unsigned long long target_s;
-    __shared__ int timed_out;
-    const unsigned long long G = gridDim.x;
-    if (threadIdx.x == 0) {
-        unsigned long long v;
-        asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(ctr) : "memory");
-        target_s = (v / G) * G + G;  // fewer than G arrivals can precede this read
-        timed_out = 0;
-    }
-    const int npx = f.kp.rows * f.kp.cols, W = f.kp.cols, ns = f.sp.rows * f.sp.cols;
-    const int nthreads = gridDim.x * blockDim.x;
-    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-    // hole-fill atomics first: they are few, and the fill after the barrier waits on the last of them
-    for (int j = tid; j < ns; j += nthreads) {
-        int k;
-        unsigned long long key;
-        float r;
-        float4 m;
-        if (!holefill_key(f, T, j, k, key, r, m)) continue;
-        if (__ldg(f.kdepth + k) > 0.0f) continue;
-        atomicMin(f.zbuf + k, key);
-    }
-    for (int base = blockIdx.x * blockDim.x * kFuseB + threadIdx.x; base < npx; base += nthreads * kFuseB) {
-        constexpr int kB = kFuseB;
-        float4 n[kB];
-        float d[kB];
-#pragma unroll
-        for (int b = 0; b < kB; ++b) {
-            const int k = base + b * blockDim.x;
-            d[b] = k < npx ? __ldg(f.kdepth + k) : 0.0f;
-        }
-#pragma unroll
-        for (int b = 0; b < kB; ++b) {
-            const int k = base + b * blockDim.x;
-            n[b] = d[b] > 0.0f ? load_nw(f.knw, k, f.kprec) : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-#pragma unroll
-        for (int b = 0; b < kB; ++b) {
-            const int k = base + b * blockDim.x;
-            if (!(n[b].w > 0.0f)) continue;
-            const int v = k / W;
-            fuse_average(f, T, k, pixel_point(f.kdirs, f.kp.rows, v, k - v * W, d[b]), n[b], d[b]);
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        asm volatile("red.release.gpu.global.add.u64 [%0], 1;" ::"l"(ctr) : "memory");
-        const long long t0 = clock64();
-        unsigned long long v;
-        for (;;) {
-            asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(ctr) : "memory");
-            if (v >= target_s) break;
-            if (clock64() - t0 > kFuseWaitCycles) {
-                timed_out = 1;
-                break;
-            }
-        }
-        asm volatile("fence.acq_rel.gpu;" ::: "memory");
-    }
-    __syncthreads();
-    if (timed_out) {
-        if (st && threadIdx.x == 0) st->status = UPSLAM_ERR_TIMEOUT;
-        return;
-    }
-    for (int j = tid; j < ns; j += nthreads) {
-        int k;
-        unsigned long long key;
-        float r;
-        float4 m;
-        if (!holefill_key(f, T, j, k, key, r, m)) continue;
-        if (__ldcg(f.zbuf + k) != key) continue;
-        holefill_write(f, T, k, r, m);
-    }
-    if (st && blockIdx.x == 0 && threadIdx.x == 0) st->accepted = 1;
-}
-
 }  // namespace upslam
 
 using namespace upslam;
@@ -244,33 +157,5 @@ extern "C" upslam_status upslam_fuse(const upslam_keyframe *kf, const upslam_swe
     UPSLAM_CHECK_LAUNCH();
     fuse_fill_kernel<<<gs, 256, 0, s>>>(f, d_pose12, d_stats);
     UPSLAM_CHECK_LAUNCH();
-    return UPSLAM_OK;
-}
-
-extern "C" size_t upslam_fuse_workspace_bytes(void) { return 256; }
-
-extern "C" upslam_status upslam_fuse_persistent(const upslam_keyframe *kf, const upslam_sweep *sw,
-                                                const double *d_pose12, const upslam_fuse_params *fp,
-                                                upslam_icp_stats *d_stats, uint64_t *d_zbuf_kf, void *d_ws,
-                                                size_t ws_bytes, void *stream) {
-    FuseView f;
-    if (!d_pose12 || !upslam_fuse_view(kf, sw, fp, d_zbuf_kf, f)) return UPSLAM_ERR_INVALID_ARG;
-    if (!d_ws || ws_bytes < upslam_fuse_workspace_bytes() || !upslam_aligned(d_ws, 8)) return UPSLAM_ERR_INVALID_ARG;
-    int dev = 0, coop = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return UPSLAM_ERR_CUDA;
-    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
-    if (!coop) return UPSLAM_ERR_UNSUPPORTED;
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fuse_persistent_kernel, 256, 0) != cudaSuccess ||
-        per_sm < 1)
-        return UPSLAM_ERR_UNSUPPORTED;
-    const int grid = per_sm * upslam_sm_count();  // one wave: every CTA resident, as the grid barrier needs
-    unsigned long long *ctr = reinterpret_cast<unsigned long long *>(d_ws);
-    void *args[] = {&f, (void *)&d_pose12, &d_stats, &ctr};
-    if (cudaLaunchCooperativeKernel((const void *)fuse_persistent_kernel, dim3(grid), dim3(256), args, 0,
-                                    (cudaStream_t)stream) != cudaSuccess) {
-        (void)cudaGetLastError();
-        return UPSLAM_ERR_CUDA;
-    }
     return UPSLAM_OK;
 }

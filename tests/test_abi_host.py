@@ -70,11 +70,6 @@ def test_invalid_arguments_are_rejected_on_the_host():
     ks_bad = _abi.Keyframe(pp, 256, 256, 5, 256)
     assert L.upslam_icp_step(ctypes.byref(ks_bad), ctypes.byref(ss), fake, ctypes.byref(ip), fake, fake, ws,
                              None) == _abi.ERR_INVALID_ARG
-    fp_ok = _abi.FuseParams(0.2, 0.86, 10.0, 0.1)
-    assert L.upslam_fuse_workspace_bytes() >= 8
-    for ws_ptr, ws_n in ((None, 256), (fake, 4)):  # no workspace / too small
-        assert L.upslam_fuse_persistent(ctypes.byref(ks), ctypes.byref(ss), fake, ctypes.byref(fp_ok), None, fake,
-                                        ws_ptr, ws_n, None) == _abi.ERR_INVALID_ARG
     fp = _abi.FuseParams(0.2, 0.86, 0.5, 0.1)  # w_max < 1
     assert L.upslam_fuse(ctypes.byref(ks), ctypes.byref(ss), fake, ctypes.byref(fp), None, fake,
                          None) == _abi.ERR_INVALID_ARG

@@ -367,33 +367,6 @@ def test_fuse_hole_fill_and_saturation_workload2():
     _fuse_compare(kf_ref, sp2, sn2, seq.sweep, synth.relative(seq.poses[0], seq.poses[2]), prm)
 
 
-def test_fuse_one_launch_equals_two_launches():
-    """upslam_fuse_persistent (one cooperative launch with a grid barrier) and upslam_fuse (two launches) leave
-    the same keyframe, bit for bit, at full tunnel size: a keyframe that has averaged a few sweeps, fused with
-    the next one (averaging and hole fill); the z-buffer scratch is left empty, and repeated calls on one
-    workspace keep working."""
-    seq = configs.tunnel_sequence(n_scans=4)
-    p = up.Params(accept_quality=0.1)
-    trk = up.Tracker(seq.sweep, seq.kf, p)
-    trk.new_keyframe(dev(seq.scan(0)))
-    for k in (1, 2):
-        trk.track(dev(seq.scan(k)))
-    sw = up.SweepFrame(seq.sweep)
-    sw.load(dev(seq.scan(3)), p)
-    T = pose_dev(synth.relative(seq.poses[0], seq.poses[3]))
-    d0, n0 = trk.kf.depth.clone(), trk.kf.nw.clone()
-    outs = []
-    for one in (False, True, True):
-        trk.kf.set(d0, n0)
-        up.fuse(trk.kf, sw, T, p, None, one_launch=one)
-        torch.cuda.synchronize()
-        outs.append((trk.kf.depth.clone(), trk.kf.nw.clone()))
-        assert bool((trk.kf.zbuf == -1).all())
-    for d, n in outs[1:]:
-        assert torch.equal(d, outs[0][0]) and torch.equal(n, outs[0][1])
-    assert not torch.equal(outs[0][0], d0)
-
-
 def test_fuse_gated_by_registration_quality():
     c, prm, sp4, sn4, kd, kn = room_sweep_and_keyframe(noise=True)
     kf = _kf_buffers(kd, kn, c.kf)
