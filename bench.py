@@ -408,14 +408,19 @@ def run_ours(args, ws, rank, local):
     kf_px, sw_px = KF_ROWS * KF_COLS, seq.sweep.pixels
     icp_avg, fuse_avg, proj_avg = (statistics.mean(icp_ms), statistics.mean(fuse_ms), statistics.mean(proj_ms))
     if trk.front_fused:
-        # one persistent launch per sweep: projection, resolve and normals (points 16 B, z-buffer
-        # touched, read and reset 24 B, depth + index + point + normal written 40 B, normals reading
-        # point + depth 20 B per sweep pixel), then ICP + keyframe update (keyframe read once and written
-        # once, 20 B/px each way; sweep read once, 32 B/px)
-        track_bytes = kf_px * 40 + sw_px * 32 + sw_px * (16 + 24 + 40 + 20)
+        # one persistent launch per sweep.  Algorithmic bytes, the survey's per-unit figures for this
+        # workload: projection (the points, 16 B; the z-buffer touched twice and the outputs, 24 B per sweep
+        # pixel: 2.6 MB), normals (32 B per sweep pixel: 2.1 MB), each Gauss-Newton step's correspondences
+        # (48 B per sweep pixel: 3.1 MB per step, times the steps run), the keyframe read and written once
+        # (40 B per keyframe pixel: 42 MB) and the hole fill's read of the sweep (24 B per sweep pixel)
+        iters_mean = statistics.mean(iters)
+        track_bytes = sw_px * (16 + 24) + sw_px * 32 + sw_px * 48 * iters_mean + kf_px * 40 + sw_px * 24
+        # the same launch counted by what it touches once (the sweep read once by all steps)
+        touched = kf_px * 40 + sw_px * 32 + sw_px * (16 + 24 + 40 + 20)
         name = "icp_tile_kernel (project + normals + register + keyframe update)"
-        kernels = {name: {"ms_avg": icp_avg, "share": sum(icp_ms) / total_ms, "bytes": track_bytes,
-                          "gbs": track_bytes / (icp_avg * 1e-3) / 1e9, "iters_avg": statistics.mean(iters)}}
+        kernels = {name: {"ms_avg": icp_avg, "share": sum(icp_ms) / total_ms, "bytes": round(track_bytes),
+                          "bytes_touched_once": touched, "gbs": track_bytes / (icp_avg * 1e-3) / 1e9,
+                          "iters_avg": iters_mean}}
         dom = name
     elif trk.fused:
         # one persistent launch: ICP + keyframe update; the keyframe must be read once and written
@@ -855,29 +860,47 @@ def run_campus(args, local):
     for k in range(1, 1 + W):
         step(k)
     torch.cuda.synchronize()
-    total = 0.0
-    iters = []
-    for i in range(K):
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        step(1 + W + i)
-        b.record()
-        b.synchronize()
-        total += a.elapsed_time(b)
-        iters.append(trk.state.read_stats()["iters"])
-        flush.zero_()
+    # the timed sweeps as one captured graph, as the headline: an event node pair around each sweep's
+    # launches, the L2 flush between sweeps outside them; the records are copied out per sweep
+    cr = Cudart()
+    cr.external = True
+    evs = [(cr.event(), cr.event()) for _ in range(K)]
+    hist = torch.zeros((K, up._abi.STATS_BYTES), dtype=torch.uint8, device=device)
+    s = torch.cuda.Stream(device)
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    saved = pos[0]
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            st = torch.cuda.current_stream().cuda_stream
+            for i in range(K):
+                flush.zero_()
+                cr.record(evs[i][0], st)
+                step(1 + W + i)
+                cr.record(evs[i][1], st)
+                hist[i].copy_(trk.state.stats)
+        pos[0] = saved
+        g.replay()
+    torch.cuda.synchronize()
+    ms = [cr.elapsed(a, b) for a, b in evs]
+    total = float(sum(ms))
+    from paper_2101_00585_gb300._abi import IcpStats
+    raw = hist.cpu().numpy()
+    iters = [IcpStats.from_buffer_copy(bytes(raw[i])).iters for i in range(K)]
     kf_px, sw_px = seq.kf.pixels, seq.sweep.pixels
-    bytes_track = kf_px * 12 * 2 + sw_px * 24
+    # the survey's bytes: the FP16 keyframe read and written once (12 B each way per pixel) and, per
+    # Gauss-Newton step, the sweep pixel's point, normal and the keyframe sample (16 + 8 + 12 B per sweep pixel)
+    bytes_track = kf_px * 24 + sw_px * 36 * float(np.mean(iters))
     hbm, src = peaks()
     gbs = bytes_track * K / (total * 1e-3) / 1e9
     return {"metric": "ICP+fusion scans/s at 128x2048 vs 1024x4096 FP16 keyframes (precision form)",
             "value": round(K / (total * 1e-3), 2), "unit": UNIT, "n_gpus": 1, "steps": K, "warmup": W,
             "ms_per_step": round(total / K, 4), "higher_is_better": True, "dtype": "f32 arithmetic, f16 normals/counts",
             "data": "synthetic", "config": {"workload": "campus 128x2048 sweeps vs 1024x4096 keyframes, FP16 storage",
-                                            "l2": "flushed between steps", "launch": "eager, one sync per step"},
+                                            "l2": "flushed between steps", "graph": True},
             "roofline_step": {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
                               "frac": round(gbs / hbm, 4), "peak_source": src,
-                              "bytes_per_step": bytes_track},
+                              "bytes_per_step": round(bytes_track)},
             "icp_iters_avg": float(np.mean(iters))}
 
 
@@ -997,12 +1020,17 @@ def run_room(args, local):
     cr = Cudart()
     cr.external = False
     st = torch.cuda.current_stream().cuda_stream
-    evs = [(cr.event(), cr.event()) for _ in range(K)]
-    iters = []
-    for i in range(K + 3):
+
+    def pre():
         trk.kf.set(d0, n0)
         trk.prev.copy_(trk.identity)
         flush.zero_()
+
+    scan_us = 1e3 * _time_graph_diff(lambda: trk.track(scan), 20, pre)
+    evs = [(cr.event(), cr.event()) for _ in range(K)]
+    iters = []
+    for i in range(K + 3):
+        pre()
         if i >= 3:
             cr.record(evs[i - 3][0], st)
         trk.track(scan)
@@ -1010,24 +1038,18 @@ def run_room(args, local):
             cr.record(evs[i - 3][1], st)
             iters.append(trk.state.read_stats()["iters"])
     torch.cuda.synchronize()
-    scan_us = 1e3 * statistics.median(cr.elapsed(a, b) for a, b in evs)
+    eager_us = 1e3 * statistics.median(cr.elapsed(a, b) for a, b in evs)
     err = synth.pose_error(trk.state.pose.cpu().numpy().reshape(3, 4), c.T_true)
     # ICP steps alone: the same sweep, ten forced steps per launch
     trk.kf.set(d0, n0)
     trk.sw.load(scan, p)
     state = up.IcpState(trk.kf, device)
     p10 = up.Params(max_iters=10, eps_rot=0.0, eps_trans=0.0)
-    evs2 = [(cr.event(), cr.event()) for _ in range(K)]
-    for i in range(K + 3):
+    def pre_icp():
         state.pose.copy_(trk.identity)
         flush.zero_()
-        if i >= 3:
-            cr.record(evs2[i - 3][0], st)
-        up.icp(trk.kf, trk.sw, state, p10)
-        if i >= 3:
-            cr.record(evs2[i - 3][1], st)
-    torch.cuda.synchronize()
-    icp_us = 1e3 * statistics.median(cr.elapsed(a, b) for a, b in evs2)
+
+    icp_us = 1e3 * _time_graph_diff(lambda: up.icp(trk.kf, trk.sw, state, p10), 20, pre_icp)
     cpu = None
     if not args.no_cpu_baseline:
         # the FP64 oracle on the same registration: sweep frame, 10 Gauss-Newton steps, keyframe update
@@ -1046,11 +1068,14 @@ def run_room(args, local):
                "sample": f"the same room registration, {reps} repetitions on one host thread"}
     return {"metric": "latency of one 16x512 room sweep vs a 256x512 keyframe", "unit": "us",
             "higher_is_better": False, "us_per_scan": round(scan_us, 2), "us_per_icp_step": round(icp_us / 10, 3),
+            "us_per_scan_eager": round(eager_us, 2),
             "icp_launch_us_10_steps": round(icp_us, 2), "icp_iters_avg": float(np.mean(iters)), "reps": K,
             "pose_error_m": float(err[0]), "pose_error_deg": float(math.degrees(err[1])), "cpu_baseline": cpu,
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": "room 16x512 sweep (8192 points) vs 256x512 keyframe, 5 cm / 2 deg, <=10 steps",
-                       "l2": "flushed before each call", "stat": "median of reps"}}
+                       "l2": "flushed before each call",
+                       "timing": "device time by difference of graph replays (" + DIFF_TIMING + "); us_per_scan_eager: "
+                                 "one eager call between two events on an idle stream, median of reps"}}
 
 
 def run_learned(args, local):
