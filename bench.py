@@ -61,7 +61,7 @@ def parse():
                          "form; learned: train the pose proposal and evaluate learned vs plain initialisation")
     ap.add_argument("--train-pairs", type=int, default=200000)
     ap.add_argument("--eval-pairs", type=int, default=5000)
-    ap.add_argument("--epochs", type=int, default=8)
+    ap.add_argument("--epochs", type=int, default=24)
     ap.add_argument("--e2e-steps", type=int, default=300)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-graph", action="store_true", help="launch eagerly instead of replaying a CUDA graph")

@@ -231,6 +231,25 @@ class KeyframeBuffer:
         self.depth.copy_(depth)
         self.nw.copy_(nw)
 
+    def save(self, path: str) -> None:
+        """Write the keyframe (geometry, depth, normals and counts) to a ``.npz`` file."""
+        import numpy as np
+        pp = self.pp
+        np.savez(path, rows=int(pp.rows), cols=int(pp.cols), el_top=float(pp.el_top), s_az=float(pp.s_az),
+                 s_el=float(pp.s_el), r_min=float(pp.r_min), r_max=float(pp.r_max), precision=int(self.precision),
+                 depth=self.depth.cpu().numpy(), nw=self.nw.cpu().numpy())
+
+    @classmethod
+    def load(cls, path: str, device="cuda") -> "KeyframeBuffer":
+        """A keyframe written by ``save``, on ``device``."""
+        import numpy as np
+        from types import SimpleNamespace
+        z = np.load(path)
+        pp = SimpleNamespace(**{k: z[k].item() for k in ("rows", "cols", "el_top", "s_az", "s_el", "r_min", "r_max")})
+        kf = cls(pp, device, int(z["precision"]))
+        kf.set(torch.from_numpy(z["depth"]).to(device), torch.from_numpy(z["nw"]).to(device))
+        return kf
+
 
 class IcpState:
     """Device-resident pose, stats and workspace for one registration problem."""

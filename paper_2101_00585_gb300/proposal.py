@@ -176,6 +176,13 @@ class PoseNet:
         self.v.copy_(sd["v"])
         self.step = int(sd["step"])
 
+    def save(self, path: str) -> None:
+        """Checkpoint: parameters and Adam state (``torch.save``), so training can resume."""
+        torch.save(self.state_dict(), path)
+
+    def load(self, path: str) -> None:
+        self.load_state_dict(torch.load(path, map_location="cpu"))
+
 
 def poses_from_twists(xi: torch.Tensor) -> torch.Tensor:
     """FP64 [B, 12] poses exp(xi^) of FP32 twists [B, 6] (device kernel)."""
