@@ -478,7 +478,9 @@ def run_ours(args, ws, rank, local):
                                 "grid_score_kernel": run_grid(trk, device, up, hbm, hbm_src),
                                 "consistency_kernels": (run_consistency(pool, hist_pose[kf_every].clone(), device, up,
                                                                         hbm, hbm_src) if n_scans > kf_every else
-                                                        {"skipped": "the run opened no second keyframe"}),
+                                                        run_consistency(switch_pair(trk, seq, device, up),
+                                                                        trk.state.pose.clone(), device, up, hbm,
+                                                                        hbm_src)),
                                 "fuse_kernels": run_fuse(pool[0], seq, d_scans[k_fuse], hist_pose[k_fuse].clone(),
                                                          device, up, hbm, hbm_src),
                                 "keyframe_switch": run_switch(trk, seq, device, up, hbm, hbm_src)}
@@ -551,9 +553,20 @@ def run_grid(trk, device, up, hbm, hbm_src):
             "timing": DIFF_TIMING}
 
 
+def switch_pair(trk, seq, device, up):
+    """The two keyframes of a switch at the tracker's last sweep, as copies (the check removes samples): a copy
+    of the current keyframe, and a new one hole-filled from the last sweep in that sweep's frame."""
+    a = up.KeyframeBuffer(seq.kf, device)
+    a.set(trk.kf.depth, trk.kf.nw)
+    b = up.KeyframeBuffer(seq.kf, device)
+    up.fuse(b, trk.sw, trk.identity, up.Params(accept_quality=0.1))
+    return [a, b]
+
+
 def run_consistency(pool, T_ab, device, up, hbm, hbm_src):
     """Keyframe mutual consistency check (Sec. III-C) between the first two 512 x 2048 keyframes of the run
-    (T_ab: the registered pose of the sweep that started the second one, in the first).
+    (T_ab: the registered pose of the sweep that started the second one, in the first), or, when the run
+    opened no second keyframe, between the current one and one started from its last sweep.
     Algorithmic bytes per keyframe pixel and side: depth read (4 B), flag written (1 B) and read back (1 B);
     the neighbourhood gathers of the other keyframe hit L1/L2."""
     import ctypes
