@@ -111,6 +111,42 @@ def test_project_workload2_full_size_bit_exact():
     _assert_project_equal(sc, seq.kf, T)
 
 
+def _workload_projection_cases():
+    """(name, scan, panorama, pose or None) for the other workloads' sweeps and keyframe scatters: the campus
+    128 x 2048 sweep and its 1024 x 4096 keyframe a few sweeps on; the forest sweep binned into each keyframe
+    size of the batch at a 2 m / 20 deg hypothesis; a road pair of the learned form."""
+    out = []
+    camp = configs.campus_sequence(n_scans=4)
+    sc = camp.scan(3)
+    out.append(("campus sweep", sc, camp.sweep, None))
+    out.append(("campus keyframe", sc, camp.kf, synth.relative(camp.poses[0], camp.poses[3])))
+    case = configs.forest_batch(n_kf=3, n_hyp=1, kf_sizes=((256, 1024), (512, 2048), (1024, 4096)))
+    out.append(("forest sweep", case.scan, case.sweep, None))
+    for k in range(3):
+        out.append((f"forest keyframe {k}", case.scan, case.kf_panos[k], case.T_init[k][0]))
+    road = synth.road(20210105)
+    lid = configs.LIDAR_64
+    P = synth.pose(synth.rot_zyx(0.3, 0.0, 0.0), [2.0, 0.5, 1.8])
+    rs = synth.scan(road, lid, P, np.random.default_rng(5))
+    out.append(("road sweep", rs, lid.pano(), None))
+    out.append(("road keyframe", rs, synth.keyframe_pano(512, 2048, 0.3, 150.0),
+                synth.perturb(IDENTITY, np.random.default_rng(6), 1.0, math.radians(30.0))))
+    return out
+
+
+def test_project_bit_exact_on_every_workload():
+    """Pixel winners and depths bit for bit against the oracle for the sweeps and keyframe scatters of
+    workloads 3 to 5 (workloads 1 and 2 above), and the sweep normals of the campus form within the
+    conditioning bound, in FP32 and FP16 storage."""
+    for name, sc, pp, T in _workload_projection_cases():
+        _assert_project_equal(sc, pp, T)
+    camp = configs.campus_sequence(n_scans=2)
+    depth, idx = oracle.project(camp.scan(1), camp.sweep)
+    pix = oracle.pixel_points(camp.scan(1), idx)
+    assert _normals_compare(pix, depth, camp.sweep) > 0.8 * (idx >= 0).sum()
+    _normals_compare(pix, depth, camp.sweep, up.F16)
+
+
 def test_project_collisions_ragged_and_empty():
     """Many points per pixel (z-buffer ties), odd sizes, no points, all invalid."""
     pp = tiny_pano(8, 16)
