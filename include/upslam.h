@@ -324,7 +324,7 @@ upslam_status upslam_fuse(const upslam_keyframe *kf, const upslam_sweep *sw, con
  * sweep deadline), a plugin whose host runtime owns the device allocator, or
  * code that may only use memory fixed at load time.  It runs exactly what
  * upslam_icp runs, but its workspace is a static device array inside the
- * library (upslam_icp_noalloc_capacity_bytes() = 528384 bytes, 516 KiB: the
+ * library (upslam_icp_noalloc_capacity_bytes() = 561152 bytes, 548 KiB: the
  * control block plus 2048 per-CTA records, enough for devices of up to 1024
  * SMs) instead of d_ws.  The caller still provides the keyframe, sweep, pose
  * and stats buffers.

@@ -15,10 +15,13 @@
 //
 // Two launch forms:
 //  * icp_step_kernel: one Gauss-Newton step, "last CTA done" ticket.
-//  * icp_persistent_kernel: all iterations in one cooperative launch; each
-//    step ends at a grid barrier whose last arriver solves and then releases
-//    the others through a generation counter.  Every wait is bounded by a
-//    clock64 budget and reports UPSLAM_ERR_TIMEOUT instead of hanging.
+//  * icp_tile_kernel: all iterations in one cooperative launch, one CTA per SM,
+//    the CTA's keyframe samples staged in shared memory once.  Each step's sums
+//    are exact fixed-point integers that every CTA adds into global words; the
+//    same words carry an arrival count, so one poll of them is both the grid
+//    barrier and the read of the totals.  Every CTA then solves the identical
+//    system itself.  Every wait is bounded by a clock64 budget and reports
+//    UPSLAM_ERR_TIMEOUT instead of hanging.
 //
 // Roofline: per step the keyframe is streamed once (4 B depth + 16 B or 8 B
 // normal/weight per pixel) and each correspondence gathers 32 B (16 B in FP16)
@@ -35,13 +38,25 @@ constexpr int kIcpWarps = kIcpThreads / 32;
 // Per-CTA partial: 28 FP32 sums and their Neumaier compensations, then the
 // inlier and valid counts as integers (64 words = 256 bytes per CTA).
 constexpr int kSlots = 64;
-constexpr size_t kCtrlBytes = 4096;  // IcpCtrl, then the persistent form's exact accumulators
-constexpr size_t kAccOffset = 256;   // three buffers of kAccWords 64-bit integers
-constexpr int kAccWords = 96;        // 28 sums x 3 chunks, inliers, valid (86 used)
+constexpr size_t kCtrlBytes = 36864;  // IcpCtrl, then the tiled form's exact accumulators
+constexpr size_t kAccOffset = 256;    // three buffers of kFxWords accumulators
+constexpr int kFxWords = 86;          // 28 sums x 3 chunks, inliers, valid
+// 64-bit words from one accumulator to the next: each sits on its own 128-byte L2 line, so the
+// adds and polls of 152 CTAs spread over many L2 slices instead of queueing on six lines
+constexpr int kAccStride = 16;
+// Each CTA adds into every accumulator of a step exactly once: its partial (a CTA's partial lies
+// in (-2^36, 2^36): 16 warps of chunks below 2^32) plus kFxBias, which makes the addend positive,
+// plus one arrival unit in bits 48-63.  With at most kFxMaxCtas CTAs the low 48 bits never carry
+// into the count, so a word holds its whole total exactly when its count equals the grid size.
+constexpr unsigned long long kFxBias = 1ull << 36;
+constexpr unsigned long long kFxCount = 1ull << 48;
+constexpr int kFxMaxCtas = 2048;
 constexpr long long kWaitCycles = 4000000000ll;  // about 2 s at 2 GHz
 // the exact accumulators sit after IcpCtrl inside the control block that every call clears
-static_assert(kAccOffset + 3 * kAccWords * sizeof(unsigned long long) <= kCtrlBytes,
+static_assert(kAccOffset + 3 * (size_t)kFxWords * kAccStride * sizeof(unsigned long long) <= kCtrlBytes,
               "three accumulator buffers fit the control block");
+static_assert((long long)kFxMaxCtas * 2 * (long long)kFxBias <= (long long)kFxCount,
+              "the biased partials of the largest grid stay below the count field");
 
 struct IcpArgs {
     upslam_pano kp;
@@ -466,7 +481,7 @@ __global__ void __launch_bounds__(kTileThreads, 1)
     int *sk = reinterpret_cast<int *>(stage + 8 * cap);
     __shared__ double tot[32];
     __shared__ long long totn[2];
-    __shared__ unsigned long long fxs[kAccWords];
+    __shared__ unsigned long long fxs[kFxWords];
     __shared__ int gbm_s;
     __shared__ double Tsh[12];
     __shared__ double Tprev[12], Tmot[12];
@@ -485,17 +500,21 @@ __global__ void __launch_bounds__(kTileThreads, 1)
         base = (*((volatile unsigned long long *)&ctrl->arrive64) / G) * G;
         gbm_s = (int)((base / G) % 3ull);
     }
-    // exact step sums: barrier number j (counted over the whole workspace's life) adds into
-    // buffer j mod 3; CTA 0 clears buffer j - 1 once it has passed barrier j (all of its readers
-    // have then arrived at barrier j, and nobody adds into it before barrier j + 1 has passed)
+    // exact step sums: barrier number j (counted over the whole workspace's life) owns buffer
+    // j mod 3, and only the Gauss-Newton steps' barriers add into theirs.  CTA 0 clears buffer
+    // j - 1 once it has passed barrier j (every CTA has then finished reading it, and nobody adds
+    // into it before barrier j + 1 has passed).  So at a launch's start only the buffer of the
+    // last barrier before it can hold sums, and the launch's first barrier clears it.
     unsigned long long *const acc_base =
         reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(ctrl) + kAccOffset);
-    auto acc_buf = [&](unsigned long long j) { return acc_base + (size_t)((gbm_s + j) % 3ull) * kAccWords; };
+    auto acc_buf = [&](unsigned long long j) {
+        return acc_base + (size_t)((gbm_s + j) % 3ull) * kFxWords * kAccStride;
+    };
+    auto clear_buf = [&](unsigned long long *b) {  // one warp
+        for (int i = lane; i < kFxWords; i += 32) b[(size_t)i * kAccStride] = 0ull;
+    };
     auto clear_prev = [&](unsigned long long j) {  // after passing barrier j; warp 1 of CTA 0
-        if (blockIdx.x == 0 && warp == 1) {
-            unsigned long long *b = acc_buf(j + 2);  // = buffer j - 1
-            for (int i = lane; i < kAccWords; i += 32) b[i] = 0ull;
-        }
+        if (blockIdx.x == 0 && warp == 1) clear_buf(acc_buf(j + 2));  // = buffer j - 1
     };
     if (pr.mode == 0) {
         if (threadIdx.x < 12) Tsh[threadIdx.x] = __ldcg(pose + threadIdx.x);
@@ -617,7 +636,7 @@ __global__ void __launch_bounds__(kTileThreads, 1)
         cta_grid_arrive(ctrl);
         stage_groups(my_groups / 2, my_groups);
         if (!cta_grid_await(ctrl, base + G * ++nbar, st, &flag, a.wait_cycles)) return;
-        clear_prev(nbar);
+        // (the buffer before this barrier belongs to the front end's first barrier: never added into)
         for (int k = blockIdx.x * kTileThreads + threadIdx.x; k < ns; k += stride) fr.zbuf[k] = kEmptyKey;
     } else {
         stage_groups(0, my_groups);
@@ -630,7 +649,7 @@ __global__ void __launch_bounds__(kTileThreads, 1)
     for (; it < ip.max_iters; ++it) {
         // the pose in FP32: converted once per CTA (FP64 conversions are slow on GB300), read by all
         if (threadIdx.x < 12) Tf[threadIdx.x] = (float)Tsh[threadIdx.x];
-        if (threadIdx.x < kAccWords) fxs[threadIdx.x] = 0ull;
+        if (threadIdx.x < kFxWords) fxs[threadIdx.x] = 0ull;
         __syncthreads();
         PoseF T;
 #pragma unroll
@@ -665,57 +684,92 @@ __global__ void __launch_bounds__(kTileThreads, 1)
         __syncthreads();
         const unsigned long long jb = nbar + (unsigned long long)(it + 1);  // this step's barrier
         unsigned long long *const buf = acc_buf(jb);
-        if (threadIdx.x < 86) {
-            const unsigned long long v = fxs[threadIdx.x];
-            if (v) asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(buf + threadIdx.x), "l"(v) : "memory");
+        // (test support: with `withhold`, CTA 0 skips its first contribution, so no CTA's wait can end)
+        if (!(a.withhold && it == 0 && blockIdx.x == 0)) {
+            if (threadIdx.x < kFxWords) {
+                const unsigned long long v = fxs[threadIdx.x] + kFxBias + kFxCount;
+                asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(buf + (size_t)threadIdx.x * kAccStride),
+                             "l"(v)
+                             : "memory");
+            } else if (threadIdx.x == kTileThreads - 32) {
+                grid_arrive(&ctrl->arrive64);  // keeps the barrier count that the later phases wait on
+            }
         }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            flag = 0;
-            // (test support: with `withhold`, CTA 0 skips its first arrival, so no CTA's wait can end)
-            if (!(a.withhold && it == 0 && blockIdx.x == 0)) grid_arrive(&ctrl->arrive64);
-            if (!grid_wait(&ctrl->arrive64, base + G * jb, a.wait_cycles)) {
-                flag = 3;
-                st->status = UPSLAM_ERR_TIMEOUT;
+        if (warp == 0) {
+            // wait until every CTA has added into every word: the last loads hold the step's totals
+            // (lane i < 28 reads sum i's three chunks, lane 28 the inlier and valid counts)
+            // (lanes past the last word re-read it)
+            unsigned long long w[3];
+            const long long t0 = clock64();
+            bool late = false;
+            for (;;) {
+                bool done = true;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];"
+                                 : "=l"(w[k])
+                                 : "l"(buf + (size_t)min(3 * lane + k, kFxWords - 1) * kAccStride)
+                                 : "memory");
+                    done = done && (w[k] >> 48) == G;
+                }
+                if (__all_sync(0xffffffffu, done)) break;
+                if (__any_sync(0xffffffffu, clock64() - t0 > a.wait_cycles)) {
+                    late = true;
+                    break;
+                }
+            }
+            if (lane == 0) {
+                flag = late ? 3 : 0;
+                if (late) st->status = UPSLAM_ERR_TIMEOUT;
+            }
+            // acquire every CTA's step (their reads of the previous buffer included)
+            if (!late) asm volatile("fence.acq_rel.gpu;" ::: "memory");
+            if (blockIdx.x == 0) asm volatile("bar.arrive 1, 64;" ::: "memory");  // warp 1 may clear
+            if (!late) {
+                const long long off = (long long)G * (long long)kFxBias;
+                if (lane < 28) {
+                    tot[lane] = fx_value((long long)(w[0] & (kFxCount - 1)) - off,
+                                         (long long)(w[1] & (kFxCount - 1)) - off,
+                                         (long long)(w[2] & (kFxCount - 1)) - off);
+                } else if (lane == 28) {
+                    totn[0] = (long long)(w[0] & (kFxCount - 1)) - off;
+                    totn[1] = (long long)(w[1] & (kFxCount - 1)) - off;
+                }
+                __syncwarp();
+                const long long inliers = totn[0];
+                double xi[6] = {0, 0, 0, 0, 0, 0};
+                int status = UPSLAM_OK, conv = 0;
+                if (inliers < ip.min_inliers) {
+                    status = UPSLAM_ERR_DEGENERATE;
+                } else {
+                    if (!warp_solve6(tot, ip.pivot_eps, xi)) {
+                        status = UPSLAM_ERR_DEGENERATE;
+#pragma unroll
+                        for (int i = 0; i < 6; ++i) xi[i] = 0.0;
+                    } else {
+                        warp_se3_update(xi, Tsh);
+                        conv = warp_converged(xi, er2, et2) ? 1 : 0;
+                    }
+                }
+                if (lane == 0) {
+                    status_s = status;
+                    conv_s = conv;
+                    if (it == 0) valid_s = (int)totn[1];
+#pragma unroll
+                    for (int i = 0; i < 6; ++i) xi_sh[i] = xi[i];
+                }
+            }
+        } else if (warp == 1 && blockIdx.x == 0) {
+            // every CTA has added into this step's buffer, so every CTA has read the previous one:
+            // clear that, and fence so the zeros are ordered before CTA 0's next contribution
+            asm volatile("bar.sync 1, 64;" ::: "memory");
+            if (*((volatile int *)&flag) != 3) {
+                clear_buf(acc_buf(jb + 2));
+                asm volatile("fence.acq_rel.gpu;" ::: "memory");
             }
         }
         __syncthreads();
         if (flag == 3) return;
-        clear_prev(jb);
-        if (warp == 0) {
-            // the step's totals: one L2 round trip for the 86 words every CTA added into
-            if (lane < 28) {
-                const long long s0 = (long long)__ldcg(buf + 3 * lane), s1 = (long long)__ldcg(buf + 3 * lane + 1),
-                                s2 = (long long)__ldcg(buf + 3 * lane + 2);
-                tot[lane] = fx_value(s0, s1, s2);
-            } else if (lane < 30) {
-                totn[lane - 28] = (long long)__ldcg(buf + 84 + (lane - 28));
-            }
-            __syncwarp();
-            const long long inliers = totn[0];
-            double xi[6] = {0, 0, 0, 0, 0, 0};
-            int status = UPSLAM_OK, conv = 0;
-            if (inliers < ip.min_inliers) {
-                status = UPSLAM_ERR_DEGENERATE;
-            } else {
-                if (!warp_solve6(tot, ip.pivot_eps, xi)) {
-                    status = UPSLAM_ERR_DEGENERATE;
-#pragma unroll
-                    for (int i = 0; i < 6; ++i) xi[i] = 0.0;
-                } else {
-                    warp_se3_update(xi, Tsh);
-                    conv = warp_converged(xi, er2, et2) ? 1 : 0;
-                }
-            }
-            if (lane == 0) {
-                status_s = status;
-                conv_s = conv;
-                if (it == 0) valid_s = (int)totn[1];
-#pragma unroll
-                for (int i = 0; i < 6; ++i) xi_sh[i] = xi[i];
-            }
-        }
-        __syncthreads();
         if (status_s != UPSLAM_OK || conv_s) {
             ++it;
             break;
@@ -888,6 +942,7 @@ static upslam_status launch_tile(const IcpArgs &a, double *pose, const upslam_ic
         }
     }
     const int grid = upslam_sm_count();
+    if (grid > kFxMaxCtas) return UPSLAM_ERR_UNSUPPORTED;
     const int64_t npx = (int64_t)a.kp.rows * a.kp.cols;
     const int64_t nchunks = (npx + kTileThreads - 1) / kTileThreads;
     const int64_t per = (nchunks + grid - 1) / grid * kTileThreads;  // most pixels one CTA can stage
@@ -1084,11 +1139,11 @@ namespace upslam {
 
 // A launch needs the control block plus two 64-float records per CTA (one CTA per SM), so the
 // array's record count fixes the largest device it serves: 2048 records = 1024 CTAs, and
-// 4096 + 2048 * 64 * 4 = 528384 bytes (516 KiB).
+// 36864 + 2048 * 64 * 4 = 561152 bytes (548 KiB).
 constexpr int kNoAllocMaxRecords = 2048;
 constexpr int kNoAllocMaxCtas = kNoAllocMaxRecords / 2;
 constexpr size_t kNoAllocBytes = kCtrlBytes + (size_t)kNoAllocMaxRecords * kSlots * sizeof(float);
-static_assert(kNoAllocBytes == 528384, "the documented capacity of the allocation-free scratch");
+static_assert(kNoAllocBytes == 561152, "the documented capacity of the allocation-free scratch");
 static_assert(kCtrlBytes + 2 * (size_t)kNoAllocMaxCtas * kSlots * sizeof(float) <= kNoAllocBytes,
               "the largest accepted grid fits the array");
 
