@@ -722,8 +722,8 @@ __global__ void __launch_bounds__(kTileThreads, 1)
                 flag = late ? 3 : 0;
                 if (late) st->status = UPSLAM_ERR_TIMEOUT;
             }
-            // acquire every CTA's step (their reads of the previous buffer included)
-            if (!late) asm volatile("fence.acq_rel.gpu;" ::: "memory");
+            // (no fence here: the solve reads nothing but these words, and a fence would cost the
+            // critical path about 800 cycles; warp 1 of CTA 0 takes the fences that the clearing needs)
             if (blockIdx.x == 0) asm volatile("bar.arrive 1, 64;" ::: "memory");  // warp 1 may clear
             if (!late) {
                 const long long off = (long long)G * (long long)kFxBias;
@@ -761,9 +761,13 @@ __global__ void __launch_bounds__(kTileThreads, 1)
             }
         } else if (warp == 1 && blockIdx.x == 0) {
             // every CTA has added into this step's buffer, so every CTA has read the previous one:
-            // clear that, and fence so the zeros are ordered before CTA 0's next contribution
+            // clear that one.  The first fence orders the clearing after warp 0's observation of
+            // those adds; the second orders the zeros before CTA 0's next contribution, which every
+            // CTA must observe before it can add into the cleared buffer again.  Both run while
+            // warp 0 solves.
             asm volatile("bar.sync 1, 64;" ::: "memory");
             if (*((volatile int *)&flag) != 3) {
+                asm volatile("fence.acq_rel.gpu;" ::: "memory");
                 clear_buf(acc_buf(jb + 2));
                 asm volatile("fence.acq_rel.gpu;" ::: "memory");
             }
