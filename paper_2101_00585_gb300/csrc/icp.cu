@@ -333,7 +333,9 @@ __global__ void __launch_bounds__(kIcpThreads) icp_step_kernel(IcpArgs a, double
 
 constexpr int kTileThreads = 512;
 constexpr int kTileWarps = kTileThreads / 32;
-constexpr int kStageGroup = 4;  // keyframe chunks staged per memory round trip
+// keyframe chunks staged per memory round trip: a 512x2048 keyframe deals 13-14 chunks to each of
+// 152 CTAs, so each half of the front end's staging is one round trip (8 spills registers)
+constexpr int kStageGroup = 7;
 
 // The sweep pixel a staged keyframe point lands in: its point and normal,
 // gathered from L2, and whether the point binned at all.
