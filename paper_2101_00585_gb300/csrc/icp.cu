@@ -624,8 +624,12 @@ __global__ void __launch_bounds__(kTileThreads, 1)
     if (fr.on) {
         const int ns = a.sp.rows * a.sp.cols;
         const int stride = gridDim.x * kTileThreads;
-        for (int i = blockIdx.x * kTileThreads + threadIdx.x; i < fr.n; i += stride)
-            project_point(fr.pts, i, a.sp, fr.zbuf);
+        // (warps 1.. project while warp 0 forms the motion prior above)
+        if (warp > 0) {
+            const int pstride = gridDim.x * (kTileThreads - 32);
+            for (int i = blockIdx.x * (kTileThreads - 32) + threadIdx.x - 32; i < fr.n; i += pstride)
+                project_point(fr.pts, i, a.sp, fr.zbuf);
+        }
         cta_grid_arrive(ctrl);
         stage_groups(0, my_groups / 2);
         if (!cta_grid_await(ctrl, base + G * ++nbar, st, &flag, a.wait_cycles)) return;
@@ -781,6 +785,19 @@ __global__ void __launch_bounds__(kTileThreads, 1)
             break;
         }
     }
+    // the motion update M = T_prev^-1 T, by warp 0 of CTA 0
+    auto publish_motion = [&]() {
+        if (blockIdx.x == 0 && warp == 0 && pr.mode != 0 && pr.motion_out) {
+            warp_pose_inv(Tprev, Tmot);
+            double M[12];
+            warp_pose_mul(Tmot, Tsh, Tmot);
+            if (lane == 0) {
+                for (int i = 0; i < 12; ++i) M[i] = Tmot[i];
+                orthonormalise_rows(M);
+                for (int i = 0; i < 12; ++i) pr.motion_out[i] = M[i];
+            }
+        }
+    };
     // ---- keyframe update with the registered pose (Sec. III-C), gated by the
     // registration quality: every CTA holds the same totals, so all take the same decision.
     int accepted_flag = 0;
@@ -796,9 +813,14 @@ __global__ void __launch_bounds__(kTileThreads, 1)
 #pragma unroll
         for (int i = 0; i < 12; ++i) T.r[i] = Tf[i];
         const int ns = fz.sp.rows * fz.sp.cols;
+        // warp 0 of CTA 0 forms the motion update meanwhile; the other threads take its share
+        const int ex = (pr.mode != 0 && pr.motion_out) ? 32 : 0;
+        publish_motion();
         if (acc_ok) {
             // average the staged samples straight from shared memory, spilled chunks from global memory
-            for (int e = threadIdx.x; e < staged; e += kTileThreads)
+            const int e0 = blockIdx.x == 0 ? (int)threadIdx.x - ex : (int)threadIdx.x;
+            const int es = blockIdx.x == 0 ? kTileThreads - ex : kTileThreads;
+            for (int e = e0; e >= 0 && e < staged; e += es)
                 fuse_average(fz, T, sk[e], make_float3(sx[e], sy[e], sz[e]), make_float4(snx[e], sny[e], snz[e], sw8[e]),
                              sd[e]);
             for (int q = spill_q; q < nchunks; q += gridDim.x) {
@@ -811,7 +833,8 @@ __global__ void __launch_bounds__(kTileThreads, 1)
                 fuse_average(fz, T, k, pixel_point(fz.kdirs, fz.kp.rows, v, k - v * W, d), n4, d);
             }
             // hole fill, first pass: z-buffer atomics into empty keyframe pixels
-            for (int j = blockIdx.x * kTileThreads + threadIdx.x; j < ns; j += gridDim.x * kTileThreads) {
+            for (int j = (int)(blockIdx.x * kTileThreads + threadIdx.x) - ex; j >= 0 && j < ns;
+                 j += (int)(gridDim.x * kTileThreads) - ex) {
                 int k;
                 unsigned long long key;
                 float r;
@@ -846,17 +869,9 @@ __global__ void __launch_bounds__(kTileThreads, 1)
             }
         }
     }
-    // CTA 0 publishes the pose, the motion update and the record of the last linearisation
-    if (blockIdx.x == 0 && warp == 0 && pr.mode != 0 && pr.motion_out) {
-        warp_pose_inv(Tprev, Tmot);
-        double M[12];
-        warp_pose_mul(Tmot, Tsh, Tmot);
-        if (lane == 0) {
-            for (int i = 0; i < 12; ++i) M[i] = Tmot[i];
-            orthonormalise_rows(M);
-            for (int i = 0; i < 12; ++i) pr.motion_out[i] = M[i];
-        }
-    }
+    // CTA 0 publishes the pose, the motion update (already, when the keyframe update ran) and the
+    // record of the last linearisation
+    if (!fuse_on) publish_motion();
     if (blockIdx.x == 0 && pr.prev_out && threadIdx.x < 12) pr.prev_out[threadIdx.x] = Tsh[threadIdx.x];
     if (blockIdx.x == 0) {
         if (threadIdx.x < 12) pose[threadIdx.x] = Tsh[threadIdx.x];
