@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(512, 1) icp_batched_kernel(BatchArgs a) {
     __shared__ int kf_wb[kBatchMaxKf];                       // where this CTA's own samples go
     __shared__ int wcnt[32];
     __shared__ int pcnt[2][kPx][16];
-    __shared__ int base_s, flag_s, any_active;
+    __shared__ int flag_s, any_active;
     __shared__ double totq[16][32];   // step sums of the problems being solved, one per warp
     __shared__ double Tsh[16][12];    // their poses
     __shared__ int pown[16];
