@@ -21,6 +21,8 @@ namespace upslam {
 template <int PREC>
 __global__ void __launch_bounds__(256, 4) atrous_kernel(upslam_pano pp, const float4 *__restrict__ pix, const void *nin,
                                                      void *nout, int step, float inv_sn2, float inv_sx2) {
+    pdl_wait();     // the previous level's output is complete
+    pdl_release();  // and the next level may place its CTAs
     const int W = pp.cols, H = pp.rows, npx = H * W;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= npx) return;
@@ -94,11 +96,21 @@ extern "C" upslam_status upslam_atrous_normals(const upslam_pano *pp, const floa
     const void *src = d_nrm_in;
     for (int l = 0; l < ap->levels; ++l) {
         void *dst = ((ap->levels - 1 - l) % 2 == 0) ? d_nrm_out : d_tmp;
-        if (precision == UPSLAM_F32)
-            atrous_kernel<UPSLAM_F32><<<blocks, 256, 0, s>>>(*pp, pix, src, dst, 1 << l, inv_sn2, inv_sx2);
-        else
-            atrous_kernel<UPSLAM_F16><<<blocks, 256, 0, s>>>(*pp, pix, src, dst, 1 << l, inv_sn2, inv_sx2);
-        UPSLAM_CHECK_LAUNCH();
+        if (l == 0) {
+            if (precision == UPSLAM_F32)
+                atrous_kernel<UPSLAM_F32><<<blocks, 256, 0, s>>>(*pp, pix, src, dst, 1 << l, inv_sn2, inv_sx2);
+            else
+                atrous_kernel<UPSLAM_F16><<<blocks, 256, 0, s>>>(*pp, pix, src, dst, 1 << l, inv_sn2, inv_sx2);
+            UPSLAM_CHECK_LAUNCH();
+        } else {
+            // later levels overlap the previous level's tail (each waits for its input first)
+            const bool ok = precision == UPSLAM_F32
+                                ? launch_dependent(atrous_kernel<UPSLAM_F32>, dim3(blocks), dim3(256), 0, s, *pp, pix,
+                                                   src, dst, 1 << l, inv_sn2, inv_sx2)
+                                : launch_dependent(atrous_kernel<UPSLAM_F16>, dim3(blocks), dim3(256), 0, s, *pp, pix,
+                                                   src, dst, 1 << l, inv_sn2, inv_sx2);
+            if (!ok) return UPSLAM_ERR_CUDA;
+        }
         src = dst;
     }
     return UPSLAM_OK;

@@ -851,6 +851,16 @@ __device__ __forceinline__ void holefill_write(const FuseView &f, const PoseF &T
     store_nw(f.knw, k, f.kprec, make_float4(Rm.x * l, Rm.y * l, Rm.z * l, 1.0f));
 }
 
+// ----------------------------------------------------------------------------- programmatic dependent launch
+//
+// Where one entry point runs several kernels in a row, the later ones are launched with
+// launch_dependent: their CTAs may be placed while the kernel before them drains, and each runs
+// pdl_wait() before it reads anything (the wait returns once the previous grid has finished and its
+// writes are visible).  A kernel lets its successor start early with pdl_release(); without it the
+// successor starts at its end, as an ordinary launch would.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 }  // namespace upslam
 
 // ----------------------------------------------------------------------------- host helpers
@@ -862,6 +872,28 @@ __device__ __forceinline__ void holefill_write(const FuseView &f, const PoseF &T
             return UPSLAM_ERR_CUDA;                               \
         }                                                         \
     } while (0)
+
+// A launch that may overlap the previous kernel on the stream (the kernel must call pdl_wait()
+// before it reads that kernel's results).  False when the launch fails.
+template <typename... KArgs, typename... Args>
+static inline bool launch_dependent(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                                    Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if (cudaLaunchKernelEx(&cfg, kernel, args...) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    return true;
+}
 
 static inline bool upslam_pano_ok(const upslam_pano *pp) {
     return pp && pp->rows > 0 && pp->cols > 0 && (int64_t)pp->rows * pp->cols < (int64_t(1) << 31) &&

@@ -88,6 +88,7 @@ __device__ __forceinline__ bool seen_through(const ConsSide &src, const ConsSide
 __global__ void __launch_bounds__(256) consistency_flags_kernel(ConsSide a, ConsSide b, const double *T_ab, float rel,
                                                                 float abs_m, unsigned char *flags_a,
                                                                 unsigned char *flags_b, int ga) {
+    pdl_release();  // the removal launch may place its CTAs while this grid drains
     const bool side_a = (int)blockIdx.x < ga;
     const PoseF T = cta_pose_or_inverse(T_ab, !side_a);
     const ConsSide &src = side_a ? a : b;
@@ -102,6 +103,7 @@ __global__ void __launch_bounds__(256) consistency_flags_kernel(ConsSide a, Cons
 __global__ void __launch_bounds__(256) consistency_apply_kernel(ConsSide a, ConsSide b, const unsigned char *flags_a,
                                                                 const unsigned char *flags_b, int ga,
                                                                 unsigned long long *removed) {
+    pdl_wait();  // every flag is written
     const bool side_a = (int)blockIdx.x < ga;
     const ConsSide &src = side_a ? a : b;
     const unsigned char *flags = side_a ? flags_a : flags_b;
@@ -153,8 +155,9 @@ extern "C" upslam_status upslam_keyframe_consistency(const upslam_keyframe *kf_a
     if (d_removed2 && cudaMemsetAsync(d_removed2, 0, 2 * sizeof(int64_t), s) != cudaSuccess) return UPSLAM_ERR_CUDA;
     consistency_flags_kernel<<<ga + gb, 256, 0, s>>>(a, b, d_T_ab12, rel, abs_m, flags_a, flags_b, ga);
     UPSLAM_CHECK_LAUNCH();
-    consistency_apply_kernel<<<ga + gb, 256, 0, s>>>(a, b, flags_a, flags_b, ga,
-                                                     reinterpret_cast<unsigned long long *>(d_removed2));
-    UPSLAM_CHECK_LAUNCH();
+    if (!launch_dependent(consistency_apply_kernel, dim3(ga + gb), dim3(256), 0, s, a, b,
+                          (const unsigned char *)flags_a, (const unsigned char *)flags_b, ga,
+                          reinterpret_cast<unsigned long long *>(d_removed2)))
+        return UPSLAM_ERR_CUDA;
     return UPSLAM_OK;
 }

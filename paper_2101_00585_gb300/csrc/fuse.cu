@@ -16,7 +16,9 @@
 //     (a pixel holds a sample exactly when its depth and count are positive;
 //     averaging only writes such pixels, hole fill only targets depth 0).
 //  2. fuse_fill_kernel: each sweep pixel re-derives its key; the one whose key
-//     won writes the pixel and resets the z-buffer word to all-ones.
+//     won writes the pixel and resets the z-buffer word to all-ones.  Launched as
+//     a programmatic dependent of the first, so its CTAs are placed while the
+//     first drains; it waits for the first's results before it reads anything.
 // Both launches read the registration record first and do nothing unless the
 // sweep was accepted (inliers / valid >= accept_quality, status OK).  The same
 // per-pixel functions (common.cuh) serve the fused register + update launch.
@@ -46,6 +48,7 @@ __device__ __forceinline__ bool accepted(const upslam_icp_stats *st, float accep
 }
 
 __global__ void __launch_bounds__(256) fuse_main_kernel(FuseView f, const double *pose, upslam_icp_stats *st, int gk) {
+    pdl_release();  // the hole-fill write launch may place its CTAs while this grid drains
     if (!accepted(st, f.accept)) return;
     const PoseF T = cta_pose_f32(pose);
     if ((int)blockIdx.x < gk) {
@@ -94,6 +97,7 @@ __global__ void __launch_bounds__(256) fuse_main_kernel(FuseView f, const double
 }
 
 __global__ void __launch_bounds__(256) fuse_fill_kernel(FuseView f, const double *pose, upslam_icp_stats *st) {
+    pdl_wait();  // the averaging and the z-buffer atomics have finished
     if (!accepted(st, f.accept)) return;
     const PoseF T = cta_pose_f32(pose);
     const int ns = f.sp.rows * f.sp.cols;
@@ -155,7 +159,6 @@ extern "C" upslam_status upslam_fuse(const upslam_keyframe *kf, const upslam_swe
     const int gs = upslam_grid(ns, 256, 2);
     fuse_main_kernel<<<gk + gs, 256, 0, s>>>(f, d_pose12, d_stats, gk);
     UPSLAM_CHECK_LAUNCH();
-    fuse_fill_kernel<<<gs, 256, 0, s>>>(f, d_pose12, d_stats);
-    UPSLAM_CHECK_LAUNCH();
+    if (!launch_dependent(fuse_fill_kernel, dim3(gs), dim3(256), 0, s, f, d_pose12, d_stats)) return UPSLAM_ERR_CUDA;
     return UPSLAM_OK;
 }

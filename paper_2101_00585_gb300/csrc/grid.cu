@@ -43,6 +43,7 @@ struct GridArgs {
 };
 
 __global__ void __launch_bounds__(kGridThreads) grid_score_kernel(GridArgs g) {
+    pdl_release();  // the arg-max launch may place its CTA while this grid drains
     __shared__ float Ts[kCand][12];
     const int c0 = blockIdx.y * kCand;
     const int nc = min(kCand, g.n - c0);
@@ -105,6 +106,7 @@ __global__ void __launch_bounds__(kGridThreads) grid_score_kernel(GridArgs g) {
 // One CTA: the first candidate with the largest score, and (optionally) its pose.
 __global__ void __launch_bounds__(1024) grid_best_kernel(const unsigned long long *scores, int n, const double *poses,
                                                          int *best, double *best_pose) {
+    pdl_wait();  // every score is in
     __shared__ unsigned long long ws[32];
     __shared__ int wi[32];
     __shared__ int win;
@@ -224,7 +226,8 @@ extern "C" upslam_status upslam_grid_score(const upslam_keyframe *kf, const upsl
     if (cand_blocks > 65535) return UPSLAM_ERR_INVALID_ARG;
     grid_score_kernel<<<dim3(xb, cand_blocks), kGridThreads, 0, s>>>(g);
     UPSLAM_CHECK_LAUNCH();
-    grid_best_kernel<<<1, 1024, 0, s>>>(g.scores, n, d_poses, d_best, d_best_pose12);
-    UPSLAM_CHECK_LAUNCH();
+    if (!launch_dependent(grid_best_kernel, dim3(1), dim3(1024), 0, s, (const unsigned long long *)g.scores, n,
+                          (const double *)d_poses, d_best, d_best_pose12))
+        return UPSLAM_ERR_CUDA;
     return UPSLAM_OK;
 }

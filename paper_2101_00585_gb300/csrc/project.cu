@@ -36,6 +36,7 @@ __global__ void pano_dirs_kernel(upslam_pano pp, float *dirs) {
 template <bool kPose>
 __global__ void __launch_bounds__(256) project_kernel(const float4 *__restrict__ pts, int n, const double *pose,
                                                       upslam_pano pp, unsigned long long *__restrict__ zbuf) {
+    pdl_release();  // the resolve launch may place its CTAs while this grid drains
     if (!kPose) {
         for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
             project_point(pts, i, pp, zbuf);
@@ -57,6 +58,7 @@ __global__ void __launch_bounds__(256) project_kernel(const float4 *__restrict__
 __global__ void __launch_bounds__(256) resolve_kernel(const float4 *__restrict__ pts, int npx,
                                                       unsigned long long *__restrict__ zbuf, float *__restrict__ depth,
                                                       int *__restrict__ idx, float4 *__restrict__ pix) {
+    pdl_wait();  // every point of the projection has reached the z-buffer
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < npx; k += gridDim.x * blockDim.x)
         resolve_pixel<false>(pts, k, zbuf, depth, idx, pix);
 }
@@ -110,9 +112,10 @@ extern "C" upslam_status upslam_project(const float *d_pts, int32_t n, const dou
         UPSLAM_CHECK_LAUNCH();
     }
     const int npx = pp->rows * pp->cols;
-    resolve_kernel<<<upslam_grid(npx, 256), 256, 0, s>>>(reinterpret_cast<const float4 *>(d_pts), npx, zb, d_depth, d_idx,
-                                                       reinterpret_cast<float4 *>(d_pix));
-    UPSLAM_CHECK_LAUNCH();
+    if (!launch_dependent(resolve_kernel, dim3(upslam_grid(npx, 256)), dim3(256), 0, s,
+                          reinterpret_cast<const float4 *>(d_pts), npx, zb, d_depth, d_idx,
+                          reinterpret_cast<float4 *>(d_pix)))
+        return UPSLAM_ERR_CUDA;
     return UPSLAM_OK;
 }
 
