@@ -74,8 +74,26 @@ enum {
     LD_IM2COL_MNT = 8,  // TMA: im2col of an input with C >= 64, MN-major (weight gradient)
     LD_DENSE_MNT = 9,   // TMA: dY [P][N], MN-major (weight gradient)
     LD_IM2COL_KT32 = 10,  // TMA: as LD_IM2COL_KT for C = 32 (two taps per K step, 64-byte swizzle)
-    LD_IM2COL_MNT32 = 11  // TMA: as LD_IM2COL_MNT for C = 32 (64-byte swizzle)
+    LD_IM2COL_MNT32 = 11,  // TMA: as LD_IM2COL_MNT for C = 32 (64-byte swizzle)
+    LD_S2D_KT = 12,        // TMA: the 8-channel input as a 2x2 space-to-depth convolution (forward)
+    LD_S2D_MNT = 13,       // TMA: the same, MN-major (weight gradient)
+    LD_DENSE_MNT32 = 14    // TMA: dY [P][32], MN-major, 64-byte swizzle (weight gradient, N = 32)
 };
+
+// The first layer (C = 8) as a space-to-depth convolution.  Input pixels (2Y + dy, 2X + dx) form the
+// 32-channel pixel (Y, X) with channel 16 dy + 8 dx + c, and the 3x3 stride-2 pad-1 convolution becomes a
+// 2x2 stride-1 one over taps (ty, tx) at (oy + ty - 1, ox + tx - 1): feature f = 32 (2 ty + tx) + 16 dy +
+// 8 dx + c carries the weight of tap (ky, kx) = (2 ty + dy - 1, 2 tx + dx - 1) and channel c, and is zero
+// where ky or kx is -1 (56 of the 128 features).  No copy is made: the NHWC input read as [B][H][W/2][16]
+// (pairs of pixels along W) gives, for one dy, 16 of a feature's 32 channels in one 32-byte box row.
+// The first 16 features (tap (0, 0), dy = 0) are all unused, so the weight gradient reads its feature of
+// ones (the bias gradient) there.
+constexpr int kS2dK = 128;
+__host__ __device__ inline int s2d_feature_source(int f) {  // the 3x3 feature of f, or -1
+    const int tap = f >> 5, dy = (f >> 4) & 1, dx = (f >> 3) & 1, c = f & 7;
+    const int ky = 2 * (tap >> 1) + dy - 1, kx = 2 * (tap & 1) + dx - 1;
+    return ky < 0 || kx < 0 ? -1 : (3 * ky + kx) * 8 + c;
+}
 
 // Channels per im2col TMA box: 64 (128-byte swizzle) or 32 (64-byte swizzle).
 template <int LD>
@@ -116,6 +134,7 @@ struct TcGemm {
     float *db;                  // EPI_F32_RED_T with a ones row: the bias gradient it feeds
     unsigned long long timeout_ns;  // limit of every mbarrier wait (global-timer nanoseconds)
     int withhold;  // test support: the MMA thread does not signal its first accumulator as full
+    int s2d;       // EPI_F32_RED_T: row m is feature m of the space-to-depth first layer
 };
 
 constexpr int kTcBM = 128, kTcBK = 64;
@@ -233,7 +252,7 @@ __device__ __forceinline__ void class_tap(int q, int t, int &ky, int &kx) {
 template <int LA>
 constexpr bool tc_a_tma() {
     return LA == LD_DY_TAPS_K || LA == LD_IM2COL_KT || LA == LD_IM2COL_MNT || LA == LD_IM2COL_KT32 ||
-           LA == LD_IM2COL_MNT32;
+           LA == LD_IM2COL_MNT32 || LA == LD_S2D_KT || LA == LD_S2D_MNT;
 }
 template <int LA>
 constexpr int tc_prod() { return tc_a_tma<LA>() ? 1 : 8; }
@@ -283,6 +302,29 @@ __device__ __forceinline__ TcUnit tc_unit(const TcGemm &g, int u) {
 template <int LA>
 __device__ __forceinline__ void tc_tma_a(unsigned stage, unsigned mbar, const TcOperand &a, const CUtensorMap *ma,
                                          const CUtensorMap *mo, const TcUnit &t, int k0) {
+    if (LA == LD_S2D_KT || LA == LD_S2D_MNT) {
+        // boxes of 16 features (one dy of a tap: 32-byte rows, 32-byte swizzle) over the NHWC input read as
+        // [B][H][W/2][16], at (X, y) = (ox + tx - 1, 2 (oy + ty - 1) + dy); padding reads zeros.  Forward:
+        // rows = 128 output pixels from t.r0a, the K step's 64 features = 4 boxes [128][32 B] 4 KB apart.
+        // Weight gradient: k = 64 output pixels from k0, rows = the 128 features as 8 boxes [64][32 B] 2 KB
+        // apart, the first box the feature of ones.
+        constexpr bool FWD = LA == LD_S2D_KT;
+        const int wo = a.ws - 1, ho = a.hs - 1;
+        const int p0 = FWD ? t.r0a : k0;
+        const int ox0 = p0 & ((1 << wo) - 1), oy0 = (p0 >> wo) & ((1 << ho) - 1), b0 = p0 >> (wo + ho);
+#pragma unroll 1
+        for (int h = 0; h < (FWD ? 4 : 8); ++h) {
+            const int f = (FWD ? k0 : t.r0a) + 16 * h;
+            const unsigned dst = stage + h * (FWD ? 4096 : 2048);
+            if (!FWD && f == a.ones_row) {
+                tma_load4(dst, mo, 0, 0, 0, 0, mbar);
+                continue;
+            }
+            const int tap = f >> 5, dy = (f >> 4) & 1;
+            tma_load4(dst, ma, 0, ox0 + (tap & 1) - 1, 2 * (oy0 + (tap >> 1) - 1) + dy, b0, mbar);
+        }
+        return;
+    }
     if (LA == LD_IM2COL_MNT || LA == LD_IM2COL_MNT32) {
         // k: 64 pixels from k0; rows: features t.r0a.. as boxes of CB channels, [64 k][2 CB bytes] each, 128 CB
         // bytes apart (the appended feature of ones from mo; features past it read zeros from image nb)
@@ -344,6 +386,11 @@ __device__ __forceinline__ void tc_tma_b(unsigned sb, unsigned mbar, const TcOpe
     if (LB == LD_DENSE_KT) {
         // weights [N][K]: BN rows from t.r0b by 64 k from k0, one 128-byte-swizzled box
         tma_load4(sb, mb, k0, t.r0b, 0, 0, mbar);
+        return;
+    }
+    if (LB == LD_DENSE_MNT32) {
+        // dY [P][32]: k = 64 pixels from k0, rows = the 32 channels, one 64-byte-swizzled box
+        tma_load4(sb, mb, t.r0b, k0, 0, 0, mbar);
         return;
     }
     if (LB == LD_DENSE_MNT) {
@@ -499,10 +546,13 @@ __device__ __forceinline__ void tc_epilogue(const TcGemm &g, const TcUnit &cur, 
                 for (int jj = 0; jj < 8; ++jj)
                     if (n + jj < g.N) atomicAdd(g.db + n + jj, __uint_as_float(w[jj]));
             } else {
+                // (the space-to-depth first layer: its feature m is 3x3 feature s2d_feature_source(m), or unused)
+                const int mc = g.s2d ? s2d_feature_source(m) : m;
+                if (mc < 0) continue;
 #pragma unroll
                 for (int jj = 0; jj < 8; ++jj)
                     if (n + jj < g.N)
-                        atomicAdd(reinterpret_cast<float *>(g.C) + (long long)(n + jj) * g.ldc + m,
+                        atomicAdd(reinterpret_cast<float *>(g.C) + (long long)(n + jj) * g.ldc + mc,
                                   __uint_as_float(w[jj]));
             }
         }
@@ -525,8 +575,8 @@ __global__ void __launch_bounds__(tc_threads<LA>(), 2)
     constexpr int kLag = S - 2;  // cp.async groups a gather thread keeps in flight before signalling a stage
     constexpr int kA = kTcBM * kTcBK * 2, kStage = (kTcBM + BN) * kTcBK * 2;
     constexpr unsigned kTxBytes = (unsigned)kStage;  // TMA boxes are written in full (zeros outside)
-    constexpr bool A_MN = LA == LD_IM2COL_MN || LA == LD_IM2COL_MNT || LA == LD_IM2COL_MNT32;
-    constexpr bool B_MN = LB == LD_DENSE_MN || LB == LD_W_TAPS_MN || LB == LD_DENSE_MNT;
+    constexpr bool A_MN = LA == LD_IM2COL_MN || LA == LD_IM2COL_MNT || LA == LD_IM2COL_MNT32 || LA == LD_S2D_MNT;
+    constexpr bool B_MN = LB == LD_DENSE_MN || LB == LD_W_TAPS_MN || LB == LD_DENSE_MNT || LB == LD_DENSE_MNT32;
     // descriptor byte offsets (leading = along K, stride = along M/N); an MMA (16 k) advances two core
     // matrices along K
     constexpr unsigned kALbo = A_TMA ? 2048 : 128, kASbo = A_TMA ? 128 : 1024;
@@ -659,11 +709,16 @@ __global__ void __launch_bounds__(tc_threads<LA>(), 2)
                             // K-major: two 64-byte-row sub-tiles 8 KB apart, an MMA's 16 k 32 bytes along the row
                             : LA == LD_IM2COL_MNT32 ? umma_desc_sw(a0 + kk * 1024, 4096, 512, 4)
                             : LA == LD_IM2COL_KT32  ? umma_desc_sw(a0 + (kk >> 1) * 8192 + (kk & 1) * 32, 16, 512, 4)
+                            // 32-byte swizzle: K-major, one [128][32 B] box per MMA (8-row groups 256 B
+                            // apart); MN-major, 8-row K groups 256 B apart, 16-feature atoms 2 KB apart
+                            : LA == LD_S2D_KT  ? umma_desc_sw(a0 + kk * 4096, 16, 256, 6)
+                            : LA == LD_S2D_MNT ? umma_desc_sw(a0 + kk * 512, 2048, 256, 6)
                                                   : umma_desc_sw(a0 + kk * 32, 16, 1024, 2);
                         const unsigned long long bd =
                             !A_TMA                ? umma_desc(b0 + kk * 2 * kBLbo, kBLbo, kBSbo)
                             : LB == LD_DENSE_KT  ? umma_desc_sw(b0 + kk * 32, 16, 1024, 2)
                             : LB == LD_DENSE_MNT ? umma_desc_sw(b0 + kk * 2048, 8192, 1024, 2)
+                            : LB == LD_DENSE_MNT32 ? umma_desc_sw(b0 + kk * 1024, 512, 512, 4)
                             : BN == 32           ? umma_desc_sw(b0 + kk * 1024, 512, 512, 4)
                                                  : umma_desc_sw(b0 + kk * 2048, 8192, 1024, 2);
                         const unsigned accum = (k > 0 || kk > 0) ? 1u : 0u;
@@ -844,7 +899,13 @@ __global__ void pack_weights_kernel(PackArgs a) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
         int l = 0, k = i;
         while (k >= a.n[l]) k -= a.n[l++];
-        a.dst[l][k] = __float2bfloat16(a.src[l][k]);
+        if (l == 0) {
+            // the first layer in the space-to-depth order: row n, feature f (zero where unused)
+            const int n = k / kS2dK, src = s2d_feature_source(k - n * kS2dK);
+            a.dst[0][k] = __float2bfloat16(src < 0 ? 0.0f : a.src[0][n * cnn_k(0) + src]);
+        } else {
+            a.dst[l][k] = __float2bfloat16(a.src[l][k]);
+        }
     }
 }
 
@@ -936,7 +997,7 @@ static size_t cnn_ws_layout(int B, CnnWs *w, char *base) {
     int H = kCnnH, W = kCnnW;
     for (int l = 0; l < 4; ++l) {
         const size_t M = (size_t)B * (H / 2) * (W / 2);
-        void *wb = take((size_t)cnn_co(l) * cnn_k(l) * 2);
+        void *wb = take((size_t)cnn_co(l) * (l == 0 ? kS2dK : cnn_k(l)) * 2);  // the GEMM's weight layout
         void *a = take(M * cnn_co(l) * 2);
         void *d = take(M * cnn_co(l) * 2);
         if (w) {
@@ -1055,6 +1116,15 @@ static bool tmap_im2col_wide(CUtensorMap *m, const TcOperand &o, int pix, int cb
                  cb == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B);
 }
 
+// The 8-channel input [B][H][W][8] read as [B][H][W/2][16] for the space-to-depth first layer: boxes of `pix`
+// consecutive pairs of pixels along one row (16 BF16, 32 bytes each), written with the 32-byte swizzle.
+static bool tmap_s2d(CUtensorMap *m, const TcOperand &o, int pix) {
+    const int H = 1 << o.hs, W = 1 << o.ws, C = 1 << o.cs;
+    const unsigned box[4] = {16u, (unsigned)pix, 1u, 1u}, estr[4] = {1, 1, 1, 1};
+    return tmap4(m, o.p, 16, W / 2, H, o.nb, 32ull, 2ull * C * W, 2ull * C * W * H, box, estr,
+                 CU_TENSOR_MAP_SWIZZLE_32B);
+}
+
 // A row-major matrix [rows][cols] (cols contiguous) in boxes of `box_rows` rows by `box_cols` columns.
 static bool tmap_matrix(CUtensorMap *m, const void *p, long long rows, long long cols, int box_rows, int box_cols,
                         CUtensorMapSwizzle swz) {
@@ -1105,7 +1175,19 @@ static bool gemm(TcGemm g, int *err, cudaStream_t s, int splits = 1) {
     memset(&mo, 0, sizeof(mo));
     constexpr int CB = tma_cb<LA>();
     constexpr CUtensorMapSwizzle kSwzA = CB == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
-    if (LA == LD_IM2COL_MNT || LA == LD_IM2COL_MNT32) {
+    if (LA == LD_S2D_KT) {
+        // forward of the first layer: the input in 128-pixel boxes, the weights [N][128] in BN-row boxes
+        if (!tmap_s2d(&ma, g.a, kTcBM) || !tmap_matrix(&mb, g.b.p, g.N, g.b.ld, BN, 64, CU_TENSOR_MAP_SWIZZLE_128B))
+            return false;
+    } else if (LA == LD_S2D_MNT) {
+        // weight gradient of the first layer: the input in 64-pixel boxes, dY [P][32] in 64-pixel boxes, the
+        // feature of ones from the constant box (its first 16 columns)
+        const void *ones = ones_box_address();
+        if (!ones || !tmap_s2d(&ma, g.a, kTcBK) ||
+            !tmap_matrix(&mb, g.b.p, g.K, g.b.ld, kTcBK, 32, CU_TENSOR_MAP_SWIZZLE_64B) ||
+            !tmap_matrix(&mo, ones, 64, 64, 64, 16, CU_TENSOR_MAP_SWIZZLE_32B))
+            return false;
+    } else if (LA == LD_IM2COL_MNT || LA == LD_IM2COL_MNT32) {
         // weight gradient with C >= 32: the input in 64-pixel boxes of CB channels, dY [P][N] in 64-pixel boxes
         // of 64 channels, the appended feature of ones from a constant box
         const void *ones = ones_box_address();
@@ -1184,13 +1266,13 @@ static upslam_status cnn_forward(const float *d_params, const void *d_x, int32_t
     for (int l = 0; l < 4; ++l) {
         pk.src[l] = d_params + L.off_w[l];
         pk.dst[l] = w.wb[l];
-        pk.n[l] = cnn_co(l) * cnn_k(l);
+        pk.n[l] = cnn_co(l) * (l == 0 ? kS2dK : cnn_k(l));
         n_w += pk.n[l];
     }
     pack_weights_kernel<<<grid1d(n_w), 256, 0, s>>>(pk);
     int H = kCnnH, W = kCnnW;
     for (int l = 0; l < 4; ++l) {
-        const int C = kCnnCh[l], N = cnn_co(l), K = cnn_k(l);
+        const int C = kCnnCh[l], N = cnn_co(l), K = l == 0 ? kS2dK : cnn_k(l);
         TcGemm g{};
         g.a = op_im2col(x, H, W, C);
         g.a.nb = batch;
@@ -1206,10 +1288,11 @@ static upslam_status cnn_forward(const float *d_params, const void *d_x, int32_t
             g.withhold = withhold;
         }
         // the staged-bias epilogue needs one column tile: BN = N
-        // layers with C >= 32 load through TMA (128- or 64-byte swizzle); the 8-channel input is gathered
+        // layers with C >= 32 load through TMA (128- or 64-byte swizzle); the 8-channel input as the 2x2
+        // space-to-depth convolution (32-byte swizzle)
         const bool ok = C >= 64   ? gemm<EPI_BIAS_RELU_BF16, 128, LD_IM2COL_KT, LD_DENSE_KT>(g, w.err, s)
                         : C == 32 ? gemm<EPI_BIAS_RELU_BF16, 64, LD_IM2COL_KT32, LD_DENSE_KT>(g, w.err, s)
-                                  : gemm<EPI_BIAS_RELU_BF16, 32, LD_IM2COL_K, LD_DENSE_K>(g, w.err, s);
+                                  : gemm<EPI_BIAS_RELU_BF16, 32, LD_S2D_KT, LD_DENSE_KT>(g, w.err, s);
         if (!ok) return UPSLAM_ERR_CUDA;
         x = w.act[l];
         H /= 2;
@@ -1279,10 +1362,16 @@ extern "C" upslam_status upslam_cnn_backward(const float *d_params, const void *
         int splits = (2 * sms + tiles - 1) / tiles;
         if (splits > ktiles / 16) splits = ktiles / 16;
         if (splits < 1) splits = 1;
-        // layers with C >= 32 load through TMA (128- or 64-byte swizzle); the 8-channel input is gathered
+        // layers with C >= 32 load through TMA (128- or 64-byte swizzle); the 8-channel input as the 2x2
+        // space-to-depth convolution, its 128 features one M tile with the feature of ones at 0 (unused there)
+        if (C == 8) {
+            gw.M = kS2dK;
+            gw.a.ones_row = 0;
+            gw.s2d = 1;
+        }
         const bool okw = C >= 64   ? gemm<EPI_F32_RED_T, 128, LD_IM2COL_MNT, LD_DENSE_MNT>(gw, w.err, s, splits)
                          : C == 32 ? gemm<EPI_F32_RED_T, 64, LD_IM2COL_MNT32, LD_DENSE_MNT>(gw, w.err, s, splits)
-                                   : gemm<EPI_F32_RED_T, 32, LD_IM2COL_MN, LD_DENSE_MN>(gw, w.err, s, splits);
+                                   : gemm<EPI_F32_RED_T, 32, LD_S2D_MNT, LD_DENSE_MNT32>(gw, w.err, s, splits);
         if (!okw) return UPSLAM_ERR_CUDA;
         if (l > 0) {
             // dY of the layer below = its ReLU mask x sum over the taps that read each input pixel of dY W,

@@ -71,6 +71,18 @@ def random_motion(rng: np.random.Generator, max_t: float = 1.0, max_deg: float =
 
 # ----------------------------------------------------------------------------- network
 
+S2D_FEATURES = 128  # features of the first layer's 2x2 space-to-depth convolution (4 taps x 32 channels)
+
+
+def s2d_feature_source(f: int) -> int:
+    """The 3x3 feature (ky, kx, c) -> 8 (3 ky + kx) + c whose weight the library's first-layer GEMM holds at
+    feature f = 32 (2 ty + tx) + 16 dy + 8 dx + c of its space-to-depth order, where (ky, kx) =
+    (2 ty + dy - 1, 2 tx + dx - 1); -1 where ky or kx is -1 (a feature the convolution never reads)."""
+    tap, dy, dx, c = f >> 5, (f >> 4) & 1, (f >> 3) & 1, f & 7
+    ky, kx = 2 * (tap >> 1) + dy - 1, 2 * (tap & 1) + dx - 1
+    return -1 if ky < 0 or kx < 0 else (3 * ky + kx) * 8 + c
+
+
 class PoseNet:
     """The pose-proposal network with its FP32 master parameters and Adam state on the device."""
 
@@ -132,7 +144,9 @@ class PoseNet:
     def workspace_tensors(self, B: int) -> dict:
         """Views of the tensors the last forward / backward left in the workspace for batch B: BF16 conv
         weights ``wb`` [4], layer outputs ``act`` [4] and pre-activation gradients ``dy`` [4] (NHWC), FP32
-        pooled features ``g`` and their gradient ``dg``."""
+        pooled features ``g`` and their gradient ``dg``.  The library holds the first layer's weights in the
+        order of its 2x2 space-to-depth convolution ([32][128]); ``wb[0]`` is a copy of them put back in
+        the 3x3 order [32][72] (``s2d_feature_source`` gives the correspondence)."""
         L = _abi.lib()
         offs = (ctypes.c_size_t * 16)()
         if L.upslam_cnn_workspace_layout(B, offs) == 0:
@@ -146,7 +160,14 @@ class PoseNet:
         for l in range(4):
             ci, co = CHANNELS[l], CHANNELS[l + 1]
             shape = (B, IN_H >> (l + 1), IN_W >> (l + 1), co)
-            out["wb"].append(view(l, (co, 9 * ci), torch.bfloat16))
+            if l == 0:
+                w_s2d = view(0, (co, S2D_FEATURES), torch.bfloat16)
+                w = torch.zeros((co, 9 * ci), dtype=torch.bfloat16, device=w_s2d.device)
+                f = [i for i in range(S2D_FEATURES) if s2d_feature_source(i) >= 0]
+                w[:, [s2d_feature_source(i) for i in f]] = w_s2d[:, f]
+                out["wb"].append(w)
+            else:
+                out["wb"].append(view(l, (co, 9 * ci), torch.bfloat16))
             out["act"].append(view(4 + l, shape, torch.bfloat16))
             out["dy"].append(view(8 + l, shape, torch.bfloat16))
         out["g"] = view(12, (B, 128), torch.float32)
