@@ -42,31 +42,23 @@ __host__ __device__ constexpr int cnn_co(int l) { return l == 0 ? 32 : (l == 1 ?
 // class); each persistent CTA walks the units blockIdx.x, blockIdx.x +
 // gridDim.x, ... and, inside each, K in steps of 64, through a ring of S
 // shared-memory stages shared by three warp roles (gemm_tc_kernel):
-//   * producer warps copy each step's operand chunks with 16-byte cp.async
-//     (zero-filled outside the matrix), running ahead across unit boundaries;
+//   * one producer thread issues each step's TMA tensor-map loads (coordinates
+//     outside the tensor read zeros), running ahead across unit boundaries;
 //   * one thread issues the step's tcgen05.mma.kind::f16 (BF16 in, FP32
 //     accumulate, K = 16 each) into one of two tensor-memory accumulators;
 //   * epilogue warps read a finished accumulator with tcgen05.ld while the
 //     next unit's MMAs fill the other one.
-// An operand tile is R rows (along M or N) x 64 (along K) in the no-swizzle
-// canonical layout: 8 x 8 core matrices of 128 contiguous bytes, core matrix
-// (row group g, k group h) at g * 1024 + h * 128 bytes.  Inside a core matrix
-// a K-major operand holds 8 rows of 8 consecutive k, an MN-major one 8 k of 8
-// consecutive rows (instruction descriptor bits 15/16 say which).  A 16-byte
-// chunk is (a, f): a indexes one row of a K-major operand (8 consecutive k = f)
-// or one k of an MN-major operand (8 consecutive rows = f).  The sources:
-//   dense:  X[a * ld + f];
-//   im2col: pixel p and feature f of a 3x3 stride-2 pad-1 convolution over an
-//           NHWC activation [B][H][W][C] (H, W, C powers of two):
-//           x[b][2oy+ky-1][2ox+kx-1][ci..ci+7], zero outside the image.
+// Operand tiles are R rows (along M or N) x 64 (along K), written by TMA with
+// a 128-, 64- or 32-byte swizzle and read through matching UMMA descriptors
+// (K-major or MN-major; instruction descriptor bits 15/16 say which).  The
+// im2col operands are the taps of a 3x3 stride-2 pad-1 convolution over an
+// NHWC activation [B][H][W][C] (H, W, C powers of two), x[b][2oy+ky-1][2ox+kx-1][c],
+// loaded as boxes that step 2 along W and H; the 8-channel first layer is read
+// as a space-to-depth convolution instead (below).
 // Every wait is bounded; a wait that gives up sets *err and the CTA stops.
 
 enum { EPI_BIAS_RELU_BF16 = 0, EPI_F32_RED_T = 1, EPI_DGRAD_MASK_BF16 = 2 };
 enum {
-    LD_DENSE_K = 0,
-    LD_IM2COL_K = 1,
-    LD_DENSE_MN = 2,
-    LD_IM2COL_MN = 3,
     LD_DY_TAPS_K = 4,   // TMA: dY rows of one tap (data gradient)
     LD_W_TAPS_MN = 5,   // TMA: W per tap, MN-major (data gradient)
     LD_IM2COL_KT = 6,   // TMA: im2col of an input with C >= 64, one tap's 64 channels per K step (forward)
@@ -104,16 +96,13 @@ struct TcOperand {
     long long ld;    // dense and LD_W_TAPS_MN: elements between consecutive a
     int rows;        // extent along M (operand A) or N (operand B)
     int hs, ws, cs;  // im2col: log2 of the input's H, W, C; LD_DY_TAPS_K: log2 of dY's H, W, C
-    int ones_row;    // LD_IM2COL_MN: feature index whose every element reads 1 (or -1: none)
+    int ones_row;    // weight gradient: feature index whose every element reads 1 (or -1: none)
     int kf;          // im2col: number of features (9 C)
     int nb;          // im2col and LD_DY_TAPS_K: number of images (a chunk loaded at image nb reads zeros)
 };
 
-// A 16-byte chunk holding (1, 0, 0, 0, 0, 0, 0, 0) in BF16: the source of an appended feature of ones, which makes
-// the weight-gradient GEMM also produce the bias gradient sum_p dY[p][n].
-static __device__ __align__(16) const unsigned short kUnitChunk[8] = {0x3F80, 0, 0, 0, 0, 0, 0, 0};
-
-// The same feature for the TMA weight gradient: 64 pixels by 64 features, feature 0 = 1, as one box.
+// An appended feature of ones makes the weight-gradient GEMM also produce the bias gradient
+// sum_p dY[p][n]; its source is this box of 64 pixels by 64 features, feature 0 = 1.
 struct OnesBox {
     unsigned short v[64 * 64];
     constexpr OnesBox() : v() {
@@ -142,15 +131,10 @@ constexpr unsigned kTcWaitIters = 1u << 26;
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 
-// UMMA shared-memory descriptor, no swizzle: start, leading (K) and stride (M/N) byte offsets.
-__device__ __forceinline__ unsigned long long umma_desc(unsigned addr, unsigned lbo, unsigned sbo) {
-    return (unsigned long long)((addr >> 4) & 0x3FFFu) | ((unsigned long long)((lbo >> 4) & 0x3FFFu) << 16) |
-           ((unsigned long long)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
-}
-
-// The same for a tile written by TMA with a swizzle (layout type in bits 61-63: 2 = 128-byte, 4 = 64-byte;
-// tile aligned to the swizzle atom).  K-major: rows of 64 BF16, 8-row groups `sbo` apart, the leading offset
-// unused.  MN-major: rows along K of 64 (or 32) BF16, 8-row K groups `sbo` apart, atoms along M/N `lbo` apart.
+// UMMA shared-memory descriptor (start, leading and stride byte offsets) for a tile written by TMA with a
+// swizzle (layout type in bits 61-63: 2 = 128-byte, 4 = 64-byte, 6 = 32-byte; tile aligned to the swizzle
+// atom).  K-major: rows of one swizzle width, 8-row groups `sbo` apart, the leading offset unused.  MN-major:
+// rows along K of one swizzle width, 8-row K groups `sbo` apart, atoms along M/N `lbo` apart.
 __device__ __forceinline__ unsigned long long umma_desc_sw(unsigned addr, unsigned lbo, unsigned sbo, unsigned type) {
     return (unsigned long long)((addr >> 4) & 0x3FFFu) | ((unsigned long long)((lbo >> 4) & 0x3FFFu) << 16) |
            ((unsigned long long)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46) | ((unsigned long long)type << 61);
@@ -170,69 +154,6 @@ __device__ __forceinline__ void tma_load4(unsigned dst, const CUtensorMap *map, 
         : "memory");
 }
 
-__device__ __forceinline__ void cp_async16_ca(unsigned dst, const void *src, bool ok) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(ok ? 16 : 0) : "memory");
-}
-__device__ __forceinline__ void cp_async16_cg(unsigned dst, const void *src, bool ok) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(ok ? 16 : 0) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-
-// The forward and weight-gradient operands are gathered by NPROD producer warps with 16-byte cp.async,
-// zero-filled outside the matrix, into the no-swizzle layout with core matrix (row group g, k group h) at
-// g * 1024 + h * 128 bytes (LBO 128, SBO 1024).  A chunk (a, f) is 8 consecutive k of row a (K-major) or 8
-// consecutive rows f at k a (MN-major):
-//   LD_IM2COL_K  (forward A):  row a = output pixel, k f = feature (one 8-channel chunk of one tap);
-//   LD_IM2COL_MN (wgrad A):    k a = output pixel, row f = feature (feature o.ones_row reads 1);
-//   LD_DENSE_K   (forward B):  X[a * ld + f], the weights;  LD_DENSE_MN (wgrad B): X[a * ld + f], dY.
-// A warp takes 8 consecutive a by 4 consecutive f chunks: the 8 a land in the 8 distinct 16-byte rows of a
-// core matrix (no bank conflict).  Chunks at or past kread (beyond what the step's MMAs read) are skipped.
-template <int LD, int R, int NPROD>
-__device__ __forceinline__ void tc_gather(unsigned tile, const TcOperand &o, int r0, int k0, int kend, int kread,
-                                          int ptid) {
-    constexpr bool MN = LD == LD_IM2COL_MN || LD == LD_DENSE_MN;
-    constexpr bool IM = LD == LD_IM2COL_K || LD == LD_IM2COL_MN;
-    constexpr int NA8 = MN ? kTcBK / 8 : R / 8;  // groups of 8 along a
-    const int lane = ptid & 31, warp = ptid >> 5;
-#pragma unroll
-    for (int it = 0; it < R / (4 * NPROD); ++it) {
-        const int q = it * NPROD + warp;
-        const int i = (q % NA8) * 8 + (lane & 7);
-        const int j = (q / NA8) * 4 + (lane >> 3);
-        int a, f;
-        bool ok;
-        if (MN) {
-            a = k0 + i;
-            f = r0 + 8 * j;
-            ok = a < kend && f < o.rows;
-        } else {
-            a = r0 + i;
-            f = k0 + 8 * j;
-            ok = a < o.rows && f < kend;
-        }
-        if ((MN ? a : f) >= kread) continue;
-        const __nv_bfloat16 *src = o.p;
-        if (!IM) {
-            if (ok) src = o.p + (long long)a * o.ld + f;
-        } else if (MN && f == o.ones_row) {
-            if (ok) src = reinterpret_cast<const __nv_bfloat16 *>(kUnitChunk);
-        } else {
-            const int wo = o.ws - 1, ho = o.hs - 1;
-            const int ox = a & ((1 << wo) - 1), oy = (a >> wo) & ((1 << ho) - 1), b = a >> (wo + ho);
-            const int tap = f >> o.cs, ci = f & ((1 << o.cs) - 1);
-            const int ky = tap / 3, kx = tap - 3 * ky;
-            const int y = 2 * oy + ky - 1, x = 2 * ox + kx - 1;
-            ok = ok && (unsigned)y < (1u << o.hs) && (unsigned)x < (1u << o.ws);
-            if (ok) src = o.p + ((((((long long)b << o.hs) + y) << o.ws) + x) << o.cs) + ci;
-        }
-        const unsigned off = MN ? j * 1024 + (i >> 3) * 128 : (i >> 3) * 1024 + j * 128;
-        if (IM) cp_async16_ca(tile + off + (i & 7) * 16, src, ok);
-        else cp_async16_cg(tile + off + (i & 7) * 16, src, ok);
-    }
-}
-
 // The data gradient of a 3x3 stride-2 pad-1 convolution, without the column matrix: an input pixel
 // (y, x) = (2i + py, 2j + px) is read by the taps ky = 1 (py = 0) or ky in {0, 2} (py = 1), and likewise kx,
 // from output pixel ((y + 1 - ky) / 2, (x + 1 - kx) / 2).  Parity class q = 2 py + px has
@@ -246,18 +167,8 @@ __device__ __forceinline__ void class_tap(int q, int t, int &ky, int &kx) {
     kx = px ? 2 * tx : 1;
 }
 
-// Warps: 0-3 epilogue, then the producers, then one MMA-issue warp.  The data gradient is loaded by one TMA
-// thread; the forward and weight-gradient operands by eight cp.async warps (their address arithmetic and copy
-// issue set the pace).
-template <int LA>
-constexpr bool tc_a_tma() {
-    return LA == LD_DY_TAPS_K || LA == LD_IM2COL_KT || LA == LD_IM2COL_MNT || LA == LD_IM2COL_KT32 ||
-           LA == LD_IM2COL_MNT32 || LA == LD_S2D_KT || LA == LD_S2D_MNT;
-}
-template <int LA>
-constexpr int tc_prod() { return tc_a_tma<LA>() ? 1 : 8; }
-template <int LA>
-constexpr int tc_threads() { return 32 * (4 + tc_prod<LA>() + 1); }
+// Warps: 0-3 epilogue, 4 the TMA producer (one thread), 5 the MMA issue (one thread).
+constexpr int kTcThreads = 32 * 6;
 
 struct TcUnit {
     int r0a, r0b, kbeg, kend, nkt, cls;
@@ -290,15 +201,14 @@ __device__ __forceinline__ TcUnit tc_unit(const TcGemm &g, int u) {
     return t;
 }
 
-// TMA loads of one K step of the data gradient (tensor maps built on the host; one 16-byte-wide box per chunk
-// of 8; coordinates past the tensor read as zeros):
+// TMA loads of the A operand of one K step (tensor maps built on the host; coordinates past the tensor read as
+// zeros).  The data gradient's:
 //   A, LD_DY_TAPS_K: class pixels (b, i, j) from t.r0a by (tap, n) from k0: one box [128 rows][128 B] in the
 //     128-byte-swizzled K-major layout (SBO 1024; an MMA's 16 k start 32 bytes further along the row); a tap's
 //     offset pixels past dY read zeros;
 //   B, LD_W_TAPS_MN, at stage + 16 KB: per 64 channels one box [64 k][128 B] (128-byte swizzle), or for
 //     BN = 32 one box [64 k][64 B] (64-byte swizzle).
-// With these dense boxes TMA beats the cp.async gather; for the im2col operands (8-channel boxes stepping 2
-// pixels) it measured slower, so the forward and weight-gradient GEMMs gather with cp.async.
+// The im2col operands of the forward and the weight gradient follow in the function's branches.
 template <int LA>
 __device__ __forceinline__ void tc_tma_a(unsigned stage, unsigned mbar, const TcOperand &a, const CUtensorMap *ma,
                                          const CUtensorMap *mo, const TcUnit &t, int k0) {
@@ -565,22 +475,15 @@ __device__ __forceinline__ void tc_epilogue(const TcGemm &g, const TcUnit &cur, 
 // stage's empty barrier, and after a unit's last step to the accumulator's full barrier; the epilogue warps
 // (0-3) drain one accumulator while the MMAs of the next unit fill the other, then arrive on its empty barrier.
 template <int EPI, int BN, int LA, int LB>
-__global__ void __launch_bounds__(tc_threads<LA>(), 2)
+__global__ void __launch_bounds__(kTcThreads, 2)
     gemm_tc_kernel(TcGemm g, int *err, const __grid_constant__ CUtensorMap tma_a,
                    const __grid_constant__ CUtensorMap tma_b, const __grid_constant__ CUtensorMap tma_one) {
     constexpr int S = tc_stages<BN>();
     static_assert(S >= 2 && S <= 8, "stage ring");
-    constexpr bool A_TMA = tc_a_tma<LA>();
-    constexpr int kProd = tc_prod<LA>();
-    constexpr int kLag = S - 2;  // cp.async groups a gather thread keeps in flight before signalling a stage
     constexpr int kA = kTcBM * kTcBK * 2, kStage = (kTcBM + BN) * kTcBK * 2;
     constexpr unsigned kTxBytes = (unsigned)kStage;  // TMA boxes are written in full (zeros outside)
-    constexpr bool A_MN = LA == LD_IM2COL_MN || LA == LD_IM2COL_MNT || LA == LD_IM2COL_MNT32 || LA == LD_S2D_MNT;
-    constexpr bool B_MN = LB == LD_DENSE_MN || LB == LD_W_TAPS_MN || LB == LD_DENSE_MNT || LB == LD_DENSE_MNT32;
-    // descriptor byte offsets (leading = along K, stride = along M/N); an MMA (16 k) advances two core
-    // matrices along K
-    constexpr unsigned kALbo = A_TMA ? 2048 : 128, kASbo = A_TMA ? 128 : 1024;
-    constexpr unsigned kBLbo = 128, kBSbo = 1024;
+    constexpr bool A_MN = LA == LD_IM2COL_MNT || LA == LD_IM2COL_MNT32 || LA == LD_S2D_MNT;
+    constexpr bool B_MN = LB == LD_W_TAPS_MN || LB == LD_DENSE_MNT || LB == LD_DENSE_MNT32;
     extern __shared__ __align__(1024) unsigned char tc_smem[];
     __shared__ __align__(8) TcSync sy;
     __shared__ float sbias[EPI == EPI_BIAS_RELU_BF16 ? BN : 1];
@@ -595,7 +498,7 @@ __global__ void __launch_bounds__(tc_threads<LA>(), 2)
     }
     if (threadIdx.x == 32) {
         for (int i = 0; i < S; ++i) {
-            mbar_init(smem_u32(&sy.full[i]), A_TMA ? 1 : kProd);
+            mbar_init(smem_u32(&sy.full[i]), 1);
             mbar_init(smem_u32(&sy.empty[i]), 1);
         }
         for (int i = 0; i < 2; ++i) {
@@ -610,13 +513,12 @@ __global__ void __launch_bounds__(tc_threads<LA>(), 2)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const unsigned tmem = sy.tmem_base;
 
-    if (warp >= 4 && warp < 4 + kProd) {
-        // ---- producers
-        const int ptid = threadIdx.x - 128;
-        const bool tma_thread = warp == 4 && lane == 0;
+    if (warp == 4) {
+        // ---- producer (one thread)
+        const bool tma_thread = lane == 0;
         int it = 0;
         bool ok = true;
-        if (!A_TMA || tma_thread) {
+        if (tma_thread) {
             for (int u = blockIdx.x; ok && u < g.units; u += gridDim.x) {
                 const TcUnit t = tc_unit<EPI, BN>(g, u);
                 for (int k = 0; k < t.nkt; ++k, ++it) {
@@ -627,34 +529,13 @@ __global__ void __launch_bounds__(tc_threads<LA>(), 2)
                     }
                     const unsigned stage = smem0 + st * kStage, fb = smem_u32(&sy.full[st]);
                     const int k0 = t.kbeg + k * kTcBK;
-                    if (A_TMA) {
-                        mbar_expect_tx(fb, kTxBytes);
-                        tc_tma_a<LA>(stage, fb, g.a, &tma_a, &tma_one, t, k0);
-                        tc_tma_b<LB, BN>(stage + kA, fb, g.b, &tma_b, t, k0);
-                    } else {
-                        const int kread = k0 + 16 * min(kTcBK / 16, (t.kend - k0 + 15) / 16);
-                        tc_gather<LA, kTcBM, kProd>(stage, g.a, t.r0a, k0, t.kend, kread, ptid);
-                        tc_gather<LB, BN, kProd>(stage + kA, g.b, t.r0b, k0, t.kend, kread, ptid);
-                        cp_async_commit();
-                        if (it >= kLag) {
-                            cp_async_wait<kLag>();
-                            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                            __syncwarp();
-                            if (lane == 0) mbar_arrive(smem_u32(&sy.full[(it - kLag) % S]));
-                        }
-                    }
+                    mbar_expect_tx(fb, kTxBytes);
+                    tc_tma_a<LA>(stage, fb, g.a, &tma_a, &tma_one, t, k0);
+                    tc_tma_b<LB, BN>(stage + kA, fb, g.b, &tma_b, t, k0);
                 }
             }
         }
-        if (!A_TMA) {
-            // signal the steps still in flight
-            cp_async_wait<0>();
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            __syncwarp();
-            if (lane == 0)
-                for (int j = it > kLag ? it - kLag : 0; j < it; ++j) mbar_arrive(smem_u32(&sy.full[j % S]));
-        }
-        if (A_TMA && tma_thread && !ok) {
+        if (tma_thread && !ok) {
             // let the loads already issued land before the CTA's shared memory goes away
             for (int j = it > S ? it - S : 0; j < it; ++j)
                 for (unsigned w = 0; w < kTcWaitIters; ++w) {
@@ -669,7 +550,7 @@ __global__ void __launch_bounds__(tc_threads<LA>(), 2)
                 }
         }
         __syncwarp();
-    } else if (warp == 4 + kProd) {
+    } else if (warp == 5) {
         // ---- MMA issue
         if (lane == 0) {
             // instruction descriptor: FP32 accumulator, BF16 A and B, majors, N = BN, M = 128
@@ -703,8 +584,7 @@ __global__ void __launch_bounds__(tc_threads<LA>(), 2)
                         // MN-major, 128-byte swizzle (BN >= 64: 8-row K groups 1024 B apart, 64-channel atoms
                         // 8 KB apart) or 64-byte swizzle (BN = 32: K groups 512 B apart); an MMA spans two K groups
                         const unsigned long long ad =
-                            !A_TMA               ? umma_desc(a0 + kk * 2 * kALbo, kALbo, kASbo)
-                            : LA == LD_IM2COL_MNT ? umma_desc_sw(a0 + kk * 2048, 8192, 1024, 2)
+                            LA == LD_IM2COL_MNT ? umma_desc_sw(a0 + kk * 2048, 8192, 1024, 2)
                             // 64-byte swizzle: MN-major 8-row K groups 512 B apart, 32-feature atoms 4 KB apart;
                             // K-major: two 64-byte-row sub-tiles 8 KB apart, an MMA's 16 k 32 bytes along the row
                             : LA == LD_IM2COL_MNT32 ? umma_desc_sw(a0 + kk * 1024, 4096, 512, 4)
@@ -715,8 +595,7 @@ __global__ void __launch_bounds__(tc_threads<LA>(), 2)
                             : LA == LD_S2D_MNT ? umma_desc_sw(a0 + kk * 512, 2048, 256, 6)
                                                   : umma_desc_sw(a0 + kk * 32, 16, 1024, 2);
                         const unsigned long long bd =
-                            !A_TMA                ? umma_desc(b0 + kk * 2 * kBLbo, kBLbo, kBSbo)
-                            : LB == LD_DENSE_KT  ? umma_desc_sw(b0 + kk * 32, 16, 1024, 2)
+                            LB == LD_DENSE_KT    ? umma_desc_sw(b0 + kk * 32, 16, 1024, 2)
                             : LB == LD_DENSE_MNT ? umma_desc_sw(b0 + kk * 2048, 8192, 1024, 2)
                             : LB == LD_DENSE_MNT32 ? umma_desc_sw(b0 + kk * 1024, 512, 512, 4)
                             : BN == 32           ? umma_desc_sw(b0 + kk * 1024, 512, 512, 4)
@@ -1200,19 +1079,16 @@ static bool gemm(TcGemm g, int *err, cudaStream_t s, int splits = 1) {
         if (!tmap_im2col_wide(&ma, g.a, kTcBM, CB) ||
             !tmap_matrix(&mb, g.b.p, g.N, g.b.ld, BN, 64, CU_TENSOR_MAP_SWIZZLE_128B))
             return false;
-    } else if (tc_a_tma<LA>()) {
+    } else {
         // data gradient: dY in 128-pixel tiles, W [N_out][9 C] in 64-row boxes
         const bool narrow = BN < 64;
         if (!tmap_dy_tiles(&ma, g.a) ||
             !tmap_matrix(&mb, g.b.p, 1 << g.b.cs, g.b.ld, kTcBK, narrow ? 32 : 64,
                          narrow ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B))
             return false;
-    } else {
-        memset(&ma, 0, sizeof(ma));  // unused: these operands are gathered with cp.async
-        mb = ma;
     }
     const int cap = 2 * upslam_sm_count();  // persistent: two CTAs per SM
-    gemm_tc_kernel<EPI, BN, LA, LB><<<g.units < cap ? g.units : cap, tc_threads<LA>(), smem, s>>>(g, err, ma, mb, mo);
+    gemm_tc_kernel<EPI, BN, LA, LB><<<g.units < cap ? g.units : cap, kTcThreads, smem, s>>>(g, err, ma, mb, mo);
     return true;
 }
 
