@@ -320,22 +320,29 @@ __global__ void __launch_bounds__(kIcpThreads) icp_step_kernel(IcpArgs a, double
 
 // ----------------------------------------------------------------------------- tiled persistent form
 //
-// One CTA of 512 threads per SM.  The keyframe is cut into chunks of 512
+// One CTA of 512 threads per SM.  The keyframe is cut into slices of 64
 // pixels dealt round-robin to the CTAs (samples only occupy the rows the sensor
-// sees, so contiguous slices would leave most CTAs idle).  Before the first
-// step each CTA streams its chunks once from HBM and stages every pixel that
+// sees, so contiguous ranges would leave most CTAs idle; and short slices mix
+// every azimuth into every CTA, where chunks of whole row quarters or eighths
+// would give each CTA one azimuth sector).  Before the first step each CTA
+// streams its slices once from HBM and stages every pixel that
 // holds a sample (depth > 0, unit normal) into shared memory as its FP32 point
 // s = d * dir and normal n, compacted in pixel order (a block-wide ballot
 // prefix, so the order and therefore the sums are deterministic).  Every
 // Gauss-Newton step then reads the staged points from shared memory and gathers
-// only the sweep pixel each one lands in.  Chunks beyond the shared-memory
+// only the sweep pixel each one lands in.  Units beyond the shared-memory
 // capacity are read from global memory each step.
 
 constexpr int kTileThreads = 512;
 constexpr int kTileWarps = kTileThreads / 32;
-// keyframe chunks staged per memory round trip: a 512x2048 keyframe deals 13-14 chunks to each of
-// 152 CTAs, so each half of the front end's staging is one round trip (8 spills registers)
+// keyframe units (kTileThreads pixels) staged per memory round trip: a 512x2048 keyframe deals 14 units
+// to each of 152 CTAs, so each half of the front end's staging is one round trip (8 spills registers)
 constexpr int kStageGroup = 7;
+// The keyframe is dealt to the CTAs in slices of kSlice pixels, slice s to CTA s mod gridDim, and a
+// CTA walks its slices in units of kTileThreads pixels (one per thread).  The fine interleave evens
+// the CTAs' sample counts, whatever rows of the panorama hold samples.
+constexpr int kSlice = 64;
+constexpr int kUnitSlices = kTileThreads / kSlice;
 
 // The sweep pixel a staged keyframe point lands in: its point and normal,
 // gathered from L2, and whether the point binned at all.
@@ -494,7 +501,7 @@ __global__ void __launch_bounds__(kTileThreads, 1)
     __shared__ int flag, status_s, conv_s, valid_s;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int npx = a.kp.rows * a.kp.cols;
-    const int nchunks = (npx + kTileThreads - 1) / kTileThreads;
+    const int nslices = (npx + kSlice - 1) / kSlice;
     const int W = a.kp.cols;
     const unsigned long long G = gridDim.x;
     unsigned long long base = 0;
@@ -536,30 +543,37 @@ __global__ void __launch_bounds__(kTileThreads, 1)
         __syncwarp();
     }
 
-    // ---- stage the CTA's chunks into shared memory (once per launch).  Chunks of
-    // 512 pixels are dealt round-robin (chunk q goes to CTA q mod gridDim), so every
-    // CTA gets an even share of the rows that hold samples.  kStageGroup chunks are
-    // loaded together (one memory round trip for the group) and compacted with one
-    // barrier: the per-warp counts are double-buffered by group parity.  A chunk
-    // that no longer fits is left, with every later chunk of this CTA, to the
+    // ---- stage the CTA's slices into shared memory (once per launch), a unit of
+    // eight slices (one pixel per thread) at a time.  kStageGroup units are loaded
+    // together (one memory round trip for the group) and compacted with one
+    // barrier: the per-warp counts are double-buffered by group parity.  A unit
+    // that no longer fits is left, with every later unit of this CTA, to the
     // global-memory path.
-    int staged = 0, spill_q = nchunks, par = 0;
+    const int my_slices = (int)blockIdx.x < nslices ? (nslices - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int my_units = (my_slices + kUnitSlices - 1) / kUnitSlices;
+    const int my_groups = (my_units + kStageGroup - 1) / kStageGroup;
+    // this thread's pixel of the CTA's unit u; false past the panorama
+    auto unit_pixel = [&](int u, int &k) -> bool {
+        const int s = (u * kUnitSlices + (int)threadIdx.x / kSlice) * (int)gridDim.x + (int)blockIdx.x;
+        k = s * kSlice + ((int)threadIdx.x & (kSlice - 1));
+        return s < nslices && k < npx;
+    };
+    int staged = 0, spill_u = my_units, par = 0;
     bool spilled = false;
-    const int my_chunks = blockIdx.x < nchunks ? (nchunks - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-    const int my_groups = (my_chunks + kStageGroup - 1) / kStageGroup;
     auto stage_groups = [&](int g_begin, int g_end) {
         for (int gi = g_begin; gi < g_end && !spilled; ++gi, par ^= 1) {
-            const int q0 = blockIdx.x + gi * kStageGroup * gridDim.x;
+            const int u0 = gi * kStageGroup;
             float dg[kStageGroup];
             float4 ng[kStageGroup];
             float2 eg[kStageGroup], ag[kStageGroup];
 #pragma unroll
             for (int g = 0; g < kStageGroup; ++g) {
-                const int k = (q0 + g * gridDim.x) * kTileThreads + threadIdx.x;
+                int k;
+                const bool in = unit_pixel(u0 + g, k);
                 dg[g] = 0.0f;
                 ng[g] = make_float4(0.f, 0.f, 0.f, 0.f);
                 eg[g] = ag[g] = make_float2(0.f, 0.f);
-                if (q0 + g * (int)gridDim.x < nchunks && k < npx) {
+                if (in) {
                     const int v = k / W;
                     dg[g] = __ldg(a.kdepth + k);
                     ng[g] = load_nw(a.knw, k, a.kprec);
@@ -596,7 +610,8 @@ __global__ void __launch_bounds__(kTileThreads, 1)
 #pragma unroll
             for (int g = 0; g < kStageGroup; ++g) {
                 if (g >= fit || !((bal[g] >> lane) & 1u)) continue;
-                const int k = (q0 + g * gridDim.x) * kTileThreads + threadIdx.x;
+                int k;
+                unit_pixel(u0 + g, k);
                 const int slot = off[g];
                 const float d = dg[g];
                 sx[slot] = __fmul_rn(d, __fmul_rn(eg[g].x, ag[g].x));
@@ -610,7 +625,7 @@ __global__ void __launch_bounds__(kTileThreads, 1)
                 sk[slot] = k;
             }
             if (fit < kStageGroup) {  // uniform across the CTA: the counts are shared
-                spill_q = q0 + fit * gridDim.x;
+                spill_u = u0 + fit;
                 spilled = true;
             }
         }
@@ -681,9 +696,9 @@ __global__ void __launch_bounds__(kTileThreads, 1)
                 h = h1;
             }
         }
-        for (int q = spill_q; q < nchunks; q += gridDim.x) {
-            const int k = q * kTileThreads + threadIdx.x;
-            if (k < npx) accumulate_pixel<L1>(as, T, k, acc, inl);
+        for (int u = spill_u; u < my_units; ++u) {
+            int k;
+            if (unit_pixel(u, k)) accumulate_pixel<L1>(as, T, k, acc, inl);
         }
         const int valid = it == 0 ? count_valid(a) : 0;
         tile_fx(acc, inl, valid, fxs);
@@ -817,15 +832,15 @@ __global__ void __launch_bounds__(kTileThreads, 1)
         const int ex = (pr.mode != 0 && pr.motion_out) ? 32 : 0;
         publish_motion();
         if (acc_ok) {
-            // average the staged samples straight from shared memory, spilled chunks from global memory
+            // average the staged samples straight from shared memory, spilled units from global memory
             const int e0 = blockIdx.x == 0 ? (int)threadIdx.x - ex : (int)threadIdx.x;
             const int es = blockIdx.x == 0 ? kTileThreads - ex : kTileThreads;
             for (int e = e0; e >= 0 && e < staged; e += es)
                 fuse_average(fz, T, sk[e], make_float3(sx[e], sy[e], sz[e]), make_float4(snx[e], sny[e], snz[e], sw8[e]),
                              sd[e]);
-            for (int q = spill_q; q < nchunks; q += gridDim.x) {
-                const int k = q * kTileThreads + threadIdx.x;
-                if (k >= npx) continue;
+            for (int u = spill_u; u < my_units; ++u) {
+                int k;
+                if (!unit_pixel(u, k)) continue;
                 const float4 n4 = load_nw(fz.knw, k, fz.kprec);
                 if (!(n4.w > 0.0f)) continue;
                 const float d = __ldg(fz.kdepth + k);
@@ -965,8 +980,8 @@ static upslam_status launch_tile(const IcpArgs &a, double *pose, const upslam_ic
     const int grid = upslam_sm_count();
     if (grid > kFxMaxCtas) return UPSLAM_ERR_UNSUPPORTED;
     const int64_t npx = (int64_t)a.kp.rows * a.kp.cols;
-    const int64_t nchunks = (npx + kTileThreads - 1) / kTileThreads;
-    const int64_t per = (nchunks + grid - 1) / grid * kTileThreads;  // most pixels one CTA can stage
+    const int64_t nslices = (npx + kSlice - 1) / kSlice;
+    const int64_t per = (nslices + grid - 1) / grid * kSlice;  // most pixels one CTA can stage
     // each staged sample: point (3), normal (3), count, depth, pixel index
     constexpr int64_t kWords = 9;
     const int64_t cap_max =
