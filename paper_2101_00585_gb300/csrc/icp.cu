@@ -478,16 +478,29 @@ __device__ __forceinline__ bool cta_grid_await(IcpCtrl *ctrl, unsigned long long
 // parity), arrive at a grid barrier (a monotonic 64-bit arrival counter), then
 // every CTA sums all records and solves redundantly: identical arithmetic on
 // identical data gives every CTA the same pose, so no CTA waits for another
-// to broadcast it.  CTA 0 writes the pose and the record at the end.
-template <int L1>
+// to broadcast it.  CTA 0 writes the pose and the record at the end.  L1: the IRLS
+// reading of Eq. 1; KF16: the keyframe stores FP16 normals and counts.
+template <int L1, int KF16>
 __global__ void __launch_bounds__(kTileThreads, 1)
     icp_tile_kernel(IcpArgs a, double *pose, upslam_icp_params ip, upslam_icp_stats *st, IcpCtrl *ctrl,
                     float *partials, int cap, PriorArgs pr, FuseView fz, int fuse_on, FrontArgs fr) {
+    // staged samples, structure of arrays of length cap (a multiple of 4): the point s = d * dir, the
+    // normal and count (FP32 keyframes: three floats and the count; FP16 keyframes: the keyframe's own four
+    // halves, which lose nothing) and the pixel index.  The depth is read again from the keyframe when the
+    // update averages a sample (no step writes it before then).
     extern __shared__ float stage[];
+    constexpr bool kf16 = KF16 != 0;
     float *sx = stage, *sy = stage + cap, *sz = stage + 2 * cap;
-    float *snx = stage + 3 * cap, *sny = stage + 4 * cap, *snz = stage + 5 * cap;
-    float *sw8 = stage + 6 * cap, *sd = stage + 7 * cap;
-    int *sk = reinterpret_cast<int *>(stage + 8 * cap);
+    float *snx = stage + 3 * cap, *sny = stage + 4 * cap, *snz = stage + 5 * cap, *sw8 = stage + 6 * cap;
+    uint2 *snh = reinterpret_cast<uint2 *>(stage + 3 * cap);
+    int *sk = reinterpret_cast<int *>(stage + (kf16 ? 5 : 7) * cap);
+    auto staged_nw = [&](int e) -> float4 {
+        if (!kf16) return make_float4(snx[e], sny[e], snz[e], sw8[e]);
+        const uint2 h = snh[e];
+        const float2 lo = __half22float2(*reinterpret_cast<const __half2 *>(&h.x));
+        const float2 hi = __half22float2(*reinterpret_cast<const __half2 *>(&h.y));
+        return make_float4(lo.x, lo.y, hi.x, hi.y);
+    };
     __shared__ double tot[32];
     __shared__ long long totn[2];
     __shared__ unsigned long long fxs[kFxWords];
@@ -617,11 +630,17 @@ __global__ void __launch_bounds__(kTileThreads, 1)
                 sx[slot] = __fmul_rn(d, __fmul_rn(eg[g].x, ag[g].x));
                 sy[slot] = __fmul_rn(d, __fmul_rn(eg[g].x, ag[g].y));
                 sz[slot] = __fmul_rn(d, eg[g].y);
-                snx[slot] = ng[g].x;
-                sny[slot] = ng[g].y;
-                snz[slot] = ng[g].z;
-                sw8[slot] = ng[g].w;
-                sd[slot] = d;
+                if (kf16) {
+                    // the halves the keyframe holds (converting them to FP32 and back is exact)
+                    const __half2 lo = __floats2half2_rn(ng[g].x, ng[g].y), hi = __floats2half2_rn(ng[g].z, ng[g].w);
+                    snh[slot] = make_uint2(*reinterpret_cast<const unsigned *>(&lo),
+                                           *reinterpret_cast<const unsigned *>(&hi));
+                } else {
+                    snx[slot] = ng[g].x;
+                    sny[slot] = ng[g].y;
+                    snz[slot] = ng[g].z;
+                    sw8[slot] = ng[g].w;
+                }
                 sk[slot] = k;
             }
             if (fit < kStageGroup) {  // uniform across the CTA: the counts are shared
@@ -691,8 +710,9 @@ __global__ void __launch_bounds__(kTileThreads, 1)
             for (int e = threadIdx.x; e < staged; e += kTileThreads) {
                 const int e1 = min(e + kTileThreads, staged - 1);  // the last prefetch repeats an entry, unused
                 const SweepHit h1 = gather_entry(as, T, make_float3(sx[e1], sy[e1], sz[e1]));
-                accumulate_entry<L1>(as, T, make_float3(sx[e], sy[e], sz[e]), make_float3(snx[e], sny[e], snz[e]), h,
-                                     acc, inl);
+                const float4 n4 = staged_nw(e);
+                accumulate_entry<L1>(as, T, make_float3(sx[e], sy[e], sz[e]), make_float3(n4.x, n4.y, n4.z), h, acc,
+                                     inl);
                 h = h1;
             }
         }
@@ -836,8 +856,7 @@ __global__ void __launch_bounds__(kTileThreads, 1)
             const int e0 = blockIdx.x == 0 ? (int)threadIdx.x - ex : (int)threadIdx.x;
             const int es = blockIdx.x == 0 ? kTileThreads - ex : kTileThreads;
             for (int e = e0; e >= 0 && e < staged; e += es)
-                fuse_average(fz, T, sk[e], make_float3(sx[e], sy[e], sz[e]), make_float4(snx[e], sny[e], snz[e], sw8[e]),
-                             sd[e]);
+                fuse_average(fz, T, sk[e], make_float3(sx[e], sy[e], sz[e]), staged_nw(e), fz.kdepth[sk[e]]);
             for (int u = spill_u; u < my_units; ++u) {
                 int k;
                 if (!unit_pixel(u, k)) continue;
@@ -957,11 +976,13 @@ static upslam_status launch_tile(const IcpArgs &a, double *pose, const upslam_ic
     // per device and kernel variant: the kernel's static shared memory, recorded when its dynamic
     // limit is raised (once, so later calls under stream capture change no attribute); any host
     // thread may call, so the flags are atomic (the release store publishes static_smem)
-    static std::atomic<bool> attr_set[2][64];
-    static size_t static_smem[2][64] = {{0}};
+    static std::atomic<bool> attr_set[4][64];
+    static size_t static_smem[4][64] = {{0}};
     if (dev < 0 || dev >= 64) return UPSLAM_ERR_UNSUPPORTED;
-    const int var = a.l1 ? 1 : 0;
-    const void *fn = var ? (const void *)icp_tile_kernel<1> : (const void *)icp_tile_kernel<0>;
+    const int var = (a.l1 ? 1 : 0) + (a.kprec == UPSLAM_F16 ? 2 : 0);
+    const void *const kernels[4] = {(const void *)icp_tile_kernel<0, 0>, (const void *)icp_tile_kernel<1, 0>,
+                                    (const void *)icp_tile_kernel<0, 1>, (const void *)icp_tile_kernel<1, 1>};
+    const void *fn = kernels[var];
     const size_t reserve = 1024;
     if (!attr_set[var][dev].load(std::memory_order_acquire)) {
         static std::mutex mu;
@@ -982,11 +1003,13 @@ static upslam_status launch_tile(const IcpArgs &a, double *pose, const upslam_ic
     const int64_t npx = (int64_t)a.kp.rows * a.kp.cols;
     const int64_t nslices = (npx + kSlice - 1) / kSlice;
     const int64_t per = (nslices + grid - 1) / grid * kSlice;  // most pixels one CTA can stage
-    // each staged sample: point (3), normal (3), count, depth, pixel index
-    constexpr int64_t kWords = 9;
+    // each staged sample: point (3), normal and count (4 floats, or 4 halves for an FP16 keyframe), pixel index
+    const int64_t kWords = a.kprec == UPSLAM_F16 ? 6 : 8;
     const int64_t cap_max =
-        ((int64_t)optin - (int64_t)static_smem[var][dev] - (int64_t)reserve) / (kWords * (int64_t)sizeof(float));
-    const int cap = (int)(per < cap_max ? (per > 0 ? per : 1) : cap_max);
+        (((int64_t)optin - (int64_t)static_smem[var][dev] - (int64_t)reserve) / (kWords * (int64_t)sizeof(float))) &
+        ~(int64_t)3;
+    const int64_t per4 = (per + 3) & ~(int64_t)3;
+    const int cap = (int)(per4 < cap_max ? (per4 > 0 ? per4 : 4) : cap_max);
     const size_t dyn = (size_t)cap * kWords * sizeof(float);
     if (kCtrlBytes + 2 * (size_t)grid * kSlots * sizeof(float) > ws_bytes) return UPSLAM_ERR_CAPACITY;
     int per_sm = 0;
