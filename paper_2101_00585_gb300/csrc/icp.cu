@@ -589,10 +589,16 @@ __global__ void __launch_bounds__(kTileThreads, 1)
                 if (in) {
                     const int v = k / W;
                     dg[g] = __ldg(a.kdepth + k);
-                    ng[g] = load_nw(a.knw, k, a.kprec);
                     eg[g] = __ldg(reinterpret_cast<const float2 *>(a.kdirs) + v);
                     ag[g] = __ldg(reinterpret_cast<const float2 *>(a.kdirs + 2 * a.kp.rows) + (k - v * W));
                 }
+            }
+            // the normal and count only where the depth holds a sample (empty pixels have depth 0)
+#pragma unroll
+            for (int g = 0; g < kStageGroup; ++g) {
+                int k;
+                unit_pixel(u0 + g, k);
+                if (dg[g] > 0.0f) ng[g] = load_nw(a.knw, k, a.kprec);
             }
             unsigned bal[kStageGroup];
 #pragma unroll
@@ -610,12 +616,17 @@ __global__ void __launch_bounds__(kTileThreads, 1)
             int total = staged;
 #pragma unroll
             for (int g = 0; g < kStageGroup; ++g) {
-                int o = total;
-                for (int w = 0; w < kTileWarps; ++w) {
-                    const int c = wcnt[par][g][w];
-                    o += w < warp ? c : 0;
-                    total += c;
+                // the warps' counts, scanned across lanes 0..15: the count before this warp, and the group's
+                const int c = lane < kTileWarps ? wcnt[par][g][lane] : 0;
+                int incl = c;
+#pragma unroll
+                for (int d = 1; d < kTileWarps; d <<= 1) {
+                    const int v = __shfl_up_sync(0xffffffffu, incl, d);
+                    if (lane >= d) incl += v;
                 }
+                const int before = __shfl_sync(0xffffffffu, incl - c, warp);
+                const int o = total + before;
+                total += __shfl_sync(0xffffffffu, incl, kTileWarps - 1);
                 off[g] = o + __popc(bal[g] & ((1u << lane) - 1u));
                 if (fit == kStageGroup && total > cap) fit = g;
                 if (fit == kStageGroup) staged = total;
