@@ -8,13 +8,14 @@
 // J^T J and J^T r with r = (T s2 - s1) . N(s1) and J = [p x N, N] (p = T s2,
 // left update T <- exp(xi^) T).
 //
-// Reduction: FP32 per thread -> warp shuffles -> compensated FP32 per CTA ->
-// compensated FP32 over CTAs in a fixed order (deterministic) -> FP64.  The CTA
-// that arrives last solves the 6x6 system with an FP64 square-root-free
-// Cholesky (L D L^T) and applies the SE(3) exponential in FP64.
+// The 6x6 system is solved with an FP64 square-root-free Cholesky (L D L^T)
+// and the SE(3) exponential is applied in FP64.
 //
 // Two launch forms:
-//  * icp_step_kernel: one Gauss-Newton step, "last CTA done" ticket.
+//  * icp_step_kernel: one Gauss-Newton step.  FP32 per thread -> warp shuffles
+//    -> compensated FP32 per CTA -> compensated FP32 over CTAs in a fixed order
+//    (deterministic) -> FP64; the CTA that arrives last ("last CTA done"
+//    ticket) solves.
 //  * icp_tile_kernel: all iterations in one cooperative launch, one CTA per SM,
 //    the CTA's keyframe samples staged in shared memory once.  Each step's sums
 //    are exact fixed-point integers that every CTA adds into global words; the
@@ -23,9 +24,10 @@
 //    system itself.  Every wait is bounded by a clock64 budget and reports
 //    UPSLAM_ERR_TIMEOUT instead of hanging.
 //
-// Roofline: per step the keyframe is streamed once (4 B depth + 16 B or 8 B
-// normal/weight per pixel) and each correspondence gathers 32 B (16 B in FP16)
-// of sweep data that stays resident in L2.
+// Roofline: icp_step_kernel streams the keyframe once per step (4 B depth +
+// 16 B or 8 B normal/weight per pixel); icp_tile_kernel streams it once per
+// launch.  Each correspondence gathers 32 B (16 B in FP16) of sweep data that
+// stays resident in L2.
 #include <mutex>
 #include <string.h>
 
