@@ -1111,6 +1111,7 @@ def run_learned(args, local):
     steps = args.epochs * (args.train_pairs // net.batch)
     pairs_trained = steps * net.batch
     flops = pairs_trained * 0.34e9  # forward 0.113 GFLOP + backward about twice that, per pair
+    step_bytes = cnn_step_bytes(net.batch)
     del x
     xt, xit, ext = proposal.make_pairs(args.eval_pairs, seed=20210107, keep_scans=True)
     # the learned start is close, so its ICP gets fewer Gauss-Newton steps (12 of the plain start's 15); the
@@ -1118,6 +1119,7 @@ def run_learned(args, local):
     res = proposal.evaluate(net, xt, ext["motions"], ext["scans"], learned_max_iters=LEARNED_ICP_STEPS)
     full = proposal.evaluate(net, xt, ext["motions"], ext["scans"])
     peak, peak_src = bf16_peak("sustained")  # training is a seconds-long loop of GEMMs
+    hbm_peak, hbm_src = peaks()
     return {"metric": "learned-init vs plain-init ICP success within 2 cm / 0.1 deg (held-out pairs)",
             "value": res["gated_success"] / res["pairs"], "unit": "fraction of pairs", "higher_is_better": True,
             "plain_fraction": res["plain_success"] / res["pairs"], "learned_only_fraction":
@@ -1139,9 +1141,34 @@ def run_learned(args, local):
                       "tflops": round(flops / t_train / 1e12, 2),
                       "frac_of_bf16_peak": round(flops / t_train / 1e12 / peak, 5),
                       "bf16_peak_tflops": peak, "peak_source": peak_src,
+                      "hbm": {"bytes_per_step": step_bytes,
+                              "achieved_gbs": round(step_bytes * steps / t_train / 1e9, 1),
+                              "frac": round(step_bytes * steps / t_train / 1e9 / hbm_peak, 4), "peak": hbm_peak,
+                              "peak_source": hbm_src,
+                              "basis": "each BF16 activation and gradient tensor read or written once per use "
+                                       "(mini-batch gather, forward, backward); weights not counted"},
                       "pair_generation_s": round(t_gen, 1)},
             "dtype": "bf16 weights/activations, f32 accumulate", "data": "synthetic",
             "config": {"workload": "tunnel/forest/road pairs, motion <= 1 m / 30 deg, 64x256 inputs"}}
+
+
+def cnn_step_bytes(batch):
+    """Compulsory DRAM bytes of one pose-network training step: every BF16 activation and gradient tensor
+    read or written once per use.  Inputs [B, 64, 256, 8]; layer l writes [B, 64 >> (l+1), 256 >> (l+1), C].
+    Forward: read the input, write each layer's output, read it as the next layer's input (the last by the
+    pool).  Backward: write the last dY; per layer the weight gradient reads its input and dY, and the data
+    gradient (layers 2-4) reads dY and the ReLU mask and writes the dY below.  Plus the mini-batch gather
+    (the inputs read from the pool and written to the batch)."""
+    chans = [8, 32, 64, 128, 128]
+    x0 = batch * 64 * 256 * 8 * 2
+    act = [batch * (64 >> (l + 1)) * (256 >> (l + 1)) * chans[l + 1] * 2 for l in range(4)]
+    fwd = x0 + sum(act) + sum(act)
+    bwd = act[3]
+    for l in range(3, -1, -1):
+        bwd += (x0 if l == 0 else act[l - 1]) + act[l]
+        if l > 0:
+            bwd += act[l] + act[l - 1] + act[l - 1]
+    return fwd + bwd + 2 * x0
 
 
 def main():
