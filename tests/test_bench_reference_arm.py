@@ -41,3 +41,17 @@ def test_reference_arm_other_ranks_do_no_work():
     r = _run({"RANK": "1", "LOCAL_RANK": "1", "WORLD_SIZE": "2"})
     assert r.returncode == 0, r.stderr[-2000:]
     assert r.stdout.strip() == ""
+
+
+def test_training_step_bytes_count_each_tensor_use():
+    """The training step's compulsory traffic, counted tensor by tensor for batch 1 (BF16, 2 bytes):
+    x0 = 64*256*8, layer outputs a0..a3 = 32*128*32, 16*64*64, 8*32*128, 4*16*128 elements."""
+    import bench
+    x0, a = 64 * 256 * 8, [32 * 128 * 32, 16 * 64 * 64, 8 * 32 * 128, 4 * 16 * 128]
+    forward = x0 + 2 * sum(a)                       # read x0; each output written, then read once
+    weight_grads = (x0 + a[0]) + (a[0] + a[1]) + (a[1] + a[2]) + (a[2] + a[3])
+    data_grads = sum(a[l] + 2 * a[l - 1] for l in (1, 2, 3))  # read dY and the mask, write the dY below
+    gather = 2 * x0
+    elems = forward + a[3] + weight_grads + data_grads + gather  # + the last dY, written by the head
+    assert bench.cnn_step_bytes(1) == 2 * elems
+    assert bench.cnn_step_bytes(256) == 256 * bench.cnn_step_bytes(1)
