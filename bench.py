@@ -408,7 +408,7 @@ def run_ours(args, ws, rank, local):
     kf_px, sw_px = KF_ROWS * KF_COLS, seq.sweep.pixels
     icp_avg, fuse_avg, proj_avg = (statistics.mean(icp_ms), statistics.mean(fuse_ms), statistics.mean(proj_ms))
     if trk.front_fused:
-        # one persistent launch per sweep.  Algorithmic bytes, the survey's per-unit figures for this
+        # one persistent launch per sweep.  Algorithmic bytes, the per-unit figures for this
         # workload: projection (the points, 16 B; the z-buffer touched twice and the outputs, 24 B per sweep
         # pixel: 2.6 MB), normals (32 B per sweep pixel: 2.1 MB), each Gauss-Newton step's correspondences
         # (48 B per sweep pixel: 3.1 MB per step, times the steps run), the keyframe read and written once
@@ -666,7 +666,7 @@ def run_fuse(kf, seq, scan, T, device, up, hbm, hbm_src, reps=20):
     kf.depth.copy_(d0)
     kf.nw.copy_(n0)
     kf_px, sw_px = kf.depth.numel(), seq.sweep.pixels
-    # the survey's algorithmic bytes: every keyframe pixel read and written once (20 B each way) and the
+    # the algorithmic bytes: every keyframe pixel read and written once (20 B each way) and the
     # hole fill's read of the sweep (24 B per sweep pixel)
     nbytes = kf_px * 40 + sw_px * 24
     touched = kf_px * 20 + changed * 20 + sw_px * 64
@@ -901,7 +901,7 @@ def run_campus(args, local):
     raw = hist.cpu().numpy()
     iters = [IcpStats.from_buffer_copy(bytes(raw[i])).iters for i in range(K)]
     kf_px, sw_px = seq.kf.pixels, seq.sweep.pixels
-    # the survey's bytes: the FP16 keyframe read and written once (12 B each way per pixel) and, per
+    # the algorithmic bytes: the FP16 keyframe read and written once (12 B each way per pixel) and, per
     # Gauss-Newton step, the sweep pixel's point, normal and the keyframe sample (16 + 8 + 12 B per sweep pixel)
     bytes_track = kf_px * 24 + sw_px * 36 * float(np.mean(iters))
     hbm, src = peaks()
@@ -925,7 +925,7 @@ def run_forest_batch(args, local):
 
     Algorithmic bytes per launch: every keyframe pixel read once by the staging prologue (depth 4 B +
     normal and count 16 B), then per problem and step the sweep pixel each of the keyframe's samples
-    bins into (point 16 B + normal 16 B).  The same bytes by the survey's per-iteration estimate
+    bins into (point 16 B + normal 16 B).  The same bytes by a coarser per-iteration estimate
     (0.67 GB per step over all 64 keyframes) are reported beside it."""
     import torch
     import paper_2101_00585_gb300 as up
@@ -982,7 +982,7 @@ def run_forest_batch(args, local):
     steps_by_problem = [r["iters"] for r in recs]
     gather_bytes = sum(steps_by_problem[q] * samples[q // case.n_hyp] * 32 for q in range(batch.n_prob))
     alg = kf_bytes + gather_bytes
-    survey_bytes = 0.67e9 * float(np.mean(steps_by_problem))
+    est_bytes = 0.67e9 * float(np.mean(steps_by_problem))
     hbm, src = peaks()
     gbs = alg / (avg * 1e-3) / 1e9
     return {"metric": "batched ICP problems/s (64 keyframes x 8 hypotheses, one launch)",
@@ -998,8 +998,8 @@ def run_forest_batch(args, local):
             "roofline": {"kernel": "icp_batched_kernel", "bound": "hbm", "achieved": round(gbs, 1), "peak": hbm,
                          "unit": "GB/s", "frac": round(gbs / hbm, 4), "bytes_per_launch": alg,
                          "peak_source": src,
-                         "survey_estimate": {"bytes_per_launch": round(survey_bytes),
-                                             "frac": round(survey_bytes / (avg * 1e-3) / 1e9 / hbm, 4)}},
+                         "per_iteration_estimate": {"bytes_per_launch": round(est_bytes),
+                                                    "frac": round(est_bytes / (avg * 1e-3) / 1e9 / hbm, 4)}},
             "samples_per_keyframe_mean": float(np.mean(samples)),
             "iters_avg": float(np.mean(steps_by_problem)),
             "within_2cm_0.1deg": int(ok), "problems": batch.n_prob}
