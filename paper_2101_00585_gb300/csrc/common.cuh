@@ -724,45 +724,37 @@ struct PixZbuf {
     }
 };
 
-// A neighbour is usable when it holds a point and its range is within jump_rel * d + jump_abs (FP32, RN).
-template <typename Acc>
-__device__ __forceinline__ bool normal_nb_ok(const Acc &px, int kn, float d, const upslam_normal_params &np,
-                                             float4 &q) {
-    q = px.point(kn);
-    if (q.w == 0.0f) return false;
-    const float dn = px.range(kn);
-    const float jump = fabsf(__fsub_rn(dn, d));
-    const float lim = __fadd_rn(__fmul_rn(np.jump_rel, d), np.jump_abs);
-    return !(jump > lim);
-}
-
 // Normal of pixel k: a toward column + 1 (wrapping), b toward row + 1, each replaced by the
 // opposite neighbour with the sign flipped when unusable; n = a x b, normalised, toward the
-// sensor; (0, 0, 0, 0) when there is none.
+// sensor; (0, 0, 0, 0) when there is none.  A neighbour is usable when it holds a point and its
+// range is within jump_rel * d + jump_abs of the pixel's (FP32, round to nearest).
 template <typename Acc>
 __device__ __forceinline__ float4 normal_pixel(const Acc &px, const upslam_pano &pp, const upslam_normal_params &np,
                                                int k) {
     const int H = pp.rows, W = pp.cols;
-    const float4 c = px.point(k);
-    float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (c.w == 0.0f) return out;
     const int v = k / W, u = k - v * W;
-    const float d = px.range(k);
     const int kr = v * W + (u + 1 == W ? 0 : u + 1);
     const int kl = v * W + (u == 0 ? W - 1 : u - 1);
+    const int kd = v + 1 < H ? k + W : k, ku = v >= 1 ? k - W : k;  // (past the edge: k, unused)
+    // every pixel the normal may use, read before any test, so the reads overlap
+    const float4 c = px.point(k), qr = px.point(kr), ql = px.point(kl), qd = px.point(kd), qu = px.point(ku);
+    const float d = px.range(k), dr = px.range(kr), dl = px.range(kl), dd = px.range(kd), du = px.range(ku);
+    float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (c.w == 0.0f) return out;
+    const float lim = __fadd_rn(__fmul_rn(np.jump_rel, d), np.jump_abs);
+    auto usable = [&](const float4 &q, float dn) { return q.w != 0.0f && !(fabsf(__fsub_rn(dn, d)) > lim); };
     float3 a, b;
-    float4 q;
-    if (normal_nb_ok(px, kr, d, np, q)) {
-        a = make_float3(q.x - c.x, q.y - c.y, q.z - c.z);
-    } else if (normal_nb_ok(px, kl, d, np, q)) {
-        a = make_float3(c.x - q.x, c.y - q.y, c.z - q.z);
+    if (usable(qr, dr)) {
+        a = make_float3(qr.x - c.x, qr.y - c.y, qr.z - c.z);
+    } else if (usable(ql, dl)) {
+        a = make_float3(c.x - ql.x, c.y - ql.y, c.z - ql.z);
     } else {
         return out;
     }
-    if (v + 1 < H && normal_nb_ok(px, k + W, d, np, q)) {
-        b = make_float3(q.x - c.x, q.y - c.y, q.z - c.z);
-    } else if (v >= 1 && normal_nb_ok(px, k - W, d, np, q)) {
-        b = make_float3(c.x - q.x, c.y - q.y, c.z - q.z);
+    if (v + 1 < H && usable(qd, dd)) {
+        b = make_float3(qd.x - c.x, qd.y - c.y, qd.z - c.z);
+    } else if (v >= 1 && usable(qu, du)) {
+        b = make_float3(c.x - qu.x, c.y - qu.y, c.z - qu.z);
     } else {
         return out;
     }
