@@ -822,8 +822,8 @@ __device__ __forceinline__ void fuse_average(const FuseView &f, const PoseF &T, 
 __device__ __forceinline__ bool holefill_key(const FuseView &f, const PoseF &T, int j, int &k,
                                              unsigned long long &key, float &range, float4 &m) {
     const float4 P = __ldcg(f.spix + j);
+    m = load_nw_cg(f.snrm, j, f.sprec);  // read with the point (unused when the point is empty)
     if (P.w == 0.0f) return false;
-    m = load_nw_cg(f.snrm, j, f.sprec);
     if (m.w == 0.0f) return false;
     const float3 p = xform(T, P.x, P.y, P.z);
     int v, u;
