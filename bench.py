@@ -547,9 +547,23 @@ def run_grid(trk, device, up, hbm, hbm_src):
     ms = _time_graph_diff(lambda: up.grid_score(trk.kf, trk.sw, poses, p, 4), 20, flush.zero_)
     samples = int((trk.kf.depth[::4, ::4] > 0).sum().item())
     pairs = samples * poses.shape[0]
+    # ALU roofline: the FP32 arithmetic a binned pair needs by its definition (an FMA counted once): the
+    # inverse transform (12); the binning rule (59: the two ranges' squares, sums and square roots 7, two
+    # atan2 polynomials of 23 each (the max / min, one division, the square, eight multiply-add pairs, the
+    # product and two quadrant fixes), the column and row scalings 4 and their two floors); then the sweep
+    # point and normal transformed and the two gate tests (27).  Against the SMs' FP32 issue rate, 128
+    # lanes per SM per cycle at the 2070 MHz maximum SM clock
+    ops_per_pair = 12 + 59 + 27
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    peak_tops = sms * 128 * 2.07e9 / 1e12
+    tops = pairs * ops_per_pair / (ms * 1e-3) / 1e12
     return {"candidates": int(poses.shape[0]), "stride": 4, "sampled_keyframe_samples": samples,
             "launches": 2, "ms_avg": round(ms, 5), "pairs_per_s": round(pairs / (ms * 1e-3), 1),
             "bound": "alu (FP32 binning rule per pair) + L2 gathers", "l2": "flushed before each call",
+            "roofline": {"bound": "alu", "achieved": round(tops, 2), "peak": round(peak_tops, 2),
+                         "unit": "T FP32 ops/s", "frac": round(tops / peak_tops, 4),
+                         "ops_per_pair": ops_per_pair,
+                         "peak_source": f"{sms} SMs x 128 FP32 lanes x 2070 MHz (derived)"},
             "timing": DIFF_TIMING}
 
 
