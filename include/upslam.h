@@ -429,7 +429,7 @@ upslam_status upslam_track_scan(const upslam_keyframe *kf, const float *d_pts4, 
  * d_scores: u64 [n] (overwritten; 8-byte aligned).  d_best: int32 [1], the
  * first candidate with the largest score.  d_best_pose12: FP64 [12] copy of
  * that candidate, or NULL.  Two launches (scores, winner) after a memset of
- * d_scores, all on `stream`; n <= 524280.  Invalid arguments return
+ * d_scores, all on `stream`; n <= 2097120.  Invalid arguments return
  * UPSLAM_ERR_INVALID_ARG before any launch.
  */
 upslam_status upslam_grid_score(const upslam_keyframe *kf, const upslam_sweep *sw, const double *d_poses, int32_t n,

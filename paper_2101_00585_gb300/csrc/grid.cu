@@ -8,22 +8,34 @@
 // stride j); a candidate scores its number of inliers.  The best candidate is
 // the first one with the largest score.
 //
-// grid_score_kernel: each CTA takes a slice of the sampled keyframe pixels and
-// kCand candidates; a sample's depth, normal and point are loaded once and
-// tested against every candidate of the CTA.  Counts leave the CTA as one
-// 64-bit integer atomic per candidate, so the scores do not depend on the order
-// in which CTAs finish.  grid_best_kernel picks the winner and copies its pose.
+// grid_score_kernel: CTA (x, y) scores candidates [32 y, 32 y + 32) on the
+// sampled keyframe pixels of column x.  The sampled grid is dealt to the CTA
+// columns in slices of kGridSlice pixels (slice s to column s mod gridDim.x),
+// so that every column holds rows of every elevation band.  Each round the CTA
+// loads kGridChunk of its pixels, every thread a few, all loads in flight, and
+// compacts the ones that hold a sample (depth > 0, unit normal) into shared
+// memory as keyframe point and normal.  Then every warp walks the staged
+// samples, one sample per step for the whole warp (a shared-memory broadcast),
+// and lane c scores candidate 32 y + c against it: no lane idles on an empty
+// pixel, and a lane keeps its candidate's pose and count in registers.  Counts
+// leave the CTA as one 64-bit integer atomic per candidate, so the scores do
+// not depend on the order in which CTAs finish.  grid_best_kernel picks the
+// winner and copies its pose.
 //
 // Roofline: per candidate a sample costs an L2 gather of 32 B (16 B in FP16) of
 // sweep data; the sampled keyframe (20 B per sample) is read once per CTA
-// column, i.e. n / kCand times, mostly from L2.  The work is gather- and
-// ALU-bound (the binning rule), not HBM-bound.
+// row, i.e. n / 32 times, mostly from L2.  The work is gather- and ALU-bound
+// (the binning rule), not HBM-bound.
 #include "common.cuh"
 
 namespace upslam {
 
 constexpr int kGridThreads = 256;
-constexpr int kCand = 8;  // candidates per CTA
+constexpr int kGridWarps = kGridThreads / 32;
+constexpr int kCand = 32;         // candidates per CTA: one per lane
+constexpr int kGridSlice = 64;    // sampled pixels dealt to a CTA column at a time
+constexpr int kGridChunk = 1024;  // sampled pixels staged per round
+constexpr int kGridPer = kGridChunk / kGridThreads;
 
 struct GridArgs {
     upslam_pano kp;
@@ -42,65 +54,102 @@ struct GridArgs {
     unsigned long long *scores;  // [n], zeroed by the host before the launch
 };
 
-__global__ void __launch_bounds__(kGridThreads) grid_score_kernel(GridArgs g) {
+// Sampled pixel m of round r, thread slot i (kGridPer per thread), or -1 past the grid.
+__device__ __forceinline__ int grid_pixel(const GridArgs &g, int r, int i) {
+    const int p = i * kGridThreads + threadIdx.x;  // 0 .. kGridChunk - 1
+    const long long slice = ((long long)r * (kGridChunk / kGridSlice) + p / kGridSlice) * gridDim.x + blockIdx.x;
+    const long long m = slice * kGridSlice + (p % kGridSlice);
+    return m < (long long)g.rows_s * g.cols_s ? (int)m : -1;
+}
+
+__global__ void __launch_bounds__(kGridThreads) grid_score_kernel(GridArgs g, int rounds) {
     pdl_release();  // the arg-max launch may place its CTA while this grid drains
-    __shared__ float Ts[kCand][12];
+    __shared__ float sx[kGridChunk], sy[kGridChunk], sz[kGridChunk];
+    __shared__ float snx[kGridChunk], sny[kGridChunk], snz[kGridChunk];
+    __shared__ int staged[2];  // round r counts into slot r & 1; the other slot is reset for round r + 1
+    __shared__ unsigned cta[kCand];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int c0 = blockIdx.y * kCand;
     const int nc = min(kCand, g.n - c0);
-    if (threadIdx.x < kCand * 12) {
-        const int c = threadIdx.x / 12, i = threadIdx.x % 12;
-        Ts[c][i] = c < nc ? (float)__ldg(g.poses + (size_t)(c0 + c) * 12 + i) : 0.0f;
-    }
-    __syncthreads();
-    unsigned cnt[kCand];
+    const bool mine = lane < nc;  // this lane's candidate exists
+    PoseF T;
 #pragma unroll
-    for (int c = 0; c < kCand; ++c) cnt[c] = 0;
-    const int ms = g.rows_s * g.cols_s;
-    for (int m = blockIdx.x * kGridThreads + threadIdx.x; m < ms; m += gridDim.x * kGridThreads) {
-        const int vs = m / g.cols_s;
-        const int v = vs * g.stride, u = (m - vs * g.cols_s) * g.stride;
-        const int k = v * g.kp.cols + u;
-        const float d = __ldg(g.kdepth + k);
-        if (!(d > 0.0f)) continue;
-        const float4 n4 = load_nw(g.knw, k, g.kprec);
-        if (!(__fadd_rn(__fadd_rn(__fmul_rn(n4.x, n4.x), __fmul_rn(n4.y, n4.y)), __fmul_rn(n4.z, n4.z)) > 0.25f))
-            continue;
-        const float3 s = pixel_point(g.kdirs, g.kp.rows, v, u, d);
+    for (int i = 0; i < 12; ++i) T.r[i] = mine ? (float)__ldg(g.poses + (size_t)(c0 + lane) * 12 + i) : 0.0f;
+    if (threadIdx.x < kCand) cta[threadIdx.x] = 0;
+    if (threadIdx.x == 0) staged[0] = 0;
+    unsigned cnt = 0;
+    for (int r = 0; r < rounds; ++r) {
+        __syncthreads();  // the previous round's samples are consumed, and its count read by every thread
+        if (threadIdx.x == 0) staged[(r + 1) & 1] = 0;
+        // stage: every depth of the round in flight, then the normals of the pixels that hold a sample
+        int k[kGridPer];
+        float d[kGridPer];
+        float4 n4[kGridPer];
 #pragma unroll
-        for (int c = 0; c < kCand; ++c) {
-            if (c >= nc) break;
-            PoseF T;
+        for (int i = 0; i < kGridPer; ++i) {
+            const int m = grid_pixel(g, r, i);
+            k[i] = -1;
+            if (m >= 0) {
+                const int vs = m / g.cols_s;
+                const int v = vs * g.stride, u = (m - vs * g.cols_s) * g.stride;
+                k[i] = v * g.kp.cols + u;
+            }
+            d[i] = k[i] >= 0 ? __ldg(g.kdepth + k[i]) : 0.0f;
+        }
 #pragma unroll
-            for (int i = 0; i < 12; ++i) T.r[i] = Ts[c][i];
-            const float3 q = xform_inv(T, s.x, s.y, s.z);
-            int jv, ju;
-            float rr;
-            if (!bin_point(q.x, q.y, q.z, g.sp, jv, ju, rr)) continue;
-            const int j = jv * g.sp.cols + ju;
-            const float4 P = __ldg(g.spix + j);
-            const float4 mm = load_nw(g.snrm, j, g.sprec);
-            if (P.w == 0.0f || mm.w == 0.0f) continue;
-            const float *r = T.r;
-            const float px = fmaf(r[0], P.x, fmaf(r[1], P.y, fmaf(r[2], P.z, r[3])));
-            const float py = fmaf(r[4], P.x, fmaf(r[5], P.y, fmaf(r[6], P.z, r[7])));
-            const float pz = fmaf(r[8], P.x, fmaf(r[9], P.y, fmaf(r[10], P.z, r[11])));
-            const float3 Rm = rotate(T, mm.x, mm.y, mm.z);
-            const float ex = px - s.x, ey = py - s.y, ez = pz - s.z;
-            const bool ok = (ex * ex + ey * ey + ez * ez <= g.d_max2) &&
-                            (Rm.x * n4.x + Rm.y * n4.y + Rm.z * n4.z >= g.cos_min);
-            cnt[c] += ok ? 1u : 0u;
+        for (int i = 0; i < kGridPer; ++i)
+            n4[i] = d[i] > 0.0f ? load_nw(g.knw, k[i], g.kprec) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int i = 0; i < kGridPer; ++i) {
+            const float nn = __fadd_rn(__fadd_rn(__fmul_rn(n4[i].x, n4[i].x), __fmul_rn(n4[i].y, n4[i].y)),
+                                       __fmul_rn(n4[i].z, n4[i].z));
+            const bool has = d[i] > 0.0f && nn > 0.25f;
+            const unsigned b = __ballot_sync(0xffffffffu, has);
+            int base = 0;
+            if (lane == 0 && b) base = atomicAdd(&staged[r & 1], __popc(b));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (has) {
+                const int e = base + __popc(b & ((1u << lane) - 1u));
+                const int v = k[i] / g.kp.cols;
+                const float3 s = pixel_point(g.kdirs, g.kp.rows, v, k[i] - v * g.kp.cols, d[i]);
+                sx[e] = s.x;
+                sy[e] = s.y;
+                sz[e] = s.z;
+                snx[e] = n4[i].x;
+                sny[e] = n4[i].y;
+                snz[e] = n4[i].z;
+            }
+        }
+        __syncthreads();
+        // score: the warp takes one staged sample per step, lane c against candidate c0 + c
+        const int ns = staged[r & 1];
+        if (mine) {
+            for (int e = warp; e < ns; e += kGridWarps) {
+                const float3 s = make_float3(sx[e], sy[e], sz[e]);
+                const float3 q = xform_inv(T, s.x, s.y, s.z);
+                int jv, ju;
+                float rr;
+                if (!bin_point(q.x, q.y, q.z, g.sp, jv, ju, rr)) continue;
+                const int j = jv * g.sp.cols + ju;
+                const float4 P = __ldg(g.spix + j);
+                const float4 mm = load_nw(g.snrm, j, g.sprec);
+                if (P.w == 0.0f || mm.w == 0.0f) continue;
+                const float *R = T.r;
+                const float px = fmaf(R[0], P.x, fmaf(R[1], P.y, fmaf(R[2], P.z, R[3])));
+                const float py = fmaf(R[4], P.x, fmaf(R[5], P.y, fmaf(R[6], P.z, R[7])));
+                const float pz = fmaf(R[8], P.x, fmaf(R[9], P.y, fmaf(R[10], P.z, R[11])));
+                const float3 Rm = rotate(T, mm.x, mm.y, mm.z);
+                const float ex = px - s.x, ey = py - s.y, ez = pz - s.z;
+                const bool ok = (ex * ex + ey * ey + ez * ez <= g.d_max2) &&
+                                (Rm.x * snx[e] + Rm.y * sny[e] + Rm.z * snz[e] >= g.cos_min);
+                cnt += ok ? 1u : 0u;
+            }
         }
     }
-    __shared__ unsigned cta[kCand];
-    if (threadIdx.x < kCand) cta[threadIdx.x] = 0;
+    if (mine && cnt) atomicAdd(&cta[lane], cnt);
     __syncthreads();
-#pragma unroll
-    for (int c = 0; c < kCand; ++c) {
-        const unsigned w = __reduce_add_sync(0xffffffffu, cnt[c]);
-        if ((threadIdx.x & 31) == 0 && w) atomicAdd(&cta[c], w);
-    }
-    __syncthreads();
-    if (threadIdx.x < nc && cta[threadIdx.x]) atomicAdd(g.scores + c0 + threadIdx.x, (unsigned long long)cta[threadIdx.x]);
+    if (threadIdx.x < nc && cta[threadIdx.x])
+        atomicAdd(g.scores + c0 + threadIdx.x, (unsigned long long)cta[threadIdx.x]);
 }
 
 // One CTA: the first candidate with the largest score, and (optionally) its pose.
@@ -197,6 +246,8 @@ extern "C" upslam_status upslam_grid_score(const upslam_keyframe *kf, const upsl
         !upslam_aligned(kf->d_dirs, 8) || !upslam_aligned(d_scores, 8) || !upslam_aligned(d_poses, 8))
         return UPSLAM_ERR_INVALID_ARG;
     if (!(ip->d_max > 0.0f)) return UPSLAM_ERR_INVALID_ARG;
+    const int64_t cand_blocks = (n + kCand - 1) / kCand;  // CTA rows of kCand candidates
+    if (cand_blocks > 65535) return UPSLAM_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     GridArgs g;
     g.kp = kf->pano;
@@ -218,13 +269,14 @@ extern "C" upslam_status upslam_grid_score(const upslam_keyframe *kf, const upsl
     g.scores = reinterpret_cast<unsigned long long *>(d_scores);
     if (cudaMemsetAsync(d_scores, 0, (size_t)n * sizeof(uint64_t), s) != cudaSuccess) return UPSLAM_ERR_CUDA;
     const int64_t ms = (int64_t)g.rows_s * g.cols_s;
-    const int cand_blocks = (n + kCand - 1) / kCand;
-    // enough sample slices that the launch covers every SM about four times over
-    int xb = (int)((4LL * upslam_sm_count() + cand_blocks - 1) / cand_blocks);
-    const int xb_max = (int)((ms + kGridThreads - 1) / kGridThreads);
-    xb = xb < 1 ? 1 : (xb > xb_max ? xb_max : xb);
-    if (cand_blocks > 65535) return UPSLAM_ERR_INVALID_ARG;
-    grid_score_kernel<<<dim3(xb, cand_blocks), kGridThreads, 0, s>>>(g);
+    // enough CTA columns that the launch covers every SM about four times over, each column at least one
+    // slice; every column then stages its slices kGridChunk pixels per round
+    const int64_t slices = (ms + kGridSlice - 1) / kGridSlice;
+    int64_t xb = (4LL * upslam_sm_count() + cand_blocks - 1) / cand_blocks;
+    xb = xb < 1 ? 1 : (xb > slices ? slices : xb);
+    const int64_t per_round = (int64_t)xb * (kGridChunk / kGridSlice);
+    const int rounds = (int)((slices + per_round - 1) / per_round);
+    grid_score_kernel<<<dim3((unsigned)xb, (unsigned)cand_blocks), kGridThreads, 0, s>>>(g, rounds);
     UPSLAM_CHECK_LAUNCH();
     if (!launch_dependent(grid_best_kernel, dim3(1), dim3(1024), 0, s, (const unsigned long long *)g.scores, n,
                           (const double *)d_poses, d_best, d_best_pose12))

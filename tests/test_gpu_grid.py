@@ -85,6 +85,32 @@ def test_grid_score_full_size_sampled():
     assert int(best.cpu()[0]) == int(np.argmax(s))
 
 
+def test_grid_score_batch_equals_single_candidates():
+    """Each lane of a CTA scores its own candidate: a batch of 75 distinct candidates (two full CTA rows of
+    32 and a ragged 11) gives every candidate exactly the count it gets alone, at full keyframe size and on
+    the room, FP32 and FP16 keyframe storage."""
+    seq = configs.tunnel_sequence(n_scans=3)
+    prm = oracle.Params(accept_quality=0.1, d_max=0.2)
+    kf_ref = oracle.Keyframe(seq.kf)
+    sp0, sn0, _, _ = oracle.sweep_frame(seq.scan(0), seq.sweep, prm)
+    oracle.fuse(kf_ref, sp0, sn0, seq.sweep, IDENTITY, prm)
+    sp4, sn4, _, _ = oracle.sweep_frame(seq.scan(2), seq.sweep, prm)
+    kd, kn = kf_ref.depth_f32(), kf_ref.nrm4_f32()
+    c, _, rsp4, rsn4, rkd, rkn = room_sweep_and_keyframe(noise=True)
+    cases = [(kd, kn, seq.kf, sp4, sn4, seq.sweep, synth.relative(seq.poses[0], seq.poses[2]), 4, up.F32),
+             (rkd, rkn, c.kf, rsp4, rsn4, c.sweep, c.T_true, 2, up.F16)]
+    for kd_, kn_, kpp, sp_, sn_, spp, center, stride, prec in cases:
+        kf, sw = _kf_buffers(kd_, kn_, kpp, prec), _sweep_buffers(sp_, sn_, spp)
+        xi = _grid_twists(n_xy=5, n_yaw=3, step=0.05, yaw_step_deg=1.0)  # 75 candidates
+        poses = dev(_host_poses(center, xi))
+        scores, _, _ = up.grid_score(kf, sw, poses, up.Params(d_max=0.2), stride)
+        s = scores.cpu().numpy()
+        assert s.max() > 0
+        for i in range(poses.shape[0]):
+            one, _, _ = up.grid_score(kf, sw, poses[i:i + 1].contiguous(), up.Params(d_max=0.2), stride)
+            assert int(one.cpu()[0]) == int(s[i]), (i, int(one.cpu()[0]), int(s[i]))
+
+
 def test_grid_candidates_match_host_composition():
     center = synth.perturb(IDENTITY, np.random.default_rng(83), 1.0, 0.3)
     xi = np.random.default_rng(84).normal(0, 0.3, (37, 6)).astype(np.float32)
@@ -97,7 +123,7 @@ def test_grid_edge_cases():
     c, prm, sp4, sn4, kd, kn = room_sweep_and_keyframe(noise=True)
     kf, sw = _kf_buffers(kd, kn, c.kf), _sweep_buffers(sp4, sn4, c.sweep)
     p = up.Params(d_max=0.1)
-    # identical candidates: equal scores, the first one wins; a ragged count (13, not a multiple of 8)
+    # identical candidates: equal scores, the first one wins; a ragged count (13, fewer than one CTA's 32)
     poses = np.stack([c.T_true.reshape(12)] * 13)
     scores, best, _ = up.grid_score(kf, sw, dev(poses), p, 3)
     s = scores.cpu().numpy()
