@@ -579,7 +579,11 @@ __global__ void __launch_bounds__(kTileThreads, 1)
         for (int gi = g_begin; gi < g_end && !spilled; ++gi, par ^= 1) {
             const int u0 = gi * kStageGroup;
             float dg[kStageGroup];
+            // FP16 keyframes hold a unit in three registers (the depth and the keyframe's four halves as
+            // stored; the direction tables are read at the commit, for samples only), which leaves the
+            // kernel room below its register limit; FP32 keyframes hold the normal, count and directions
             float4 ng[kStageGroup];
+            uint2 hg[kStageGroup];
             float2 eg[kStageGroup], ag[kStageGroup];
 #pragma unroll
             for (int g = 0; g < kStageGroup; ++g) {
@@ -587,12 +591,15 @@ __global__ void __launch_bounds__(kTileThreads, 1)
                 const bool in = unit_pixel(u0 + g, k);
                 dg[g] = 0.0f;
                 ng[g] = make_float4(0.f, 0.f, 0.f, 0.f);
+                hg[g] = make_uint2(0u, 0u);
                 eg[g] = ag[g] = make_float2(0.f, 0.f);
                 if (in) {
-                    const int v = k / W;
                     dg[g] = __ldg(a.kdepth + k);
-                    eg[g] = __ldg(reinterpret_cast<const float2 *>(a.kdirs) + v);
-                    ag[g] = __ldg(reinterpret_cast<const float2 *>(a.kdirs + 2 * a.kp.rows) + (k - v * W));
+                    if (!kf16) {
+                        const int v = k / W;
+                        eg[g] = __ldg(reinterpret_cast<const float2 *>(a.kdirs) + v);
+                        ag[g] = __ldg(reinterpret_cast<const float2 *>(a.kdirs + 2 * a.kp.rows) + (k - v * W));
+                    }
                 }
             }
             // the normal and count only where the depth holds a sample (empty pixels have depth 0)
@@ -600,12 +607,20 @@ __global__ void __launch_bounds__(kTileThreads, 1)
             for (int g = 0; g < kStageGroup; ++g) {
                 int k;
                 unit_pixel(u0 + g, k);
-                if (dg[g] > 0.0f) ng[g] = load_nw(a.knw, k, a.kprec);
+                if (dg[g] > 0.0f) {
+                    if (kf16) hg[g] = __ldg(reinterpret_cast<const uint2 *>(a.knw) + k);
+                    else ng[g] = load_nw(a.knw, k, a.kprec);
+                }
             }
             unsigned bal[kStageGroup];
 #pragma unroll
             for (int g = 0; g < kStageGroup; ++g) {
-                const float4 n4 = ng[g];
+                float4 n4 = ng[g];
+                if (kf16) {
+                    const float2 lo = __half22float2(*reinterpret_cast<const __half2 *>(&hg[g].x));
+                    const float2 hi = __half22float2(*reinterpret_cast<const __half2 *>(&hg[g].y));
+                    n4 = make_float4(lo.x, lo.y, hi.x, hi.y);
+                }
                 const bool ok = dg[g] > 0.0f && __fadd_rn(__fadd_rn(__fmul_rn(n4.x, n4.x), __fmul_rn(n4.y, n4.y)),
                                                           __fmul_rn(n4.z, n4.z)) > 0.25f;
                 bal[g] = __ballot_sync(0xffffffffu, ok);
@@ -640,14 +655,17 @@ __global__ void __launch_bounds__(kTileThreads, 1)
                 unit_pixel(u0 + g, k);
                 const int slot = off[g];
                 const float d = dg[g];
-                sx[slot] = __fmul_rn(d, __fmul_rn(eg[g].x, ag[g].x));
-                sy[slot] = __fmul_rn(d, __fmul_rn(eg[g].x, ag[g].y));
-                sz[slot] = __fmul_rn(d, eg[g].y);
+                float2 e = eg[g], az = ag[g];
+                if (kf16) {  // direction-table entries (small, cached) read for samples only
+                    const int v = k / W;
+                    e = __ldg(reinterpret_cast<const float2 *>(a.kdirs) + v);
+                    az = __ldg(reinterpret_cast<const float2 *>(a.kdirs + 2 * a.kp.rows) + (k - v * W));
+                }
+                sx[slot] = __fmul_rn(d, __fmul_rn(e.x, az.x));
+                sy[slot] = __fmul_rn(d, __fmul_rn(e.x, az.y));
+                sz[slot] = __fmul_rn(d, e.y);
                 if (kf16) {
-                    // the halves the keyframe holds (converting them to FP32 and back is exact)
-                    const __half2 lo = __floats2half2_rn(ng[g].x, ng[g].y), hi = __floats2half2_rn(ng[g].z, ng[g].w);
-                    snh[slot] = make_uint2(*reinterpret_cast<const unsigned *>(&lo),
-                                           *reinterpret_cast<const unsigned *>(&hi));
+                    snh[slot] = hg[g];  // the halves the keyframe holds
                 } else {
                     snx[slot] = ng[g].x;
                     sny[slot] = ng[g].y;
