@@ -13,8 +13,8 @@
 // columns in slices of kGridSlice pixels (slice s to column s mod gridDim.x),
 // so that every column holds rows of every elevation band.  Each round the CTA
 // loads kGridChunk of its pixels, every thread a few, all loads in flight, and
-// compacts the ones that hold a sample (depth > 0, unit normal) into shared
-// memory as keyframe point and normal.  Then every warp walks the staged
+// compacts the ones that hold a sample (depth > 0, normal longer than 1/2) into
+// shared memory as keyframe point and normal.  Then every warp walks the staged
 // samples, one sample per step for the whole warp (a shared-memory broadcast),
 // and lane c scores candidate 32 y + c against it: no lane idles on an empty
 // pixel, and a lane keeps its candidate's pose and count in registers.  Counts
@@ -24,8 +24,8 @@
 //
 // Roofline: per candidate a sample costs an L2 gather of 32 B (16 B in FP16) of
 // sweep data; the sampled keyframe (20 B per sample) is read once per CTA
-// row, i.e. n / 32 times, mostly from L2.  The work is gather- and ALU-bound
-// (the binning rule), not HBM-bound.
+// row, i.e. n / 32 times, mostly from L2.  The work is bound by instruction
+// issue (the FP32 binning rule), not by HBM.
 #include "common.cuh"
 
 namespace upslam {
