@@ -192,9 +192,11 @@ def test_fused_batched_and_added_entry_points_reject_bad_arguments():
     tiles = ctypes.byref(_abi.BatchTiles(512, 512))
     for n_kf, n_hyp in ((0, 8), (4, 0), (257, 1)):
         assert L.upslam_icp_batched(fake, K, n_kf, S, n_hyp, fake, I, fake, fake, 1 << 20, tiles, None) == INV
-    # grid search: no candidates, a zero stride, a negative count
+    # grid search: no candidates, a zero stride, one candidate past the documented limit (65535 CTA rows of
+    # 32), a negative count
     assert L.upslam_grid_score(K, S, fake, 0, 4, I, fake, fake, fake, None) == INV
     assert L.upslam_grid_score(K, S, fake, 9, 0, I, fake, fake, fake, None) == INV
+    assert L.upslam_grid_score(K, S, fake, 2097121, 4, I, fake, fake, fake, None) == INV
     assert L.upslam_grid_candidates(fake, fake, -1, fake, None) == INV
     assert L.upslam_grid_candidates(fake, fake, 0, fake, None) == _abi.OK  # nothing to do, nothing launched
     # consistency: a keyframe against itself in place, a negative tolerance, a misaligned workspace
